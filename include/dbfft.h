@@ -1,0 +1,260 @@
+/*
+ * dbfft.h -- C ABI of the GB300 DBFFT library.
+ *
+ * DBFFT (Lucarini & Segurado, "DBFFT: A displacement based FFT approach for
+ * non-linear homogenization of the mechanical behavior", arXiv 1905.12725)
+ * solves the periodic cell problem of a voxel microstructure with the Fourier
+ * coefficients of the displacement fluctuation as the unknown. Each linear
+ * system is solved matrix-free by a preconditioned conjugate gradient; one
+ * operator application is
+ *     Fourier gradient -> inverse 3-D FFT -> per-voxel tangent contraction
+ *     -> forward 3-D FFT -> Fourier divergence
+ * (Sec. 2.2 Eq. lineqf for small strain, Sec. 2.4 Eq. nonlineqf for finite
+ * strain) and the preconditioner is one 3x3 block per frequency (Sec. 2.5,
+ * Eqs. pred2-pred3).
+ *
+ * Conventions used by every entry point
+ * -------------------------------------
+ * Grid: n[0] x n[1] x n[2] voxels, each a power of two in [8, 256]; voxel
+ *   (i1, i2, i3) is stored at i3 + n3 * (i2 + n2 * i1) (i3 contiguous).
+ * Fourier fields ("half spectrum"): layout [B][3][n1][n2][n3/2 + 1],
+ *   interleaved complex (re, im), complex128 (FP64) or complex64 (FP32),
+ *   forward transform unnormalised with kernel e^{-i xi.x}. Frequency k_i is
+ *   stored in FFT order; xi_i = 2 pi k_i / L_i and the Nyquist index of an
+ *   even axis carries xi_i = 0 (the paper treats odd grids only, Sec. 2.1;
+ *   this is the even-grid reading). The null set Z = {xi = 0} (8 modes on an
+ *   all-even grid) carries no unknown: inputs there are ignored and outputs
+ *   are zero.
+ * Operator: the library applies the Hermitian positive definite form
+ *   K = B^H C B with B(u, e) = F^-1(s.u) + E e, which is -1/N times the
+ *   paper's d:F(C:F^-1(s.u)). Its solution is the paper's.
+ * Macro unknowns (stress and mixed control, Sec. 2.3 and Sec. 2.4 "Stress
+ *   and mixed control"): arrays [B][9]. Small strain stores the coefficients
+ *   on the orthonormal Mandel basis (order 11, 22, 33, 23, 13, 12) in entries
+ *   0..5; finite strain stores F components at index 3i + j. Only the
+ *   stress-controlled components are unknowns; the others are ignored on
+ *   input and zero on output.
+ * Inner product: Re sum over the full spectrum of conj(a) b (the half
+ *   spectrum weighted 1 on the k3 = 0 and k3 = n3/2 planes, 2 elsewhere) plus
+ *   the dot product of the macro unknowns.
+ * Ownership: every pointer passed in is borrowed for the duration of the
+ *   call. The context copies the material and load data at creation. Device
+ *   pointers must be on the context's device and must be 16-byte aligned.
+ * Errors: every entry point returns a dbfft_status; nothing is thrown across
+ *   the ABI. On failure dbfft_last_error(ctx) describes the cause. CUDA
+ *   errors are reported as DBFFT_E_CUDA and leave the context unusable.
+ * Streams: all device work of a context runs on the stream given at
+ *   creation; calls return after that work is complete unless stated.
+ */
+#ifndef DBFFT_H
+#define DBFFT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    DBFFT_OK = 0,
+    DBFFT_E_ARG = 1,              /* invalid argument or inconsistent sizes           */
+    DBFFT_E_UNSUPPORTED_GRID = 2, /* grid size outside the compiled set               */
+    DBFFT_E_NOMEM = 3,            /* device allocation failed                         */
+    DBFFT_E_CUDA = 4,             /* a CUDA call failed                               */
+    DBFFT_E_NOT_CONVERGED = 5,    /* iteration cap hit; results and report written    */
+    DBFFT_E_NONFINITE = 6,        /* NaN/Inf met in a residual or a material table    */
+    DBFFT_E_TIMEOUT = 7,          /* a bounded device wait gave up                    */
+    DBFFT_E_MATERIAL = 8,         /* a local constitutive update failed               */
+    DBFFT_E_STATE = 9             /* call not valid in the context's current state    */
+} dbfft_status;
+
+enum { DBFFT_SMALL = 0, DBFFT_FINITE = 1 };       /* kinematics (Sec. 2.2 / Sec. 2.4) */
+enum { DBFFT_FP64 = 0, DBFFT_MIXED = 1 };        /* precision of the solve           */
+enum {                                           /* constitutive model of a phase    */
+    DBFFT_ISO_ELASTIC = 0,     /* linear isotropic elasticity (E, nu), small strain     */
+    DBFFT_NEO_HOOKE = 1,       /* compressible Neo-Hookean (mu, lambda), finite strain  */
+    DBFFT_CP_FCC_POWERLAW = 2  /* small-strain FCC crystal plasticity, power-law flow   */
+};
+
+/* Problem size and solver settings. */
+typedef struct {
+    int n[3];          /* voxels per axis: powers of two in [8, 256]                    */
+    double L[3];       /* box edge lengths; 0 means 1                                    */
+    int batch;         /* B: right-hand sides solved together (>= 1)                     */
+    int n_materials;   /* Bm: distinct material maps; B % Bm == 0; solve b uses map
+                          b / (B / Bm), so B / Bm right-hand sides share one map          */
+    int kinematics;    /* DBFFT_SMALL or DBFFT_FINITE                                    */
+    int precision;     /* DBFFT_FP64: everything FP64. DBFFT_MIXED: FFTs, contraction
+                          and inner CG in FP32; residual, update and stresses in FP64     */
+    double tol;        /* linear problems: stop at ||b - K x|| <= tol ||b|| (FP64 residual) */
+    int max_iter;      /* cap on inner CG iterations per inner solve                     */
+    double newton_tol; /* nonlinear: equilibrium residual ||div P||_L2 / ||<P>||         */
+    double load_tol;   /* nonlinear: loading residual ||<P>_IJ - Pbar_IJ|| / ||<P>||     */
+    double eta_inner;  /* inner CG relative tolerance (refinement and Newton forcing)    */
+    int max_newton;    /* cap on Newton (or refinement) steps per increment              */
+} dbfft_grid;
+
+/* One phase. Only the fields of its model are read. */
+typedef struct {
+    int model;                /* DBFFT_ISO_ELASTIC, DBFFT_NEO_HOOKE, DBFFT_CP_FCC_POWERLAW */
+    double E, nu;             /* ISO_ELASTIC                                               */
+    double mu, lambda;        /* NEO_HOOKE                                                 */
+    double C11, C12, C44;     /* CP: cubic stiffness in the crystal frame                  */
+    double gdot0, m, tau_c;   /* CP: gdot = gdot0 |tau/tau_c|^(1/m) sign(tau)              */
+    double quat[4];           /* CP: unit quaternion (w, x, y, z), crystal -> sample       */
+} dbfft_phase;
+
+/* Microstructure. All arrays are host memory, copied at creation. */
+typedef struct {
+    const uint16_t* phase_id; /* [n_materials][n1][n2][n3] phase index per voxel          */
+    const double* E_scale;    /* optional [n_materials][n1][n2][n3]: factor on the
+                                 stiffness of ISO_ELASTIC voxels (NULL means 1)            */
+    int n_phases;
+    const dbfft_phase* phases;/* [n_phases]; one context uses one model kind               */
+} dbfft_materials;
+
+/* Macroscopic load program (Sec. 2.3, Sec. 2.4). */
+typedef struct {
+    unsigned stress_mask;  /* bit 3i+j set: component ij of the macro stress (sigma or P)
+                              is prescribed; otherwise the macro strain (or F) is.
+                              Must be symmetric for DBFFT_SMALL.                            */
+    const double* target;  /* host [B][9] (row-major 3x3): end-of-ramp value of the
+                              prescribed strain / F on strain-controlled components and of
+                              the stress on stress-controlled ones                          */
+    int n_increments;      /* increment k (0-based) applies the fraction (k+1)/n of the
+                              ramp from 0 (small strain) or I (finite strain)               */
+    double total_time;     /* rate-dependent models: time step = total_time / n_increments */
+} dbfft_load;
+
+/* Optional device allocator (e.g. a framework's caching allocator). */
+typedef struct {
+    void* (*alloc)(size_t bytes, void* user);
+    void (*free)(void* ptr, void* user);
+    void* user;
+} dbfft_allocator;
+
+/* Per-call report. */
+typedef struct {
+    int newton_iters;      /* Newton steps (nonlinear) or FP64 refinement steps (linear)  */
+    int outer_iters;       /* FP64 residual evaluations                                   */
+    long long cg_iters;    /* inner CG iterations summed over the batch                   */
+    int cg_iters_max;      /* max over the batch of inner CG iterations                   */
+    double eps_eq;         /* max over the batch of ||div sigma||_L2 / ||<sigma>||       */
+    double load_res;       /* max over the batch of the loading residual                  */
+    double true_rel_res;   /* linear: max over the batch of ||b - K x|| / ||b|| in FP64   */
+    double wall_ms;        /* wall time of the call                                       */
+} dbfft_report;
+
+typedef struct dbfft_ctx dbfft_ctx;
+
+/* Flags of dbfft_apply. */
+enum {
+    DBFFT_APPLY_FP32 = 1,     /* fields are complex64 / float, operator in FP32 (else FP64) */
+    DBFFT_APPLY_PRECOND = 2,  /* out = M u, the preconditioner of Sec. 2.5 (else K u)      */
+    DBFFT_APPLY_RESIDUAL = 4  /* out = b - K u for increment 0 (FP64 only): the residual of
+                                 Eq. lineqf / Sec. 2.3 with the macro load                  */
+};
+
+/*
+ * Create a context: copies the materials and the load, allocates device
+ * memory (through *alloc when given, else cudaMalloc) and prepares twiddle
+ * tables. stream is a cudaStream_t (NULL: the legacy default stream).
+ * Grid limits: see dbfft_grid.n. All phases must use one model kind, and
+ * the kind must match the kinematics (ISO_ELASTIC and CP with SMALL,
+ * NEO_HOOKE with FINITE). Errors: E_ARG, E_UNSUPPORTED_GRID, E_NOMEM,
+ * E_NONFINITE (a non-finite material parameter), E_CUDA.
+ */
+dbfft_status dbfft_create(const dbfft_grid* grid, const dbfft_materials* mat,
+                          const dbfft_load* load, const dbfft_allocator* alloc,
+                          void* stream, dbfft_ctx** out);
+
+/*
+ * Apply the DBFFT operator K (Sec. 2.2 Eq. lineqf in SPD form; with macro
+ * unknowns the system of Sec. 2.3), its preconditioner M (Sec. 2.5) or the
+ * residual b - K u, to a batch of device vectors, with the tangent the
+ * context holds now (the stiffness for linear phases; the tangent of the
+ * last constitutive update otherwise). u_hat / out: device, layout above;
+ * e_in / e_out: device [B][9] macro parts, or NULL when no component is
+ * stress-controlled. out may not alias u_hat.
+ */
+dbfft_status dbfft_apply(dbfft_ctx* ctx, int flags, const void* u_hat, const void* e_in,
+                         void* out, void* e_out);
+
+/*
+ * Solve load increment inc (0 <= inc < n_increments; increments must be
+ * called in order for path-dependent models). Linear phases: PCG (FP64) or
+ * FP32 PCG inside FP64 iterative refinement (MIXED) to grid.tol. Nonlinear:
+ * Newton (Sec. 2.4, Eq. lineariz) with inner PCG to eta_inner, stopped by
+ * newton_tol and load_tol; the preconditioner uses the mean tangent at the
+ * first iterate of the increment. rep may be NULL. Returns E_NOT_CONVERGED
+ * when a cap is hit (the state and report are still written).
+ */
+dbfft_status dbfft_solve_increment(dbfft_ctx* ctx, int inc, dbfft_report* rep);
+
+/* Homogenized stress <sigma> (small) or <P> (finite) of the current state,
+ * computed in FP64: host out[B][9], row-major 3x3. */
+dbfft_status dbfft_homogenized_stress(dbfft_ctx* ctx, double* out);
+
+/*
+ * Effective stiffness of linear elastic microstructures: the six unit Mandel
+ * macro strains solved as right-hand sides of one batched solve. Requires
+ * DBFFT_SMALL, ISO_ELASTIC phases, no stress-controlled components and
+ * B == 6 * n_materials. host out[n_materials][6][6], Mandel basis,
+ * out[g][i][j] = sigma_i for unit strain j. Overwrites the current solution.
+ */
+dbfft_status dbfft_homogenized_tangent(dbfft_ctx* ctx, double* out, dbfft_report* rep);
+
+/*
+ * Sensitivity of J_b = sum_ij dJ_dsigma[b][ij] <sigma>_ij to the per-voxel
+ * Young's modulus E(x) of ISO_ELASTIC phases under full strain control
+ * (C(x) = E(x) C1(nu(x))). Solves the forward problem of increment 0, then
+ * the adjoint problem with the same self-adjoint operator (Sec. 2.2: the
+ * system is Hermitian) and assembles
+ *   dJ/dE(x) = (1/N) (g + B lam)(x) : C1(x) : eps(x),  g = sym(dJ_dsigma),
+ * where lam solves K lam = -B^H C g. dJ_dsigma: host [B][9];
+ * dJ_dE: device [B][n1][n2][n3] double. Not available with stress control.
+ */
+dbfft_status dbfft_adjoint(dbfft_ctx* ctx, const double* dJ_dsigma, double* dJ_dE,
+                           dbfft_report* rep);
+
+/* Copy the current FP64 solution: u_hat device complex128 [B][3][n1][n2][n3/2+1]
+ * (may be NULL), e host [B][9] (may be NULL). */
+dbfft_status dbfft_get_solution(dbfft_ctx* ctx, void* u_hat, double* e);
+
+/* One row of the per-pass profile. */
+typedef struct {
+    char name[40];       /* pass and precision, e.g. "axis3_apply_f32"                  */
+    long long launches;  /* launches recorded                                           */
+    double ms;           /* summed device time between CUDA events around each launch    */
+    double bytes;        /* summed algorithmic DRAM bytes (reads + writes the pass needs) */
+} dbfft_profile_entry;
+
+/*
+ * Profiling of the context's own kernels (no counterpart in the paper; a
+ * measurement aid). dbfft_profile(ctx, 1) clears the table and brackets every
+ * later launch on the context's stream with CUDA events; dbfft_profile(ctx, 0)
+ * stops. dbfft_profile_read fills up to max_entries rows and returns the
+ * number of rows. dbfft_launch_count returns the number of kernels the
+ * context has launched since creation.
+ */
+dbfft_status dbfft_profile(dbfft_ctx* ctx, int enable);
+int dbfft_profile_read(dbfft_ctx* ctx, dbfft_profile_entry* out, int max_entries);
+long long dbfft_launch_count(const dbfft_ctx* ctx);
+
+/* Device bytes held by the context. */
+size_t dbfft_device_bytes(const dbfft_ctx* ctx);
+
+/* Release the context and its device memory (NULL is a no-op). */
+void dbfft_destroy(dbfft_ctx* ctx);
+
+/* Message of the last error of ctx ("" if none); valid until the next call. */
+const char* dbfft_last_error(const dbfft_ctx* ctx);
+
+/* Name of a status code. */
+const char* dbfft_status_string(dbfft_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DBFFT_H */

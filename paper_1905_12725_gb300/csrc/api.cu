@@ -1,0 +1,1431 @@
+// api.cu -- host driver and C ABI of the DBFFT library (declared in dbfft.h).
+//
+// A context owns device buffers for one batch of right-hand sides. A solve
+// (dbfft_solve_increment) runs an outer loop in FP64: the residual
+// r = b - K x (or the Newton residual -B^H P(F) + macro rows) is formed by the
+// FP64 pass chain with the constitutive update in pass 3, then an inner
+// preconditioned CG (FP64, or FP32 for the MIXED precision mode) solves
+// K d = r / ||r|| and x += ||r|| d in FP64. Linear problems in FP64 solve the
+// inner system straight to the tolerance; MIXED is iterative refinement;
+// nonlinear problems are Newton steps with an inexact inner solve
+// (Sec. 2.4, Eqs. lineariz and nonlineqf).
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/dbfft.h"
+#include "launch.h"
+#include "misc.h"
+
+using namespace dbfft;
+
+namespace {
+
+const double kPi = 3.14159265358979323846264338327950288;
+
+struct DevBuf {
+    void* p = nullptr;
+    size_t n = 0;
+};
+
+}  // namespace
+
+struct dbfft_ctx {
+    // ---- configuration
+    dbfft_grid grid{};
+    int n1 = 0, n2 = 0, n3 = 0, h = 0, m = 0;
+    long long H = 0, V = 0;
+    int B = 0, Bm = 0, Rm = 0, RB = 1;
+    int kin = 0, nc = 6, prec = 0, model = 0;
+    Dims dims{};
+    unsigned stress_mask = 0;
+    int activeflag_h[9] = {0};
+    std::vector<double> target;  // [B][9]
+    int n_inc = 1;
+    double total_time = 1.0;
+    int cur_inc = -1;
+    cudaStream_t stream = nullptr;
+    dbfft_allocator alloc{};
+    bool use_cb = false;
+    std::string err;
+    size_t bytes = 0;
+    std::vector<DevBuf> bufs;
+
+    // ---- tables
+    double* xi_d[3] = {nullptr, nullptr, nullptr};
+    float* xi_f[3] = {nullptr, nullptr, nullptr};
+    cplx<double>* tw_d[4] = {nullptr, nullptr, nullptr, nullptr};
+    cplx<float>* tw_f[4] = {nullptr, nullptr, nullptr, nullptr};
+    int* activeflag = nullptr;
+
+    // ---- materials
+    uint16_t* phase = nullptr;
+    double* scale = nullptr;
+    double* lam = nullptr;
+    double* mu = nullptr;
+    double* lam1 = nullptr;  // per unit Young's modulus (adjoint)
+    double* mu1 = nullptr;
+    std::vector<double> lam_h, mu_h, E_h;
+    CpGrain* grains = nullptr;
+    CpParams cp{};
+    PrecondData* pre = nullptr;
+    std::vector<PrecondData> pre_h;
+
+    // ---- vectors
+    cplx<double>* x64 = nullptr;
+    cplx<double>* r64 = nullptr;
+    double* xe64 = nullptr;
+    double* re64 = nullptr;
+    void* xi = nullptr;  // inner precision
+    void* ri = nullptr;
+    void* pi = nullptr;
+    double* xe_i = nullptr;
+    double* re_i = nullptr;
+    double* pe_i = nullptr;
+    void* W = nullptr;   // [B][nc][H] sized for FP64
+    void* W2 = nullptr;  // adjoint assembly
+    cplx<double>* xfwd = nullptr;
+    double* fU = nullptr;
+    double* sigf = nullptr;
+    double* sig0 = nullptr;
+    double* macroW = nullptr;
+    double* macroW2 = nullptr;
+    double* scal = nullptr;  // [B] scale factors
+    CgState* cg = nullptr;
+    double* partials = nullptr;
+    size_t partials_n = 0;
+    unsigned* counters = nullptr;
+    unsigned* errw = nullptr;
+
+    // ---- nonlinear
+    void* tan = nullptr;  // [B][V][ntan] inner precision
+    int ntan = 0;
+    double* eps_p = nullptr;
+    double* sig_prev = nullptr;
+    double* eps_p_t = nullptr;
+    double* sig_t = nullptr;
+
+    // ---- pinned host staging
+    CgState* cg_h = nullptr;
+    double* part_h = nullptr;
+    double* small_h = nullptr;  // [B][9] + [B]
+
+    bool have_solution = false;
+    int nblk_max = 0;
+
+    // ---- profiling: launch count and per-pass device time (CUDA events on the stream)
+    long long launches = 0;
+    bool prof = false;
+    struct ProfRec {
+        int slot;
+        cudaEvent_t a, b;
+        double bytes;
+    };
+    std::vector<ProfRec> pending;
+    std::vector<cudaEvent_t> pool;
+    std::vector<std::string> prof_name;
+    std::vector<long long> prof_n;
+    std::vector<double> prof_ms, prof_bytes;
+    int active_b = 0;  // right-hand sides still iterating (bytes accounting)
+};
+
+namespace {
+
+#define CK(call)                                                                                     \
+    do {                                                                                             \
+        cudaError_t e_ = (call);                                                                     \
+        if (e_ != cudaSuccess) {                                                                     \
+            ctx->err = std::string("CUDA error: ") + cudaGetErrorString(e_) + " at " #call;          \
+            return DBFFT_E_CUDA;                                                                     \
+        }                                                                                            \
+    } while (0)
+
+#define TRY(expr)                                 \
+    do {                                          \
+        dbfft_status s_ = (expr);                 \
+        if (s_ != DBFFT_OK) return s_;            \
+    } while (0)
+
+dbfft_status fail(dbfft_ctx* ctx, dbfft_status s, const std::string& msg) {
+    ctx->err = msg;
+    return s;
+}
+
+cudaEvent_t get_event(dbfft_ctx* ctx) {
+    if (!ctx->pool.empty()) {
+        cudaEvent_t e = ctx->pool.back();
+        ctx->pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+int prof_slot(dbfft_ctx* ctx, const char* name) {
+    for (size_t i = 0; i < ctx->prof_name.size(); ++i)
+        if (ctx->prof_name[i] == name) return (int)i;
+    ctx->prof_name.push_back(name);
+    ctx->prof_n.push_back(0);
+    ctx->prof_ms.push_back(0.0);
+    ctx->prof_bytes.push_back(0.0);
+    return (int)ctx->prof_name.size() - 1;
+}
+
+// Launch through f(), counting it; when profiling, bracket it with events.
+// bytes: algorithmic DRAM bytes of this launch (reads + writes it must do).
+template <class F>
+dbfft_status run(dbfft_ctx* ctx, const char* name, double bytes, F&& f) {
+    cudaEvent_t a = nullptr;
+    if (ctx->prof) {
+        a = get_event(ctx);
+        CK(cudaEventRecord(a, ctx->stream));
+    }
+    CK(f());
+    ctx->launches++;
+    if (ctx->prof) {
+        cudaEvent_t b = get_event(ctx);
+        CK(cudaEventRecord(b, ctx->stream));
+        ctx->pending.push_back({prof_slot(ctx, name), a, b, bytes});
+    }
+    return DBFFT_OK;
+}
+
+// Resolve pending event pairs (call after the stream has been synchronised).
+void prof_flush(dbfft_ctx* ctx) {
+    for (auto& r : ctx->pending) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
+            ctx->prof_ms[r.slot] += ms;
+            ctx->prof_n[r.slot] += 1;
+            ctx->prof_bytes[r.slot] += r.bytes;
+        }
+        ctx->pool.push_back(r.a);
+        ctx->pool.push_back(r.b);
+    }
+    ctx->pending.clear();
+    cudaGetLastError();
+}
+
+// Bytes of one component pass (one complex component over the half spectrum).
+double cpass(const dbfft_ctx* ctx, bool dbl, int nb) { return (double)nb * ctx->H * (dbl ? 16.0 : 8.0); }
+
+double mat_bytes(const dbfft_ctx* ctx, bool dbl, bool update) {
+    const double V = (double)ctx->V;
+    if (ctx->model == DBFFT_ISO_ELASTIC) return (double)ctx->Bm * V * (2.0 + (ctx->scale ? 8.0 : 0.0));
+    const double t = dbl ? 8.0 : 4.0;
+    if (!update) return (double)ctx->B * V * (2.0 + ctx->ntan * t);
+    const double tw = ctx->prec == DBFFT_FP64 ? 8.0 : 4.0;
+    if (ctx->model == DBFFT_NEO_HOOKE) return (double)ctx->B * V * (2.0 + ctx->ntan * tw);
+    return (double)ctx->B * V * (2.0 + ctx->ntan * tw + 4 * 6 * 8.0);
+}
+
+dbfft_status dalloc(dbfft_ctx* ctx, size_t bytes, void** out) {
+    bytes = (bytes + 255) & ~(size_t)255;
+    void* p = nullptr;
+    if (ctx->use_cb) {
+        p = ctx->alloc.alloc(bytes, ctx->alloc.user);
+        if (!p) return fail(ctx, DBFFT_E_NOMEM, "allocator callback returned NULL");
+    } else {
+        cudaError_t e = cudaMalloc(&p, bytes);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(ctx, DBFFT_E_NOMEM, std::string("cudaMalloc failed: ") + cudaGetErrorString(e));
+        }
+    }
+    ctx->bufs.push_back(DevBuf{p, bytes});
+    ctx->bytes += bytes;
+    *out = p;
+    return DBFFT_OK;
+}
+
+template <typename P>
+dbfft_status dalloc_t(dbfft_ctx* ctx, size_t count, P** out) {
+    void* p = nullptr;
+    TRY(dalloc(ctx, count * sizeof(P), &p));
+    *out = reinterpret_cast<P*>(p);
+    return DBFFT_OK;
+}
+
+// ---------------------------------------------------------------- host math
+void iso_C(double lam, double mu, double C[3][3][3][3]) {
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j)
+            for (int k = 0; k < 3; ++k)
+                for (int l = 0; l < 3; ++l)
+                    C[i][j][k][l] = lam * (i == j) * (k == l) + mu * ((i == k) * (j == l) + (i == l) * (j == k));
+}
+
+// Macro basis tensor m (Mandel for small strain, e_i x e_j for finite).
+void basis_tensor(int nc, int m, double T[3][3]) {
+    std::memset(T, 0, sizeof(double) * 9);
+    if (nc == 9) {
+        T[m / 3][m % 3] = 1.0;
+        return;
+    }
+    static const int pi[6] = {0, 1, 2, 1, 0, 0}, pj[6] = {0, 1, 2, 2, 2, 1};
+    if (m < 3) {
+        T[m][m] = 1.0;
+    } else {
+        T[pi[m]][pj[m]] = T[pj[m]][pi[m]] = 1.0 / std::sqrt(2.0);
+    }
+}
+
+bool invert(int n, std::vector<double>& A) {  // Gauss-Jordan with partial pivoting, row-major n x n
+    std::vector<double> I(n * n, 0.0);
+    for (int i = 0; i < n; ++i) I[i * n + i] = 1.0;
+    for (int c = 0; c < n; ++c) {
+        int piv = c;
+        for (int r = c + 1; r < n; ++r)
+            if (std::fabs(A[r * n + c]) > std::fabs(A[piv * n + c])) piv = r;
+        if (A[piv * n + c] == 0.0) return false;
+        for (int k = 0; k < n; ++k) {
+            std::swap(A[c * n + k], A[piv * n + k]);
+            std::swap(I[c * n + k], I[piv * n + k]);
+        }
+        const double d = A[c * n + c];
+        for (int k = 0; k < n; ++k) {
+            A[c * n + k] /= d;
+            I[c * n + k] /= d;
+        }
+        for (int r = 0; r < n; ++r)
+            if (r != c) {
+                const double f = A[r * n + c];
+                if (f != 0.0)
+                    for (int k = 0; k < n; ++k) {
+                        A[r * n + k] -= f * A[c * n + k];
+                        I[r * n + k] -= f * I[c * n + k];
+                    }
+            }
+    }
+    A = I;
+    return true;
+}
+
+// Preconditioner constants from a mean fourth-order tangent (Sec. 2.5):
+// Q_ik(xi) = sum_jl xi_j Cbar_ijkl xi_l written on the six monomials, and the
+// macro block (N Cbar_ee)^-1 on the active basis (R4 reading of M(0)).
+bool precond_from(const dbfft_ctx* ctx, const double C[3][3][3][3], PrecondData& pd) {
+    std::memset(&pd, 0, sizeof(pd));
+    static const int ik[6][2] = {{0, 0}, {1, 1}, {2, 2}, {1, 2}, {0, 2}, {0, 1}};
+    static const int jl[6][2] = {{0, 0}, {1, 1}, {2, 2}, {1, 2}, {0, 2}, {0, 1}};
+    for (int a = 0; a < 6; ++a)
+        for (int b = 0; b < 6; ++b) {
+            const int i = ik[a][0], k = ik[a][1], j = jl[b][0], l = jl[b][1];
+            pd.coef[a][b] = (j == l) ? C[i][j][k][j] : (C[i][j][k][l] + C[i][l][k][j]);
+        }
+    const int ne = ctx->dims.ne;
+    if (ne > 0) {
+        std::vector<double> A(ne * ne);
+        const double N = (double)ctx->V;
+        for (int p = 0; p < ne; ++p)
+            for (int q = 0; q < ne; ++q) {
+                double Tp[3][3], Tq[3][3];
+                basis_tensor(ctx->nc, ctx->dims.active[p], Tp);
+                basis_tensor(ctx->nc, ctx->dims.active[q], Tq);
+                double s = 0.0;
+                for (int i = 0; i < 3; ++i)
+                    for (int j = 0; j < 3; ++j)
+                        for (int k = 0; k < 3; ++k)
+                            for (int l = 0; l < 3; ++l) s += Tp[i][j] * C[i][j][k][l] * Tq[k][l];
+                A[p * ne + q] = N * s;
+            }
+        if (!invert(ne, A)) return false;
+        for (int p = 0; p < ne; ++p)
+            for (int q = 0; q < ne; ++q) pd.Me[p][q] = A[p * ne + q];
+    }
+    return true;
+}
+
+void quat_rot(const double* q0, double R[3][3]) {
+    double n = std::sqrt(q0[0] * q0[0] + q0[1] * q0[1] + q0[2] * q0[2] + q0[3] * q0[3]);
+    const double w = q0[0] / n, x = q0[1] / n, y = q0[2] / n, z = q0[3] / n;
+    R[0][0] = 1 - 2 * (y * y + z * z); R[0][1] = 2 * (x * y - w * z);     R[0][2] = 2 * (x * z + w * y);
+    R[1][0] = 2 * (x * y + w * z);     R[1][1] = 1 - 2 * (x * x + z * z); R[1][2] = 2 * (y * z - w * x);
+    R[2][0] = 2 * (x * z - w * y);     R[2][1] = 2 * (y * z + w * x);     R[2][2] = 1 - 2 * (x * x + y * y);
+}
+
+void to_mandel(const double C[3][3][3][3], double Cm[6][6]) {
+    for (int a = 0; a < 6; ++a)
+        for (int b = 0; b < 6; ++b) {
+            double Ta[3][3], Tb[3][3];
+            basis_tensor(6, a, Ta);
+            basis_tensor(6, b, Tb);
+            double s = 0.0;
+            for (int i = 0; i < 3; ++i)
+                for (int j = 0; j < 3; ++j)
+                    for (int k = 0; k < 3; ++k)
+                        for (int l = 0; l < 3; ++l) s += Ta[i][j] * C[i][j][k][l] * Tb[k][l];
+            Cm[a][b] = s;
+        }
+}
+
+// Crystal data of one grain: Mandel compliance of the rotated cubic
+// stiffness and the Schmid tensors of the 12 {111}<110> systems.
+bool cp_grain(const dbfft_phase& ph, CpGrain& g) {
+    static const double planes[4][3] = {{1, 1, 1}, {-1, 1, 1}, {1, -1, 1}, {1, 1, -1}};
+    static const double dirs[4][3][3] = {{{0, 1, -1}, {1, 0, -1}, {1, -1, 0}},
+                                         {{0, 1, -1}, {1, 0, 1}, {1, 1, 0}},
+                                         {{0, 1, 1}, {1, 0, -1}, {1, 1, 0}},
+                                         {{0, 1, 1}, {1, 0, 1}, {1, -1, 0}}};
+    double R[3][3];
+    quat_rot(ph.quat, R);
+    double Cc[3][3][3][3], Cg[3][3][3][3];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j)
+            for (int k = 0; k < 3; ++k)
+                for (int l = 0; l < 3; ++l) {
+                    double v = 0.0;
+                    if (i == j && k == l) v = (i == k) ? ph.C11 : ph.C12;
+                    else if ((i == k && j == l) || (i == l && j == k)) v = ph.C44;
+                    Cc[i][j][k][l] = v;
+                }
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j)
+            for (int k = 0; k < 3; ++k)
+                for (int l = 0; l < 3; ++l) {
+                    double s = 0.0;
+                    for (int a = 0; a < 3; ++a)
+                        for (int b = 0; b < 3; ++b)
+                            for (int c = 0; c < 3; ++c)
+                                for (int d = 0; d < 3; ++d)
+                                    s += R[i][a] * R[j][b] * R[k][c] * R[l][d] * Cc[a][b][c][d];
+                    Cg[i][j][k][l] = s;
+                }
+    double Cm[6][6];
+    to_mandel(Cg, Cm);
+    std::vector<double> A(36);
+    for (int a = 0; a < 6; ++a)
+        for (int b = 0; b < 6; ++b) A[a * 6 + b] = Cm[a][b];
+    if (!invert(6, A)) return false;
+    for (int a = 0; a < 6; ++a)
+        for (int b = a; b < 6; ++b) g.S[sym6(a, b)] = 0.5 * (A[a * 6 + b] + A[b * 6 + a]);
+    for (int p = 0; p < 4; ++p)
+        for (int dd = 0; dd < 3; ++dd) {
+            double n[3], s[3], nr[3] = {0, 0, 0}, sr[3] = {0, 0, 0};
+            for (int i = 0; i < 3; ++i) {
+                n[i] = planes[p][i] / std::sqrt(3.0);
+                s[i] = dirs[p][dd][i] / std::sqrt(2.0);
+            }
+            for (int i = 0; i < 3; ++i)
+                for (int k = 0; k < 3; ++k) {
+                    nr[i] += R[i][k] * n[k];
+                    sr[i] += R[i][k] * s[k];
+                }
+            double Pt[3][3];
+            for (int i = 0; i < 3; ++i)
+                for (int j = 0; j < 3; ++j) Pt[i][j] = 0.5 * (sr[i] * nr[j] + nr[i] * sr[j]);
+            for (int mm = 0; mm < 6; ++mm) {
+                double Tm[3][3];
+                basis_tensor(6, mm, Tm);
+                double v = 0.0;
+                for (int i = 0; i < 3; ++i)
+                    for (int j = 0; j < 3; ++j) v += Tm[i][j] * Pt[i][j];
+                g.P[p * 3 + dd][mm] = v;
+            }
+        }
+    return true;
+}
+
+// ---------------------------------------------------------------- tables
+template <typename T>
+Freq<T> freq(dbfft_ctx* ctx);
+template <>
+Freq<double> freq<double>(dbfft_ctx* ctx) { return Freq<double>{ctx->xi_d[0], ctx->xi_d[1], ctx->xi_d[2]}; }
+template <>
+Freq<float> freq<float>(dbfft_ctx* ctx) { return Freq<float>{ctx->xi_f[0], ctx->xi_f[1], ctx->xi_f[2]}; }
+template <typename T>
+Twiddles<T> twid(dbfft_ctx* ctx);
+template <>
+Twiddles<double> twid<double>(dbfft_ctx* ctx) {
+    return Twiddles<double>{ctx->tw_d[0], ctx->tw_d[1], ctx->tw_d[2], ctx->tw_d[3]};
+}
+template <>
+Twiddles<float> twid<float>(dbfft_ctx* ctx) {
+    return Twiddles<float>{ctx->tw_f[0], ctx->tw_f[1], ctx->tw_f[2], ctx->tw_f[3]};
+}
+
+dbfft_status upload_tables(dbfft_ctx* ctx) {
+    const int lens[4] = {ctx->n1, ctx->n2, ctx->n3, ctx->m};
+    for (int t = 0; t < 4; ++t) {
+        const int n = lens[t];
+        std::vector<cplx<double>> td(n);
+        std::vector<cplx<float>> tf(n);
+        for (int k = 0; k < n; ++k) {
+            const long double ang = -2.0L * 3.14159265358979323846264338327950288L * (long double)k / (long double)n;
+            td[k].x = (double)cosl(ang);
+            td[k].y = (double)sinl(ang);
+            tf[k].x = (float)td[k].x;
+            tf[k].y = (float)td[k].y;
+        }
+        TRY(dalloc_t(ctx, n, &ctx->tw_d[t]));
+        TRY(dalloc_t(ctx, n, &ctx->tw_f[t]));
+        CK(cudaMemcpyAsync(ctx->tw_d[t], td.data(), n * sizeof(cplx<double>), cudaMemcpyHostToDevice, ctx->stream));
+        CK(cudaMemcpyAsync(ctx->tw_f[t], tf.data(), n * sizeof(cplx<float>), cudaMemcpyHostToDevice, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+    }
+    // frequencies xi_i = 2 pi k_i / L_i in FFT order, Nyquist index set to 0
+    const int nax[3] = {ctx->n1, ctx->n2, ctx->n3};
+    for (int ax = 0; ax < 3; ++ax) {
+        const int n = nax[ax];
+        const int cnt = (ax == 2) ? ctx->h : n;
+        const double L = ctx->grid.L[ax] > 0 ? ctx->grid.L[ax] : 1.0;
+        std::vector<double> xd(cnt);
+        std::vector<float> xf(cnt);
+        for (int k = 0; k < cnt; ++k) {
+            const int kk = (k < (n + 1) / 2) ? k : k - n;
+            double v = 2.0 * kPi * (double)kk / L;
+            if (n % 2 == 0 && (k == n / 2)) v = 0.0;
+            xd[k] = v;
+            xf[k] = (float)v;
+        }
+        TRY(dalloc_t(ctx, cnt, &ctx->xi_d[ax]));
+        TRY(dalloc_t(ctx, cnt, &ctx->xi_f[ax]));
+        CK(cudaMemcpyAsync(ctx->xi_d[ax], xd.data(), cnt * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+        CK(cudaMemcpyAsync(ctx->xi_f[ax], xf.data(), cnt * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+    }
+    return DBFFT_OK;
+}
+
+// ---------------------------------------------------------------- load
+// Prescribed macro field (W components) and stress targets (macro basis) of
+// increment inc: fraction (inc+1)/n of the ramp from 0 (small) / I (finite).
+dbfft_status set_load(dbfft_ctx* ctx, int inc, const double* tgt /* [B][9] */) {
+    const double f = (double)(inc + 1) / (double)ctx->n_inc;
+    std::vector<double> fU(ctx->B * 9, 0.0), sf(ctx->B * 9, 0.0);
+    static const int pi[6] = {0, 1, 2, 1, 0, 0}, pj[6] = {0, 1, 2, 2, 2, 1};
+    for (int b = 0; b < ctx->B; ++b) {
+        const double* t = tgt + b * 9;
+        if (ctx->nc == 6) {
+            for (int mm = 0; mm < 6; ++mm) {
+                const double sym = 0.5 * (t[3 * pi[mm] + pj[mm]] + t[3 * pj[mm] + pi[mm]]);
+                if (ctx->activeflag_h[mm]) sf[b * 9 + mm] = f * sym * (mm >= 3 ? std::sqrt(2.0) : 1.0);
+                else fU[b * 9 + mm] = f * sym;
+            }
+        } else {
+            for (int q = 0; q < 9; ++q) {
+                const double id = (q / 3 == q % 3) ? 1.0 : 0.0;
+                if (ctx->activeflag_h[q]) {
+                    sf[b * 9 + q] = f * t[q];
+                    fU[b * 9 + q] = id;
+                } else {
+                    fU[b * 9 + q] = id + f * (t[q] - id);
+                }
+            }
+        }
+    }
+    CK(cudaMemcpyAsync(ctx->fU, fU.data(), fU.size() * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->sigf, sf.data(), sf.size() * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return DBFFT_OK;
+}
+
+// ---------------------------------------------------------------- chains
+template <typename T>
+Dims dims_of(dbfft_ctx* ctx) { return ctx->dims; }
+
+int opk_apply(const dbfft_ctx* ctx) {
+    return ctx->model == DBFFT_ISO_ELASTIC ? OP_ISO : (ctx->model == DBFFT_NEO_HOOKE ? OP_NH_APPLY : OP_CP_APPLY);
+}
+int opk_update(const dbfft_ctx* ctx) {
+    return ctx->model == DBFFT_ISO_ELASTIC ? OP_ISO : (ctx->model == DBFFT_NEO_HOOKE ? OP_NH_UPDATE : OP_CP_UPDATE);
+}
+
+template <typename T>
+Ax3Args<T> ax3_base(dbfft_ctx* ctx, cplx<T>* W) {
+    Ax3Args<T> a;
+    std::memset(&a, 0, sizeof(a));
+    a.d = ctx->dims;
+    a.tw = twid<T>(ctx);
+    a.W = W;
+    a.RB = ctx->RB;
+    a.L = ax3_lines(ctx->n3, ctx->nc, ctx->RB, sizeof(T) == 8);
+    a.phase = ctx->phase;
+    a.scale = ctx->scale;
+    a.lam = ctx->lam;
+    a.mu = ctx->mu;
+    a.grains = ctx->grains;
+    a.cp = ctx->cp;
+    a.err = ctx->errw;
+    return a;
+}
+
+// One operator application in precision T: out = K u (flags: macro e_in/e_out).
+template <typename T>
+dbfft_status chain_apply(dbfft_ctx* ctx, const cplx<T>* u, const double* macroW, cplx<T>* out, double* e_out) {
+    cplx<T>* W = reinterpret_cast<cplx<T>*>(ctx->W);
+    const bool dbl = sizeof(T) == 8;
+    const double cp = cpass(ctx, dbl, ctx->B);
+    const int nc = ctx->nc;
+    Ax1InvArgs<T> a1{ctx->dims, freq<T>(ctx), twid<T>(ctx), u, nullptr, W, nullptr, ctx->pre};
+    TRY(run(ctx, dbl ? "axis1_inv_f64" : "axis1_inv_f32", (3 + nc) * cp,
+            [&] { return launch_ax1_inv<T>(AX1_PLAIN, a1, ctx->stream); }));
+    Ax2Args<T> a2{ctx->dims, twid<T>(ctx), W, nullptr};
+    TRY(run(ctx, dbl ? "axis2_f64" : "axis2_f32", 2 * nc * cp, [&] { return launch_ax2<T>(+1, a2, ctx->stream); }));
+    Ax3Args<T> a3 = ax3_base<T>(ctx, W);
+    a3.macroW = macroW;
+    a3.tan_in = reinterpret_cast<const T*>(ctx->tan);
+    TRY(run(ctx, dbl ? "axis3_apply_f64" : "axis3_apply_f32", 2 * nc * cp + mat_bytes(ctx, dbl, false),
+            [&] { return launch_ax3<T>(opk_apply(ctx), a3, ctx->stream); }));
+    TRY(run(ctx, dbl ? "axis2_f64" : "axis2_f32", 2 * nc * cp, [&] { return launch_ax2<T>(-1, a2, ctx->stream); }));
+    Ax1FwdArgs<T> a5;
+    std::memset(&a5, 0, sizeof(a5));
+    a5.d = ctx->dims;
+    a5.f = freq<T>(ctx);
+    a5.tw = twid<T>(ctx);
+    a5.W = W;
+    a5.out = out;
+    a5.e_out = e_out;
+    TRY(run(ctx, dbl ? "axis1_fwd_f64" : "axis1_fwd_f32", (3 + nc) * cp,
+            [&] { return launch_ax1_fwd<T>(AX5_PLAIN, a5, ctx->stream); }));
+    return DBFFT_OK;
+}
+
+// FP64 residual of the current state: r64 = -B^H sigma(fU + E x_e + B x) + (0, N sigma_f),
+// constitutive update in pass 3 (tangent written in the inner precision).
+// Returns per-RHS ||r_u||^2 and ||r_e||^2 on the host and fills sig0.
+dbfft_status chain_residual(dbfft_ctx* ctx, const cplx<double>* x, const double* xe, std::vector<double>& ru2,
+                            std::vector<double>& re2) {
+    cplx<double>* W = reinterpret_cast<cplx<double>*>(ctx->W);
+    const double cp = cpass(ctx, true, ctx->B);
+    const int nc = ctx->nc;
+    TRY(run(ctx, "macro", 0.0,
+            [&] { return launch_macro(ctx->B, ctx->nc, ctx->activeflag, ctx->fU, xe, ctx->macroW, ctx->stream); }));
+    Ax1InvArgs<double> a1{ctx->dims, freq<double>(ctx), twid<double>(ctx), x, nullptr, W, nullptr, ctx->pre};
+    TRY(run(ctx, "axis1_inv_f64", (3 + nc) * cp, [&] { return launch_ax1_inv<double>(AX1_PLAIN, a1, ctx->stream); }));
+    Ax2Args<double> a2{ctx->dims, twid<double>(ctx), W, nullptr};
+    TRY(run(ctx, "axis2_f64", 2 * nc * cp, [&] { return launch_ax2<double>(+1, a2, ctx->stream); }));
+    Ax3Args<double> a3 = ax3_base<double>(ctx, W);
+    a3.macroW = ctx->macroW;
+    if (ctx->model != DBFFT_ISO_ELASTIC) {
+        if (ctx->prec == DBFFT_MIXED) a3.tan_out_f = reinterpret_cast<float*>(ctx->tan);
+        else a3.tan_out_d = reinterpret_cast<double*>(ctx->tan);
+        a3.eps_p = ctx->eps_p;
+        a3.sig_prev = ctx->sig_prev;
+        a3.eps_p_t = ctx->eps_p_t;
+        a3.sig_t = ctx->sig_t;
+    }
+    CK(cudaMemsetAsync(ctx->errw, 0, sizeof(unsigned), ctx->stream));
+    TRY(run(ctx, "axis3_update_f64", 2 * nc * cp + mat_bytes(ctx, true, true),
+            [&] { return launch_ax3<double>(opk_update(ctx), a3, ctx->stream); }));
+    TRY(run(ctx, "axis2_f64", 2 * nc * cp, [&] { return launch_ax2<double>(-1, a2, ctx->stream); }));
+    Ax1FwdArgs<double> a5;
+    std::memset(&a5, 0, sizeof(a5));
+    a5.d = ctx->dims;
+    a5.f = freq<double>(ctx);
+    a5.tw = twid<double>(ctx);
+    a5.W = W;
+    a5.out = ctx->r64;
+    a5.sig0 = ctx->sig0;
+    a5.sig_f = ctx->sigf;
+    a5.r_e = ctx->re64;
+    a5.partials = ctx->partials;
+    TRY(run(ctx, "axis1_fwd_resid_f64", (3 + nc) * cp,
+            [&] { return launch_ax1_fwd<double>(AX5_RESID, a5, ctx->stream); }));
+    const int TW = ax1_tile(ctx->n1, true);
+    const int nblk = (int)((ctx->dims.plane + TW - 1) / TW);
+    CK(cudaMemcpyAsync(ctx->part_h, ctx->partials, (size_t)ctx->B * nblk * 2 * sizeof(double),
+                       cudaMemcpyDeviceToHost, ctx->stream));
+    unsigned* errh = reinterpret_cast<unsigned*>(ctx->small_h + ctx->B * 10);
+    CK(cudaMemcpyAsync(errh, ctx->errw, sizeof(unsigned), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    prof_flush(ctx);
+    ru2.assign(ctx->B, 0.0);
+    re2.assign(ctx->B, 0.0);
+    for (int b = 0; b < ctx->B; ++b)
+        for (int k = 0; k < nblk; ++k) {
+            ru2[b] += ctx->part_h[((size_t)b * nblk + k) * 2 + 0];
+            re2[b] += ctx->part_h[((size_t)b * nblk + k) * 2 + 1];
+        }
+    if (*errh) return fail(ctx, DBFFT_E_MATERIAL, "local constitutive update failed (non-positive J or local Newton)");
+    for (int b = 0; b < ctx->B; ++b)
+        if (!std::isfinite(ru2[b]) || !std::isfinite(re2[b])) return fail(ctx, DBFFT_E_NONFINITE, "non-finite residual");
+    return DBFFT_OK;
+}
+
+// Inner PCG in precision T on K d = ri (already scaled), x = xi.
+template <typename T>
+dbfft_status inner_cg(dbfft_ctx* ctx, double tol, long long& it_sum, int& it_max) {
+    cplx<T>* W = reinterpret_cast<cplx<T>*>(ctx->W);
+    cplx<T>* xi = reinterpret_cast<cplx<T>*>(ctx->xi);
+    cplx<T>* ri = reinterpret_cast<cplx<T>*>(ctx->ri);
+    cplx<T>* pi = reinterpret_cast<cplx<T>*>(ctx->pi);
+    CK(cudaMemsetAsync(pi, 0, (size_t)ctx->B * 3 * ctx->H * sizeof(cplx<T>), ctx->stream));
+    CgInitArgs<T> ai;
+    ai.d = ctx->dims;
+    ai.f = freq<T>(ctx);
+    ai.r = ri;
+    ai.r_e = ctx->re_i;
+    ai.p_e = ctx->pe_i;
+    ai.macroW = ctx->macroW;
+    ai.cg = ctx->cg;
+    ai.pre = ctx->pre;
+    ai.partials = ctx->partials;
+    ai.counters = ctx->counters;
+    ai.tol = tol;
+    ai.max_iter = ctx->grid.max_iter;
+    const dim3 gi((unsigned)((ctx->H + 255) / 256), ctx->B);
+    const bool dbl = sizeof(T) == 8;
+    TRY(run(ctx, dbl ? "cg_init_f64" : "cg_init_f32", 3 * cpass(ctx, dbl, ctx->B), [&] {
+        k_cg_init<T><<<gi, 256, 0, ctx->stream>>>(ai);
+        return cudaGetLastError();
+    }));
+
+    Ax1InvArgs<T> a1{ctx->dims, freq<T>(ctx), twid<T>(ctx), ri, pi, W, ctx->cg, ctx->pre};
+    Ax2Args<T> a2{ctx->dims, twid<T>(ctx), W, ctx->cg};
+    Ax3Args<T> a3 = ax3_base<T>(ctx, W);
+    a3.macroW = ctx->macroW;
+    a3.cg = ctx->cg;
+    a3.partials = ctx->partials;
+    a3.counters = ctx->counters;
+    a3.tan_in = reinterpret_cast<const T*>(ctx->tan);
+    Ax1FwdArgs<T> a5;
+    std::memset(&a5, 0, sizeof(a5));
+    a5.d = ctx->dims;
+    a5.f = freq<T>(ctx);
+    a5.tw = twid<T>(ctx);
+    a5.W = W;
+    a5.x = xi;
+    a5.p = pi;
+    a5.r = ri;
+    a5.r_e = ctx->re_i;
+    a5.x_e = ctx->xe_i;
+    a5.p_e = ctx->pe_i;
+    a5.macroW = ctx->macroW;
+    a5.cg = ctx->cg;
+    a5.pre = ctx->pre;
+    a5.partials = ctx->partials;
+    a5.counters = ctx->counters;
+    const int opk = opk_apply(ctx);
+
+    int launched = 0;
+    int chunk = 4;
+    const int nc = ctx->nc;
+    int nact = ctx->B;
+    while (true) {
+        const double cp = cpass(ctx, dbl, nact);
+        const double mb = mat_bytes(ctx, dbl, false) * (ctx->model == DBFFT_ISO_ELASTIC ? 1.0 : (double)nact / ctx->B);
+        for (int k = 0; k < chunk; ++k) {
+            TRY(run(ctx, dbl ? "axis1_inv_cg_f64" : "axis1_inv_cg_f32", (9 + nc) * cp,
+                    [&] { return launch_ax1_inv<T>(AX1_CG, a1, ctx->stream); }));
+            TRY(run(ctx, dbl ? "axis2_f64" : "axis2_f32", 2 * nc * cp, [&] { return launch_ax2<T>(+1, a2, ctx->stream); }));
+            TRY(run(ctx, dbl ? "axis3_apply_f64" : "axis3_apply_f32", 2 * nc * cp + mb,
+                    [&] { return launch_ax3<T>(opk, a3, ctx->stream); }));
+            TRY(run(ctx, dbl ? "axis2_f64" : "axis2_f32", 2 * nc * cp, [&] { return launch_ax2<T>(-1, a2, ctx->stream); }));
+            TRY(run(ctx, dbl ? "axis1_fwd_cg_f64" : "axis1_fwd_cg_f32", (15 + nc) * cp,
+                    [&] { return launch_ax1_fwd<T>(AX5_CG, a5, ctx->stream); }));
+        }
+        launched += chunk;
+        CK(cudaMemcpyAsync(ctx->cg_h, ctx->cg, ctx->B * sizeof(CgState), cudaMemcpyDeviceToHost, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+        prof_flush(ctx);
+        bool all = true;
+        nact = 0;
+        for (int b = 0; b < ctx->B; ++b) {
+            all &= (ctx->cg_h[b].done != 0);
+            nact += ctx->cg_h[b].done ? 0 : 1;
+        }
+        if (all || launched >= ctx->grid.max_iter + 1) break;
+        chunk = chunk < 16 ? chunk * 2 : 16;
+    }
+    it_max = 0;
+    for (int b = 0; b < ctx->B; ++b) {
+        it_sum += ctx->cg_h[b].iter;
+        if (ctx->cg_h[b].iter > it_max) it_max = ctx->cg_h[b].iter;
+        if (ctx->cg_h[b].flags & 2) return fail(ctx, DBFFT_E_NONFINITE, "non-finite value in the inner CG");
+    }
+    return DBFFT_OK;
+}
+
+// Mean tangent of the current state -> preconditioner (R10), nonlinear only.
+dbfft_status refresh_precond(dbfft_ctx* ctx) {
+    const int nblk = 64;
+    const int kind = ctx->model == DBFFT_NEO_HOOKE ? 0 : 1;
+    TRY(run(ctx, "mean_tangent", 0.0, [&] {
+        if (ctx->prec == DBFFT_MIXED)
+            return launch_mean_tangent<float>(kind, ctx->B, ctx->V, reinterpret_cast<const float*>(ctx->tan),
+                                              ctx->phase, ctx->lam, ctx->mu, ctx->partials, nblk, ctx->stream);
+        return launch_mean_tangent<double>(kind, ctx->B, ctx->V, reinterpret_cast<const double*>(ctx->tan),
+                                           ctx->phase, ctx->lam, ctx->mu, ctx->partials, nblk, ctx->stream);
+    }));
+    std::vector<double> ph((size_t)ctx->B * nblk * 81);
+    CK(cudaMemcpyAsync(ph.data(), ctx->partials, ph.size() * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    for (int b = 0; b < ctx->B; ++b) {
+        double C[3][3][3][3];
+        double* Cf = &C[0][0][0][0];
+        for (int q = 0; q < 81; ++q) {
+            double s = 0.0;
+            for (int k = 0; k < nblk; ++k) s += ph[((size_t)b * nblk + k) * 81 + q];
+            Cf[q] = s / (double)ctx->V;
+        }
+        if (!precond_from(ctx, C, ctx->pre_h[b / ctx->Rm]))
+            return fail(ctx, DBFFT_E_NONFINITE, "singular macro block of the mean tangent");
+    }
+    CK(cudaMemcpyAsync(ctx->pre, ctx->pre_h.data(), ctx->pre_h.size() * sizeof(PrecondData), cudaMemcpyHostToDevice,
+                       ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return DBFFT_OK;
+}
+
+dbfft_status set_scales(dbfft_ctx* ctx, const std::vector<double>& s) {
+    std::memcpy(ctx->small_h, s.data(), ctx->B * sizeof(double));
+    CK(cudaMemcpyAsync(ctx->scal, ctx->small_h, ctx->B * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+    return DBFFT_OK;
+}
+
+// Outer FP64 loop of one increment (linear refinement or Newton).
+dbfft_status solve_current(dbfft_ctx* ctx, dbfft_report* rep) {
+    const bool linear = ctx->model == DBFFT_ISO_ELASTIC;
+    const bool inner64 = ctx->prec == DBFFT_FP64;
+    std::vector<double> ru2, re2, bn(ctx->B, 0.0);
+    std::vector<char> done(ctx->B, 0);
+    long long it_sum = 0;
+    int it_max_all = 0;
+    int outer = 0, steps = 0;
+    bool converged = false;
+    double worst_eq = 0.0, worst_ld = 0.0, worst_rel = 0.0;
+    if (linear) {
+        CK(cudaMemsetAsync(ctx->x64, 0, (size_t)ctx->B * 3 * ctx->H * sizeof(cplx<double>), ctx->stream));
+        CK(cudaMemsetAsync(ctx->xe64, 0, (size_t)ctx->B * 9 * sizeof(double), ctx->stream));
+    }
+    const int max_steps = ctx->grid.max_newton > 0 ? ctx->grid.max_newton : 50;
+    for (int step = 0; step <= max_steps; ++step) {
+        TRY(chain_residual(ctx, ctx->x64, ctx->xe64, ru2, re2));
+        ++outer;
+        // convergence per right-hand side
+        CK(cudaMemcpyAsync(ctx->small_h, ctx->sig0, ctx->B * 9 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+        bool all = true;
+        worst_eq = worst_ld = worst_rel = 0.0;
+        for (int b = 0; b < ctx->B; ++b) {
+            const double rn = std::sqrt(ru2[b] + re2[b]);
+            double sn = 0.0;
+            for (int q = 0; q < ctx->nc; ++q) {
+                const double v = ctx->small_h[b * 9 + q];
+                sn += (ctx->nc == 6 && q >= 3 ? 2.0 : 1.0) * v * v;
+            }
+            sn = std::sqrt(sn);
+            const double eq = sn > 0 ? std::sqrt(ru2[b]) / sn : std::sqrt(ru2[b]);
+            const double ld = (sn > 0 && ctx->dims.ne) ? std::sqrt(re2[b]) / ((double)ctx->V * sn) : 0.0;
+            if (linear) {
+                if (step == 0) bn[b] = rn;
+                const double rel = bn[b] > 0 ? rn / bn[b] : 0.0;
+                done[b] = (bn[b] == 0.0) || rel <= ctx->grid.tol;
+                worst_rel = std::max(worst_rel, rel);
+            } else {
+                done[b] = eq <= ctx->grid.newton_tol && ld <= ctx->grid.load_tol;
+            }
+            worst_eq = std::max(worst_eq, eq);
+            worst_ld = std::max(worst_ld, ld);
+            all &= done[b] != 0;
+        }
+        if (all) { converged = true; break; }
+        if (step == max_steps) break;
+        if (!linear && step == 0) TRY(refresh_precond(ctx));
+        // inner solve on r / ||r||
+        std::vector<double> sc(ctx->B), sb(ctx->B);
+        for (int b = 0; b < ctx->B; ++b) {
+            const double rn = std::sqrt(ru2[b] + re2[b]);
+            sc[b] = (!done[b] && rn > 0) ? 1.0 / rn : 0.0;
+            sb[b] = (!done[b] && rn > 0) ? rn : 0.0;
+        }
+        TRY(set_scales(ctx, sc));
+        const double itol = (linear && inner64) ? ctx->grid.tol : ctx->grid.eta_inner;
+        int itm = 0;
+        const double c64 = cpass(ctx, true, ctx->B), ci = cpass(ctx, inner64, ctx->B);
+        if (inner64) {
+            TRY(run(ctx, "to_inner", 3 * (c64 + 2 * ci), [&] {
+                return launch_to_inner<double>(ctx->dims, ctx->r64, ctx->re64, ctx->scal,
+                                               reinterpret_cast<cplx<double>*>(ctx->ri), ctx->re_i,
+                                               reinterpret_cast<cplx<double>*>(ctx->xi), ctx->xe_i, ctx->stream);
+            }));
+            TRY(inner_cg<double>(ctx, itol, it_sum, itm));
+        } else {
+            TRY(run(ctx, "to_inner", 3 * (c64 + 2 * ci), [&] {
+                return launch_to_inner<float>(ctx->dims, ctx->r64, ctx->re64, ctx->scal,
+                                              reinterpret_cast<cplx<float>*>(ctx->ri), ctx->re_i,
+                                              reinterpret_cast<cplx<float>*>(ctx->xi), ctx->xe_i, ctx->stream);
+            }));
+            TRY(inner_cg<float>(ctx, itol, it_sum, itm));
+        }
+        it_max_all += itm;
+        TRY(set_scales(ctx, sb));
+        TRY(run(ctx, "from_inner", 3 * (2 * c64 + ci), [&] {
+            if (inner64)
+                return launch_from_inner<double>(ctx->dims, reinterpret_cast<const cplx<double>*>(ctx->xi), ctx->xe_i,
+                                                 ctx->scal, ctx->x64, ctx->xe64, ctx->stream);
+            return launch_from_inner<float>(ctx->dims, reinterpret_cast<const cplx<float>*>(ctx->xi), ctx->xe_i,
+                                            ctx->scal, ctx->x64, ctx->xe64, ctx->stream);
+        }));
+        ++steps;
+    }
+    ctx->have_solution = true;
+    if (rep) {
+        rep->newton_iters = steps;
+        rep->outer_iters = outer;
+        rep->cg_iters = it_sum;
+        rep->cg_iters_max = it_max_all;
+        rep->eps_eq = worst_eq;
+        rep->load_res = worst_ld;
+        rep->true_rel_res = worst_rel;
+    }
+    if (!converged) return fail(ctx, DBFFT_E_NOT_CONVERGED, "iteration cap reached before the tolerance");
+    return DBFFT_OK;
+}
+
+dbfft_status commit_state(dbfft_ctx* ctx) {
+    if (ctx->model == DBFFT_CP_FCC_POWERLAW) {
+        std::swap(ctx->eps_p, ctx->eps_p_t);
+        std::swap(ctx->sig_prev, ctx->sig_t);
+    }
+    return DBFFT_OK;
+}
+
+}  // namespace
+
+// ======================================================================== C ABI
+extern "C" {
+
+const char* dbfft_status_string(dbfft_status s) {
+    switch (s) {
+        case DBFFT_OK: return "DBFFT_OK";
+        case DBFFT_E_ARG: return "DBFFT_E_ARG";
+        case DBFFT_E_UNSUPPORTED_GRID: return "DBFFT_E_UNSUPPORTED_GRID";
+        case DBFFT_E_NOMEM: return "DBFFT_E_NOMEM";
+        case DBFFT_E_CUDA: return "DBFFT_E_CUDA";
+        case DBFFT_E_NOT_CONVERGED: return "DBFFT_E_NOT_CONVERGED";
+        case DBFFT_E_NONFINITE: return "DBFFT_E_NONFINITE";
+        case DBFFT_E_TIMEOUT: return "DBFFT_E_TIMEOUT";
+        case DBFFT_E_MATERIAL: return "DBFFT_E_MATERIAL";
+        case DBFFT_E_STATE: return "DBFFT_E_STATE";
+    }
+    return "unknown";
+}
+
+const char* dbfft_last_error(const dbfft_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+long long dbfft_launch_count(const dbfft_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+dbfft_status dbfft_profile(dbfft_ctx* ctx, int enable) {
+    if (!ctx) return DBFFT_E_ARG;
+    CK(cudaStreamSynchronize(ctx->stream));
+    prof_flush(ctx);
+    ctx->prof = enable != 0;
+    ctx->prof_name.clear();
+    ctx->prof_n.clear();
+    ctx->prof_ms.clear();
+    ctx->prof_bytes.clear();
+    return DBFFT_OK;
+}
+
+int dbfft_profile_read(dbfft_ctx* ctx, dbfft_profile_entry* out, int max_entries) {
+    if (!ctx) return 0;
+    cudaStreamSynchronize(ctx->stream);
+    prof_flush(ctx);
+    const int n = (int)ctx->prof_name.size();
+    for (int i = 0; i < n && i < max_entries; ++i) {
+        std::memset(out[i].name, 0, sizeof(out[i].name));
+        std::strncpy(out[i].name, ctx->prof_name[i].c_str(), sizeof(out[i].name) - 1);
+        out[i].launches = ctx->prof_n[i];
+        out[i].ms = ctx->prof_ms[i];
+        out[i].bytes = ctx->prof_bytes[i];
+    }
+    return n;
+}
+
+size_t dbfft_device_bytes(const dbfft_ctx* ctx) { return ctx ? ctx->bytes : 0; }
+
+void dbfft_destroy(dbfft_ctx* ctx) {
+    if (!ctx) return;
+    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    prof_flush(ctx);
+    for (cudaEvent_t e : ctx->pool) cudaEventDestroy(e);
+    for (auto& b : ctx->bufs) {
+        if (ctx->use_cb) ctx->alloc.free(b.p, ctx->alloc.user);
+        else cudaFree(b.p);
+    }
+    if (ctx->cg_h) cudaFreeHost(ctx->cg_h);
+    if (ctx->part_h) cudaFreeHost(ctx->part_h);
+    if (ctx->small_h) cudaFreeHost(ctx->small_h);
+    delete ctx;
+}
+
+static dbfft_status create_impl(dbfft_ctx* ctx, const dbfft_grid* grid, const dbfft_materials* mat,
+                                const dbfft_load* load) {
+    ctx->grid = *grid;
+    ctx->n1 = grid->n[0];
+    ctx->n2 = grid->n[1];
+    ctx->n3 = grid->n[2];
+    for (int a = 0; a < 3; ++a)
+        if (!supported_len(grid->n[a]))
+            return fail(ctx, DBFFT_E_UNSUPPORTED_GRID, "grid sizes must be powers of two in [8, 256]");
+    ctx->m = ctx->n3 / 2;
+    ctx->h = ctx->m + 1;
+    ctx->H = (long long)ctx->n1 * ctx->n2 * ctx->h;
+    ctx->V = (long long)ctx->n1 * ctx->n2 * ctx->n3;
+    ctx->B = grid->batch;
+    ctx->Bm = grid->n_materials;
+    if (ctx->B < 1 || ctx->Bm < 1 || ctx->B % ctx->Bm) return fail(ctx, DBFFT_E_ARG, "batch must be a multiple of n_materials");
+    if (ctx->B > 65535) return fail(ctx, DBFFT_E_ARG, "batch too large");
+    ctx->Rm = ctx->B / ctx->Bm;
+    ctx->kin = grid->kinematics;
+    if (ctx->kin != DBFFT_SMALL && ctx->kin != DBFFT_FINITE) return fail(ctx, DBFFT_E_ARG, "kinematics");
+    ctx->nc = ctx->kin == DBFFT_SMALL ? 6 : 9;
+    ctx->prec = grid->precision;
+    if (ctx->prec != DBFFT_FP64 && ctx->prec != DBFFT_MIXED) return fail(ctx, DBFFT_E_ARG, "precision");
+    if (!(grid->tol > 0) || grid->max_iter < 1) return fail(ctx, DBFFT_E_ARG, "tol / max_iter");
+    if (!mat || !mat->phase_id || mat->n_phases < 1 || !mat->phases) return fail(ctx, DBFFT_E_ARG, "materials");
+    ctx->model = mat->phases[0].model;
+    for (int p = 0; p < mat->n_phases; ++p)
+        if (mat->phases[p].model != ctx->model) return fail(ctx, DBFFT_E_ARG, "all phases must use one model kind");
+    if ((ctx->model == DBFFT_NEO_HOOKE) != (ctx->kin == DBFFT_FINITE))
+        return fail(ctx, DBFFT_E_ARG, "NEO_HOOKE needs FINITE kinematics; ISO_ELASTIC and CP need SMALL");
+    if (ctx->model != DBFFT_ISO_ELASTIC && ctx->Rm != 1)
+        return fail(ctx, DBFFT_E_ARG, "nonlinear models need one material map per right-hand side");
+    if (!load || !load->target || load->n_increments < 1) return fail(ctx, DBFFT_E_ARG, "load");
+    ctx->stress_mask = load->stress_mask;
+    ctx->n_inc = load->n_increments;
+    ctx->total_time = load->total_time > 0 ? load->total_time : 1.0;
+    ctx->target.assign(load->target, load->target + ctx->B * 9);
+    for (double v : ctx->target)
+        if (!std::isfinite(v)) return fail(ctx, DBFFT_E_NONFINITE, "non-finite load target");
+
+    // macro unknowns (R8)
+    Dims& d = ctx->dims;
+    std::memset(&d, 0, sizeof(d));
+    d.n1 = ctx->n1; d.n2 = ctx->n2; d.n3 = ctx->n3; d.h = ctx->h; d.m = ctx->m;
+    d.H = ctx->H; d.V = ctx->V; d.plane = (long long)ctx->n2 * ctx->h;
+    d.B = ctx->B; d.Rm = ctx->Rm; d.nc = ctx->nc; d.kin = ctx->kin;
+    d.invN = 1.0 / (double)ctx->V;
+    if (ctx->nc == 6) {
+        static const int pi[6] = {0, 1, 2, 1, 0, 0}, pj[6] = {0, 1, 2, 2, 2, 1};
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j)
+                if (((ctx->stress_mask >> (3 * i + j)) & 1u) != ((ctx->stress_mask >> (3 * j + i)) & 1u))
+                    return fail(ctx, DBFFT_E_ARG, "small-strain stress mask must be symmetric");
+        for (int mm = 0; mm < 6; ++mm)
+            if ((ctx->stress_mask >> (3 * pi[mm] + pj[mm])) & 1u) {
+                ctx->activeflag_h[mm] = 1;
+                d.active[d.ne++] = mm;
+            }
+    } else {
+        for (int q = 0; q < 9; ++q)
+            if ((ctx->stress_mask >> q) & 1u) {
+                ctx->activeflag_h[q] = 1;
+                d.active[d.ne++] = q;
+            }
+    }
+    // right-hand sides per CTA of pass 3: a divisor of Rm that keeps the CTA within 256 threads
+    ctx->RB = 1;
+    for (int rb = std::min(ctx->Rm, 8); rb >= 1; --rb)
+        if (ctx->Rm % rb == 0 && ax3_threads_per_line(ctx->n3, ctx->nc, rb, true) <= 256 &&
+            ax3_threads_per_line(ctx->n3, ctx->nc, rb, false) <= 256) {
+            ctx->RB = rb;
+            break;
+        }
+
+    TRY(upload_tables(ctx));
+    TRY(dalloc_t(ctx, 9, &ctx->activeflag));
+    CK(cudaMemcpyAsync(ctx->activeflag, ctx->activeflag_h, 9 * sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
+
+    // materials
+    const size_t nvox = (size_t)ctx->Bm * ctx->V;
+    TRY(dalloc_t(ctx, nvox, &ctx->phase));
+    for (size_t i = 0; i < nvox; ++i)
+        if (mat->phase_id[i] >= mat->n_phases) return fail(ctx, DBFFT_E_ARG, "phase id out of range");
+    CK(cudaMemcpyAsync(ctx->phase, mat->phase_id, nvox * sizeof(uint16_t), cudaMemcpyHostToDevice, ctx->stream));
+    if (mat->E_scale) {
+        for (size_t i = 0; i < nvox; ++i)
+            if (!std::isfinite(mat->E_scale[i])) return fail(ctx, DBFFT_E_NONFINITE, "non-finite E_scale");
+        TRY(dalloc_t(ctx, nvox, &ctx->scale));
+        CK(cudaMemcpyAsync(ctx->scale, mat->E_scale, nvox * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+    }
+    const int np = mat->n_phases;
+    ctx->lam_h.assign(np, 0.0);
+    ctx->mu_h.assign(np, 0.0);
+    ctx->E_h.assign(np, 1.0);
+    std::vector<double> lam1(np, 0.0), mu1(np, 0.0);
+    for (int p = 0; p < np; ++p) {
+        const dbfft_phase& ph = mat->phases[p];
+        if (ctx->model == DBFFT_ISO_ELASTIC) {
+            if (!std::isfinite(ph.E) || !std::isfinite(ph.nu)) return fail(ctx, DBFFT_E_NONFINITE, "non-finite E or nu");
+            if (!(ph.E > 0) || !(ph.nu > -1 && ph.nu < 0.5)) return fail(ctx, DBFFT_E_ARG, "E > 0 and -1 < nu < 1/2 required");
+            ctx->lam_h[p] = ph.E * ph.nu / ((1 + ph.nu) * (1 - 2 * ph.nu));
+            ctx->mu_h[p] = ph.E / (2 * (1 + ph.nu));
+            ctx->E_h[p] = ph.E;
+            lam1[p] = ctx->lam_h[p] / ph.E;
+            mu1[p] = ctx->mu_h[p] / ph.E;
+        } else if (ctx->model == DBFFT_NEO_HOOKE) {
+            if (!std::isfinite(ph.mu) || !std::isfinite(ph.lambda)) return fail(ctx, DBFFT_E_NONFINITE, "non-finite mu or lambda");
+            if (!(ph.mu > 0)) return fail(ctx, DBFFT_E_ARG, "mu > 0 required");
+            ctx->lam_h[p] = ph.lambda;
+            ctx->mu_h[p] = ph.mu;
+        } else if (ctx->model == DBFFT_CP_FCC_POWERLAW) {
+            const double vals[9] = {ph.C11, ph.C12, ph.C44, ph.gdot0, ph.m, ph.tau_c, ph.quat[0], ph.quat[1], ph.quat[2]};
+            for (double v : vals)
+                if (!std::isfinite(v)) return fail(ctx, DBFFT_E_NONFINITE, "non-finite crystal parameter");
+        } else {
+            return fail(ctx, DBFFT_E_ARG, "unknown model");
+        }
+    }
+    TRY(dalloc_t(ctx, np, &ctx->lam));
+    TRY(dalloc_t(ctx, np, &ctx->mu));
+    TRY(dalloc_t(ctx, np, &ctx->lam1));
+    TRY(dalloc_t(ctx, np, &ctx->mu1));
+    CK(cudaMemcpyAsync(ctx->lam, ctx->lam_h.data(), np * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->mu, ctx->mu_h.data(), np * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->lam1, lam1.data(), np * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->mu1, mu1.data(), np * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    if (ctx->model == DBFFT_CP_FCC_POWERLAW) {
+        std::vector<CpGrain> gr(np);
+        for (int p = 0; p < np; ++p)
+            if (!cp_grain(mat->phases[p], gr[p])) return fail(ctx, DBFFT_E_ARG, "singular crystal stiffness");
+        TRY(dalloc_t(ctx, np, &ctx->grains));
+        CK(cudaMemcpyAsync(ctx->grains, gr.data(), np * sizeof(CpGrain), cudaMemcpyHostToDevice, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+        const dbfft_phase& p0 = mat->phases[0];
+        ctx->cp.gdot0 = p0.gdot0;
+        ctx->cp.inv_m = 1.0 / p0.m;
+        ctx->cp.tau_c = p0.tau_c;
+        ctx->cp.dt = ctx->total_time / ctx->n_inc;
+        ctx->cp.rtol = 1e-12;
+        ctx->cp.max_it = 100;
+    }
+
+    // preconditioner of the linear problem: mean stiffness (Sec. 2.5, R10)
+    ctx->pre_h.assign(ctx->Bm, PrecondData{});
+    for (int g = 0; g < ctx->Bm; ++g) {
+        double C[3][3][3][3];
+        if (ctx->model == DBFFT_ISO_ELASTIC) {
+            double sl = 0.0, sm = 0.0;
+            for (long long v = 0; v < ctx->V; ++v) {
+                const int p = mat->phase_id[(size_t)g * ctx->V + v];
+                const double s = mat->E_scale ? mat->E_scale[(size_t)g * ctx->V + v] : 1.0;
+                sl += ctx->lam_h[p] * s;
+                sm += ctx->mu_h[p] * s;
+            }
+            iso_C(sl / ctx->V, sm / ctx->V, C);
+        } else if (ctx->model == DBFFT_NEO_HOOKE) {  // initial tangent K(I) = isotropic C
+            double sl = 0.0, sm = 0.0;
+            for (long long v = 0; v < ctx->V; ++v) {
+                const int p = mat->phase_id[(size_t)g * ctx->V + v];
+                sl += ctx->lam_h[p];
+                sm += ctx->mu_h[p];
+            }
+            iso_C(sl / ctx->V, sm / ctx->V, C);
+        } else {  // elastic stiffness of the grains
+            double Cs[3][3][3][3] = {};
+            std::vector<long long> cnt(np, 0);
+            for (long long v = 0; v < ctx->V; ++v) cnt[mat->phase_id[(size_t)g * ctx->V + v]]++;
+            for (int p = 0; p < np; ++p) {
+                if (!cnt[p]) continue;
+                CpGrain gg;
+                cp_grain(mat->phases[p], gg);
+                std::vector<double> A(36);
+                for (int a = 0; a < 6; ++a)
+                    for (int b = 0; b < 6; ++b) A[a * 6 + b] = gg.S[sym6(a, b)];
+                invert(6, A);
+                for (int a = 0; a < 6; ++a)
+                    for (int b = 0; b < 6; ++b) {
+                        double Ta[3][3], Tb[3][3];
+                        basis_tensor(6, a, Ta);
+                        basis_tensor(6, b, Tb);
+                        for (int i = 0; i < 3; ++i)
+                            for (int j = 0; j < 3; ++j)
+                                for (int k = 0; k < 3; ++k)
+                                    for (int l = 0; l < 3; ++l)
+                                        Cs[i][j][k][l] += (double)cnt[p] / ctx->V * Ta[i][j] * A[a * 6 + b] * Tb[k][l];
+                    }
+            }
+            std::memcpy(C, Cs, sizeof(C));
+        }
+        if (!precond_from(ctx, C, ctx->pre_h[g])) return fail(ctx, DBFFT_E_ARG, "singular mean stiffness");
+    }
+    TRY(dalloc_t(ctx, ctx->Bm, &ctx->pre));
+    CK(cudaMemcpyAsync(ctx->pre, ctx->pre_h.data(), ctx->Bm * sizeof(PrecondData), cudaMemcpyHostToDevice, ctx->stream));
+
+    // vectors and work buffers
+    const size_t nU = (size_t)ctx->B * 3 * ctx->H;
+    const size_t isz = ctx->prec == DBFFT_FP64 ? sizeof(cplx<double>) : sizeof(cplx<float>);
+    TRY(dalloc_t(ctx, nU, &ctx->x64));
+    TRY(dalloc_t(ctx, nU, &ctx->r64));
+    TRY(dalloc(ctx, nU * isz, &ctx->xi));
+    TRY(dalloc(ctx, nU * isz, &ctx->ri));
+    TRY(dalloc(ctx, nU * isz, &ctx->pi));
+    TRY(dalloc(ctx, (size_t)ctx->B * ctx->nc * ctx->H * sizeof(cplx<double>), &ctx->W));
+    double** smalls[] = {&ctx->xe64, &ctx->re64, &ctx->xe_i, &ctx->re_i, &ctx->pe_i, &ctx->fU,
+                         &ctx->sigf, &ctx->sig0, &ctx->macroW, &ctx->macroW2};
+    for (double** s : smalls) TRY(dalloc_t(ctx, (size_t)ctx->B * 9, s));
+    TRY(dalloc_t(ctx, (size_t)ctx->B, &ctx->scal));
+    TRY(dalloc_t(ctx, (size_t)ctx->B, &ctx->cg));
+    TRY(dalloc_t(ctx, (size_t)ctx->B, &ctx->counters));
+    TRY(dalloc_t(ctx, 1, &ctx->errw));
+    CK(cudaMemsetAsync(ctx->counters, 0, ctx->B * sizeof(unsigned), ctx->stream));
+    CK(cudaMemsetAsync(ctx->x64, 0, nU * sizeof(cplx<double>), ctx->stream));
+    CK(cudaMemsetAsync(ctx->xe64, 0, ctx->B * 9 * sizeof(double), ctx->stream));
+    CK(cudaMemsetAsync(ctx->macroW2, 0, ctx->B * 9 * sizeof(double), ctx->stream));
+    // reduction partials: the largest grid of any reducing kernel
+    {
+        const long long nb1 = (ctx->dims.plane + ax1_tile(ctx->n1, false) - 1) / ax1_tile(ctx->n1, false);
+        const long long nb1d = (ctx->dims.plane + ax1_tile(ctx->n1, true) - 1) / ax1_tile(ctx->n1, true);
+        const long long nlines = (long long)ctx->n1 * ctx->n2;
+        const long long nb3 = (nlines + ax3_lines(ctx->n3, ctx->nc, ctx->RB, false) - 1) /
+                              ax3_lines(ctx->n3, ctx->nc, ctx->RB, false);
+        const long long nb3d = (nlines + ax3_lines(ctx->n3, ctx->nc, ctx->RB, true) - 1) /
+                               ax3_lines(ctx->n3, ctx->nc, ctx->RB, true);
+        const long long nbi = (ctx->H + 255) / 256;
+        long long nb = std::max(std::max(nb1, nb1d), std::max(std::max(nb3, nb3d), nbi));
+        ctx->nblk_max = (int)nb;
+        ctx->partials_n = std::max((size_t)ctx->B * (size_t)nb * 2, (size_t)ctx->B * 64 * 81);
+        TRY(dalloc_t(ctx, ctx->partials_n, &ctx->partials));
+        if (cudaMallocHost(&ctx->part_h, ctx->partials_n * sizeof(double)) != cudaSuccess)
+            return fail(ctx, DBFFT_E_NOMEM, "pinned host allocation failed");
+    }
+    if (cudaMallocHost(&ctx->cg_h, ctx->B * sizeof(CgState)) != cudaSuccess ||
+        cudaMallocHost(&ctx->small_h, (ctx->B * 10 + 8) * sizeof(double)) != cudaSuccess)
+        return fail(ctx, DBFFT_E_NOMEM, "pinned host allocation failed");
+    // nonlinear tangent and state
+    if (ctx->model != DBFFT_ISO_ELASTIC) {
+        ctx->ntan = ctx->model == DBFFT_NEO_HOOKE ? 10 : 21;
+        const size_t tsz = ctx->prec == DBFFT_FP64 ? 8 : 4;
+        TRY(dalloc(ctx, (size_t)ctx->B * ctx->V * ctx->ntan * tsz, &ctx->tan));
+        if (ctx->model == DBFFT_CP_FCC_POWERLAW) {
+            const size_t ns = (size_t)ctx->B * ctx->V * 6;
+            TRY(dalloc_t(ctx, ns, &ctx->eps_p));
+            TRY(dalloc_t(ctx, ns, &ctx->sig_prev));
+            TRY(dalloc_t(ctx, ns, &ctx->eps_p_t));
+            TRY(dalloc_t(ctx, ns, &ctx->sig_t));
+            CK(cudaMemsetAsync(ctx->eps_p, 0, ns * sizeof(double), ctx->stream));
+            CK(cudaMemsetAsync(ctx->sig_prev, 0, ns * sizeof(double), ctx->stream));
+        }
+    }
+    TRY(set_load(ctx, 0, ctx->target.data()));
+    ctx->cur_inc = -1;
+    CK(cudaStreamSynchronize(ctx->stream));
+    return DBFFT_OK;
+}
+
+dbfft_status dbfft_create(const dbfft_grid* grid, const dbfft_materials* mat, const dbfft_load* load,
+                          const dbfft_allocator* alloc, void* stream, dbfft_ctx** out) {
+    if (!out || !grid) return DBFFT_E_ARG;
+    *out = nullptr;
+    dbfft_ctx* ctx = new dbfft_ctx();
+    ctx->stream = reinterpret_cast<cudaStream_t>(stream);
+    if (alloc && alloc->alloc && alloc->free) {
+        ctx->alloc = *alloc;
+        ctx->use_cb = true;
+    }
+    dbfft_status s = create_impl(ctx, grid, mat, load);
+    if (s != DBFFT_OK) {
+        std::fprintf(stderr, "dbfft_create: %s\n", ctx->err.c_str());
+        dbfft_destroy(ctx);
+        return s;
+    }
+    *out = ctx;
+    return DBFFT_OK;
+}
+
+dbfft_status dbfft_solve_increment(dbfft_ctx* ctx, int inc, dbfft_report* rep) {
+    if (!ctx) return DBFFT_E_ARG;
+    if (inc < 0 || inc >= ctx->n_inc) return fail(ctx, DBFFT_E_ARG, "increment out of range");
+    if (ctx->model != DBFFT_ISO_ELASTIC && inc != ctx->cur_inc + 1)
+        return fail(ctx, DBFFT_E_STATE, "path-dependent solves must run increments in order");
+    const auto t0 = std::chrono::steady_clock::now();
+    if (rep) std::memset(rep, 0, sizeof(*rep));
+    TRY(set_load(ctx, inc, ctx->target.data()));
+    dbfft_status s = solve_current(ctx, rep);
+    if (s == DBFFT_OK || s == DBFFT_E_NOT_CONVERGED) {
+        commit_state(ctx);
+        ctx->cur_inc = inc;
+    }
+    if (rep) rep->wall_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    return s;
+}
+
+dbfft_status dbfft_homogenized_stress(dbfft_ctx* ctx, double* out) {
+    if (!ctx || !out) return DBFFT_E_ARG;
+    if (!ctx->have_solution) return fail(ctx, DBFFT_E_STATE, "no solution yet");
+    std::vector<double> s(ctx->B * 9);
+    CK(cudaMemcpyAsync(s.data(), ctx->sig0, s.size() * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    static const int pi[6] = {0, 1, 2, 1, 0, 0}, pj[6] = {0, 1, 2, 2, 2, 1};
+    for (int b = 0; b < ctx->B; ++b) {
+        if (ctx->nc == 9) {
+            for (int q = 0; q < 9; ++q) out[b * 9 + q] = s[b * 9 + q];
+        } else {
+            for (int mm = 0; mm < 6; ++mm) {
+                out[b * 9 + 3 * pi[mm] + pj[mm]] = s[b * 9 + mm];
+                out[b * 9 + 3 * pj[mm] + pi[mm]] = s[b * 9 + mm];
+            }
+        }
+    }
+    return DBFFT_OK;
+}
+
+dbfft_status dbfft_get_solution(dbfft_ctx* ctx, void* u_hat, double* e) {
+    if (!ctx) return DBFFT_E_ARG;
+    if (u_hat)
+        CK(cudaMemcpyAsync(u_hat, ctx->x64, (size_t)ctx->B * 3 * ctx->H * sizeof(cplx<double>),
+                           cudaMemcpyDeviceToDevice, ctx->stream));
+    if (e) CK(cudaMemcpyAsync(e, ctx->xe64, (size_t)ctx->B * 9 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return DBFFT_OK;
+}
+
+dbfft_status dbfft_apply(dbfft_ctx* ctx, int flags, const void* u_hat, const void* e_in, void* out, void* e_out) {
+    if (!ctx || !u_hat || !out) return DBFFT_E_ARG;
+    if (u_hat == out) return fail(ctx, DBFFT_E_ARG, "out may not alias u_hat");
+    const bool f32 = (flags & DBFFT_APPLY_FP32) != 0;
+    const double* ein = reinterpret_cast<const double*>(e_in);
+    double* eout = reinterpret_cast<double*>(e_out);
+    if (flags & DBFFT_APPLY_RESIDUAL) {
+        if (f32) return fail(ctx, DBFFT_E_ARG, "the residual is formed in FP64 only");
+        // copy e_in into the macro unknown buffer used by the residual chain
+        std::vector<double> ru2, re2;
+        if (ein) CK(cudaMemcpyAsync(ctx->xe_i, ein, ctx->B * 9 * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
+        else CK(cudaMemsetAsync(ctx->xe_i, 0, ctx->B * 9 * sizeof(double), ctx->stream));
+        cplx<double>* save = ctx->r64;
+        ctx->r64 = reinterpret_cast<cplx<double>*>(out);
+        dbfft_status s = chain_residual(ctx, reinterpret_cast<const cplx<double>*>(u_hat), ctx->xe_i, ru2, re2);
+        ctx->r64 = save;
+        TRY(s);
+        if (eout) CK(cudaMemcpyAsync(eout, ctx->re64, ctx->B * 9 * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+        return DBFFT_OK;
+    }
+    if (flags & DBFFT_APPLY_PRECOND) {
+        TRY(run(ctx, "precond", 0.0, [&] {
+            if (f32)
+                return launch_precond_field<float>(ctx->dims, freq<float>(ctx), ctx->pre,
+                                                   reinterpret_cast<const cplx<float>*>(u_hat),
+                                                   reinterpret_cast<cplx<float>*>(out), ein, eout, ctx->stream);
+            return launch_precond_field<double>(ctx->dims, freq<double>(ctx), ctx->pre,
+                                                reinterpret_cast<const cplx<double>*>(u_hat),
+                                                reinterpret_cast<cplx<double>*>(out), ein, eout, ctx->stream);
+        }));
+        CK(cudaStreamSynchronize(ctx->stream));
+        return DBFFT_OK;
+    }
+    if (ctx->model != DBFFT_ISO_ELASTIC) {
+        const bool stored64 = ctx->prec == DBFFT_FP64;
+        if (stored64 == f32) return fail(ctx, DBFFT_E_STATE, "the tangent is stored in the other precision");
+    }
+    TRY(run(ctx, "macro", 0.0,
+            [&] { return launch_macro(ctx->B, ctx->nc, ctx->activeflag, nullptr, ein, ctx->macroW, ctx->stream); }));
+    if (f32)
+        TRY(chain_apply<float>(ctx, reinterpret_cast<const cplx<float>*>(u_hat), ctx->macroW,
+                               reinterpret_cast<cplx<float>*>(out), eout));
+    else
+        TRY(chain_apply<double>(ctx, reinterpret_cast<const cplx<double>*>(u_hat), ctx->macroW,
+                                reinterpret_cast<cplx<double>*>(out), eout));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return DBFFT_OK;
+}
+
+dbfft_status dbfft_homogenized_tangent(dbfft_ctx* ctx, double* out, dbfft_report* rep) {
+    if (!ctx || !out) return DBFFT_E_ARG;
+    if (ctx->model != DBFFT_ISO_ELASTIC || ctx->nc != 6 || ctx->dims.ne != 0 || ctx->B != 6 * ctx->Bm)
+        return fail(ctx, DBFFT_E_STATE, "homogenized tangent needs linear small strain, strain control, B = 6 n_materials");
+    const auto t0 = std::chrono::steady_clock::now();
+    if (rep) std::memset(rep, 0, sizeof(*rep));
+    std::vector<double> tgt(ctx->B * 9, 0.0);
+    static const int pi[6] = {0, 1, 2, 1, 0, 0}, pj[6] = {0, 1, 2, 2, 2, 1};
+    for (int b = 0; b < ctx->B; ++b) {
+        const int mm = b % 6;
+        const double v = mm < 3 ? 1.0 : 1.0 / std::sqrt(2.0);  // unit Mandel strain
+        tgt[b * 9 + 3 * pi[mm] + pj[mm]] = v;
+        tgt[b * 9 + 3 * pj[mm] + pi[mm]] = v;
+    }
+    const int save_n = ctx->n_inc;
+    ctx->n_inc = 1;
+    dbfft_status s = set_load(ctx, 0, tgt.data());
+    if (s == DBFFT_OK) s = solve_current(ctx, rep);
+    ctx->n_inc = save_n;
+    if (s != DBFFT_OK && s != DBFFT_E_NOT_CONVERGED) return s;
+    std::vector<double> sg(ctx->B * 9);
+    CK(cudaMemcpyAsync(sg.data(), ctx->sig0, sg.size() * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    for (int g = 0; g < ctx->Bm; ++g)
+        for (int j = 0; j < 6; ++j)
+            for (int i = 0; i < 6; ++i)
+                out[(g * 6 + i) * 6 + j] = sg[(g * 6 + j) * 9 + i] * (i >= 3 ? std::sqrt(2.0) : 1.0);
+    TRY(set_load(ctx, 0, ctx->target.data()));
+    if (rep) rep->wall_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    return s;
+}
+
+dbfft_status dbfft_adjoint(dbfft_ctx* ctx, const double* dJ_dsigma, double* dJ_dE, dbfft_report* rep) {
+    if (!ctx || !dJ_dsigma || !dJ_dE) return DBFFT_E_ARG;
+    if (ctx->model != DBFFT_ISO_ELASTIC || ctx->dims.ne != 0)
+        return fail(ctx, DBFFT_E_STATE, "adjoint needs linear elastic phases under full strain control");
+    const auto t0 = std::chrono::steady_clock::now();
+    if (rep) std::memset(rep, 0, sizeof(*rep));
+    dbfft_report r1{}, r2{};
+    // forward solve of increment 0
+    TRY(set_load(ctx, 0, ctx->target.data()));
+    dbfft_status s = solve_current(ctx, &r1);
+    if (s != DBFFT_OK && s != DBFFT_E_NOT_CONVERGED) return s;
+    const size_t nU = (size_t)ctx->B * 3 * ctx->H;
+    if (!ctx->xfwd) TRY(dalloc_t(ctx, nU, &ctx->xfwd));
+    if (!ctx->W2) TRY(dalloc(ctx, (size_t)ctx->B * ctx->nc * ctx->H * sizeof(cplx<double>), &ctx->W2));
+    CK(cudaMemcpyAsync(ctx->xfwd, ctx->x64, nU * sizeof(cplx<double>), cudaMemcpyDeviceToDevice, ctx->stream));
+    std::vector<double> fUfwd(ctx->B * 9);
+    CK(cudaMemcpyAsync(fUfwd.data(), ctx->fU, fUfwd.size() * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    // adjoint problem: strain control with macro strain g = sym(dJ/dsigma); lam' = its fluctuation
+    std::vector<double> g(ctx->B * 9);
+    for (int b = 0; b < ctx->B; ++b)
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) g[b * 9 + 3 * i + j] = 0.5 * (dJ_dsigma[b * 9 + 3 * i + j] + dJ_dsigma[b * 9 + 3 * j + i]);
+    const int save_n = ctx->n_inc;
+    ctx->n_inc = 1;
+    s = set_load(ctx, 0, g.data());
+    if (s == DBFFT_OK) s = solve_current(ctx, &r2);
+    ctx->n_inc = save_n;
+    if (s != DBFFT_OK && s != DBFFT_E_NOT_CONVERGED) return s;
+    // assembly: dJ/dE = (1/N) (g + B lam')(x) : C1 : (epsbar + B u)(x)
+    CK(cudaMemcpyAsync(ctx->macroW2, ctx->fU, ctx->B * 9 * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->macroW, fUfwd.data(), ctx->B * 9 * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+    cplx<double>* W = reinterpret_cast<cplx<double>*>(ctx->W);
+    cplx<double>* W2 = reinterpret_cast<cplx<double>*>(ctx->W2);
+    Ax1InvArgs<double> a1{ctx->dims, freq<double>(ctx), twid<double>(ctx), ctx->xfwd, nullptr, W, nullptr, ctx->pre};
+    TRY(run(ctx, "axis1_inv_f64", 0.0, [&] { return launch_ax1_inv<double>(AX1_PLAIN, a1, ctx->stream); }));
+    Ax2Args<double> a2{ctx->dims, twid<double>(ctx), W, nullptr};
+    TRY(run(ctx, "axis2_f64", 0.0, [&] { return launch_ax2<double>(+1, a2, ctx->stream); }));
+    Ax1InvArgs<double> b1{ctx->dims, freq<double>(ctx), twid<double>(ctx), ctx->x64, nullptr, W2, nullptr, ctx->pre};
+    TRY(run(ctx, "axis1_inv_f64", 0.0, [&] { return launch_ax1_inv<double>(AX1_PLAIN, b1, ctx->stream); }));
+    Ax2Args<double> b2{ctx->dims, twid<double>(ctx), W2, nullptr};
+    TRY(run(ctx, "axis2_f64", 0.0, [&] { return launch_ax2<double>(+1, b2, ctx->stream); }));
+    Ax3Args<double> a3 = ax3_base<double>(ctx, W);
+    a3.W2 = W2;
+    a3.macroW = ctx->macroW;
+    a3.macroW2 = ctx->macroW2;
+    a3.lam = ctx->lam1;
+    a3.mu = ctx->mu1;
+    a3.scale = nullptr;
+    a3.dJdE = dJ_dE;
+    TRY(run(ctx, "axis3_adjoint_f64", 0.0, [&] { return launch_ax3<double>(OP_ADJ, a3, ctx->stream); }));
+    // restore the forward state
+    CK(cudaMemcpyAsync(ctx->x64, ctx->xfwd, nU * sizeof(cplx<double>), cudaMemcpyDeviceToDevice, ctx->stream));
+    TRY(set_load(ctx, 0, ctx->target.data()));
+    std::vector<double> ru2, re2;
+    TRY(chain_residual(ctx, ctx->x64, ctx->xe64, ru2, re2));  // restores sig0 of the forward solution
+    if (rep) {
+        rep->cg_iters = r1.cg_iters + r2.cg_iters;
+        rep->cg_iters_max = std::max(r1.cg_iters_max, r2.cg_iters_max);
+        rep->outer_iters = r1.outer_iters + r2.outer_iters + 1;
+        rep->newton_iters = r1.newton_iters + r2.newton_iters;
+        rep->true_rel_res = std::max(r1.true_rel_res, r2.true_rel_res);
+        rep->eps_eq = std::max(r1.eps_eq, r2.eps_eq);
+        rep->wall_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    }
+    return s;
+}
+
+}  // extern "C"

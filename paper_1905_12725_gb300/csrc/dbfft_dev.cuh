@@ -1,0 +1,67 @@
+// dbfft_dev.cuh -- device-side data structures shared by the pass kernels and
+// the host driver.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "fft.cuh"
+
+namespace dbfft {
+
+enum { KIN_SMALL = 0, KIN_FINITE = 1 };
+
+// Per-solve CG scalars (one per right-hand side), always FP64.
+struct CgState {
+    double rho;      // <r, M r>
+    double alpha;    // rho / <p, K p>
+    double beta;
+    double bnorm2;   // ||b||^2 of this inner solve
+    double rnorm2;   // ||r||^2 after the last update
+    double pq;       // <p, K p>
+    double tol2;     // stop when rnorm2 <= tol2 * bnorm2
+    int iter;        // iterations done
+    int done;        // 1: converged (or stopped); kernels skip this RHS
+    int flags;       // bit 0: breakdown (non-positive curvature), bit 1: non-finite
+    int max_iter;
+};
+
+// Preconditioner constants of one material group (Sec. 2.5, Eqs. pred2-pred3):
+// Q(xi)_ik = sum_mono coef[ik][mono] mono(xi), with ik over (11,22,33,23,13,12)
+// and mono over (x1^2, x2^2, x3^2, x2 x3, x1 x3, x1 x2); z = N Q^-1 r.
+// Macro block: z_e = Me r_e with Me = (N Cbar_ee)^-1 on the active basis.
+struct PrecondData {
+    double coef[6][6];
+    double Me[9][9];
+};
+
+// Everything a pass needs about the grid and the macro basis.
+struct Dims {
+    int n1, n2, n3, h, m;   // h = n3/2 + 1, m = n3/2
+    long long H;            // n1 n2 h
+    long long V;            // n1 n2 n3
+    long long plane;        // n2 h (one k1 plane of the half spectrum)
+    int B;                  // right-hand sides
+    int Rm;                 // right-hand sides per material map
+    int nc;                 // 6 (small) or 9 (finite)
+    int kin;
+    int ne;                 // number of active macro unknowns
+    int active[9];          // active macro basis indices (Mandel or 3i+j)
+    double invN;
+};
+
+template <typename T>
+struct Freq {
+    const T* xi1;  // [n1]
+    const T* xi2;  // [n2]
+    const T* xi3;  // [h]
+};
+
+template <typename T>
+struct Twiddles {
+    const cplx<T>* t1;  // [n1]
+    const cplx<T>* t2;  // [n2]
+    const cplx<T>* t3;  // [n3]  exp(-2 pi i k / n3)
+    const cplx<T>* tm;  // [m]
+};
+
+}  // namespace dbfft

@@ -1,0 +1,225 @@
+// fft.cuh -- register-resident Stockham FFT building blocks for sm_103a.
+//
+// A length-N transform of one column is carried by P = N / R threads; each
+// thread holds R complex values in registers. Stage s (radix R, span
+// Ns = R^s) reads x[p + r P], twiddles by w_{Ns R}^{r (p mod Ns)}, does a
+// radix-R DFT in registers and writes y[(p / Ns) Ns R + p mod Ns + q Ns]
+// (the Stockham autosort schedule); consecutive stages exchange through
+// shared memory. When log2 N is not a multiple of log2 R, the last stage uses
+// a smaller radix and each thread does R / R_last of them. Before the first
+// and after the last stage a thread holds the elements p + r P, r < R, so
+// global loads and stores are strided the same way on both sides and a warp
+// that spans consecutive columns touches contiguous memory.
+//
+// Twiddles come from a table tw[k] = exp(-2 pi i k / N) computed on the host
+// in extended precision; radix-R butterflies use the constants cos/sin of
+// 2 pi m / 32 written out below.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace dbfft {
+
+template <typename T> struct cplx { T x, y; };
+template <typename T> struct vec2 {};
+template <> struct vec2<float> { typedef float2 type; };
+template <> struct vec2<double> { typedef double2 type; };
+
+template <typename T> __device__ __forceinline__ cplx<T> mk(T a, T b) { cplx<T> c; c.x = a; c.y = b; return c; }
+template <typename T> __device__ __forceinline__ cplx<T> operator+(cplx<T> a, cplx<T> b) { return mk(a.x + b.x, a.y + b.y); }
+template <typename T> __device__ __forceinline__ cplx<T> operator-(cplx<T> a, cplx<T> b) { return mk(a.x - b.x, a.y - b.y); }
+template <typename T> __device__ __forceinline__ cplx<T> operator*(cplx<T> a, cplx<T> b) {
+    return mk(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+template <typename T> __device__ __forceinline__ cplx<T> operator*(T s, cplx<T> a) { return mk(s * a.x, s * a.y); }
+template <typename T> __device__ __forceinline__ cplx<T> conjg(cplx<T> a) { return mk(a.x, -a.y); }
+// multiply by i * s (s real)
+template <typename T> __device__ __forceinline__ cplx<T> mul_i(T s, cplx<T> a) { return mk(-s * a.y, s * a.x); }
+// a * conj(w) when INV, else a * w  (w from the forward table)
+template <int DIR, typename T> __device__ __forceinline__ cplx<T> twmul(cplx<T> a, cplx<T> w) {
+    if (DIR > 0) w.y = -w.y;
+    return a * w;
+}
+
+template <typename T> __device__ __forceinline__ cplx<T> ldc(const cplx<T>* p) {
+    typename vec2<T>::type v = *reinterpret_cast<const typename vec2<T>::type*>(p);
+    return mk<T>(v.x, v.y);
+}
+template <typename T> __device__ __forceinline__ void stc(cplx<T>* p, cplx<T> a) {
+    typename vec2<T>::type v; v.x = a.x; v.y = a.y;
+    *reinterpret_cast<typename vec2<T>::type*>(p) = v;
+}
+template <typename T> __device__ __forceinline__ cplx<T> ldg_c(const cplx<T>* p) {
+    typename vec2<T>::type v = __ldg(reinterpret_cast<const typename vec2<T>::type*>(p));
+    return mk<T>(v.x, v.y);
+}
+
+// cos(2 pi m / 32) for m = 0..8 (first octant), mathematical constants.
+__device__ __forceinline__ constexpr double c32(int m) {
+    return m == 0 ? 1.0
+         : m == 1 ? 0.98078528040323044912618223613424
+         : m == 2 ? 0.92387953251128675612818318939679
+         : m == 3 ? 0.83146961230254523707878837761791
+         : m == 4 ? 0.70710678118654752440084436210485
+         : m == 5 ? 0.55557023301960222474283081394853
+         : m == 6 ? 0.38268343236508977172845998403040
+         : m == 7 ? 0.19509032201612826784828486847702
+         : 0.0;
+}
+// cos and sin of 2 pi m / 32 for any m in [0, 32)
+__device__ __forceinline__ constexpr double cos32(int m) {
+    return m <= 8 ? c32(m) : m <= 16 ? -c32(16 - m) : m <= 24 ? -c32(m - 16) : c32(32 - m);
+}
+__device__ __forceinline__ constexpr double sin32(int m) { return cos32((m + 24) & 31); }
+
+// Multiply by exp(DIR * 2 pi i k / L) with k, L compile-time.
+template <int DIR, int L, int K, typename T>
+__device__ __forceinline__ cplx<T> rot(cplx<T> a) {
+    constexpr int k = ((K % L) + L) % L;
+    if constexpr (k == 0) {
+        return a;
+    } else if constexpr (4 * k == L) {  // * (DIR i)
+        return DIR > 0 ? mk(-a.y, a.x) : mk(a.y, -a.x);
+    } else if constexpr (2 * k == L) {
+        return mk(-a.x, -a.y);
+    } else if constexpr (4 * k == 3 * L) {
+        return DIR > 0 ? mk(a.y, -a.x) : mk(-a.y, a.x);
+    } else {
+        constexpr int m = k * (32 / L);
+        const T c = (T)cos32(m);
+        const T s = (T)(DIR * sin32(m));
+        return mk(a.x * c - a.y * s, a.x * s + a.y * c);
+    }
+}
+
+template <int N> struct ilog2 { static constexpr int value = 1 + ilog2<N / 2>::value; };
+template <> struct ilog2<1> { static constexpr int value = 0; };
+
+template <int R> __host__ __device__ constexpr int bitrev(int i) {
+    int r = 0;
+    for (int b = 1, rb = R >> 1; b < R; b <<= 1, rb >>= 1)
+        if (i & b) r |= rb;
+    return r;
+}
+
+// In-register DFT of length R (2..32), natural order in and out, on the
+// elements v[OFF + STRIDE * r]. DIR = -1 forward, +1 inverse (unnormalised).
+template <int R, int DIR, int STRIDE, int OFF, typename T>
+struct RegDFT {
+    template <int LEN, int I, int K>
+    __device__ __forceinline__ static void bfly(cplx<T>* v) {
+        constexpr int a = OFF + STRIDE * (I + K), b = OFF + STRIDE * (I + K + LEN / 2);
+        cplx<T> t = rot<DIR, LEN, K>(v[b]);
+        cplx<T> u = v[a];
+        v[a] = u + t;
+        v[b] = u - t;
+    }
+    template <int LEN, int I, int K>
+    __device__ __forceinline__ static void inner(cplx<T>* v) {
+        if constexpr (K < LEN / 2) {
+            bfly<LEN, I, K>(v);
+            inner<LEN, I, K + 1>(v);
+        }
+    }
+    template <int LEN, int I>
+    __device__ __forceinline__ static void groups(cplx<T>* v) {
+        if constexpr (I < R) {
+            inner<LEN, I, 0>(v);
+            groups<LEN, I + LEN>(v);
+        }
+    }
+    template <int LEN>
+    __device__ __forceinline__ static void stages(cplx<T>* v) {
+        if constexpr (LEN <= R) {
+            groups<LEN, 0>(v);
+            stages<LEN * 2>(v);
+        }
+    }
+    template <int I>
+    __device__ __forceinline__ static void perm(cplx<T>* v) {
+        if constexpr (I < R) {
+            constexpr int j = bitrev<R>(I);
+            if constexpr (j > I) {
+                cplx<T> t = v[OFF + STRIDE * I];
+                v[OFF + STRIDE * I] = v[OFF + STRIDE * j];
+                v[OFF + STRIDE * j] = t;
+            }
+            perm<I + 1>(v);
+        }
+    }
+    __device__ __forceinline__ static void run(cplx<T>* v) {
+        perm<0>(v);
+        stages<2>(v);
+    }
+};
+
+// Column FFT of length N with P = N / R threads per column.
+//  v:   the thread's R registers, holding x[p + r P] on entry and X[p + r P]
+//       on exit.
+//  sm:  shared exchange buffer for this column: element i lives at
+//       sm[i * SS] (SS = stride between positions); it must hold N entries
+//       and is only touched when there is more than one stage.
+//  tw:  twiddle table of length N (forward sign).
+// Every thread of the block must call this (it contains __syncthreads()),
+// including threads whose column is out of range.
+template <typename T, int N, int R, int DIR>
+struct ColFFT {
+    static_assert(N >= R, "radix larger than the transform");
+    static constexpr int P = N / R;
+    static constexpr int LOGN = ilog2<N>::value;
+    static constexpr int LOGR = ilog2<R>::value;
+    static constexpr int NST = (LOGN + LOGR - 1) / LOGR;
+    static constexpr int LASTR = 1 << (LOGN - (NST - 1) * LOGR);
+
+    template <int S, int NS>
+    __device__ __forceinline__ static void stage(cplx<T>* v, cplx<T>* sm, int SS, int p, const cplx<T>* tw) {
+        if constexpr (S < NST) {
+            if constexpr (S == NST - 1 && LASTR != R) {
+                // smaller last radix: sub-transform t uses v[t + rp (R/LASTR)]
+                constexpr int G = R / LASTR;
+#pragma unroll
+                for (int t = 0; t < G; ++t) {
+                    const int jp = p + t * P;
+#pragma unroll
+                    for (int rp = 1; rp < LASTR; ++rp)
+                        v[t + rp * G] = twmul<DIR>(v[t + rp * G], ldg_c(tw + (rp * jp) % N));
+                }
+                sub_dft<0, G>(v);
+            } else {
+                if constexpr (S > 0) {
+                    const int k = p % NS;
+#pragma unroll
+                    for (int r = 1; r < R; ++r)
+                        v[r] = twmul<DIR>(v[r], ldg_c(tw + r * k * (N / (NS * R))));
+                }
+                RegDFT<R, DIR, 1, 0, T>::run(v);
+                if constexpr (S < NST - 1) {
+                    const int base = (p / NS) * NS * R + (p % NS);
+                    __syncthreads();
+#pragma unroll
+                    for (int q = 0; q < R; ++q) sm[(base + q * NS) * SS] = v[q];
+                    __syncthreads();
+#pragma unroll
+                    for (int r = 0; r < R; ++r) v[r] = sm[(p + r * P) * SS];
+                }
+            }
+            stage<S + 1, NS * R>(v, sm, SS, p, tw);
+        }
+    }
+    template <int TI, int G>
+    __device__ __forceinline__ static void sub_dft(cplx<T>* v) {
+        if constexpr (TI < G) {
+            RegDFT<LASTR, DIR, G, TI, T>::run(v);
+            sub_dft<TI + 1, G>(v);
+        }
+    }
+    __device__ __forceinline__ static void run(cplx<T>* v, cplx<T>* sm, int SS, int p, const cplx<T>* tw) {
+        stage<0, 1>(v, sm, SS, p, tw);
+    }
+};
+
+// Radix used per transform length and precision.
+template <typename T, int N> struct RadixFor { static constexpr int value = N < 16 ? N : 16; };
+template <int N> struct RadixFor<double, N> { static constexpr int value = N < 8 ? N : 8; };
+
+}  // namespace dbfft

@@ -1,0 +1,5 @@
+// Pass 5 (axis 1, forward) in F64, 9 field components.
+#include "k_ax1_impl.cuh"
+namespace dbfft {
+template cudaError_t launch_ax1_fwd_nc<double, 9>(int, const Ax1FwdArgs<double>&, cudaStream_t);
+}

@@ -1,0 +1,16 @@
+// Pass 3 in FP64: tangent applications, constitutive updates and the adjoint assembly.
+#include "k_ax3_impl.cuh"
+namespace dbfft {
+template <>
+cudaError_t launch_ax3<double>(int opk, const Ax3Args<double>& a, cudaStream_t s) {
+    switch (opk) {
+        case OP_ISO: return ax3_sz<double, 6, OP_ISO>(a, s);
+        case OP_NH_APPLY: return ax3_sz<double, 9, OP_NH_APPLY>(a, s);
+        case OP_CP_APPLY: return ax3_sz<double, 6, OP_CP_APPLY>(a, s);
+        case OP_NH_UPDATE: return ax3_sz<double, 9, OP_NH_UPDATE>(a, s);
+        case OP_CP_UPDATE: return ax3_sz<double, 6, OP_CP_UPDATE>(a, s);
+        case OP_ADJ: return ax3_sz<double, 6, OP_ADJ>(a, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+}

@@ -1,0 +1,187 @@
+// k_misc.cu -- small kernels around the passes: macro fields, precision
+// conversion between the FP64 outer loop and the inner CG, the
+// preconditioner as a stand-alone operator, and the mean tangent.
+#include "launch.h"
+#include "misc.h"
+
+namespace dbfft {
+
+__global__ void k_macro(int B, int nc, const int* activeflag, const double* fU, const double* e, double* macroW) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= B * 9) return;
+    const int q = i % 9;
+    double v = fU ? fU[i] : 0.0;
+    if (e && activeflag[q]) v += ((nc == 6 && q >= 3) ? 0.70710678118654752440084436210485 : 1.0) * e[i];
+    macroW[i] = v;
+}
+
+cudaError_t launch_macro(int B, int nc, const int* activeflag, const double* fU, const double* e, double* macroW,
+                         cudaStream_t s) {
+    k_macro<<<(B * 9 + 127) / 128, 128, 0, s>>>(B, nc, activeflag, fU, e, macroW);
+    return cudaGetLastError();
+}
+
+template <typename Ti>
+__global__ void k_to_inner(long long n3H, int B, const cplx<double>* r64, const double* re64, const double* sc,
+                           cplx<Ti>* ri, double* re_i, cplx<Ti>* xi, double* xe_i) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int b = blockIdx.y;
+    const double s = sc[b];
+    if (i < n3H) {
+        const cplx<double> v = r64[(long long)b * n3H + i];
+        cplx<Ti> o;
+        o.x = (Ti)(v.x * s);
+        o.y = (Ti)(v.y * s);
+        ri[(long long)b * n3H + i] = o;
+        cplx<Ti> z;
+        z.x = Ti(0);
+        z.y = Ti(0);
+        xi[(long long)b * n3H + i] = z;
+    }
+    if (blockIdx.x == 0 && threadIdx.x < 9) {
+        re_i[b * 9 + threadIdx.x] = re64[b * 9 + threadIdx.x] * s;
+        xe_i[b * 9 + threadIdx.x] = 0.0;
+    }
+}
+
+template <typename Ti>
+__global__ void k_from_inner(long long n3H, int B, const cplx<Ti>* xi, const double* xe_i, const double* sb,
+                             cplx<double>* x64, double* xe64) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int b = blockIdx.y;
+    const double s = sb[b];
+    if (i < n3H) {
+        cplx<double> v = x64[(long long)b * n3H + i];
+        const cplx<Ti> d = xi[(long long)b * n3H + i];
+        v.x += s * (double)d.x;
+        v.y += s * (double)d.y;
+        x64[(long long)b * n3H + i] = v;
+    }
+    if (blockIdx.x == 0 && threadIdx.x < 9) xe64[b * 9 + threadIdx.x] += s * xe_i[b * 9 + threadIdx.x];
+}
+
+template <typename Ti>
+cudaError_t launch_to_inner(const Dims& d, const cplx<double>* r64, const double* re64, const double* sc, cplx<Ti>* ri,
+                            double* re_i, cplx<Ti>* xi, double* xe_i, cudaStream_t s) {
+    const long long n = 3 * d.H;
+    k_to_inner<Ti><<<dim3((unsigned)((n + 255) / 256), d.B), 256, 0, s>>>(n, d.B, r64, re64, sc, ri, re_i, xi, xe_i);
+    return cudaGetLastError();
+}
+template <typename Ti>
+cudaError_t launch_from_inner(const Dims& d, const cplx<Ti>* xi, const double* xe_i, const double* sb,
+                              cplx<double>* x64, double* xe64, cudaStream_t s) {
+    const long long n = 3 * d.H;
+    k_from_inner<Ti><<<dim3((unsigned)((n + 255) / 256), d.B), 256, 0, s>>>(n, d.B, xi, xe_i, sb, x64, xe64);
+    return cudaGetLastError();
+}
+template cudaError_t launch_to_inner<float>(const Dims&, const cplx<double>*, const double*, const double*,
+                                            cplx<float>*, double*, cplx<float>*, double*, cudaStream_t);
+template cudaError_t launch_to_inner<double>(const Dims&, const cplx<double>*, const double*, const double*,
+                                             cplx<double>*, double*, cplx<double>*, double*, cudaStream_t);
+template cudaError_t launch_from_inner<float>(const Dims&, const cplx<float>*, const double*, const double*,
+                                              cplx<double>*, double*, cudaStream_t);
+template cudaError_t launch_from_inner<double>(const Dims&, const cplx<double>*, const double*, const double*,
+                                               cplx<double>*, double*, cudaStream_t);
+
+// out = M u: N Q(xi)^-1 u per frequency (zero on the null set), macro block Me e.
+template <typename T>
+__global__ void k_precond_field(Dims d, Freq<T> f, const PrecondData* pre, const cplx<T>* u, cplx<T>* out,
+                                const double* e_in, double* e_out) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int b = blockIdx.y;
+    const PrecondData& pd = pre[b / d.Rm];
+    if (i < d.H) {
+        const long long k1 = i / d.plane;
+        const long long rem = i - k1 * d.plane;
+        const int k2 = (int)(rem / d.h), k3 = (int)(rem - (long long)k2 * d.h);
+        cplx<T> r[3], z[3];
+        for (int c = 0; c < 3; ++c) r[c] = u[(long long)(b * 3 + c) * d.H + i];
+        precond_apply<T>(pd.coef, f.xi1[k1], f.xi2[k2], f.xi3[k3], (T)(1.0 / d.invN), r, z);
+        for (int c = 0; c < 3; ++c) out[(long long)(b * 3 + c) * d.H + i] = z[c];
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0 && e_out) {
+        for (int q = 0; q < 9; ++q) e_out[b * 9 + q] = 0.0;
+        for (int k = 0; k < d.ne; ++k) {
+            double acc = 0.0;
+            for (int l = 0; l < d.ne; ++l) acc += pd.Me[k][l] * (e_in ? e_in[b * 9 + d.active[l]] : 0.0);
+            e_out[b * 9 + d.active[k]] = acc;
+        }
+    }
+}
+
+template <typename T>
+cudaError_t launch_precond_field(const Dims& d, const Freq<T>& f, const PrecondData* pre, const cplx<T>* u,
+                                 cplx<T>* out, const double* e_in, double* e_out, cudaStream_t s) {
+    k_precond_field<T><<<dim3((unsigned)((d.H + 255) / 256), d.B), 256, 0, s>>>(d, f, pre, u, out, e_in, e_out);
+    return cudaGetLastError();
+}
+template cudaError_t launch_precond_field<float>(const Dims&, const Freq<float>&, const PrecondData*,
+                                                 const cplx<float>*, cplx<float>*, const double*, double*,
+                                                 cudaStream_t);
+template cudaError_t launch_precond_field<double>(const Dims&, const Freq<double>&, const PrecondData*,
+                                                  const cplx<double>*, cplx<double>*, const double*, double*,
+                                                  cudaStream_t);
+
+// Mean of the fourth-order tangent K_ijkl over the voxels of one right-hand
+// side (81 components), from the stored tangent data:
+//   kind 0: Neo-Hookean data (F^-T, mu - lam ln J) with per-phase mu, lam;
+//   kind 1: 21-entry Mandel tangent.
+template <typename TT>
+__global__ void k_mean_tangent(int kind, long long V, const TT* tan, const uint16_t* phase, const double* lam,
+                               const double* mu, double* partials /* [B][gridDim.x][81] */) {
+    __shared__ double acc[81];
+    const int b = blockIdx.y;
+    for (int q = threadIdx.x; q < 81; q += blockDim.x) acc[q] = 0.0;
+    __syncthreads();
+    double loc[81];
+    for (int q = 0; q < 81; ++q) loc[q] = 0.0;
+    for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < V; v += (long long)gridDim.x * blockDim.x) {
+        if (kind == 0) {
+            const TT* t = tan + ((long long)b * V + v) * 10;
+            const int ph = phase[(long long)b * V + v];
+            double A[9];
+            for (int q = 0; q < 9; ++q) A[q] = (double)t[q];
+            const double c1 = (double)t[9];
+            // K_iJkL = mu d_ik d_JL + c1 A_iL A_kJ + lam A_iJ A_kL
+            for (int i = 0; i < 3; ++i)
+                for (int J = 0; J < 3; ++J)
+                    for (int k = 0; k < 3; ++k)
+                        for (int L = 0; L < 3; ++L) {
+                            double val = c1 * A[3 * i + L] * A[3 * k + J] + lam[ph] * A[3 * i + J] * A[3 * k + L];
+                            if (i == k && J == L) val += mu[ph];
+                            loc[((i * 3 + J) * 3 + k) * 3 + L] += val;
+                        }
+        } else {
+            const TT* t = tan + ((long long)b * V + v) * 21;
+            // Mandel -> tensor: K_ijkl = sum_mn Psi_m,ij Cm_mn Psi_n,kl
+            const int pi[6] = {0, 1, 2, 1, 0, 0}, pj[6] = {0, 1, 2, 2, 2, 1};
+            for (int m = 0; m < 6; ++m)
+                for (int n = 0; n < 6; ++n) {
+                    const double c = (double)t[sym6(m, n)] * (m >= 3 ? 0.70710678118654752440 : 1.0) *
+                                     (n >= 3 ? 0.70710678118654752440 : 1.0);
+                    const int ii[2] = {pi[m], pj[m]}, jj[2] = {pj[m], pi[m]};
+                    const int kk[2] = {pi[n], pj[n]}, ll[2] = {pj[n], pi[n]};
+                    for (int s1 = 0; s1 < (m >= 3 ? 2 : 1); ++s1)
+                        for (int s2 = 0; s2 < (n >= 3 ? 2 : 1); ++s2)
+                            loc[((ii[s1] * 3 + jj[s1]) * 3 + kk[s2]) * 3 + ll[s2]] += c;
+                }
+        }
+    }
+    for (int q = 0; q < 81; ++q) atomicAdd(&acc[q], loc[q]);
+    __syncthreads();
+    for (int q = threadIdx.x; q < 81; q += blockDim.x)
+        partials[((long long)b * gridDim.x + blockIdx.x) * 81 + q] = acc[q];
+}
+
+template <typename TT>
+cudaError_t launch_mean_tangent(int kind, int B, long long V, const TT* tan, const uint16_t* phase, const double* lam,
+                                const double* mu, double* partials, int nblk, cudaStream_t s) {
+    k_mean_tangent<TT><<<dim3(nblk, B), 128, 0, s>>>(kind, V, tan, phase, lam, mu, partials);
+    return cudaGetLastError();
+}
+template cudaError_t launch_mean_tangent<float>(int, int, long long, const float*, const uint16_t*, const double*,
+                                                const double*, double*, int, cudaStream_t);
+template cudaError_t launch_mean_tangent<double>(int, int, long long, const double*, const uint16_t*,
+                                                 const double*, const double*, double*, int, cudaStream_t);
+
+}  // namespace dbfft

@@ -1,0 +1,22 @@
+// launch.h -- host-side launchers of the pass kernels. Each translation unit
+// instantiates the kernels of one pass and precision for the compiled
+// transform lengths and dispatches on the runtime sizes.
+#pragma once
+#include "pass3.cuh"
+
+namespace dbfft {
+
+// Launch geometry shared by the launchers and the buffer sizing.
+int ax1_tile(int n1, bool dbl);                      // columns per CTA of passes 1 and 5
+int ax2_tile(int n2, bool dbl);                      // columns per CTA of passes 2 and 4
+int ax3_lines(int n3, int nc, int rb, bool dbl);     // grid lines per CTA of pass 3
+int ax3_threads_per_line(int n3, int nc, int rb, bool dbl);
+size_t ax3_smem(int n3, int nc, int rb, int lines, bool dbl, bool two_fields);
+bool supported_len(int n);
+
+template <typename T> cudaError_t launch_ax1_inv(int mode, const Ax1InvArgs<T>& a, cudaStream_t s);
+template <typename T> cudaError_t launch_ax1_fwd(int mode, const Ax1FwdArgs<T>& a, cudaStream_t s);
+template <typename T> cudaError_t launch_ax2(int dir, const Ax2Args<T>& a, cudaStream_t s);
+template <typename T> cudaError_t launch_ax3(int opk, const Ax3Args<T>& a, cudaStream_t s);
+
+}  // namespace dbfft

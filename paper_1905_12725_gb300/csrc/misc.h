@@ -1,0 +1,20 @@
+// misc.h -- launchers of the small kernels in k_misc.cu.
+#pragma once
+#include "launch.h"
+
+namespace dbfft {
+cudaError_t launch_macro(int B, int nc, const int* activeflag, const double* fU, const double* e, double* macroW,
+                         cudaStream_t s);
+template <typename Ti>
+cudaError_t launch_to_inner(const Dims& d, const cplx<double>* r64, const double* re64, const double* sc, cplx<Ti>* ri,
+                            double* re_i, cplx<Ti>* xi, double* xe_i, cudaStream_t s);
+template <typename Ti>
+cudaError_t launch_from_inner(const Dims& d, const cplx<Ti>* xi, const double* xe_i, const double* sb,
+                              cplx<double>* x64, double* xe64, cudaStream_t s);
+template <typename T>
+cudaError_t launch_precond_field(const Dims& d, const Freq<T>& f, const PrecondData* pre, const cplx<T>* u,
+                                 cplx<T>* out, const double* e_in, double* e_out, cudaStream_t s);
+template <typename TT>
+cudaError_t launch_mean_tangent(int kind, int B, long long V, const TT* tan, const uint16_t* phase, const double* lam,
+                                const double* mu, double* partials, int nblk, cudaStream_t s);
+}  // namespace dbfft

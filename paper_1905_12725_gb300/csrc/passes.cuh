@@ -1,0 +1,609 @@
+// passes.cuh -- the five passes of one DBFFT operator application and the
+// small kernels of the preconditioned CG around them.
+//
+// Layout of the work buffer W: [B][nc][n1][n2][h] interleaved complex with
+// h = n3/2 + 1 (nc = 6 strain components 11,22,33,23,13,12 at small strain,
+// nc = 9 components 3i+j of the displacement gradient at finite strain).
+//
+//   pass 1  axis 1, inverse : u (3 comps) -> s.u or g.u (nc comps), C2C   [k_axis1_inv]
+//   pass 2  axis 2, inverse : C2C                                         [k_axis2]
+//   pass 3  axis 3          : C2R, per-voxel tangent / constitutive, R2C  [k_axis3]
+//   pass 4  axis 2, forward : C2C                                         [k_axis2]
+//   pass 5  axis 1, forward : C2C, divergence d:sigma, null mask, CG      [k_axis1_fwd]
+//
+// Inside CG, pass 1 also forms the new search direction p = M r + beta p
+// (the preconditioner of Sec. 2.5 evaluated on the fly from the frequency),
+// pass 3 accumulates the curvature <p, K p> = sum_x eps : C : eps and its last
+// block sets alpha, and pass 5 applies x += alpha p, r -= alpha q, evaluates
+// <r, M r> and ||r||^2 and its last block sets beta and the stop flag. The
+// product q = K p never reaches memory.
+#pragma once
+#include "dbfft_dev.cuh"
+
+namespace dbfft {
+
+// ------------------------------------------------------------------ helpers
+template <typename T>
+__device__ __forceinline__ cplx<T> zero_c() { return mk<T>(T(0), T(0)); }
+
+// Stored weight of a half-spectrum entry in the full-spectrum inner product.
+__device__ __forceinline__ int hweight(int k3, int m) { return (k3 == 0 || k3 == m) ? 1 : 2; }
+
+// z = N Q(xi)^-1 r (zero on the null set), Q from the mean tangent.
+template <typename T>
+__device__ __forceinline__ void precond_apply(const double (*coef)[6], T x1, T x2, T x3, T N,
+                                              const cplx<T>* r, cplx<T>* z) {
+    const T k2 = x1 * x1 + x2 * x2 + x3 * x3;
+    if (k2 == T(0)) {
+        z[0] = z[1] = z[2] = zero_c<T>();
+        return;
+    }
+    const T ik2 = T(1) / k2;
+    const T mono[6] = {x1 * x1 * ik2, x2 * x2 * ik2, x3 * x3 * ik2,
+                       x2 * x3 * ik2, x1 * x3 * ik2, x1 * x2 * ik2};
+    T q[6];
+#pragma unroll
+    for (int a = 0; a < 6; ++a) {
+        T s = T(0);
+#pragma unroll
+        for (int b = 0; b < 6; ++b) s += (T)coef[a][b] * mono[b];
+        q[a] = s;
+    }
+    // Q = [[q0 q5 q4] [q5 q1 q3] [q4 q3 q2]], inverse by cofactors
+    const T A00 = q[1] * q[2] - q[3] * q[3];
+    const T A11 = q[0] * q[2] - q[4] * q[4];
+    const T A22 = q[0] * q[1] - q[5] * q[5];
+    const T A01 = q[4] * q[3] - q[5] * q[2];
+    const T A02 = q[5] * q[3] - q[4] * q[1];
+    const T A12 = q[5] * q[4] - q[0] * q[3];
+    const T det = q[0] * A00 + q[5] * A01 + q[4] * A02;
+    const T s = N * ik2 / det;
+    z[0] = s * (A00 * r[0] + (A01 * r[1] + A02 * r[2]));
+    z[1] = s * (A01 * r[0] + (A11 * r[1] + A12 * r[2]));
+    z[2] = s * (A02 * r[0] + (A12 * r[1] + A22 * r[2]));
+}
+
+// scalar * complex helpers for the real-scalar product
+template <typename T>
+__device__ __forceinline__ cplx<T> operator*(cplx<T> a, T s) { return mk(a.x * s, a.y * s); }
+
+// Block-wide sum of NV doubles; result valid in thread 0.
+template <int NV>
+__device__ __forceinline__ void block_sum(double* v, double* scratch /* >= 32*NV */) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
+    }
+    const int lane = threadIdx.x % 32 + 0, warp = (threadIdx.x + threadIdx.y * blockDim.x) / 32;
+    const int tid = threadIdx.x + threadIdx.y * blockDim.x;
+    const int nwarps = (blockDim.x * blockDim.y + 31) / 32;
+    __syncthreads();
+    if ((tid & 31) == 0) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) scratch[warp * NV + k] = v[k];
+    }
+    __syncthreads();
+    if (tid == 0) {
+        for (int k = 0; k < NV; ++k) {
+            double s = 0.0;
+            for (int w = 0; w < nwarps; ++w) s += scratch[w * NV + k];
+            v[k] = s;
+        }
+    }
+    (void)lane;
+}
+
+// Symmetric-gradient / gradient component m of u at xi, times (i * invN).
+template <typename T, int NC, int M>
+__device__ __forceinline__ cplx<T> grad_comp(const cplx<T>* u, T x1, T x2, T x3, T s) {
+    if constexpr (NC == 6) {
+        const T h = T(0.5) * s;
+        if constexpr (M == 0) return mul_i(s * x1, u[0]);
+        if constexpr (M == 1) return mul_i(s * x2, u[1]);
+        if constexpr (M == 2) return mul_i(s * x3, u[2]);
+        if constexpr (M == 3) return mul_i(h, x3 * u[1] + x2 * u[2]);
+        if constexpr (M == 4) return mul_i(h, x3 * u[0] + x1 * u[2]);
+        if constexpr (M == 5) return mul_i(h, x2 * u[0] + x1 * u[1]);
+    } else {
+        constexpr int i = M / 3, j = M % 3;
+        const T xj = j == 0 ? x1 : (j == 1 ? x2 : x3);
+        return mul_i(s * xj, u[i]);
+    }
+    return zero_c<T>();
+}
+
+// Accumulate the divergence contribution of stress component m:
+// acc_i += xi_j sigma_ij (the factor -i/N is applied at the end).
+template <typename T, int NC, int M>
+__device__ __forceinline__ void div_acc(cplx<T>* acc, cplx<T> s, T x1, T x2, T x3) {
+    if constexpr (NC == 6) {
+        if constexpr (M == 0) acc[0] = acc[0] + x1 * s;
+        if constexpr (M == 1) acc[1] = acc[1] + x2 * s;
+        if constexpr (M == 2) acc[2] = acc[2] + x3 * s;
+        if constexpr (M == 3) { acc[1] = acc[1] + x3 * s; acc[2] = acc[2] + x2 * s; }
+        if constexpr (M == 4) { acc[0] = acc[0] + x3 * s; acc[2] = acc[2] + x1 * s; }
+        if constexpr (M == 5) { acc[0] = acc[0] + x2 * s; acc[1] = acc[1] + x1 * s; }
+    } else {
+        constexpr int i = M / 3, j = M % 3;
+        const T xj = j == 0 ? x1 : (j == 1 ? x2 : x3);
+        acc[i] = acc[i] + xj * s;
+    }
+}
+
+// Macro basis: W-component value of unit macro coefficient m, and the
+// coefficient of a stress tensor on basis m (E^T sigma).
+template <int NC>
+__host__ __device__ __forceinline__ double macro_to_w(int m) {
+    return (NC == 6 && m >= 3) ? 0.70710678118654752440084436210485 : 1.0;
+}
+template <int NC>
+__host__ __device__ __forceinline__ double w_to_macro(int m) {
+    return (NC == 6 && m >= 3) ? 1.41421356237309504880168872420970 : 1.0;
+}
+
+// ------------------------------------------------------------------ pass 1
+enum { AX1_PLAIN = 0, AX1_CG = 1 };
+
+template <typename T>
+struct Ax1InvArgs {
+    Dims d;
+    Freq<T> f;
+    Twiddles<T> tw;
+    const cplx<T>* in;   // PLAIN: u [B][3][H]; CG: r [B][3][H]
+    cplx<T>* p;          // CG: search direction [B][3][H], updated in place
+    cplx<T>* W;          // [B][nc][H]
+    const CgState* cg;   // CG (beta, done)
+    const PrecondData* pre;  // [B / Rm] per material group
+};
+
+template <typename T, int N1, int NC, int MODE>
+__global__ void __launch_bounds__(256) k_axis1_inv(Ax1InvArgs<T> a) {
+    constexpr int R = RadixFor<T, N1>::value;
+    constexpr int P = N1 / R;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    cplx<T>* sm = reinterpret_cast<cplx<T>*>(smraw);
+    const int TW = blockDim.x;
+    const int w = threadIdx.x, p = threadIdx.y;
+    const int b = blockIdx.y;
+    if (MODE == AX1_CG && a.cg[b].done) return;
+    const Dims& d = a.d;
+    const long long j = (long long)blockIdx.x * TW + w;
+    const bool valid = j < d.plane;
+    const int k2 = valid ? (int)(j / d.h) : 0;
+    const int k3 = valid ? (int)(j - (long long)k2 * d.h) : 0;
+    const T x2 = a.f.xi2[k2], x3 = a.f.xi3[k3];
+
+    cplx<T> u[3][R];
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const long long idx = ((long long)(b * 3 + c) * N1 + (p + r * P)) * d.plane + j;
+            u[c][r] = valid ? ldc(a.in + idx) : zero_c<T>();
+        }
+    if constexpr (MODE == AX1_CG) {
+        const T beta = (T)a.cg[b].beta;
+        const PrecondData& pd = a.pre[b / d.Rm];
+        const T N = (T)(1.0 / d.invN);
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int k1 = p + r * P;
+            cplx<T> rr[3] = {u[0][r], u[1][r], u[2][r]};
+            cplx<T> z[3];
+            precond_apply<T>(pd.coef, a.f.xi1[k1], x2, x3, N, rr, z);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const long long idx = ((long long)(b * 3 + c) * N1 + k1) * d.plane + j;
+                cplx<T> po = valid ? ldc(a.p + idx) : zero_c<T>();
+                cplx<T> pn = z[c] + po * beta;
+                if (valid) stc(a.p + idx, pn);
+                u[c][r] = pn;
+            }
+        }
+    }
+    const T s = (T)d.invN;
+    T x1r[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) x1r[r] = a.f.xi1[p + r * P];
+
+    auto emit = [&](auto mc) {
+        constexpr int M = decltype(mc)::value;
+        cplx<T> v[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            cplx<T> uu[3] = {u[0][r], u[1][r], u[2][r]};
+            v[r] = grad_comp<T, NC, M>(uu, x1r[r], x2, x3, s);
+        }
+        ColFFT<T, N1, R, +1>::run(v, sm + w, TW, p, a.tw.t1);
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const long long idx = ((long long)(b * NC + M) * N1 + (p + r * P)) * d.plane + j;
+            if (valid) stc(a.W + idx, v[r]);
+        }
+    };
+    emit(std::integral_constant<int, 0>());
+    emit(std::integral_constant<int, 1>());
+    emit(std::integral_constant<int, 2>());
+    emit(std::integral_constant<int, 3>());
+    emit(std::integral_constant<int, 4>());
+    emit(std::integral_constant<int, 5>());
+    if constexpr (NC == 9) {
+        emit(std::integral_constant<int, 6>());
+        emit(std::integral_constant<int, 7>());
+        emit(std::integral_constant<int, 8>());
+    }
+}
+
+// ------------------------------------------------------------------ pass 2/4
+template <typename T>
+struct Ax2Args {
+    Dims d;
+    Twiddles<T> tw;
+    cplx<T>* W;
+    const CgState* cg;  // may be null
+};
+
+template <typename T, int N2, int DIR>
+__global__ void __launch_bounds__(256) k_axis2(Ax2Args<T> a) {
+    constexpr int R = RadixFor<T, N2>::value;
+    constexpr int P = N2 / R;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    cplx<T>* sm = reinterpret_cast<cplx<T>*>(smraw);
+    const Dims& d = a.d;
+    const int TW = blockDim.x;
+    const int w = threadIdx.x, p = threadIdx.y;
+    const long long ncols = (long long)d.B * d.nc * d.n1 * d.h;
+    const long long c0 = (long long)blockIdx.x * TW;
+    if (a.cg) {  // skip tiles whose right-hand sides are all finished
+        const long long per_b = (long long)d.nc * d.n1 * d.h;
+        const int bfirst = (int)(c0 / per_b);
+        const long long clast = min(c0 + TW, ncols) - 1;
+        const int blast = (int)(clast / per_b);
+        bool all_done = true;
+        for (int bb = bfirst; bb <= blast; ++bb) all_done &= (a.cg[bb].done != 0);
+        if (all_done) return;
+    }
+    const long long col = c0 + w;
+    const bool valid = col < ncols;
+    const long long outer = valid ? col / d.h : 0;
+    const long long k3 = valid ? col - outer * d.h : 0;
+    const long long base = outer * (long long)N2 * d.h + k3;
+    cplx<T> v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = valid ? ldc(a.W + base + (long long)(p + r * P) * d.h) : zero_c<T>();
+    ColFFT<T, N2, R, DIR>::run(v, sm + w, TW, p, a.tw.t2);
+    if (valid) {
+#pragma unroll
+        for (int r = 0; r < R; ++r) stc(a.W + base + (long long)(p + r * P) * d.h, v[r]);
+    }
+}
+
+// ------------------------------------------------------------------ pass 5
+enum { AX5_PLAIN = 0, AX5_CG = 1, AX5_RESID = 2 };
+
+template <typename T>
+struct Ax1FwdArgs {
+    Dims d;
+    Freq<T> f;
+    Twiddles<T> tw;
+    const cplx<T>* W;
+    cplx<T>* out;        // PLAIN: K u; RESID: residual r (= -K-part); CG: unused
+    cplx<T>* x;          // CG
+    cplx<T>* p;          // CG
+    cplx<T>* r;          // CG
+    double* e_out;       // PLAIN: [B][9] E^T sigma-hat(0) part of K u (may be null)
+    double* sig0;        // RESID: [B][9] sigma-hat(0) / N (mean stress), W components
+    const double* sig_f; // RESID: [B][9] stress targets on the macro basis
+    double* r_e;         // RESID/CG: macro residual [B][9]
+    double* x_e;         // CG: [B][9]
+    double* p_e;         // CG: [B][9]
+    double* macroW;      // CG: [B][9] (output: E p_e for the next pass 3)
+    CgState* cg;
+    const PrecondData* pre;
+    double* partials;    // [B][nblk][2]
+    unsigned* counters;  // [B]
+};
+
+template <typename T, int N1, int NC, int MODE>
+__global__ void __launch_bounds__(256) k_axis1_fwd(Ax1FwdArgs<T> a) {
+    constexpr int R = RadixFor<T, N1>::value;
+    constexpr int P = N1 / R;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    cplx<T>* sm = reinterpret_cast<cplx<T>*>(smraw);
+    __shared__ double red[32 * 2];
+    __shared__ double s0[9][2];
+    __shared__ bool is_last;
+    const int TW = blockDim.x;
+    const int w = threadIdx.x, p = threadIdx.y;
+    const int tid = w + p * TW;
+    const int b = blockIdx.y;
+    const Dims& d = a.d;
+    if (MODE == AX5_CG && a.cg[b].done) return;
+    const long long j = (long long)blockIdx.x * TW + w;
+    const bool valid = j < d.plane;
+    const int k2 = valid ? (int)(j / d.h) : 0;
+    const int k3 = valid ? (int)(j - (long long)k2 * d.h) : 0;
+    const T x2 = a.f.xi2[k2], x3 = a.f.xi3[k3];
+    T x1r[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) x1r[r] = a.f.xi1[p + r * P];
+    const bool has0 = valid && j == 0 && p == 0;  // holds k = (0,0,0) in register 0
+
+    cplx<T> acc[3][R];
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+        for (int r = 0; r < R; ++r) acc[c][r] = zero_c<T>();
+
+    auto take = [&](auto mc) {
+        constexpr int M = decltype(mc)::value;
+        cplx<T> v[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const long long idx = ((long long)(b * NC + M) * N1 + (p + r * P)) * d.plane + j;
+            v[r] = valid ? ldc(a.W + idx) : zero_c<T>();
+        }
+        ColFFT<T, N1, R, -1>::run(v, sm + w, TW, p, a.tw.t1);
+        if (has0) { s0[M][0] = (double)v[0].x; s0[M][1] = (double)v[0].y; }
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            cplx<T> ac[3] = {acc[0][r], acc[1][r], acc[2][r]};
+            div_acc<T, NC, M>(ac, v[r], x1r[r], x2, x3);
+            acc[0][r] = ac[0]; acc[1][r] = ac[1]; acc[2][r] = ac[2];
+        }
+    };
+    take(std::integral_constant<int, 0>());
+    take(std::integral_constant<int, 1>());
+    take(std::integral_constant<int, 2>());
+    take(std::integral_constant<int, 3>());
+    take(std::integral_constant<int, 4>());
+    take(std::integral_constant<int, 5>());
+    if constexpr (NC == 9) {
+        take(std::integral_constant<int, 6>());
+        take(std::integral_constant<int, 7>());
+        take(std::integral_constant<int, 8>());
+    }
+    // q = B^H sigma = -(i / N) xi_j sigma_ij, zero on the null set
+    const T ms = -(T)d.invN;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const bool z = (x1r[r] == T(0)) && (x2 == T(0)) && (x3 == T(0));
+#pragma unroll
+        for (int c = 0; c < 3; ++c) acc[c][r] = z ? zero_c<T>() : mul_i(ms, acc[c][r]);
+    }
+    const int wgt = hweight(k3, d.m);
+
+    if constexpr (MODE == AX5_PLAIN) {
+        if (valid) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+#pragma unroll
+                for (int r = 0; r < R; ++r)
+                    stc(a.out + ((long long)(b * 3 + c) * N1 + (p + r * P)) * d.plane + j, acc[c][r]);
+        }
+        if (has0 && a.e_out) {
+            for (int q = 0; q < 9; ++q) a.e_out[b * 9 + q] = 0.0;
+            for (int k = 0; k < d.ne; ++k) {
+                const int m = d.active[k];
+                a.e_out[b * 9 + m] = w_to_macro<NC>(m) * s0[m][0];
+            }
+        }
+        return;
+    }
+    if constexpr (MODE == AX5_RESID) {
+        double v2[2] = {0.0, 0.0};  // ||r_u||^2 and ||r_e||^2
+        if (valid) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    cplx<T> v = mk(-acc[c][r].x, -acc[c][r].y);
+                    stc(a.out + ((long long)(b * 3 + c) * N1 + (p + r * P)) * d.plane + j, v);
+                    v2[0] += (double)wgt * ((double)v.x * v.x + (double)v.y * v.y);
+                }
+        }
+        if (has0) {
+            const double N = 1.0 / d.invN;
+            for (int q = 0; q < 9; ++q) a.sig0[b * 9 + q] = q < NC ? s0[q][0] * d.invN : 0.0;
+            for (int q = 0; q < 9; ++q) a.r_e[b * 9 + q] = 0.0;
+            for (int k = 0; k < d.ne; ++k) {
+                const int m = d.active[k];
+                const double re = N * a.sig_f[b * 9 + m] - w_to_macro<NC>(m) * s0[m][0];
+                a.r_e[b * 9 + m] = re;
+                v2[1] += re * re;
+            }
+        }
+        block_sum<2>(v2, red);
+        if (tid == 0) {
+            a.partials[((long long)b * gridDim.x + blockIdx.x) * 2 + 0] = v2[0];
+            a.partials[((long long)b * gridDim.x + blockIdx.x) * 2 + 1] = v2[1];
+        }
+        return;
+    }
+    if constexpr (MODE == AX5_CG) {
+        const T alpha = (T)a.cg[b].alpha;
+        const PrecondData& pd = a.pre[b / d.Rm];
+        const T N = (T)(1.0 / d.invN);
+        T rz = T(0), rr = T(0);
+        if (valid) {
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                cplx<T> rv[3], z[3];
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    const long long idx = ((long long)(b * 3 + c) * N1 + (p + r * P)) * d.plane + j;
+                    cplx<T> xv = ldc(a.x + idx), pv = ldc(a.p + idx), rvv = ldc(a.r + idx);
+                    xv = xv + pv * alpha;
+                    rvv = rvv - acc[c][r] * alpha;
+                    stc(a.x + idx, xv);
+                    stc(a.r + idx, rvv);
+                    rv[c] = rvv;
+                }
+                precond_apply<T>(pd.coef, x1r[r], x2, x3, N, rv, z);
+                T lrz = T(0), lrr = T(0);
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    lrz += rv[c].x * z[c].x + rv[c].y * z[c].y;
+                    lrr += rv[c].x * rv[c].x + rv[c].y * rv[c].y;
+                }
+                rz += lrz;
+                rr += lrr;
+            }
+        }
+        double v2[2] = {(double)wgt * (double)rz, (double)wgt * (double)rr};
+        if (has0) {  // macro part: q_e = E^T sigma-hat(0); x_e += alpha p_e; r_e -= alpha q_e
+            const double al = a.cg[b].alpha;
+            double re[9];
+            for (int k = 0; k < d.ne; ++k) {
+                const int m = d.active[k];
+                const double qe = w_to_macro<NC>(m) * s0[m][0];
+                a.x_e[b * 9 + m] += al * a.p_e[b * 9 + m];
+                re[k] = a.r_e[b * 9 + m] - al * qe;
+                a.r_e[b * 9 + m] = re[k];
+            }
+            const double(*Me)[9] = pd.Me;
+            for (int k = 0; k < d.ne; ++k) {
+                double ze = 0.0;
+                for (int l = 0; l < d.ne; ++l) ze += Me[k][l] * re[l];
+                v2[0] += re[k] * ze;
+                v2[1] += re[k] * re[k];
+            }
+        }
+        block_sum<2>(v2, red);
+        const int nblk = gridDim.x;
+        if (tid == 0) {
+            a.partials[((long long)b * nblk + blockIdx.x) * 2 + 0] = v2[0];
+            a.partials[((long long)b * nblk + blockIdx.x) * 2 + 1] = v2[1];
+            __threadfence();
+            const unsigned prev = atomicAdd(a.counters + b, 1u);
+            is_last = (prev == (unsigned)nblk - 1);
+        }
+        __syncthreads();
+        if (is_last && tid == 0) {
+            __threadfence();
+            double srz = 0.0, srr = 0.0;
+            for (int k = 0; k < nblk; ++k) {
+                srz += __ldcg(a.partials + ((long long)b * nblk + k) * 2 + 0);
+                srr += __ldcg(a.partials + ((long long)b * nblk + k) * 2 + 1);
+            }
+            CgState& cs = a.cg[b];
+            cs.iter += 1;
+            cs.rnorm2 = srr;
+            const double beta = srz / cs.rho;
+            cs.rho = srz;
+            cs.beta = beta;
+            if (!(srr == srr) || !(srz == srz)) { cs.flags |= 2; cs.done = 1; }
+            if (srr <= cs.tol2 * cs.bnorm2 || cs.iter >= cs.max_iter) cs.done = 1;
+            if (!cs.done) {  // p_e = z_e + beta p_e, and E p_e for the next pass 3
+                const double(*Me)[9] = pd.Me;
+                double pe[9];
+                for (int k = 0; k < d.ne; ++k) {
+                    double ze = 0.0;
+                    for (int l = 0; l < d.ne; ++l) ze += Me[k][l] * a.r_e[b * 9 + d.active[l]];
+                    pe[k] = ze + beta * a.p_e[b * 9 + d.active[k]];
+                }
+                for (int q = 0; q < 9; ++q) a.macroW[b * 9 + q] = 0.0;
+                for (int k = 0; k < d.ne; ++k) {
+                    const int m = d.active[k];
+                    a.p_e[b * 9 + m] = pe[k];
+                    a.macroW[b * 9 + m] = macro_to_w<NC>(m) * pe[k];
+                }
+            }
+            a.counters[b] = 0u;
+        }
+    }
+}
+
+// ------------------------------------------------------------------ CG start
+// rho = <r, M r>, bnorm2 = ||r||^2 (x = 0, p = 0 preset); macro: p_e = 0.
+template <typename T>
+struct CgInitArgs {
+    Dims d;
+    Freq<T> f;
+    const cplx<T>* r;
+    const double* r_e;
+    double* p_e;
+    double* macroW;
+    CgState* cg;
+    const PrecondData* pre;
+    double* partials;
+    unsigned* counters;
+    double tol;
+    int max_iter;
+};
+
+template <typename T>
+__global__ void k_cg_init(CgInitArgs<T> a) {
+    __shared__ double red[32 * 2];
+    __shared__ bool is_last;
+    const Dims& d = a.d;
+    const int b = blockIdx.y;
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    double v2[2] = {0.0, 0.0};
+    const PrecondData& pd = a.pre[b / d.Rm];
+    if (i < d.H) {
+        const long long k1 = i / d.plane;
+        const long long rem = i - k1 * d.plane;
+        const int k2 = (int)(rem / d.h), k3 = (int)(rem - (long long)k2 * d.h);
+        cplx<T> rv[3], z[3];
+        for (int c = 0; c < 3; ++c) rv[c] = ldc(a.r + (long long)(b * 3 + c) * d.H + i);
+        precond_apply<T>(pd.coef, a.f.xi1[k1], a.f.xi2[k2], a.f.xi3[k3], (T)(1.0 / d.invN), rv, z);
+        const int wgt = hweight(k3, d.m);
+        for (int c = 0; c < 3; ++c) {
+            v2[0] += wgt * ((double)rv[c].x * z[c].x + (double)rv[c].y * z[c].y);
+            v2[1] += wgt * ((double)rv[c].x * rv[c].x + (double)rv[c].y * rv[c].y);
+        }
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        for (int k = 0; k < d.ne; ++k) {
+            double ze = 0.0;
+            for (int l = 0; l < d.ne; ++l) ze += pd.Me[k][l] * a.r_e[b * 9 + d.active[l]];
+            const double re = a.r_e[b * 9 + d.active[k]];
+            v2[0] += re * ze;
+            v2[1] += re * re;
+        }
+    }
+    block_sum<2>(v2, red);
+    const int nblk = gridDim.x;
+    if (threadIdx.x == 0) {
+        a.partials[((long long)b * nblk + blockIdx.x) * 2 + 0] = v2[0];
+        a.partials[((long long)b * nblk + blockIdx.x) * 2 + 1] = v2[1];
+        __threadfence();
+        const unsigned prev = atomicAdd(a.counters + b, 1u);
+        is_last = (prev == (unsigned)nblk - 1);
+    }
+    __syncthreads();
+    if (is_last && threadIdx.x == 0) {
+        __threadfence();
+        double srz = 0.0, srr = 0.0;
+        for (int k = 0; k < nblk; ++k) {
+            srz += __ldcg(a.partials + ((long long)b * nblk + k) * 2 + 0);
+            srr += __ldcg(a.partials + ((long long)b * nblk + k) * 2 + 1);
+        }
+        CgState& cs = a.cg[b];
+        cs.rho = srz;
+        cs.bnorm2 = srr;
+        cs.rnorm2 = srr;
+        cs.beta = 0.0;
+        cs.alpha = 0.0;
+        cs.iter = 0;
+        cs.flags = 0;
+        cs.tol2 = a.tol * a.tol;
+        cs.max_iter = a.max_iter;
+        cs.done = (srr == 0.0) ? 1 : 0;
+        if (!(srr == srr)) { cs.done = 1; cs.flags |= 2; }
+        // first direction's macro part: p_e = z_e (beta = 0)
+        for (int q = 0; q < 9; ++q) { a.p_e[b * 9 + q] = 0.0; a.macroW[b * 9 + q] = 0.0; }
+        for (int k = 0; k < d.ne; ++k) {
+            double ze = 0.0;
+            for (int l = 0; l < d.ne; ++l) ze += pd.Me[k][l] * a.r_e[b * 9 + d.active[l]];
+            const int m = d.active[k];
+            a.p_e[b * 9 + m] = ze;
+            a.macroW[b * 9 + m] = (d.nc == 6 && m >= 3 ? 0.70710678118654752440084436210485 : 1.0) * ze;
+        }
+        a.counters[b] = 0u;
+    }
+}
+
+}  // namespace dbfft

@@ -1,0 +1,89 @@
+"""GPU parity of full linear solves (FP64 and FP32-inner / FP64-outer) against the oracle.
+
+Parity runs solve both sides to 1e-12 (FP64) so that the difference is the
+solve error, not a CG rounding path: bar 1e-10 relative on fields and
+homogenized stress for FP64, 1e-6 on the homogenized stress for MIXED.
+"""
+import numpy as np
+import pytest
+
+import oracle.dbfft_oracle as o
+from paper_1905_12725_gb300 import synth
+from tests.helpers import iso_tangent, mask9, rel_err
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def _dbfft():
+    from paper_1905_12725_gb300 import dbfft
+    return dbfft
+
+
+def test_config1_fp64_parity():
+    """Centred sphere, 16^3, E 1 / 10, nu 0.3, eps_xx = 1e-3."""
+    c = synth.config1()
+    dbfft = _dbfft()
+    s = dbfft.Solver((16, 16, 16), c["phase"], dbfft.iso_phases(c["E"], c["nu"]), c["eps_bar"][None],
+                     tol=1e-12)
+    rep = s.solve_increment(0)
+    sig = s.homogenized_stress()[0]
+    u, _ = s.get_solution()
+    prob = o.Problem((16, 16, 16))
+    ref = o.solve_linear(prob, iso_tangent(c["phase"], c["E"], c["nu"]), c["eps_bar"], tol=1e-12)
+    assert rep["true_rel_res"] <= 1e-12
+    assert rel_err(sig, ref["sig_bar"]) < 1e-10
+    assert rel_err(u.cpu().numpy()[0], ref["u"]) < 1e-10
+    # the configuration's own tolerance: PCG to 1e-8
+    s2 = dbfft.Solver((16, 16, 16), c["phase"], dbfft.iso_phases(c["E"], c["nu"]), c["eps_bar"][None], tol=1e-8)
+    rep2 = s2.solve_increment(0)
+    assert rep2["true_rel_res"] <= 1e-8
+    assert rel_err(s2.homogenized_stress()[0], ref["sig_bar"]) < 1e-7
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_mixed_control_solve_parity(precision):
+    shape = (16, 16, 32)
+    g = np.random.default_rng(17)
+    phase = (g.random(shape) < 0.3).astype(np.uint16)
+    E, nu = [1.0, 50.0], [0.3, 0.25]
+    mask = mask9([(1, 1), (2, 2), (1, 2)])
+    target = np.array([[1e-3, 1e-4, 0], [1e-4, 0.0, 0.0], [0, 0.0, 0.0]])
+    dbfft = _dbfft()
+    s = dbfft.Solver(shape, phase, dbfft.iso_phases(E, nu), target[None], stress_mask=mask, tol=1e-12 if precision == 0 else 1e-9,
+                     precision=precision, eta_inner=1e-3)
+    s.solve_increment(0)
+    sig = s.homogenized_stress()[0]
+    prob = o.Problem(shape, "small", mask)
+    ref = o.solve_linear(prob, iso_tangent(phase, E, nu), target, tol=1e-12)
+    assert rel_err(sig, ref["sig_bar"]) < (1e-10 if precision == 0 else 1e-6)
+    u, e = s.get_solution()
+    if precision == 0:
+        assert rel_err(u.cpu().numpy()[0], ref["u"]) < 1e-9
+        assert np.abs(e[0][[1, 2, 3]] - ref["e"]).max() < 1e-10 * np.abs(ref["e"]).max()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_homogenized_tangent_six_rhs_batched(precision):
+    """Six unit Mandel strains solved as one batch of right-hand sides sharing one map."""
+    shape = (16, 16, 16)
+    rng = synth.Xoshiro256ss(99)
+    phase, _ = synth.rsa_spheres(16, 2.5, 0.2, rng)
+    E, nu = [1.0, 100.0], [0.3, 0.3]
+    dbfft = _dbfft()
+    s = dbfft.Solver(shape, phase, dbfft.iso_phases(E, nu), np.zeros((6, 3, 3)), batch=6,
+                     tol=1e-12 if precision == 0 else 1e-7, precision=precision, eta_inner=1e-3)
+    Ceff, rep = s.homogenized_tangent()
+    Ceff = Ceff[0]
+    Cref, _ = o.homogenized_tangent(shape, iso_tangent(phase, E, nu), tol=1e-12)
+    assert rel_err(Ceff, Cref) < (1e-10 if precision == 0 else 1e-6)
+    assert np.abs(Ceff - Ceff.T).max() < (1e-10 if precision == 0 else 1e-6) * np.abs(Ceff).max()
+
+
+def test_zero_load_returns_zero_without_iterations():
+    shape = (8, 8, 8)
+    dbfft = _dbfft()
+    s = dbfft.Solver(shape, np.zeros(shape, np.uint16), dbfft.iso_phases([1.0], [0.3]), np.zeros((1, 3, 3)))
+    rep = s.solve_increment(0)
+    assert rep["cg_iters"] == 0
+    assert np.abs(s.homogenized_stress()).max() == 0.0
