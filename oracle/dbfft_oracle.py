@@ -34,6 +34,9 @@ R3  The finite-strain gradient g-hat is read with the factor i: g_ijk = i xi_j
     delta_ik (the printed form drops it; the derivative rule needs it).
 R4  M(0) is read as the macro-block preconditioner (N Cbar_ee)^-1 on the
     stress-controlled components; M(xi) = N [xi'.Cbar.xi']^-1 off Z, 0 on Z.
+R5b The unknown lives on Hermitian-consistent spectra (v(-k) = conj v(k) on
+    the k3 = 0 and k3 = N3/2 planes); operator outputs are projected onto
+    that subspace, which only removes round-off.
 R6  Inner product: the full-spectrum Hermitian product, computed on the half
     spectrum with weight 1 on the k3 = 0 and k3 = N3/2 planes and 2 elsewhere,
     plus the plain dot product of the macro unknowns. alpha, beta are real.
@@ -141,6 +144,27 @@ def div_hat(s_hat, xi):
     for i in range(3):
         for j in range(3):
             out[i] += 1j * xi[j] * s_hat[i, j]
+    return out
+
+
+def hermitian_project(v, shape):
+    """Project a half-spectrum field onto the Hermitian-consistent subspace (R5b).
+
+    On the planes k3 = 0 and k3 = N3/2 (even N3) the entries k and -k both
+    hold one real unknown pair; the system is full rank only on spectra with
+    v(-k) = conj(v(k)) there (Sec. 2.2: "real Fourier transform symmetries
+    removed"). Exact operator outputs satisfy this; the projection removes
+    round-off that would otherwise sit in the null space of K.
+    """
+    n1, n2, n3 = shape
+    planes = [0] + ([n3 // 2] if n3 % 2 == 0 else [])
+    i1 = (-np.arange(n1)) % n1
+    i2 = (-np.arange(n2)) % n2
+    out = v.copy()
+    for k3 in planes:
+        P = v[..., k3]
+        Pc = np.conj(P[..., i1, :][..., :, i2])
+        out[..., k3] = 0.5 * (P + Pc)
     return out
 
 
@@ -290,7 +314,7 @@ class Problem:
         s^H sigma-hat = -d-hat : sigma-hat for both s-hat and g-hat.
         """
         s_hat = to_fourier(sig)
-        q = -div_hat(s_hat, self.xi) / self.N
+        q = hermitian_project(-div_hat(s_hat, self.xi) / self.N, self.shape)
         q[:, self.Z] = 0.0
         tot = s_hat[:, :, 0, 0, 0].real  # sum_x sigma
         qe = np.einsum("mij,ij->m", self.basis, tot)
@@ -579,7 +603,9 @@ class CrystalPlasticity:
         """Backward Euler at every voxel (vectorised over voxels).
 
         Solves R(sigma) = S sigma + dt sum_a gdot_a(sigma) P_a - (eps - eps_p_old) = 0
-        (Mandel 6-vectors) by Newton with backtracking on the convex potential
+        (Mandel 6-vectors) by Newton, stopped when the full Newton step is below
+        rtol (|sigma| + tau_c), with backtracking (far from the solution) on the
+        convex potential
         phi(sigma) = 1/2 sigma.S.sigma + dt sum_a gdot0 tau_c m/(1+m)|tau_a/tau_c|^(1+1/m)
                      - sigma.(eps - eps_p_old).
         Returns (sigma, tangent d sigma / d eps [.., 6, 6], eps_p_new, newton iterations).
@@ -605,18 +631,22 @@ class CrystalPlasticity:
             J = S + dt * np.einsum("va,vam,van->vmn", dgd, P, P)
             step = -np.linalg.solve(J, R[..., None])[..., 0]
             step[~active] = 0.0
-            # backtracking on phi (phi is strictly convex, Newton direction descends)
+            scale = np.linalg.norm(sig, axis=1) + self.tau_c
+            nstep = np.linalg.norm(step, axis=1)
+            conv = active & (nstep <= rtol * scale)  # full Newton step below tolerance: accept and stop
+            # backtracking on phi only far from the solution (strictly convex potential,
+            # so the Newton direction descends); the allowance 1e-13 |phi| absorbs round-off
+            far = active & (nstep > 1e-3 * scale)
             t = np.ones(sig.shape[0])
             f0 = phi(sig)
+            slope = np.einsum("vm,vm->v", R, step)
             for _ in range(60):
                 trial = sig + t[:, None] * step
-                bad = (phi(trial) > f0 + 1e-4 * t * np.einsum("vm,vm->v", R, step)) & active
+                bad = far & (phi(trial) > f0 + 1e-4 * t * slope + 1e-13 * np.abs(f0))
                 if not np.any(bad):
                     break
                 t[bad] *= 0.5
             sig = sig + t[:, None] * step
-            dn = np.linalg.norm(t[:, None] * step, axis=1)
-            conv = dn <= rtol * (np.linalg.norm(sig, axis=1) + self.tau_c)
             active &= ~conv
             it_max = it + 1
             if not np.any(active):
