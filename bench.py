@@ -1,0 +1,425 @@
+"""Benchmark of the DBFFT hot path on GB300.
+
+Workload (one step): the effective stiffness of a 64^3 random-sphere composite
+(non-overlapping spheres of radius 6 voxels to volume fraction 0.25, stiffness
+contrast 100, nu = 0.3, seed 190512725 + 2) -- the six unit Mandel macro
+strains solved as six right-hand sides of one batched, FP32-inner /
+FP64-outer refined PCG to a true FP64 relative residual of 1e-6.
+
+Metric: voxel * CG-iterations / s (inner CG iterations summed over the six
+right-hand sides), and the time to a 1e-6 relative residual of the mixed
+batched solve against FP64 PCG solving the six right-hand sides one after
+another on the same GPU.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With N > 1 (launched by torch.distributed.run) every rank solves its own copy
+of the workload (weak scaling, no collective on the data path); value is the
+total work of all ranks over the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "voxel*CG-iters/s and time to 1e-6 rel. residual, mixed batched vs FP64 plain"
+UNIT = "voxel*CG-iter/s"
+N_GRID = 64
+TOL = 1e-6
+ETA_INNER = 1e-3
+WORKLOAD = "64^3 random-sphere composite (r=6 vox, vf 0.25, contrast 100, nu 0.3), 6 unit Mandel strains"
+
+# DRAM traffic per launch of the dominant kernel from an ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum), keyed by kernel; valid only
+# for the kernel sources it was taken on.
+NCU_TRAFFIC = {}
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def _sources_hash():
+    import hashlib
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_1905_12725_gb300", "csrc")
+    for n in sorted(os.listdir(d)):
+        with open(os.path.join(d, n), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def workload_inputs():
+    from paper_1905_12725_gb300 import synth
+    c = synth.config2(n=N_GRID)
+    return c
+
+
+# ------------------------------------------------------------------ CPU oracle sample
+def oracle_sample(c, iters=40):
+    """Time the FP64 oracle's PCG on the first right-hand side for a bounded number of iterations."""
+    import oracle.dbfft_oracle as o
+    shape = (N_GRID,) * 3
+    lam, mu = o.lame(c["E"][c["phase"]], c["nu"][c["phase"]])
+    T = o.IsoTangent(lam, mu)
+    prob = o.Problem(shape)
+    b = o.linear_rhs(prob, T, o.mandel_basis()[0])
+    M = prob.make_preconditioner(T.mean())
+    t0 = time.perf_counter()
+    _, it, _ = o.pcg(prob, lambda v: prob.apply_K(T, v[0], v[1]), M, b, 1e-30, iters)
+    dt = time.perf_counter() - t0
+    V = N_GRID ** 3
+    return V * it / dt, it, dt
+
+
+def reference_arm(args, rank, world):
+    if rank != 0:
+        return
+    c = workload_inputs()
+    vals = []
+    for _ in range(args.warmup):
+        oracle_sample(c, iters=2)
+    t_all = 0.0
+    its = 0
+    for _ in range(args.steps):
+        v, it, dt = oracle_sample(c, iters=args.ref_iters)
+        vals.append(v)
+        t_all += dt
+        its += it
+    value = N_GRID ** 3 * its / t_all
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_all / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "n": N_GRID, "batch": 6},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{args.ref_iters} PCG iterations of the FP64 numpy oracle on right-hand side 1 "
+                                   f"per step (host cores: {os.cpu_count()})"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ our arm
+def make_solver(c, precision, batch, targets=None, tol=TOL):
+    from paper_1905_12725_gb300 import dbfft
+    shape = (N_GRID,) * 3
+    if targets is None:
+        targets = np.zeros((batch, 3, 3))
+    return dbfft.Solver(shape, c["phase"], dbfft.iso_phases(c["E"], c["nu"]), targets, batch=batch,
+                        precision=precision, tol=tol, eta_inner=ETA_INNER, max_iter=20000, max_newton=100)
+
+
+def unit_mandel(m):
+    pi = [0, 1, 2, 1, 0, 0]
+    pj = [0, 1, 2, 2, 2, 1]
+    t = np.zeros((3, 3))
+    v = 1.0 if m < 3 else 1.0 / math.sqrt(2.0)
+    t[pi[m], pj[m]] = t[pj[m], pi[m]] = v
+    return t
+
+
+def operator_256(torch, dbfft, peak):
+    """FP32 inner-CG pass chain on a 256^3 linear two-phase RVE (one right-hand side)."""
+    from paper_1905_12725_gb300 import synth
+    n = 256
+    rng = synth.Xoshiro256ss(synth.SEED_BASE + 42)
+    g = np.random.default_rng(7)
+    phase = (g.random((n, n, n)) < 0.3).astype(np.uint16)
+    del rng
+    eps = np.zeros((1, 3, 3))
+    eps[0, 0, 0] = 1e-3
+    s = dbfft.Solver((n, n, n), phase, dbfft.iso_phases([1.0, 100.0], [0.3, 0.3]), eps,
+                     precision=dbfft.DBFFT_MIXED, tol=1e-30, eta_inner=1e-30, max_iter=40, max_newton=1)
+    s.solve_increment(0, allow_not_converged=True)  # warm-up
+    s.profile(True)
+    t0 = time.perf_counter()
+    rep = s.solve_increment(0, allow_not_converged=True)
+    wall = time.perf_counter() - t0
+    prof = s.profile_read()
+    s.profile(False)
+    s.close()
+    names = ["axis1_inv_cg_f32", "axis2_f32", "axis3_apply_f32", "axis1_fwd_cg_f32"]
+    rows = {}
+    it_ms = 0.0
+    it_bytes = 0.0
+    for k in names:
+        e = prof.get(k)
+        if not e or not e["launches"]:
+            continue
+        gbs = e["bytes"] / (e["ms"] * 1e-3) / 1e9
+        rows[k] = {"launches": e["launches"], "ms_per_launch": e["ms"] / e["launches"], "GBps": gbs,
+                   "frac": gbs / peak}
+        it_ms += e["ms"]
+        it_bytes += e["bytes"]
+    iters = rep["cg_iters"]
+    return {"grid": "256^3, 1 RHS, FP32 inner CG, iso two-phase (vf 0.3, contrast 100)",
+            "cg_iters": iters, "ms_per_cg_iter": it_ms / max(iters, 1),
+            "voxel_cg_iters_per_s": n ** 3 * iters / (it_ms * 1e-3) if it_ms else None,
+            "chain_GBps": it_bytes / (it_ms * 1e-3) / 1e9 if it_ms else None,
+            "chain_frac": (it_bytes / (it_ms * 1e-3) / 1e9) / peak if it_ms else None,
+            "passes": rows, "wall_s": wall}
+
+
+def our_arm(args, rank, world, local_rank):
+    import torch
+    from paper_1905_12725_gb300 import dbfft
+
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+    dev = torch.device("cuda", local_rank)
+    peak, peak_kind = _peaks()
+    c = workload_inputs()
+    V = N_GRID ** 3
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def l2_flush():
+        flush.fill_(1.0)
+
+    # --- mixed batched: the timed step
+    s = make_solver(c, dbfft.DBFFT_MIXED, 6)
+    for _ in range(args.warmup):
+        s.homogenized_tangent()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    s.profile(True)
+    launches0 = s.launch_count()
+    stream = torch.cuda.current_stream(dev)
+    ms_steps, iters_steps, res_steps = [], [], []
+    for _ in range(args.steps):
+        l2_flush()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        Ceff, rep = s.homogenized_tangent()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_steps.append(e0.elapsed_time(e1))
+        iters_steps.append(rep["cg_iters"])
+        res_steps.append(rep["true_rel_res"])
+    gpu_launches = s.launch_count() - launches0
+    prof = s.profile_read()
+    s.profile(False)
+    clk = clocks.stop()
+    t_total = sum(ms_steps) * 1e-3
+    work = V * sum(iters_steps)
+    if dist:
+        tt = torch.tensor([t_total], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_total = float(tt.item())
+        wk = torch.tensor([float(work)], device=dev)
+        dist.all_reduce(wk, op=dist.ReduceOp.SUM)
+        work = float(wk.item())
+    value = work / t_total
+    Ceff = Ceff[0]
+
+    # --- dominant kernel roofline (live, CUDA events on the context stream)
+    dom = max(prof.items(), key=lambda kv: kv[1]["ms"])
+    dname, de = dom
+    per_launch_ms = de["ms"] / de["launches"]
+    per_launch_bytes = de["bytes"] / de["launches"]
+    achieved = per_launch_bytes / (per_launch_ms * 1e-3) / 1e9
+    src = _sources_hash()
+    tr = NCU_TRAFFIC.get(dname)
+    traffic = tr["bytes"] if tr and tr.get("src") == src else None
+    kernels = {k: {"launches": v["launches"], "ms": v["ms"],
+                   "GBps": (v["bytes"] / (v["ms"] * 1e-3) / 1e9) if v["ms"] > 0 and v["bytes"] > 0 else None}
+               for k, v in sorted(prof.items(), key=lambda kv: -kv[1]["ms"])}
+
+    # --- FP64 plain: six right-hand sides one after another, FP64 PCG to 1e-6
+    plain = [make_solver(c, dbfft.DBFFT_FP64, 1, targets=unit_mandel(m)[None]) for m in range(6)]
+    for p in plain:
+        p.solve_increment(0)
+    l2_flush()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    it64 = 0
+    res64 = 0.0
+    for p in plain:
+        r = p.solve_increment(0)
+        it64 += r["cg_iters"]
+        res64 = max(res64, r["true_rel_res"])
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t64 = e0.elapsed_time(e1)
+    C64 = np.zeros((6, 6))
+    for m, p in enumerate(plain):
+        sg = p.homogenized_stress()[0]
+        C64[:, m] = [sg[0, 0], sg[1, 1], sg[2, 2], math.sqrt(2) * sg[1, 2], math.sqrt(2) * sg[0, 2],
+                     math.sqrt(2) * sg[0, 1]]
+        p.close()
+
+    # --- end to end through the C ABI with host buffers (create from host map, solve, read C_eff)
+    e2e_ms = []
+    e2e_iters = []
+    for k in range(args.warmup + args.steps):
+        l2_flush()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        se = make_solver(c, dbfft.DBFFT_MIXED, 6)
+        Ce, r = se.homogenized_tangent()
+        se.close()
+        torch.cuda.synchronize()
+        if k >= args.warmup:
+            e2e_ms.append((time.perf_counter() - t0) * 1e3)
+            e2e_iters.append(r["cg_iters"])
+    e2e_t = sum(e2e_ms) * 1e-3
+    e2e_work = V * sum(e2e_iters)
+    if dist:
+        tt = torch.tensor([e2e_t], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_t = float(tt.item())
+        wk = torch.tensor([float(e2e_work)], device=dev)
+        dist.all_reduce(wk, op=dist.ReduceOp.SUM)
+        e2e_work = float(wk.item())
+
+    op256 = None
+    if rank == 0 and not args.skip_256:
+        op256 = operator_256(torch, dbfft, peak)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.skip_cpu:
+        v, it, dt = oracle_sample(c, iters=args.ref_iters)
+        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{it} PCG iterations of the FP64 numpy oracle on right-hand side 1 of the same "
+                         f"workload ({dt:.1f} s; numpy FFT single-threaded; host has {os.cpu_count()} cores)"}
+
+    if rank != 0:
+        return
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": float(np.mean(ms_steps)), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32 inner / f64 outer",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": N_GRID, "batch": 6, "tol": TOL, "eta_inner": ETA_INNER,
+                   "seed": 190512725 + 2, "l2": "flushed (512 MiB write) before every step",
+                   "parallelism": f"replicas x{world}"},
+        "time_to_1e-6_ms": {"mixed_batched": float(np.mean(ms_steps)), "fp64_plain_sequential": t64,
+                            "speedup": t64 / float(np.mean(ms_steps))},
+        "cg_iters_per_step": {"mixed_batched": int(np.mean(iters_steps)), "fp64_plain": it64},
+        "true_rel_res": {"mixed_batched": max(res_steps), "fp64_plain": res64},
+        "fp64_plain_value": V * it64 / (t64 * 1e-3),
+        "C_eff_rel_diff_mixed_vs_fp64": float(np.abs(Ceff - C64).max() / np.abs(C64).max()),
+        "roofline": {"bound": "hbm", "kernel": dname, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic, "peak_source": peak_kind,
+                     "algorithmic_bytes_per_launch": per_launch_bytes, "ms_per_launch": per_launch_ms},
+        "kernels": kernels,
+        "gpu_launches": int(gpu_launches),
+        "e2e": {"value": e2e_work / e2e_t, "unit": UNIT, "h2d_bytes_per_step": int(c["phase"].nbytes + 6 * 9 * 8),
+                "d2h_bytes_per_step": 36 * 8, "ms_per_step": float(np.mean(e2e_ms)),
+                "path": "dbfft_create from host phase map + dbfft_homogenized_tangent + dbfft_destroy"},
+        "clocks": clk,
+        "operator_256": op256,
+        "cpu_baseline": cpu,
+        "src": _sources_hash(),
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--ref-iters", type=int, default=40)
+    ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--skip-256", action="store_true")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        reference_arm(args, rank, world)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+    our_arm(args, rank, world, local_rank)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

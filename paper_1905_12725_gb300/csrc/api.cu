@@ -626,6 +626,8 @@ dbfft_status chain_residual(dbfft_ctx* ctx, const cplx<double>* x, const double*
     a5.partials = ctx->partials;
     TRY(run(ctx, "axis1_fwd_resid_f64", (3 + nc) * cp,
             [&] { return launch_ax1_fwd<double>(AX5_RESID, a5, ctx->stream); }));
+    // the unknowns are Hermitian-consistent spectra: drop the round-off that breaks it
+    TRY(run(ctx, "hermitian_planes", 0.0, [&] { return launch_herm_planes<double>(ctx->dims, ctx->r64, ctx->stream); }));
     const int TW = ax1_tile(ctx->n1, true);
     const int nblk = (int)((ctx->dims.plane + TW - 1) / TW);
     CK(cudaMemcpyAsync(ctx->part_h, ctx->partials, (size_t)ctx->B * nblk * 2 * sizeof(double),
@@ -1403,6 +1405,7 @@ dbfft_status dbfft_adjoint(dbfft_ctx* ctx, const double* dJ_dsigma, double* dJ_d
     Ax2Args<double> b2{ctx->dims, twid<double>(ctx), W2, nullptr};
     TRY(run(ctx, "axis2_f64", 0.0, [&] { return launch_ax2<double>(+1, b2, ctx->stream); }));
     Ax3Args<double> a3 = ax3_base<double>(ctx, W);
+    a3.L = ax3_lines(ctx->n3, ctx->nc, ctx->RB, true, 2);
     a3.W2 = W2;
     a3.macroW = ctx->macroW;
     a3.macroW2 = ctx->macroW2;

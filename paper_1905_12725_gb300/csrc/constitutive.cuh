@@ -7,8 +7,9 @@
 //  * small-strain FCC crystal plasticity with power-law slip rates,
 //    backward Euler on the stress (Mandel 6-vectors):
 //      R(s) = S s + dt sum_a gdot_a(s) P_a - (eps_{n+1} - eps_p,n) = 0,
-//    solved by Newton with backtracking on the convex potential whose
-//    gradient R is; consistent tangent (S + dt sum_a gdot'_a P_a P_a^T)^-1.
+//    solved by Newton (stopped on the full Newton step) with backtracking,
+//    far from the solution, on the convex potential whose gradient R is;
+//    consistent tangent (S + dt sum_a gdot'_a P_a P_a^T)^-1.
 // The stress-side math runs in FP64.
 #pragma once
 #include <cuda_runtime.h>
@@ -218,23 +219,26 @@ __device__ __forceinline__ bool cp_update(const CpGrain& G, const CpParams& cp, 
         double mR[6];
         for (int i = 0; i < 6; ++i) mR[i] = -R[i];
         chol6_solve(L, mR, step);
-        double slope = 0.0;
-        for (int i = 0; i < 6; ++i) slope += R[i] * step[i];
-        const double f0 = cp_potential(G, cp, s, target);
-        double t = 1.0;
-        for (int ls = 0; ls < 60; ++ls) {
-            double trial[6];
-            for (int i = 0; i < 6; ++i) trial[i] = s[i] + t * step[i];
-            if (!(cp_potential(G, cp, trial, target) > f0 + 1e-4 * t * slope)) break;
-            t *= 0.5;
-        }
-        double dn = 0.0, sn = 0.0;
+        double slope = 0.0, ns = 0.0, sn = 0.0;
         for (int i = 0; i < 6; ++i) {
-            s[i] += t * step[i];
-            dn += (t * step[i]) * (t * step[i]);
+            slope += R[i] * step[i];
+            ns += step[i] * step[i];
+            sn += s[i] * s[i];
         }
-        for (int i = 0; i < 6; ++i) sn += s[i] * s[i];
-        if (sqrt(dn) <= cp.rtol * (sqrt(sn) + cp.tau_c)) { conv = true; break; }
+        const double scale = sqrt(sn) + cp.tau_c;
+        ns = sqrt(ns);
+        double t = 1.0;
+        if (ns > 1e-3 * scale) {  // backtracking on the convex potential, far from the solution only
+            const double f0 = cp_potential(G, cp, s, target);
+            for (int ls = 0; ls < 60; ++ls) {
+                double trial[6];
+                for (int i = 0; i < 6; ++i) trial[i] = s[i] + t * step[i];
+                if (!(cp_potential(G, cp, trial, target) > f0 + 1e-4 * t * slope + 1e-13 * fabs(f0))) break;
+                t *= 0.5;
+            }
+        }
+        for (int i = 0; i < 6; ++i) s[i] += t * step[i];
+        if (ns <= cp.rtol * scale) { conv = true; break; }  // full Newton step below tolerance
     }
     double gd[12];
     cp_residual(G, cp, s, target, R, Jm, gd);

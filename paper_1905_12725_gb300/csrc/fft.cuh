@@ -218,8 +218,13 @@ struct ColFFT {
     }
 };
 
-// Radix used per transform length and precision.
-template <typename T, int N> struct RadixFor { static constexpr int value = N < 16 ? N : 16; };
-template <int N> struct RadixFor<double, N> { static constexpr int value = N < 8 ? N : 8; };
+// Radix per pass, transform length and precision (host and device agree on it).
+//  axis 1 (passes 1 and 5) keeps several components live per thread, so it
+//  uses radix 8 to stay at two CTAs per SM; axis 2 and the half-length
+//  transform of axis 3 use radix 16 in FP32 and 8 in FP64.
+__host__ __device__ constexpr int radix_ax1(int n, bool dbl) { return dbl ? (n < 4 ? n : 4) : (n < 8 ? n : 8); }
+__host__ __device__ constexpr int radix_ax2(int n, bool dbl) { return dbl ? (n < 8 ? n : 8) : (n < 16 ? n : 16); }
+template <typename T, int N> struct RadixAx1 { static constexpr int value = radix_ax1(N, sizeof(T) == 8); };
+template <typename T, int N> struct RadixFor { static constexpr int value = radix_ax2(N, sizeof(T) == 8); };
 
 }  // namespace dbfft

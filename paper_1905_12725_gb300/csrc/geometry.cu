@@ -5,28 +5,29 @@ namespace dbfft {
 
 bool supported_len(int n) { return n == 8 || n == 16 || n == 32 || n == 64 || n == 128 || n == 256; }
 
-static int radix_for(int n, bool dbl) { return dbl ? (n < 8 ? n : 8) : (n < 16 ? n : 16); }
+static int radix_for(int n, bool dbl) { return radix_ax2(n, dbl); }
 
 int ax1_tile(int n1, bool dbl) {
-    const int P = n1 / radix_for(n1, dbl);
+    const int P = n1 / radix_ax1(n1, dbl);  // threads per column; the block is tw x P = 256 threads
+    int tw = 256 / P;
+    if (tw > 256) tw = 256;
+    return tw;
+}
+int ax2_tile(int n2, bool dbl) {
+    const int P = n2 / radix_ax2(n2, dbl);
     int tw = 256 / P;
     if (tw < 8) tw = 8;
     if (tw > 256) tw = 256;
     return tw;
 }
-int ax2_tile(int n2, bool dbl) { return ax1_tile(n2, dbl); }
 
-int ax3_lines(int n3, int nc, int rb, bool dbl) {
-    const int m = n3 / 2;
-    const int P = m / radix_for(m, dbl);
-    const int per_line = P * rb * nc;
-    int L = 256 / per_line;
+int ax3_lines(int n3, int nc, int rb, bool dbl, int nfields) {
+    // real-space tiles of one CTA within ~96 KB so that two CTAs fit on an SM
+    const size_t sb = (size_t)(n3 + 2) * (dbl ? 8 : 4);
+    long long L = (long long)(96 * 1024) / ((long long)sb * rb * nc * nfields);
     if (L < 1) L = 1;
-    while (L > 1 && ((per_line * L + 31) / 32) * 32 > 256) --L;
-    // keep the real-space tiles within 96 KB
-    const size_t per = (size_t)rb * nc * n3 * (dbl ? 8 : 4);
-    while (L > 1 && per * L > 96 * 1024) --L;
-    return L;
+    if (L > 32) L = 32;
+    return (int)L;
 }
 
 int ax3_threads_per_line(int n3, int nc, int rb, bool dbl) {

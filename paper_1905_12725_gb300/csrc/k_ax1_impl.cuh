@@ -6,12 +6,14 @@ namespace dbfft {
 
 template <typename K>
 static void allow_smem(K kernel, size_t smem) {
-    if (smem > 48 * 1024) cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    // the axis-1 exchange tiles stay below 48 KB, so no opt-in is needed
+    (void)kernel;
+    (void)smem;
 }
 
 template <typename T, int N1, int NC>
 static cudaError_t ax1_inv_n(int mode, const Ax1InvArgs<T>& a, cudaStream_t s) {
-    constexpr int R = RadixFor<T, N1>::value;
+    constexpr int R = RadixAx1<T, N1>::value;
     constexpr int P = N1 / R;
     const int TW = ax1_tile(N1, sizeof(T) == 8);
     const dim3 block(TW, P);
@@ -29,7 +31,7 @@ static cudaError_t ax1_inv_n(int mode, const Ax1InvArgs<T>& a, cudaStream_t s) {
 
 template <typename T, int N1, int NC>
 static cudaError_t ax1_fwd_n(int mode, const Ax1FwdArgs<T>& a, cudaStream_t s) {
-    constexpr int R = RadixFor<T, N1>::value;
+    constexpr int R = RadixAx1<T, N1>::value;
     constexpr int P = N1 / R;
     const int TW = ax1_tile(N1, sizeof(T) == 8);
     const dim3 block(TW, P);

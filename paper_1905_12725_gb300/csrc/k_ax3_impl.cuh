@@ -6,19 +6,21 @@ namespace dbfft {
 
 template <typename T, int N3, int NC, int OPK>
 static cudaError_t ax3_n(const Ax3Args<T>& a, cudaStream_t s) {
-    constexpr int M = N3 / 2;
-    constexpr int R = RadixFor<T, M>::value;
-    constexpr int P = M / R;
-    const int threads = ((P * a.L * a.RB * NC + 31) / 32) * 32;  // whole warps (block reductions shuffle full warps)
+    const int threads = 256;
     const long long nlines = (long long)a.d.n1 * a.d.n2;
     const dim3 grid((unsigned)((nlines + a.L - 1) / a.L), (unsigned)(a.d.B / a.RB));
-    // one real line of N3 values per slot of P threads, padding slots included
-    const size_t smem = (size_t)(threads / P) * N3 * sizeof(T) * (OPK == OP_ADJ ? 2 : 1);
-    static bool attr_done = false;
-    if (!attr_done) {
-        cudaFuncSetAttribute(k_axis3<T, N3, NC, OPK>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        attr_done = true;
+    const int nf = OPK == OP_ADJ ? 2 : 1;
+    const size_t smem = ((size_t)nf * a.L * a.RB * NC + 1) * (N3 + 2) * sizeof(T);
+    static int max_dyn = -1;
+    if (max_dyn < 0) {  // opt in to large dynamic shared memory: 227 KB per block minus the static part
+        cudaFuncAttributes fa;
+        cudaError_t e = cudaFuncGetAttributes(&fa, k_axis3<T, N3, NC, OPK>);
+        if (e != cudaSuccess) return e;
+        max_dyn = 227 * 1024 - (int)fa.sharedSizeBytes;
+        e = cudaFuncSetAttribute(k_axis3<T, N3, NC, OPK>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_dyn);
+        if (e != cudaSuccess) return e;
     }
+    if (smem > (size_t)max_dyn) return cudaErrorInvalidConfiguration;
     k_axis3<T, N3, NC, OPK><<<grid, threads, smem, s>>>(a);
     return cudaGetLastError();
 }

@@ -184,4 +184,42 @@ template cudaError_t launch_mean_tangent<float>(int, int, long long, const float
 template cudaError_t launch_mean_tangent<double>(int, int, long long, const double*, const uint16_t*,
                                                  const double*, const double*, double*, int, cudaStream_t);
 
+// Project [B][3][H] half spectra onto Hermitian-consistent vectors: on the
+// planes k3 = 0 and k3 = n3/2 the pair (k1, k2) / (-k1, -k2) is replaced by
+// its conjugate-symmetric part (one thread per pair).
+template <typename T>
+__global__ void k_herm_planes(Dims d, cplx<T>* v) {
+    const long long per = (long long)d.n1 * d.n2;
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= per * 2) return;
+    const int plane = (int)(i / per);
+    const long long j = i - plane * per;
+    const int k1 = (int)(j / d.n2), k2 = (int)(j - (long long)k1 * d.n2);
+    const int q1 = (d.n1 - k1) % d.n1, q2 = (d.n2 - k2) % d.n2;
+    const long long jq = (long long)q1 * d.n2 + q2;
+    if (jq < j) return;
+    const int k3 = plane == 0 ? 0 : d.m;
+    const int bc = blockIdx.y;  // b * 3 + c
+    cplx<T>* base = v + (long long)bc * d.H;
+    const long long a = ((long long)k1 * d.n2 + k2) * d.h + k3;
+    const long long bq = ((long long)q1 * d.n2 + q2) * d.h + k3;
+    cplx<T> x = base[a], y = base[bq];
+    cplx<T> s;
+    s.x = T(0.5) * (x.x + y.x);
+    s.y = T(0.5) * (x.y - y.y);
+    if (jq == j) s.y = T(0);
+    base[a] = s;
+    s.y = -s.y;
+    base[bq] = s;
+}
+
+template <typename T>
+cudaError_t launch_herm_planes(const Dims& d, cplx<T>* v, cudaStream_t s) {
+    const long long n = 2LL * d.n1 * d.n2;
+    k_herm_planes<T><<<dim3((unsigned)((n + 255) / 256), d.B * 3), 256, 0, s>>>(d, v);
+    return cudaGetLastError();
+}
+template cudaError_t launch_herm_planes<double>(const Dims&, cplx<double>*, cudaStream_t);
+template cudaError_t launch_herm_planes<float>(const Dims&, cplx<float>*, cudaStream_t);
+
 }  // namespace dbfft

@@ -9,7 +9,7 @@ namespace dbfft {
 // Launch geometry shared by the launchers and the buffer sizing.
 int ax1_tile(int n1, bool dbl);                      // columns per CTA of passes 1 and 5
 int ax2_tile(int n2, bool dbl);                      // columns per CTA of passes 2 and 4
-int ax3_lines(int n3, int nc, int rb, bool dbl);     // grid lines per CTA of pass 3
+int ax3_lines(int n3, int nc, int rb, bool dbl, int nfields = 1);  // grid lines per CTA of pass 3
 int ax3_threads_per_line(int n3, int nc, int rb, bool dbl);
 size_t ax3_smem(int n3, int nc, int rb, int lines, bool dbl, bool two_fields);
 bool supported_len(int n);

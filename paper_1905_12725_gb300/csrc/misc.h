@@ -17,4 +17,6 @@ cudaError_t launch_precond_field(const Dims& d, const Freq<T>& f, const PrecondD
 template <typename TT>
 cudaError_t launch_mean_tangent(int kind, int B, long long V, const TT* tan, const uint16_t* phase, const double* lam,
                                 const double* mu, double* partials, int nblk, cudaStream_t s);
+template <typename T>
+cudaError_t launch_herm_planes(const Dims& d, cplx<T>* v, cudaStream_t s);
 }  // namespace dbfft

@@ -63,87 +63,83 @@ template <int OPK> struct OpInfo {
     static constexpr bool apply = OPK == OP_ISO || OPK == OP_NH_APPLY || OPK == OP_CP_APPLY;
 };
 
+// Shared-memory layout: one buffer of SB = N3 + 2 values per slot
+// (slot = grid line x right-hand side x component), holding either the
+// half-spectrum line (N3/2 + 1 complex values) or the real line (N3 values),
+// plus one scratch buffer for idle threads of the last FFT round. Global
+// loads and stores are done cooperatively: for one (right-hand side,
+// component) the L lines of a CTA are L h contiguous complex values.
 template <typename T, int N3, int NC, int OPK>
 __global__ void __launch_bounds__(256) k_axis3(Ax3Args<T> a) {
     constexpr int M = N3 / 2;
+    constexpr int H = M + 1;
     constexpr int R = RadixFor<T, M>::value;
     constexpr int P = M / R;
+    constexpr int SB = N3 + 2;
     extern __shared__ __align__(16) unsigned char smraw[];
-    T* sreal = reinterpret_cast<T*>(smraw);
+    T* sbuf = reinterpret_cast<T*>(smraw);
     __shared__ double red[32 * 8];
     __shared__ double ecc[8];
     __shared__ bool is_last;
     const Dims& d = a.d;
     const int RB = a.RB, L = a.L;
     const int NSLOT = L * RB * NC;
-    const int NSLOT_ALLOC = blockDim.x / P;  // padding threads of the last warp get scratch slots
+    const int NF = (OPK == OP_ADJ) ? 2 : 1;  // fields carried (the adjoint reads two)
     const int t = threadIdx.x;
-    const int p = t % P, slot = t / P;
-    const bool slot_ok = slot < NSLOT;
-    const int c = slot % NC, rl = (slot / NC) % RB, ll = slot / (NC * RB);
+    const int nthr = blockDim.x;
+    const int per_round = nthr / P;
+    const int rounds = (NSLOT + per_round - 1) / per_round;
     const int g = blockIdx.y;
-    const int b = g * RB + rl;
     const long long nlines = (long long)d.n1 * d.n2;
-    const long long line = (long long)blockIdx.x * L + ll;
-    const bool act_b = (a.cg == nullptr) || (a.cg[b].done == 0);
-    const bool valid = slot_ok && line < nlines && act_b;
-    T* my = sreal + (long long)slot * N3;
-    cplx<T>* myc = reinterpret_cast<cplx<T>*>(my);
-    const long long base = ((long long)(b * NC + c) * nlines + line) * d.h;
+    const long long line0 = (long long)blockIdx.x * L;
+    const int lines_here = (int)min((long long)L, nlines - line0);
+    T* scratch = sbuf + (long long)NF * NSLOT * SB;
+    // slot s = (ll * RB + rl) * NC + c ; field f at offset f * NSLOT
+    auto slot_ptr = [&](int f, int sl) { return sbuf + ((long long)f * NSLOT + sl) * SB; };
+    auto rhs_done = [&](int rl) { return a.cg != nullptr && a.cg[g * RB + rl].done != 0; };
 
-    // ---- C2R (and for OP_ADJ the second field in the second half of the slots)
-    {
-        cplx<T> v[R];
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-            const int k = p + r * P;
-            if (valid) {
-                const cplx<T> X = ldc(a.W + base + k);
-                const cplx<T> Xc = conjg(ldc(a.W + base + (M - k)));
-                const cplx<T> e = conjg(ldg_c(a.tw.t3 + k));  // e^{+2 pi i k / n}
-                const cplx<T> dlt = e * (X - Xc);
-                v[r] = (X + Xc) + mk(-dlt.y, dlt.x);
-            } else {
-                v[r] = zero_c<T>();
-            }
+    // ---- cooperative load of the half-spectrum lines
+    for (int f = 0; f < NF; ++f) {
+        const cplx<T>* src = f == 0 ? a.W : a.W2;
+        const int per_rc = lines_here * H;
+        for (int i = t; i < RB * NC * per_rc; i += nthr) {
+            const int rc = i / per_rc, rest = i - rc * per_rc;
+            const int rl = rc / NC, c = rc - rl * NC;
+            const int ll = rest / H, k = rest - ll * H;
+            const int b = g * RB + rl;
+            cplx<T> v = zero_c<T>();
+            if (!rhs_done(rl)) v = ldc(src + ((long long)(b * NC + c) * nlines + line0) * H + rest);
+            reinterpret_cast<cplx<T>*>(slot_ptr(f, (ll * RB + rl) * NC + c))[k] = v;
         }
-        ColFFT<T, M, R, +1>::run(v, myc, 1, p, a.tw.tm);
-        __syncthreads();
-        if (slot_ok) {
+    }
+    __syncthreads();
+
+    // ---- C2R per slot: Z[k] = (X[k] + conj X[M-k]) + i e^{+2 pi i k/n} (X[k] - conj X[M-k])
+    for (int f = 0; f < NF; ++f) {
+        for (int rd = 0; rd < rounds; ++rd) {
+            const int sl = rd * per_round + t / P;
+            const int p = t % P;
+            const bool ok = sl < NSLOT && t / P < per_round;
+            T* my = ok ? slot_ptr(f, sl) : scratch;
+            cplx<T>* myc = reinterpret_cast<cplx<T>*>(my);
+            cplx<T> v[R];
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const int k = p + r * P;
+                const cplx<T> X = myc[k];
+                const cplx<T> Xc = conjg(myc[M - k]);
+                const cplx<T> e = conjg(ldg_c(a.tw.t3 + k));
+                const cplx<T> dl = e * (X - Xc);
+                v[r] = (X + Xc) + mk(-dl.y, dl.x);
+            }
+            __syncthreads();  // every thread has read its line before it is overwritten
+            ColFFT<T, M, R, +1>::run(v, myc, 1, p, a.tw.tm);
+            __syncthreads();
 #pragma unroll
             for (int r = 0; r < R; ++r) {
                 const int jj = p + r * P;
                 my[2 * jj] = v[r].x;
                 my[2 * jj + 1] = v[r].y;
-            }
-        }
-    }
-    T* sreal2 = sreal + (long long)NSLOT_ALLOC * N3;  // OP_ADJ second field
-    if constexpr (OPK == OP_ADJ) {
-        cplx<T> v[R];
-        T* my2 = sreal2 + (long long)slot * N3;
-        cplx<T>* myc2 = reinterpret_cast<cplx<T>*>(my2);
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-            const int k = p + r * P;
-            if (valid) {
-                const cplx<T> X = ldc(a.W2 + base + k);
-                const cplx<T> Xc = conjg(ldc(a.W2 + base + (M - k)));
-                const cplx<T> e = conjg(ldg_c(a.tw.t3 + k));
-                const cplx<T> dlt = e * (X - Xc);
-                v[r] = (X + Xc) + mk(-dlt.y, dlt.x);
-            } else {
-                v[r] = zero_c<T>();
-            }
-        }
-        ColFFT<T, M, R, +1>::run(v, myc2, 1, p, a.tw.tm);
-        __syncthreads();
-        if (slot_ok) {
-#pragma unroll
-            for (int r = 0; r < R; ++r) {
-                const int jj = p + r * P;
-                my2[2 * jj] = v[r].x;
-                my2[2 * jj + 1] = v[r].y;
             }
         }
     }
@@ -154,30 +150,28 @@ __global__ void __launch_bounds__(256) k_axis3(Ax3Args<T> a) {
 #pragma unroll
     for (int q = 0; q < 8; ++q) eacc[q] = 0.0;
     const int mat = (g * RB) / d.Rm;
-    for (int idx = t; idx < L * N3; idx += blockDim.x) {
+    for (int idx = t; idx < lines_here * N3; idx += nthr) {
         const int lv = idx / N3, x3 = idx - lv * N3;
-        const long long ln = (long long)blockIdx.x * L + lv;
-        if (ln >= nlines) continue;
-        const long long vox = ln * N3 + x3;
+        const long long vox = (line0 + lv) * N3 + x3;
         if constexpr (OPK == OP_ISO || OPK == OP_ADJ) {
             const long long mv = (long long)mat * d.V + vox;
             const int ph = a.phase[mv];
-            double sc = a.scale ? a.scale[mv] : 1.0;
+            const double sc = a.scale ? a.scale[mv] : 1.0;
             const T lam = (T)(a.lam[ph] * sc), mu = (T)(a.mu[ph] * sc);
             for (int rr = 0; rr < RB; ++rr) {
                 const int bb = g * RB + rr;
-                if (a.cg && a.cg[bb].done) continue;
-                T* f = sreal + (long long)((lv * RB + rr) * NC) * N3 + x3;
+                if (rhs_done(rr)) continue;
+                T* f = slot_ptr(0, (lv * RB + rr) * NC) + x3;
                 T e[NC];
 #pragma unroll
-                for (int q = 0; q < NC; ++q) e[q] = f[q * N3] + (T)a.macroW[bb * 9 + q];
+                for (int q = 0; q < NC; ++q) e[q] = f[q * SB] + (T)a.macroW[bb * 9 + q];
                 if constexpr (OPK == OP_ADJ) {
                     // dJ/dE = (1/N) eps_adj : C1 : eps_fwd, C1 = C / E: for this
                     // op the phase tables hold lam, mu per unit Young's modulus
-                    const T* f2 = sreal2 + (long long)((lv * RB + rr) * NC) * N3 + x3;
+                    const T* f2 = slot_ptr(1, (lv * RB + rr) * NC) + x3;
                     T e2[NC];
 #pragma unroll
-                    for (int q = 0; q < NC; ++q) e2[q] = f2[q * N3] + (T)a.macroW2[bb * 9 + q];
+                    for (int q = 0; q < NC; ++q) e2[q] = f2[q * SB] + (T)a.macroW2[bb * 9 + q];
                     T sg[NC];
                     iso_stress<T, NC>(e, (T)a.lam[ph], (T)a.mu[ph], sg);
                     T acc = T(0);
@@ -194,7 +188,7 @@ __global__ void __launch_bounds__(256) k_axis3(Ax3Args<T> a) {
                         eacc[rr] += (double)en;
                     }
 #pragma unroll
-                    for (int q = 0; q < NC; ++q) f[q * N3] = sg[q];
+                    for (int q = 0; q < NC; ++q) f[q * SB] = sg[q];
                 }
             }
         } else if constexpr (OPK == OP_NH_APPLY) {
@@ -203,11 +197,11 @@ __global__ void __launch_bounds__(256) k_axis3(Ax3Args<T> a) {
             const T lam = (T)a.lam[ph], mu = (T)a.mu[ph];
             for (int rr = 0; rr < RB; ++rr) {
                 const int bb = g * RB + rr;
-                if (a.cg && a.cg[bb].done) continue;
-                T* f = sreal + (long long)((lv * RB + rr) * NC) * N3 + x3;
+                if (rhs_done(rr)) continue;
+                T* f = slot_ptr(0, (lv * RB + rr) * NC) + x3;
                 T G[9];
 #pragma unroll
-                for (int q = 0; q < 9; ++q) G[q] = f[q * N3] + (T)a.macroW[bb * 9 + q];
+                for (int q = 0; q < 9; ++q) G[q] = f[q * SB] + (T)a.macroW[bb * 9 + q];
                 const T* tn = a.tan_in + ((long long)bb * d.V + vox) * 10;
                 T sg[9];
                 nh_apply<T>(tn, mu, lam, G, sg);
@@ -218,17 +212,17 @@ __global__ void __launch_bounds__(256) k_axis3(Ax3Args<T> a) {
                     eacc[rr] += (double)en;
                 }
 #pragma unroll
-                for (int q = 0; q < 9; ++q) f[q * N3] = sg[q];
+                for (int q = 0; q < 9; ++q) f[q * SB] = sg[q];
             }
         } else if constexpr (OPK == OP_NH_UPDATE) {
             const long long mv = (long long)mat * d.V + vox;
             const int ph = a.phase[mv];
             for (int rr = 0; rr < RB; ++rr) {
                 const int bb = g * RB + rr;
-                T* f = sreal + (long long)((lv * RB + rr) * NC) * N3 + x3;
+                T* f = slot_ptr(0, (lv * RB + rr) * NC) + x3;
                 double F[9], Pk[9], tn[10];
 #pragma unroll
-                for (int q = 0; q < 9; ++q) F[q] = (double)f[q * N3] + a.macroW[bb * 9 + q];
+                for (int q = 0; q < 9; ++q) F[q] = (double)f[q * SB] + a.macroW[bb * 9 + q];
                 const bool ok = nh_stress(F, a.mu[ph], a.lam[ph], Pk, tn);
                 if (!ok) atomicOr(a.err, 1u);
                 const long long to = ((long long)bb * d.V + vox) * 10;
@@ -238,16 +232,16 @@ __global__ void __launch_bounds__(256) k_axis3(Ax3Args<T> a) {
                     if (a.tan_out_d) a.tan_out_d[to + q] = tn[q];
                 }
 #pragma unroll
-                for (int q = 0; q < 9; ++q) f[q * N3] = (T)Pk[q];
+                for (int q = 0; q < 9; ++q) f[q * SB] = (T)Pk[q];
             }
         } else if constexpr (OPK == OP_CP_APPLY) {
             for (int rr = 0; rr < RB; ++rr) {
                 const int bb = g * RB + rr;
-                if (a.cg && a.cg[bb].done) continue;
-                T* f = sreal + (long long)((lv * RB + rr) * NC) * N3 + x3;
+                if (rhs_done(rr)) continue;
+                T* f = slot_ptr(0, (lv * RB + rr) * NC) + x3;
                 T e[6];
 #pragma unroll
-                for (int q = 0; q < 6; ++q) e[q] = f[q * N3] + (T)a.macroW[bb * 9 + q];
+                for (int q = 0; q < 6; ++q) e[q] = f[q * SB] + (T)a.macroW[bb * 9 + q];
                 const T* tn = a.tan_in + ((long long)bb * d.V + vox) * 21;
                 T sg[6];
                 cp_apply<T>(tn, e, sg);
@@ -258,17 +252,17 @@ __global__ void __launch_bounds__(256) k_axis3(Ax3Args<T> a) {
                     eacc[rr] += (double)en;
                 }
 #pragma unroll
-                for (int q = 0; q < 6; ++q) f[q * N3] = sg[q];
+                for (int q = 0; q < 6; ++q) f[q * SB] = sg[q];
             }
         } else if constexpr (OPK == OP_CP_UPDATE) {
             const long long mv = (long long)mat * d.V + vox;
             const int gr = a.phase[mv];
             for (int rr = 0; rr < RB; ++rr) {
                 const int bb = g * RB + rr;
-                T* f = sreal + (long long)((lv * RB + rr) * NC) * N3 + x3;
+                T* f = slot_ptr(0, (lv * RB + rr) * NC) + x3;
                 double e[6];
 #pragma unroll
-                for (int q = 0; q < 6; ++q) e[q] = (double)f[q * N3] + a.macroW[bb * 9 + q];
+                for (int q = 0; q < 6; ++q) e[q] = (double)f[q * SB] + a.macroW[bb * 9 + q];
                 const long long so = ((long long)bb * d.V + vox) * 6;
                 double sg[6], tn[21], ep[6];
                 const bool ok = cp_update(a.grains[gr], a.cp, e, a.eps_p + so, a.sig_prev + so, sg, tn, ep);
@@ -283,7 +277,7 @@ __global__ void __launch_bounds__(256) k_axis3(Ax3Args<T> a) {
                 }
                 const double ir2 = 0.70710678118654752440084436210485;
 #pragma unroll
-                for (int q = 0; q < 6; ++q) f[q * N3] = (T)(q < 3 ? sg[q] : ir2 * sg[q]);
+                for (int q = 0; q < 6; ++q) f[q * SB] = (T)(q < 3 ? sg[q] : ir2 * sg[q]);
             }
         }
     }
@@ -308,16 +302,16 @@ __global__ void __launch_bounds__(256) k_axis3(Ax3Args<T> a) {
             if (is_last && t < RB) {
                 __threadfence();
                 const int bb = g * RB + t;
-                double s = 0.0;
-                for (int k = 0; k < nblk; ++k) s += __ldcg(a.partials + (long long)bb * nblk + k);
+                double sum = 0.0;
+                for (int k = 0; k < nblk; ++k) sum += __ldcg(a.partials + (long long)bb * nblk + k);
                 CgState& cs = a.cg[bb];
                 if (!cs.done) {
-                    cs.pq = s;
-                    if (s > 0.0 && s == s) {
-                        cs.alpha = cs.rho / s;
+                    cs.pq = sum;
+                    if (sum > 0.0 && sum == sum) {
+                        cs.alpha = cs.rho / sum;
                     } else {
                         cs.alpha = 0.0;
-                        cs.flags |= (s == s) ? 1 : 2;
+                        cs.flags |= (sum == sum) ? 1 : 2;
                         cs.done = 1;
                     }
                 }
@@ -328,8 +322,13 @@ __global__ void __launch_bounds__(256) k_axis3(Ax3Args<T> a) {
     if constexpr (!OpInfo<OPK>::forward) return;
     __syncthreads();
 
-    // ---- R2C
-    {
+    // ---- R2C per slot, result staged back into the slot buffer
+    for (int rd = 0; rd < rounds; ++rd) {
+        const int sl = rd * per_round + t / P;
+        const int p = t % P;
+        const bool ok = sl < NSLOT && t / P < per_round;
+        T* my = ok ? slot_ptr(0, sl) : scratch;
+        cplx<T>* myc = reinterpret_cast<cplx<T>*>(my);
         cplx<T> v[R];
 #pragma unroll
         for (int r = 0; r < R; ++r) {
@@ -338,27 +337,43 @@ __global__ void __launch_bounds__(256) k_axis3(Ax3Args<T> a) {
         }
         ColFFT<T, M, R, -1>::run(v, myc, 1, p, a.tw.tm);
         __syncthreads();
-        if (slot_ok) {
 #pragma unroll
-            for (int r = 0; r < R; ++r) myc[p + r * P] = v[r];
+        for (int r = 0; r < R; ++r) myc[p + r * P] = v[r];
+        __syncthreads();
+        cplx<T> X[R];
+        cplx<T> XM = zero_c<T>();
+        const T half = T(0.5);
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int k = p + r * P;
+            const cplx<T> Zk = myc[k];
+            const cplx<T> Zc = conjg(myc[(M - k) & (M - 1)]);
+            const cplx<T> e = ldg_c(a.tw.t3 + k);  // e^{-2 pi i k / n}
+            const cplx<T> dl = e * (Zk - Zc);
+            X[r] = mk(half * (Zk.x + Zc.x) + half * dl.y, half * (Zk.y + Zc.y) - half * dl.x);
+        }
+        if (p == 0) {
+            const cplx<T> Z0 = myc[0];
+            XM = mk(Z0.x - Z0.y, T(0));
         }
         __syncthreads();
-        if (valid) {
-            const T half = T(0.5);
 #pragma unroll
-            for (int r = 0; r < R; ++r) {
-                const int k = p + r * P;
-                const cplx<T> Zk = myc[k];
-                const cplx<T> Zc = conjg(myc[(M - k) & (M - 1)]);
-                const cplx<T> e = ldg_c(a.tw.t3 + k);  // e^{-2 pi i k / n}
-                const cplx<T> dlt = e * (Zk - Zc);
-                // X = (Zk + Zc)/2 - (i/2) dlt
-                stc(a.W + base + k, mk(half * (Zk.x + Zc.x) + half * dlt.y, half * (Zk.y + Zc.y) - half * dlt.x));
-            }
-            if (p == 0) {
-                const cplx<T> Z0 = myc[0];
-                stc(a.W + base + M, mk(Z0.x - Z0.y, T(0)));
-            }
+        for (int r = 0; r < R; ++r) myc[p + r * P] = X[r];
+        if (p == 0) myc[M] = XM;
+    }
+    __syncthreads();
+
+    // ---- cooperative store
+    {
+        const int per_rc = lines_here * H;
+        for (int i = t; i < RB * NC * per_rc; i += nthr) {
+            const int rc = i / per_rc, rest = i - rc * per_rc;
+            const int rl = rc / NC, c = rc - rl * NC;
+            if (rhs_done(rl)) continue;
+            const int ll = rest / H, k = rest - ll * H;
+            const int b = g * RB + rl;
+            stc(a.W + ((long long)(b * NC + c) * nlines + line0) * H + rest,
+                reinterpret_cast<const cplx<T>*>(slot_ptr(0, (ll * RB + rl) * NC + c))[k]);
         }
     }
 }

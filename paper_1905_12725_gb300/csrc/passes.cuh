@@ -158,8 +158,8 @@ struct Ax1InvArgs {
 };
 
 template <typename T, int N1, int NC, int MODE>
-__global__ void __launch_bounds__(256) k_axis1_inv(Ax1InvArgs<T> a) {
-    constexpr int R = RadixFor<T, N1>::value;
+__global__ void __launch_bounds__(256, 2) k_axis1_inv(Ax1InvArgs<T> a) {
+    constexpr int R = RadixAx1<T, N1>::value;
     constexpr int P = N1 / R;
     extern __shared__ __align__(16) unsigned char smraw[];
     cplx<T>* sm = reinterpret_cast<cplx<T>*>(smraw);
@@ -306,8 +306,8 @@ struct Ax1FwdArgs {
 };
 
 template <typename T, int N1, int NC, int MODE>
-__global__ void __launch_bounds__(256) k_axis1_fwd(Ax1FwdArgs<T> a) {
-    constexpr int R = RadixFor<T, N1>::value;
+__global__ void __launch_bounds__(256, 2) k_axis1_fwd(Ax1FwdArgs<T> a) {
+    constexpr int R = RadixAx1<T, N1>::value;
     constexpr int P = N1 / R;
     extern __shared__ __align__(16) unsigned char smraw[];
     cplx<T>* sm = reinterpret_cast<cplx<T>*>(smraw);
