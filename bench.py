@@ -188,7 +188,7 @@ def unit_mandel(m):
     return t
 
 
-def operator_256(torch, dbfft, peak):
+def operator_256(torch, dbfft, peak, iters=40):
     """FP32 inner-CG pass chain on a 256^3 linear two-phase RVE (one right-hand side)."""
     from paper_1905_12725_gb300 import synth
     n = 256
@@ -199,7 +199,7 @@ def operator_256(torch, dbfft, peak):
     eps = np.zeros((1, 3, 3))
     eps[0, 0, 0] = 1e-3
     s = dbfft.Solver((n, n, n), phase, dbfft.iso_phases([1.0, 100.0], [0.3, 0.3]), eps,
-                     precision=dbfft.DBFFT_MIXED, tol=1e-30, eta_inner=1e-30, max_iter=40, max_newton=1)
+                     precision=dbfft.DBFFT_MIXED, tol=1e-30, eta_inner=1e-30, max_iter=iters, max_newton=1)
     s.solve_increment(0, allow_not_converged=True)  # warm-up
     s.profile(True)
     t0 = time.perf_counter()
@@ -402,7 +402,22 @@ def main():
     ap.add_argument("--ref-iters", type=int, default=40)
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-256", action="store_true")
+    ap.add_argument("--case", default="", choices=["", "op256", "c2"],
+                    help="run one sub-measurement only (for profiler captures): op256 = 256^3 FP32 CG "
+                         "pass chain, c2 = one mixed batched 64^3 solve")
     args = ap.parse_args()
+    if args.case:
+        import torch
+        from paper_1905_12725_gb300 import dbfft
+        torch.cuda.set_device(0)
+        if args.case == "op256":
+            print(json.dumps(operator_256(torch, dbfft, _peaks()[0], iters=args.steps)), flush=True)
+        else:
+            s = make_solver(workload_inputs(), dbfft.DBFFT_MIXED, 6)
+            for _ in range(max(args.steps, 1)):
+                _, rep = s.homogenized_tangent()
+            print(json.dumps(rep), flush=True)
+        return
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))

@@ -68,6 +68,9 @@ struct dbfft_ctx {
     double* mu = nullptr;
     double* lam1 = nullptr;  // per unit Young's modulus (adjoint)
     double* mu1 = nullptr;
+    float* lam_f = nullptr;  // FP32 copies for the FP32 passes
+    float* mu_f = nullptr;
+    float* scale_f = nullptr;
     std::vector<double> lam_h, mu_h, E_h;
     CpGrain* grains = nullptr;
     CpParams cp{};
@@ -92,6 +95,7 @@ struct dbfft_ctx {
     double* sigf = nullptr;
     double* sig0 = nullptr;
     double* macroW = nullptr;
+    float* macroWf = nullptr;  // FP32 copy read by the FP32 passes
     double* macroW2 = nullptr;
     double* scal = nullptr;  // [B] scale factors
     CgState* cg = nullptr;
@@ -316,6 +320,7 @@ bool precond_from(const dbfft_ctx* ctx, const double C[3][3][3][3], PrecondData&
         for (int b = 0; b < 6; ++b) {
             const int i = ik[a][0], k = ik[a][1], j = jl[b][0], l = jl[b][1];
             pd.coef[a][b] = (j == l) ? C[i][j][k][j] : (C[i][j][k][l] + C[i][l][k][j]);
+            pd.coef_f[a][b] = (float)pd.coef[a][b];
         }
     const int ne = ctx->dims.ne;
     if (ne > 0) {
@@ -545,9 +550,15 @@ Ax3Args<T> ax3_base(dbfft_ctx* ctx, cplx<T>* W) {
     a.RB = ctx->RB;
     a.L = ax3_lines(ctx->n3, ctx->nc, ctx->RB, sizeof(T) == 8);
     a.phase = ctx->phase;
-    a.scale = ctx->scale;
-    a.lam = ctx->lam;
-    a.mu = ctx->mu;
+    if constexpr (sizeof(T) == 4) {
+        a.scale = ctx->scale_f;
+        a.lam = ctx->lam_f;
+        a.mu = ctx->mu_f;
+    } else {
+        a.scale = ctx->scale;
+        a.lam = ctx->lam;
+        a.mu = ctx->mu;
+    }
     a.grains = ctx->grains;
     a.cp = ctx->cp;
     a.err = ctx->errw;
@@ -556,7 +567,7 @@ Ax3Args<T> ax3_base(dbfft_ctx* ctx, cplx<T>* W) {
 
 // One operator application in precision T: out = K u (flags: macro e_in/e_out).
 template <typename T>
-dbfft_status chain_apply(dbfft_ctx* ctx, const cplx<T>* u, const double* macroW, cplx<T>* out, double* e_out) {
+dbfft_status chain_apply(dbfft_ctx* ctx, const cplx<T>* u, const T* macroW, cplx<T>* out, double* e_out) {
     cplx<T>* W = reinterpret_cast<cplx<T>*>(ctx->W);
     const bool dbl = sizeof(T) == 8;
     const double cp = cpass(ctx, dbl, ctx->B);
@@ -594,7 +605,7 @@ dbfft_status chain_residual(dbfft_ctx* ctx, const cplx<double>* x, const double*
     const double cp = cpass(ctx, true, ctx->B);
     const int nc = ctx->nc;
     TRY(run(ctx, "macro", 0.0,
-            [&] { return launch_macro(ctx->B, ctx->nc, ctx->activeflag, ctx->fU, xe, ctx->macroW, ctx->stream); }));
+            [&] { return launch_macro(ctx->B, ctx->nc, ctx->activeflag, ctx->fU, xe, ctx->macroW, ctx->macroWf, ctx->stream); }));
     Ax1InvArgs<double> a1{ctx->dims, freq<double>(ctx), twid<double>(ctx), x, nullptr, W, nullptr, ctx->pre};
     TRY(run(ctx, "axis1_inv_f64", (3 + nc) * cp, [&] { return launch_ax1_inv<double>(AX1_PLAIN, a1, ctx->stream); }));
     Ax2Args<double> a2{ctx->dims, twid<double>(ctx), W, nullptr};
@@ -664,6 +675,7 @@ dbfft_status inner_cg(dbfft_ctx* ctx, double tol, long long& it_sum, int& it_max
     ai.r_e = ctx->re_i;
     ai.p_e = ctx->pe_i;
     ai.macroW = ctx->macroW;
+    ai.macroWf = ctx->macroWf;
     ai.cg = ctx->cg;
     ai.pre = ctx->pre;
     ai.partials = ctx->partials;
@@ -680,7 +692,8 @@ dbfft_status inner_cg(dbfft_ctx* ctx, double tol, long long& it_sum, int& it_max
     Ax1InvArgs<T> a1{ctx->dims, freq<T>(ctx), twid<T>(ctx), ri, pi, W, ctx->cg, ctx->pre};
     Ax2Args<T> a2{ctx->dims, twid<T>(ctx), W, ctx->cg};
     Ax3Args<T> a3 = ax3_base<T>(ctx, W);
-    a3.macroW = ctx->macroW;
+    if constexpr (sizeof(T) == 4) a3.macroW = ctx->macroWf;
+    else a3.macroW = ctx->macroW;
     a3.cg = ctx->cg;
     a3.partials = ctx->partials;
     a3.counters = ctx->counters;
@@ -698,6 +711,7 @@ dbfft_status inner_cg(dbfft_ctx* ctx, double tol, long long& it_sum, int& it_max
     a5.x_e = ctx->xe_i;
     a5.p_e = ctx->pe_i;
     a5.macroW = ctx->macroW;
+    a5.macroWf = ctx->macroWf;
     a5.cg = ctx->cg;
     a5.pre = ctx->pre;
     a5.partials = ctx->partials;
@@ -1046,6 +1060,10 @@ static dbfft_status create_impl(dbfft_ctx* ctx, const dbfft_grid* grid, const db
             if (!std::isfinite(mat->E_scale[i])) return fail(ctx, DBFFT_E_NONFINITE, "non-finite E_scale");
         TRY(dalloc_t(ctx, nvox, &ctx->scale));
         CK(cudaMemcpyAsync(ctx->scale, mat->E_scale, nvox * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+        std::vector<float> sf(mat->E_scale, mat->E_scale + nvox);
+        TRY(dalloc_t(ctx, nvox, &ctx->scale_f));
+        CK(cudaMemcpyAsync(ctx->scale_f, sf.data(), nvox * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
     }
     const int np = mat->n_phases;
     ctx->lam_h.assign(np, 0.0);
@@ -1081,6 +1099,14 @@ static dbfft_status create_impl(dbfft_ctx* ctx, const dbfft_grid* grid, const db
     TRY(dalloc_t(ctx, np, &ctx->mu1));
     CK(cudaMemcpyAsync(ctx->lam, ctx->lam_h.data(), np * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
     CK(cudaMemcpyAsync(ctx->mu, ctx->mu_h.data(), np * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+    {
+        std::vector<float> lf(ctx->lam_h.begin(), ctx->lam_h.end()), mf(ctx->mu_h.begin(), ctx->mu_h.end());
+        TRY(dalloc_t(ctx, np, &ctx->lam_f));
+        TRY(dalloc_t(ctx, np, &ctx->mu_f));
+        CK(cudaMemcpyAsync(ctx->lam_f, lf.data(), np * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
+        CK(cudaMemcpyAsync(ctx->mu_f, mf.data(), np * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+    }
     CK(cudaMemcpyAsync(ctx->lam1, lam1.data(), np * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
     CK(cudaMemcpyAsync(ctx->mu1, mu1.data(), np * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
@@ -1164,6 +1190,7 @@ static dbfft_status create_impl(dbfft_ctx* ctx, const dbfft_grid* grid, const db
     double** smalls[] = {&ctx->xe64, &ctx->re64, &ctx->xe_i, &ctx->re_i, &ctx->pe_i, &ctx->fU,
                          &ctx->sigf, &ctx->sig0, &ctx->macroW, &ctx->macroW2};
     for (double** s : smalls) TRY(dalloc_t(ctx, (size_t)ctx->B * 9, s));
+    TRY(dalloc_t(ctx, (size_t)ctx->B * 9, &ctx->macroWf));
     TRY(dalloc_t(ctx, (size_t)ctx->B, &ctx->scal));
     TRY(dalloc_t(ctx, (size_t)ctx->B, &ctx->cg));
     TRY(dalloc_t(ctx, (size_t)ctx->B, &ctx->counters));
@@ -1319,9 +1346,9 @@ dbfft_status dbfft_apply(dbfft_ctx* ctx, int flags, const void* u_hat, const voi
         if (stored64 == f32) return fail(ctx, DBFFT_E_STATE, "the tangent is stored in the other precision");
     }
     TRY(run(ctx, "macro", 0.0,
-            [&] { return launch_macro(ctx->B, ctx->nc, ctx->activeflag, nullptr, ein, ctx->macroW, ctx->stream); }));
+            [&] { return launch_macro(ctx->B, ctx->nc, ctx->activeflag, nullptr, ein, ctx->macroW, ctx->macroWf, ctx->stream); }));
     if (f32)
-        TRY(chain_apply<float>(ctx, reinterpret_cast<const cplx<float>*>(u_hat), ctx->macroW,
+        TRY(chain_apply<float>(ctx, reinterpret_cast<const cplx<float>*>(u_hat), ctx->macroWf,
                                reinterpret_cast<cplx<float>*>(out), eout));
     else
         TRY(chain_apply<double>(ctx, reinterpret_cast<const cplx<double>*>(u_hat), ctx->macroW,

@@ -32,7 +32,14 @@ struct CgState {
 struct PrecondData {
     double coef[6][6];
     double Me[9][9];
+    float coef_f[6][6];  // FP32 copy for the FP32 passes (no FP64 work per frequency)
 };
+
+template <typename T>
+__host__ __device__ __forceinline__ const T (*pcoef(const PrecondData& pd))[6] {
+    if constexpr (sizeof(T) == 4) return pd.coef_f;
+    else return pd.coef;
+}
 
 // Everything a pass needs about the grid and the macro basis.
 struct Dims {

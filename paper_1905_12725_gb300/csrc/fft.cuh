@@ -54,6 +54,22 @@ template <typename T> __device__ __forceinline__ cplx<T> ldg_c(const cplx<T>* p)
     return mk<T>(v.x, v.y);
 }
 
+// Asynchronous global -> shared copy of one complex value (cp.async): the
+// copies of a thread stay in flight together until cp_async_wait_all().
+template <typename T>
+__device__ __forceinline__ void cp_async_c(cplx<T>* smem_dst, const cplx<T>* gsrc) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem_dst);
+    if constexpr (sizeof(T) == 4) {
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gsrc) : "memory");
+    } else {
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gsrc) : "memory");
+    }
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+}
+
 // cos(2 pi m / 32) for m = 0..8 (first octant), mathematical constants.
 __device__ __forceinline__ constexpr double c32(int m) {
     return m == 0 ? 1.0
@@ -153,16 +169,26 @@ struct RegDFT {
     }
 };
 
+// Padded position of a contiguous (SS = 1) exchange buffer: one spare entry
+// after every 128 bytes, so that the Stockham write pattern (stride R
+// entries between neighbouring threads) spreads over the shared-memory banks.
+template <typename T>
+__host__ __device__ constexpr int pad_shift() { return sizeof(T) == 8 ? 3 : 4; }
+template <typename T>
+__host__ __device__ constexpr int padded_len(int n) { return n + (n >> pad_shift<T>()) + 1; }
+
 // Column FFT of length N with P = N / R threads per column.
 //  v:   the thread's R registers, holding x[p + r P] on entry and X[p + r P]
 //       on exit.
 //  sm:  shared exchange buffer for this column: element i lives at
-//       sm[i * SS] (SS = stride between positions); it must hold N entries
-//       and is only touched when there is more than one stage.
+//       sm[i * SS] (SS = stride between positions) or, when PAD, at
+//       sm[i + i / (128 bytes)] (SS must be 1 then; the buffer needs
+//       padded_len(N) entries); it is only touched when there is more than
+//       one stage.
 //  tw:  twiddle table of length N (forward sign).
-// Every thread of the block must call this (it contains __syncthreads()),
-// including threads whose column is out of range.
-template <typename T, int N, int R, int DIR>
+// Every thread of the block (of the warp, when WARP) must call this, including
+// threads whose column is out of range.
+template <typename T, int N, int R, int DIR, bool PAD = false, bool WARP = false>
 struct ColFFT {
     static_assert(N >= R, "radix larger than the transform");
     static constexpr int P = N / R;
@@ -171,6 +197,16 @@ struct ColFFT {
     static constexpr int NST = (LOGN + LOGR - 1) / LOGR;
     static constexpr int LASTR = 1 << (LOGN - (NST - 1) * LOGR);
 
+    // WARP: the P threads of a column are one aligned group inside a warp, so
+    // the exchange only needs the warp to agree.
+    __device__ __forceinline__ static void sync() {
+        if constexpr (WARP) __syncwarp();
+        else __syncthreads();
+    }
+    __device__ __forceinline__ static int at(int i, int SS) {
+        if constexpr (PAD) return i + (i >> pad_shift<T>());
+        return i * SS;
+    }
     template <int S, int NS>
     __device__ __forceinline__ static void stage(cplx<T>* v, cplx<T>* sm, int SS, int p, const cplx<T>* tw) {
         if constexpr (S < NST) {
@@ -195,12 +231,12 @@ struct ColFFT {
                 RegDFT<R, DIR, 1, 0, T>::run(v);
                 if constexpr (S < NST - 1) {
                     const int base = (p / NS) * NS * R + (p % NS);
-                    __syncthreads();
+                    sync();
 #pragma unroll
-                    for (int q = 0; q < R; ++q) sm[(base + q * NS) * SS] = v[q];
-                    __syncthreads();
+                    for (int q = 0; q < R; ++q) sm[at(base + q * NS, SS)] = v[q];
+                    sync();
 #pragma unroll
-                    for (int r = 0; r < R; ++r) v[r] = sm[(p + r * P) * SS];
+                    for (int r = 0; r < R; ++r) v[r] = sm[at(p + r * P, SS)];
                 }
             }
             stage<S + 1, NS * R>(v, sm, SS, p, tw);
@@ -219,12 +255,14 @@ struct ColFFT {
 };
 
 // Radix per pass, transform length and precision (host and device agree on it).
-//  axis 1 (passes 1 and 5) keeps several components live per thread, so it
-//  uses radix 8 to stay at two CTAs per SM; axis 2 and the half-length
-//  transform of axis 3 use radix 16 in FP32 and 8 in FP64.
+//  axis 1 (passes 1 and 5) and the half-length transform of axis 3 keep
+//  their radix small so that several CTAs fit on an SM; axis 2 (a pure
+//  transform) uses radix 16 in FP32 and 8 in FP64.
 __host__ __device__ constexpr int radix_ax1(int n, bool dbl) { return dbl ? (n < 4 ? n : 4) : (n < 8 ? n : 8); }
 __host__ __device__ constexpr int radix_ax2(int n, bool dbl) { return dbl ? (n < 8 ? n : 8) : (n < 16 ? n : 16); }
+__host__ __device__ constexpr int radix_ax3(int m, bool dbl) { return dbl ? (m < 4 ? m : 4) : (m < 8 ? m : 8); }
 template <typename T, int N> struct RadixAx1 { static constexpr int value = radix_ax1(N, sizeof(T) == 8); };
+template <typename T, int M> struct RadixAx3 { static constexpr int value = radix_ax3(M, sizeof(T) == 8); };
 template <typename T, int N> struct RadixFor { static constexpr int value = radix_ax2(N, sizeof(T) == 8); };
 
 }  // namespace dbfft

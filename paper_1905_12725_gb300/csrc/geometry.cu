@@ -8,10 +8,8 @@ bool supported_len(int n) { return n == 8 || n == 16 || n == 32 || n == 64 || n 
 static int radix_for(int n, bool dbl) { return radix_ax2(n, dbl); }
 
 int ax1_tile(int n1, bool dbl) {
-    const int P = n1 / radix_ax1(n1, dbl);  // threads per column; the block is tw x P = 256 threads
-    int tw = 256 / P;
-    if (tw > 256) tw = 256;
-    return tw;
+    const int P = n1 / radix_ax1(n1, dbl);  // threads per column; the block is tw x P = AX1_THREADS
+    return AX1_THREADS / P;
 }
 int ax2_tile(int n2, bool dbl) {
     const int P = n2 / radix_ax2(n2, dbl);
@@ -21,10 +19,20 @@ int ax2_tile(int n2, bool dbl) {
     return tw;
 }
 
+static int slot_bytes(int n3, bool dbl) {
+    // mirrors ax3_slot_cplx<T, N3>() in pass3.cuh
+    const int m = n3 / 2;
+    const int csz = dbl ? 16 : 8;
+    const int pl = m + (m >> (dbl ? 3 : 4)) + 1;
+    int n = pl > m + 1 ? pl : m + 1;
+    while (((n * csz / 4) & 31) != 16) ++n;
+    return n * csz;
+}
+
 int ax3_lines(int n3, int nc, int rb, bool dbl, int nfields) {
-    // real-space tiles of one CTA within ~96 KB so that two CTAs fit on an SM
-    const size_t sb = (size_t)(n3 + 2) * (dbl ? 8 : 4);
-    long long L = (long long)(96 * 1024) / ((long long)sb * rb * nc * nfields);
+    // real-space tiles of one CTA within ~56 KB so that four CTAs fit on an SM
+    const size_t sb = (size_t)slot_bytes(n3, dbl);
+    long long L = (long long)(56 * 1024) / ((long long)sb * rb * nc * nfields);
     if (L < 1) L = 1;
     if (L > 32) L = 32;
     return (int)L;
@@ -32,7 +40,7 @@ int ax3_lines(int n3, int nc, int rb, bool dbl, int nfields) {
 
 int ax3_threads_per_line(int n3, int nc, int rb, bool dbl) {
     const int m = n3 / 2;
-    return (m / radix_for(m, dbl)) * rb * nc;
+    return (m / radix_ax3(m, dbl)) * rb * nc;
 }
 
 size_t ax3_smem(int n3, int nc, int rb, int lines, bool dbl, bool two_fields) {

@@ -6,19 +6,25 @@ namespace dbfft {
 
 template <typename K>
 static void allow_smem(K kernel, size_t smem) {
-    // the axis-1 exchange tiles stay below 48 KB, so no opt-in is needed
-    (void)kernel;
-    (void)smem;
+    if (smem > 48 * 1024) cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+template <typename T, int N1>
+static size_t ax1_smem() {
+    constexpr int R = RadixAx1<T, N1>::value;
+    constexpr int P = N1 / R;
+    constexpr int TW = AX1_THREADS / P;
+    return ((size_t)N1 * TW + 3 * (size_t)R * AX1_THREADS) * sizeof(cplx<T>);
 }
 
 template <typename T, int N1, int NC>
 static cudaError_t ax1_inv_n(int mode, const Ax1InvArgs<T>& a, cudaStream_t s) {
     constexpr int R = RadixAx1<T, N1>::value;
     constexpr int P = N1 / R;
-    const int TW = ax1_tile(N1, sizeof(T) == 8);
+    constexpr int TW = AX1_THREADS / P;
     const dim3 block(TW, P);
     const dim3 grid((unsigned)((a.d.plane + TW - 1) / TW), (unsigned)a.d.B);
-    const size_t smem = (ColFFT<T, N1, R, 1>::NST > 1) ? (size_t)N1 * TW * sizeof(cplx<T>) : 0;
+    const size_t smem = ax1_smem<T, N1>();
     if (mode == AX1_CG) {
         allow_smem(k_axis1_inv<T, N1, NC, AX1_CG>, smem);
         k_axis1_inv<T, N1, NC, AX1_CG><<<grid, block, smem, s>>>(a);
@@ -33,10 +39,10 @@ template <typename T, int N1, int NC>
 static cudaError_t ax1_fwd_n(int mode, const Ax1FwdArgs<T>& a, cudaStream_t s) {
     constexpr int R = RadixAx1<T, N1>::value;
     constexpr int P = N1 / R;
-    const int TW = ax1_tile(N1, sizeof(T) == 8);
+    constexpr int TW = AX1_THREADS / P;
     const dim3 block(TW, P);
     const dim3 grid((unsigned)((a.d.plane + TW - 1) / TW), (unsigned)a.d.B);
-    const size_t smem = (ColFFT<T, N1, R, 1>::NST > 1) ? (size_t)N1 * TW * sizeof(cplx<T>) : 0;
+    const size_t smem = ax1_smem<T, N1>();
     if (mode == AX5_CG) {
         allow_smem(k_axis1_fwd<T, N1, NC, AX5_CG>, smem);
         k_axis1_fwd<T, N1, NC, AX5_CG><<<grid, block, smem, s>>>(a);

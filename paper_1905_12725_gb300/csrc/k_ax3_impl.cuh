@@ -10,7 +10,7 @@ static cudaError_t ax3_n(const Ax3Args<T>& a, cudaStream_t s) {
     const long long nlines = (long long)a.d.n1 * a.d.n2;
     const dim3 grid((unsigned)((nlines + a.L - 1) / a.L), (unsigned)(a.d.B / a.RB));
     const int nf = OPK == OP_ADJ ? 2 : 1;
-    const size_t smem = ((size_t)nf * a.L * a.RB * NC + 1) * (N3 + 2) * sizeof(T);
+    const size_t smem = ((size_t)nf * a.L * a.RB * NC + 1) * ax3_slot_cplx<T, N3>() * sizeof(cplx<T>);
     static int max_dyn = -1;
     if (max_dyn < 0) {  // opt in to large dynamic shared memory: 227 KB per block minus the static part
         cudaFuncAttributes fa;

@@ -6,18 +6,20 @@
 
 namespace dbfft {
 
-__global__ void k_macro(int B, int nc, const int* activeflag, const double* fU, const double* e, double* macroW) {
+__global__ void k_macro(int B, int nc, const int* activeflag, const double* fU, const double* e, double* macroW,
+                        float* macroWf) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= B * 9) return;
     const int q = i % 9;
     double v = fU ? fU[i] : 0.0;
     if (e && activeflag[q]) v += ((nc == 6 && q >= 3) ? 0.70710678118654752440084436210485 : 1.0) * e[i];
     macroW[i] = v;
+    if (macroWf) macroWf[i] = (float)v;
 }
 
 cudaError_t launch_macro(int B, int nc, const int* activeflag, const double* fU, const double* e, double* macroW,
-                         cudaStream_t s) {
-    k_macro<<<(B * 9 + 127) / 128, 128, 0, s>>>(B, nc, activeflag, fU, e, macroW);
+                         float* macroWf, cudaStream_t s) {
+    k_macro<<<(B * 9 + 127) / 128, 128, 0, s>>>(B, nc, activeflag, fU, e, macroW, macroWf);
     return cudaGetLastError();
 }
 
@@ -96,7 +98,7 @@ __global__ void k_precond_field(Dims d, Freq<T> f, const PrecondData* pre, const
         const int k2 = (int)(rem / d.h), k3 = (int)(rem - (long long)k2 * d.h);
         cplx<T> r[3], z[3];
         for (int c = 0; c < 3; ++c) r[c] = u[(long long)(b * 3 + c) * d.H + i];
-        precond_apply<T>(pd.coef, f.xi1[k1], f.xi2[k2], f.xi3[k3], (T)(1.0 / d.invN), r, z);
+        precond_apply<T>(pcoef<T>(pd), f.xi1[k1], f.xi2[k2], f.xi3[k3], (T)(1.0 / d.invN), r, z);
         for (int c = 0; c < 3; ++c) out[(long long)(b * 3 + c) * d.H + i] = z[c];
     }
     if (blockIdx.x == 0 && threadIdx.x == 0 && e_out) {

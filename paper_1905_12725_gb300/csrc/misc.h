@@ -4,7 +4,7 @@
 
 namespace dbfft {
 cudaError_t launch_macro(int B, int nc, const int* activeflag, const double* fU, const double* e, double* macroW,
-                         cudaStream_t s);
+                         float* macroWf, cudaStream_t s);
 template <typename Ti>
 cudaError_t launch_to_inner(const Dims& d, const cplx<double>* r64, const double* re64, const double* sc, cplx<Ti>* ri,
                             double* re_i, cplx<Ti>* xi, double* xe_i, cudaStream_t s);

@@ -33,17 +33,17 @@ struct Ax3Args {
     const cplx<T>* W2;     // OP_ADJ: adjoint strain field in W layout
     int RB;                // right-hand sides per CTA (divides Rm)
     int L;                 // grid lines per CTA
-    const double* macroW;  // [B][9] constant field added before the op (W components)
-    const double* macroW2; // OP_ADJ: macro part of the adjoint field
+    const T* macroW;       // [B][9] constant field added before the op (W components)
+    const T* macroW2;      // OP_ADJ: macro part of the adjoint field
     // CG curvature (apply ops only; null outside CG)
     CgState* cg;
     double* partials;      // [B][nblk]
     unsigned* counters;    // [B / RB]
     // materials
     const uint16_t* phase; // [Bm][V]
-    const double* scale;   // [Bm][V] or null
-    const double* lam;     // per phase
-    const double* mu;
+    const T* scale;        // [Bm][V] or null
+    const T* lam;          // per phase (in the pass precision)
+    const T* mu;
     // nonlinear tangent / state
     const T* tan_in;       // apply ops: [B][V][ntan]
     float* tan_out_f;      // update ops: tangent written in FP32 (or null)
@@ -63,6 +63,18 @@ template <int OPK> struct OpInfo {
     static constexpr bool apply = OPK == OP_ISO || OPK == OP_NH_APPLY || OPK == OP_CP_APPLY;
 };
 
+// Complex entries per slot buffer: room for the half-spectrum line (M + 1),
+// the real line (M complex) and the padded FFT exchange, rounded so that the
+// slot stride is 16 banks modulo 32 (neighbouring slots of a half-warp then
+// use disjoint banks).
+template <typename T, int N3>
+__host__ __device__ constexpr int ax3_slot_cplx() {
+    constexpr int M = N3 / 2;
+    int n = padded_len<T>(M) > M + 1 ? padded_len<T>(M) : M + 1;
+    while (((n * (int)sizeof(cplx<T>) / 4) & 31) != 16) ++n;
+    return n;
+}
+
 // Shared-memory layout: one buffer of SB = N3 + 2 values per slot
 // (slot = grid line x right-hand side x component), holding either the
 // half-spectrum line (N3/2 + 1 complex values) or the real line (N3 values),
@@ -70,12 +82,13 @@ template <int OPK> struct OpInfo {
 // loads and stores are done cooperatively: for one (right-hand side,
 // component) the L lines of a CTA are L h contiguous complex values.
 template <typename T, int N3, int NC, int OPK>
-__global__ void __launch_bounds__(256) k_axis3(Ax3Args<T> a) {
+__global__ void __launch_bounds__(256, (sizeof(T) == 4 ? 4 : ((OPK == OP_CP_UPDATE || OPK == OP_NH_UPDATE) ? 1 : 2))) k_axis3(Ax3Args<T> a) {
     constexpr int M = N3 / 2;
     constexpr int H = M + 1;
-    constexpr int R = RadixFor<T, M>::value;
+    constexpr int R = RadixAx3<T, M>::value;
     constexpr int P = M / R;
-    constexpr int SB = N3 + 2;
+    constexpr int SB = 2 * ax3_slot_cplx<T, N3>();  // in T values
+    static_assert(P <= 32 && (32 % P) == 0, "a slot's threads must sit inside one warp");
     extern __shared__ __align__(16) unsigned char smraw[];
     T* sbuf = reinterpret_cast<T*>(smraw);
     __shared__ double red[32 * 8];
@@ -98,20 +111,23 @@ __global__ void __launch_bounds__(256) k_axis3(Ax3Args<T> a) {
     auto slot_ptr = [&](int f, int sl) { return sbuf + ((long long)f * NSLOT + sl) * SB; };
     auto rhs_done = [&](int rl) { return a.cg != nullptr && a.cg[g * RB + rl].done != 0; };
 
-    // ---- cooperative load of the half-spectrum lines
+    // ---- cooperative load of the half-spectrum lines: for each (rhs, comp)
+    // the lines of this CTA are lines_here * H contiguous complex values
     for (int f = 0; f < NF; ++f) {
         const cplx<T>* src = f == 0 ? a.W : a.W2;
         const int per_rc = lines_here * H;
-        for (int i = t; i < RB * NC * per_rc; i += nthr) {
-            const int rc = i / per_rc, rest = i - rc * per_rc;
+        for (int rc = 0; rc < RB * NC; ++rc) {
             const int rl = rc / NC, c = rc - rl * NC;
-            const int ll = rest / H, k = rest - ll * H;
+            if (rhs_done(rl)) continue;
             const int b = g * RB + rl;
-            cplx<T> v = zero_c<T>();
-            if (!rhs_done(rl)) v = ldc(src + ((long long)(b * NC + c) * nlines + line0) * H + rest);
-            reinterpret_cast<cplx<T>*>(slot_ptr(f, (ll * RB + rl) * NC + c))[k] = v;
+            const cplx<T>* gsrc = src + ((long long)(b * NC + c) * nlines + line0) * H;
+            for (int i = t; i < per_rc; i += nthr) {
+                const int ll = i / H, k = i - ll * H;  // H is a compile-time constant
+                cp_async_c(reinterpret_cast<cplx<T>*>(slot_ptr(f, (ll * RB + rl) * NC + c)) + k, gsrc + i);
+            }
         }
     }
+    cp_async_wait_all();
     __syncthreads();
 
     // ---- C2R per slot: Z[k] = (X[k] + conj X[M-k]) + i e^{+2 pi i k/n} (X[k] - conj X[M-k])
@@ -132,23 +148,20 @@ __global__ void __launch_bounds__(256) k_axis3(Ax3Args<T> a) {
                 const cplx<T> dl = e * (X - Xc);
                 v[r] = (X + Xc) + mk(-dl.y, dl.x);
             }
-            __syncthreads();  // every thread has read its line before it is overwritten
-            ColFFT<T, M, R, +1>::run(v, myc, 1, p, a.tw.tm);
-            __syncthreads();
+            __syncwarp();  // the slot's threads (one warp-aligned group) have read their line
+            ColFFT<T, M, R, +1, true, true>::run(v, myc, 1, p, a.tw.tm);
+            __syncwarp();
+            // real values x[2j], x[2j+1] = Re, Im z[j]: one complex store per j
 #pragma unroll
-            for (int r = 0; r < R; ++r) {
-                const int jj = p + r * P;
-                my[2 * jj] = v[r].x;
-                my[2 * jj + 1] = v[r].y;
-            }
+            for (int r = 0; r < R; ++r) myc[p + r * P] = v[r];
         }
     }
     __syncthreads();
 
     // ---- per-voxel operation
-    double eacc[8];
+    T eacc[8];
 #pragma unroll
-    for (int q = 0; q < 8; ++q) eacc[q] = 0.0;
+    for (int q = 0; q < 8; ++q) eacc[q] = T(0);
     const int mat = (g * RB) / d.Rm;
     for (int idx = t; idx < lines_here * N3; idx += nthr) {
         const int lv = idx / N3, x3 = idx - lv * N3;
@@ -156,24 +169,24 @@ __global__ void __launch_bounds__(256) k_axis3(Ax3Args<T> a) {
         if constexpr (OPK == OP_ISO || OPK == OP_ADJ) {
             const long long mv = (long long)mat * d.V + vox;
             const int ph = a.phase[mv];
-            const double sc = a.scale ? a.scale[mv] : 1.0;
-            const T lam = (T)(a.lam[ph] * sc), mu = (T)(a.mu[ph] * sc);
+            const T sc = a.scale ? a.scale[mv] : T(1);
+            const T lam = a.lam[ph] * sc, mu = a.mu[ph] * sc;
             for (int rr = 0; rr < RB; ++rr) {
                 const int bb = g * RB + rr;
                 if (rhs_done(rr)) continue;
                 T* f = slot_ptr(0, (lv * RB + rr) * NC) + x3;
                 T e[NC];
 #pragma unroll
-                for (int q = 0; q < NC; ++q) e[q] = f[q * SB] + (T)a.macroW[bb * 9 + q];
+                for (int q = 0; q < NC; ++q) e[q] = f[q * SB] + a.macroW[bb * 9 + q];
                 if constexpr (OPK == OP_ADJ) {
                     // dJ/dE = (1/N) eps_adj : C1 : eps_fwd, C1 = C / E: for this
                     // op the phase tables hold lam, mu per unit Young's modulus
                     const T* f2 = slot_ptr(1, (lv * RB + rr) * NC) + x3;
                     T e2[NC];
 #pragma unroll
-                    for (int q = 0; q < NC; ++q) e2[q] = f2[q * SB] + (T)a.macroW2[bb * 9 + q];
+                    for (int q = 0; q < NC; ++q) e2[q] = f2[q * SB] + a.macroW2[bb * 9 + q];
                     T sg[NC];
-                    iso_stress<T, NC>(e, (T)a.lam[ph], (T)a.mu[ph], sg);
+                    iso_stress<T, NC>(e, a.lam[ph], a.mu[ph], sg);
                     T acc = T(0);
 #pragma unroll
                     for (int q = 0; q < NC; ++q) acc += (q >= 3 && NC == 6 ? T(2) : T(1)) * e2[q] * sg[q];
@@ -185,7 +198,7 @@ __global__ void __launch_bounds__(256) k_axis3(Ax3Args<T> a) {
                         T en = T(0);
 #pragma unroll
                         for (int q = 0; q < NC; ++q) en += (q >= 3 && NC == 6 ? T(2) : T(1)) * e[q] * sg[q];
-                        eacc[rr] += (double)en;
+                        eacc[rr] += en;
                     }
 #pragma unroll
                     for (int q = 0; q < NC; ++q) f[q * SB] = sg[q];
@@ -194,14 +207,14 @@ __global__ void __launch_bounds__(256) k_axis3(Ax3Args<T> a) {
         } else if constexpr (OPK == OP_NH_APPLY) {
             const long long mv = (long long)mat * d.V + vox;
             const int ph = a.phase[mv];
-            const T lam = (T)a.lam[ph], mu = (T)a.mu[ph];
+            const T lam = a.lam[ph], mu = a.mu[ph];
             for (int rr = 0; rr < RB; ++rr) {
                 const int bb = g * RB + rr;
                 if (rhs_done(rr)) continue;
                 T* f = slot_ptr(0, (lv * RB + rr) * NC) + x3;
                 T G[9];
 #pragma unroll
-                for (int q = 0; q < 9; ++q) G[q] = f[q * SB] + (T)a.macroW[bb * 9 + q];
+                for (int q = 0; q < 9; ++q) G[q] = f[q * SB] + a.macroW[bb * 9 + q];
                 const T* tn = a.tan_in + ((long long)bb * d.V + vox) * 10;
                 T sg[9];
                 nh_apply<T>(tn, mu, lam, G, sg);
@@ -209,7 +222,7 @@ __global__ void __launch_bounds__(256) k_axis3(Ax3Args<T> a) {
                     T en = T(0);
 #pragma unroll
                     for (int q = 0; q < 9; ++q) en += G[q] * sg[q];
-                    eacc[rr] += (double)en;
+                    eacc[rr] += en;
                 }
 #pragma unroll
                 for (int q = 0; q < 9; ++q) f[q * SB] = sg[q];
@@ -241,7 +254,7 @@ __global__ void __launch_bounds__(256) k_axis3(Ax3Args<T> a) {
                 T* f = slot_ptr(0, (lv * RB + rr) * NC) + x3;
                 T e[6];
 #pragma unroll
-                for (int q = 0; q < 6; ++q) e[q] = f[q * SB] + (T)a.macroW[bb * 9 + q];
+                for (int q = 0; q < 6; ++q) e[q] = f[q * SB] + a.macroW[bb * 9 + q];
                 const T* tn = a.tan_in + ((long long)bb * d.V + vox) * 21;
                 T sg[6];
                 cp_apply<T>(tn, e, sg);
@@ -249,7 +262,7 @@ __global__ void __launch_bounds__(256) k_axis3(Ax3Args<T> a) {
                     T en = T(0);
 #pragma unroll
                     for (int q = 0; q < 6; ++q) en += (q >= 3 ? T(2) : T(1)) * e[q] * sg[q];
-                    eacc[rr] += (double)en;
+                    eacc[rr] += en;
                 }
 #pragma unroll
                 for (int q = 0; q < 6; ++q) f[q * SB] = sg[q];
@@ -286,7 +299,7 @@ __global__ void __launch_bounds__(256) k_axis3(Ax3Args<T> a) {
     if constexpr (OpInfo<OPK>::apply) {
         if (a.cg) {
             for (int rr = 0; rr < RB; ++rr) {
-                double v1[1] = {eacc[rr]};
+                double v1[1] = {(double)eacc[rr]};
                 block_sum<1>(v1, red);
                 if (t == 0) ecc[rr] = v1[0];
             }
@@ -331,15 +344,13 @@ __global__ void __launch_bounds__(256) k_axis3(Ax3Args<T> a) {
         cplx<T>* myc = reinterpret_cast<cplx<T>*>(my);
         cplx<T> v[R];
 #pragma unroll
-        for (int r = 0; r < R; ++r) {
-            const int jj = p + r * P;
-            v[r] = mk(my[2 * jj], my[2 * jj + 1]);
-        }
-        ColFFT<T, M, R, -1>::run(v, myc, 1, p, a.tw.tm);
-        __syncthreads();
+        for (int r = 0; r < R; ++r) v[r] = myc[p + r * P];  // z[j] = x[2j] + i x[2j+1]
+        __syncwarp();
+        ColFFT<T, M, R, -1, true, true>::run(v, myc, 1, p, a.tw.tm);
+        __syncwarp();
 #pragma unroll
         for (int r = 0; r < R; ++r) myc[p + r * P] = v[r];
-        __syncthreads();
+        __syncwarp();
         cplx<T> X[R];
         cplx<T> XM = zero_c<T>();
         const T half = T(0.5);
@@ -356,7 +367,7 @@ __global__ void __launch_bounds__(256) k_axis3(Ax3Args<T> a) {
             const cplx<T> Z0 = myc[0];
             XM = mk(Z0.x - Z0.y, T(0));
         }
-        __syncthreads();
+        __syncwarp();
 #pragma unroll
         for (int r = 0; r < R; ++r) myc[p + r * P] = X[r];
         if (p == 0) myc[M] = XM;
@@ -366,14 +377,15 @@ __global__ void __launch_bounds__(256) k_axis3(Ax3Args<T> a) {
     // ---- cooperative store
     {
         const int per_rc = lines_here * H;
-        for (int i = t; i < RB * NC * per_rc; i += nthr) {
-            const int rc = i / per_rc, rest = i - rc * per_rc;
+        for (int rc = 0; rc < RB * NC; ++rc) {
             const int rl = rc / NC, c = rc - rl * NC;
             if (rhs_done(rl)) continue;
-            const int ll = rest / H, k = rest - ll * H;
             const int b = g * RB + rl;
-            stc(a.W + ((long long)(b * NC + c) * nlines + line0) * H + rest,
-                reinterpret_cast<const cplx<T>*>(slot_ptr(0, (ll * RB + rl) * NC + c))[k]);
+            cplx<T>* gdst = a.W + ((long long)(b * NC + c) * nlines + line0) * H;
+            for (int i = t; i < per_rc; i += nthr) {
+                const int ll = i / H, k = i - ll * H;
+                stc(gdst + i, reinterpret_cast<const cplx<T>*>(slot_ptr(0, (ll * RB + rl) * NC + c))[k]);
+            }
         }
     }
 }

@@ -31,7 +31,7 @@ __device__ __forceinline__ int hweight(int k3, int m) { return (k3 == 0 || k3 ==
 
 // z = N Q(xi)^-1 r (zero on the null set), Q from the mean tangent.
 template <typename T>
-__device__ __forceinline__ void precond_apply(const double (*coef)[6], T x1, T x2, T x3, T N,
+__device__ __forceinline__ void precond_apply(const T (*coef)[6], T x1, T x2, T x3, T N,
                                               const cplx<T>* r, cplx<T>* z) {
     const T k2 = x1 * x1 + x2 * x2 + x3 * x3;
     if (k2 == T(0)) {
@@ -46,7 +46,7 @@ __device__ __forceinline__ void precond_apply(const double (*coef)[6], T x1, T x
     for (int a = 0; a < 6; ++a) {
         T s = T(0);
 #pragma unroll
-        for (int b = 0; b < 6; ++b) s += (T)coef[a][b] * mono[b];
+        for (int b = 0; b < 6; ++b) s += coef[a][b] * mono[b];
         q[a] = s;
     }
     // Q = [[q0 q5 q4] [q5 q1 q3] [q4 q3 q2]], inverse by cofactors
@@ -157,14 +157,22 @@ struct Ax1InvArgs {
     const PrecondData* pre;  // [B / Rm] per material group
 };
 
+// Threads per CTA of passes 1 and 5 (TW columns x P threads per column).
+constexpr int AX1_THREADS = 128;
+
+// Pass 1. Shared memory: the FFT exchange tile [N1][TW] and, per thread, the
+// three displacement components of its R frequencies ([3][R][threads],
+// thread-private, so no synchronisation is needed around them).
 template <typename T, int N1, int NC, int MODE>
-__global__ void __launch_bounds__(256, 2) k_axis1_inv(Ax1InvArgs<T> a) {
+__global__ void __launch_bounds__(AX1_THREADS, (sizeof(T) == 4 ? 8 : 4)) k_axis1_inv(Ax1InvArgs<T> a) {
     constexpr int R = RadixAx1<T, N1>::value;
     constexpr int P = N1 / R;
+    constexpr int TW = AX1_THREADS / P;
     extern __shared__ __align__(16) unsigned char smraw[];
     cplx<T>* sm = reinterpret_cast<cplx<T>*>(smraw);
-    const int TW = blockDim.x;
+    cplx<T>* su = sm + N1 * TW;  // [3][R][AX1_THREADS]
     const int w = threadIdx.x, p = threadIdx.y;
+    const int tid = w + p * TW;
     const int b = blockIdx.y;
     if (MODE == AX1_CG && a.cg[b].done) return;
     const Dims& d = a.d;
@@ -173,14 +181,14 @@ __global__ void __launch_bounds__(256, 2) k_axis1_inv(Ax1InvArgs<T> a) {
     const int k2 = valid ? (int)(j / d.h) : 0;
     const int k3 = valid ? (int)(j - (long long)k2 * d.h) : 0;
     const T x2 = a.f.xi2[k2], x3 = a.f.xi3[k3];
+    auto U = [&](int c, int r) -> cplx<T>& { return su[(c * R + r) * AX1_THREADS + tid]; };
 
-    cplx<T> u[3][R];
 #pragma unroll
     for (int c = 0; c < 3; ++c)
 #pragma unroll
         for (int r = 0; r < R; ++r) {
             const long long idx = ((long long)(b * 3 + c) * N1 + (p + r * P)) * d.plane + j;
-            u[c][r] = valid ? ldc(a.in + idx) : zero_c<T>();
+            U(c, r) = valid ? ldc(a.in + idx) : zero_c<T>();
         }
     if constexpr (MODE == AX1_CG) {
         const T beta = (T)a.cg[b].beta;
@@ -189,37 +197,33 @@ __global__ void __launch_bounds__(256, 2) k_axis1_inv(Ax1InvArgs<T> a) {
 #pragma unroll
         for (int r = 0; r < R; ++r) {
             const int k1 = p + r * P;
-            cplx<T> rr[3] = {u[0][r], u[1][r], u[2][r]};
+            cplx<T> rr[3] = {U(0, r), U(1, r), U(2, r)};
             cplx<T> z[3];
-            precond_apply<T>(pd.coef, a.f.xi1[k1], x2, x3, N, rr, z);
+            precond_apply<T>(pcoef<T>(pd), a.f.xi1[k1], x2, x3, N, rr, z);
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
                 const long long idx = ((long long)(b * 3 + c) * N1 + k1) * d.plane + j;
                 cplx<T> po = valid ? ldc(a.p + idx) : zero_c<T>();
                 cplx<T> pn = z[c] + po * beta;
                 if (valid) stc(a.p + idx, pn);
-                u[c][r] = pn;
+                U(c, r) = pn;
             }
         }
     }
     const T s = (T)d.invN;
-    T x1r[R];
-#pragma unroll
-    for (int r = 0; r < R; ++r) x1r[r] = a.f.xi1[p + r * P];
-
     auto emit = [&](auto mc) {
         constexpr int M = decltype(mc)::value;
         cplx<T> v[R];
 #pragma unroll
         for (int r = 0; r < R; ++r) {
-            cplx<T> uu[3] = {u[0][r], u[1][r], u[2][r]};
-            v[r] = grad_comp<T, NC, M>(uu, x1r[r], x2, x3, s);
+            cplx<T> uu[3] = {U(0, r), U(1, r), U(2, r)};
+            v[r] = grad_comp<T, NC, M>(uu, a.f.xi1[p + r * P], x2, x3, s);
         }
         ColFFT<T, N1, R, +1>::run(v, sm + w, TW, p, a.tw.t1);
+        if (valid) {
 #pragma unroll
-        for (int r = 0; r < R; ++r) {
-            const long long idx = ((long long)(b * NC + M) * N1 + (p + r * P)) * d.plane + j;
-            if (valid) stc(a.W + idx, v[r]);
+            for (int r = 0; r < R; ++r)
+                stc(a.W + ((long long)(b * NC + M) * N1 + (p + r * P)) * d.plane + j, v[r]);
         }
     };
     emit(std::integral_constant<int, 0>());
@@ -299,22 +303,26 @@ struct Ax1FwdArgs {
     double* x_e;         // CG: [B][9]
     double* p_e;         // CG: [B][9]
     double* macroW;      // CG: [B][9] (output: E p_e for the next pass 3)
+    float* macroWf;      // CG: FP32 copy of macroW
     CgState* cg;
     const PrecondData* pre;
     double* partials;    // [B][nblk][2]
     unsigned* counters;  // [B]
 };
 
+// Pass 5. Shared memory: the FFT exchange tile and, per thread, the three
+// divergence accumulators of its R frequencies ([3][R][threads], private).
 template <typename T, int N1, int NC, int MODE>
-__global__ void __launch_bounds__(256, 2) k_axis1_fwd(Ax1FwdArgs<T> a) {
+__global__ void __launch_bounds__(AX1_THREADS, (sizeof(T) == 4 ? 8 : 4)) k_axis1_fwd(Ax1FwdArgs<T> a) {
     constexpr int R = RadixAx1<T, N1>::value;
     constexpr int P = N1 / R;
+    constexpr int TW = AX1_THREADS / P;
     extern __shared__ __align__(16) unsigned char smraw[];
     cplx<T>* sm = reinterpret_cast<cplx<T>*>(smraw);
+    cplx<T>* sq = sm + N1 * TW;  // [3][R][AX1_THREADS]
     __shared__ double red[32 * 2];
     __shared__ double s0[9][2];
     __shared__ bool is_last;
-    const int TW = blockDim.x;
     const int w = threadIdx.x, p = threadIdx.y;
     const int tid = w + p * TW;
     const int b = blockIdx.y;
@@ -325,16 +333,13 @@ __global__ void __launch_bounds__(256, 2) k_axis1_fwd(Ax1FwdArgs<T> a) {
     const int k2 = valid ? (int)(j / d.h) : 0;
     const int k3 = valid ? (int)(j - (long long)k2 * d.h) : 0;
     const T x2 = a.f.xi2[k2], x3 = a.f.xi3[k3];
-    T x1r[R];
-#pragma unroll
-    for (int r = 0; r < R; ++r) x1r[r] = a.f.xi1[p + r * P];
     const bool has0 = valid && j == 0 && p == 0;  // holds k = (0,0,0) in register 0
+    auto Q = [&](int c, int r) -> cplx<T>& { return sq[(c * R + r) * AX1_THREADS + tid]; };
 
-    cplx<T> acc[3][R];
 #pragma unroll
     for (int c = 0; c < 3; ++c)
 #pragma unroll
-        for (int r = 0; r < R; ++r) acc[c][r] = zero_c<T>();
+        for (int r = 0; r < R; ++r) Q(c, r) = zero_c<T>();
 
     auto take = [&](auto mc) {
         constexpr int M = decltype(mc)::value;
@@ -348,9 +353,9 @@ __global__ void __launch_bounds__(256, 2) k_axis1_fwd(Ax1FwdArgs<T> a) {
         if (has0) { s0[M][0] = (double)v[0].x; s0[M][1] = (double)v[0].y; }
 #pragma unroll
         for (int r = 0; r < R; ++r) {
-            cplx<T> ac[3] = {acc[0][r], acc[1][r], acc[2][r]};
-            div_acc<T, NC, M>(ac, v[r], x1r[r], x2, x3);
-            acc[0][r] = ac[0]; acc[1][r] = ac[1]; acc[2][r] = ac[2];
+            cplx<T> ac[3] = {Q(0, r), Q(1, r), Q(2, r)};
+            div_acc<T, NC, M>(ac, v[r], a.f.xi1[p + r * P], x2, x3);
+            Q(0, r) = ac[0]; Q(1, r) = ac[1]; Q(2, r) = ac[2];
         }
     };
     take(std::integral_constant<int, 0>());
@@ -368,9 +373,9 @@ __global__ void __launch_bounds__(256, 2) k_axis1_fwd(Ax1FwdArgs<T> a) {
     const T ms = -(T)d.invN;
 #pragma unroll
     for (int r = 0; r < R; ++r) {
-        const bool z = (x1r[r] == T(0)) && (x2 == T(0)) && (x3 == T(0));
+        const bool z = (a.f.xi1[p + r * P] == T(0)) && (x2 == T(0)) && (x3 == T(0));
 #pragma unroll
-        for (int c = 0; c < 3; ++c) acc[c][r] = z ? zero_c<T>() : mul_i(ms, acc[c][r]);
+        for (int c = 0; c < 3; ++c) Q(c, r) = z ? zero_c<T>() : mul_i(ms, Q(c, r));
     }
     const int wgt = hweight(k3, d.m);
 
@@ -380,7 +385,7 @@ __global__ void __launch_bounds__(256, 2) k_axis1_fwd(Ax1FwdArgs<T> a) {
             for (int c = 0; c < 3; ++c)
 #pragma unroll
                 for (int r = 0; r < R; ++r)
-                    stc(a.out + ((long long)(b * 3 + c) * N1 + (p + r * P)) * d.plane + j, acc[c][r]);
+                    stc(a.out + ((long long)(b * 3 + c) * N1 + (p + r * P)) * d.plane + j, Q(c, r));
         }
         if (has0 && a.e_out) {
             for (int q = 0; q < 9; ++q) a.e_out[b * 9 + q] = 0.0;
@@ -398,7 +403,7 @@ __global__ void __launch_bounds__(256, 2) k_axis1_fwd(Ax1FwdArgs<T> a) {
             for (int c = 0; c < 3; ++c)
 #pragma unroll
                 for (int r = 0; r < R; ++r) {
-                    cplx<T> v = mk(-acc[c][r].x, -acc[c][r].y);
+                    cplx<T> v = mk(-Q(c, r).x, -Q(c, r).y);
                     stc(a.out + ((long long)(b * 3 + c) * N1 + (p + r * P)) * d.plane + j, v);
                     v2[0] += (double)wgt * ((double)v.x * v.x + (double)v.y * v.y);
                 }
@@ -435,12 +440,12 @@ __global__ void __launch_bounds__(256, 2) k_axis1_fwd(Ax1FwdArgs<T> a) {
                     const long long idx = ((long long)(b * 3 + c) * N1 + (p + r * P)) * d.plane + j;
                     cplx<T> xv = ldc(a.x + idx), pv = ldc(a.p + idx), rvv = ldc(a.r + idx);
                     xv = xv + pv * alpha;
-                    rvv = rvv - acc[c][r] * alpha;
+                    rvv = rvv - Q(c, r) * alpha;
                     stc(a.x + idx, xv);
                     stc(a.r + idx, rvv);
                     rv[c] = rvv;
                 }
-                precond_apply<T>(pd.coef, x1r[r], x2, x3, N, rv, z);
+                precond_apply<T>(pcoef<T>(pd), a.f.xi1[p + r * P], x2, x3, N, rv, z);
                 T lrz = T(0), lrr = T(0);
 #pragma unroll
                 for (int c = 0; c < 3; ++c) {
@@ -503,11 +508,12 @@ __global__ void __launch_bounds__(256, 2) k_axis1_fwd(Ax1FwdArgs<T> a) {
                     for (int l = 0; l < d.ne; ++l) ze += Me[k][l] * a.r_e[b * 9 + d.active[l]];
                     pe[k] = ze + beta * a.p_e[b * 9 + d.active[k]];
                 }
-                for (int q = 0; q < 9; ++q) a.macroW[b * 9 + q] = 0.0;
+                for (int q = 0; q < 9; ++q) { a.macroW[b * 9 + q] = 0.0; a.macroWf[b * 9 + q] = 0.f; }
                 for (int k = 0; k < d.ne; ++k) {
                     const int m = d.active[k];
                     a.p_e[b * 9 + m] = pe[k];
                     a.macroW[b * 9 + m] = macro_to_w<NC>(m) * pe[k];
+                    a.macroWf[b * 9 + m] = (float)a.macroW[b * 9 + m];
                 }
             }
             a.counters[b] = 0u;
@@ -525,6 +531,7 @@ struct CgInitArgs {
     const double* r_e;
     double* p_e;
     double* macroW;
+    float* macroWf;
     CgState* cg;
     const PrecondData* pre;
     double* partials;
@@ -548,12 +555,15 @@ __global__ void k_cg_init(CgInitArgs<T> a) {
         const int k2 = (int)(rem / d.h), k3 = (int)(rem - (long long)k2 * d.h);
         cplx<T> rv[3], z[3];
         for (int c = 0; c < 3; ++c) rv[c] = ldc(a.r + (long long)(b * 3 + c) * d.H + i);
-        precond_apply<T>(pd.coef, a.f.xi1[k1], a.f.xi2[k2], a.f.xi3[k3], (T)(1.0 / d.invN), rv, z);
+        precond_apply<T>(pcoef<T>(pd), a.f.xi1[k1], a.f.xi2[k2], a.f.xi3[k3], (T)(1.0 / d.invN), rv, z);
         const int wgt = hweight(k3, d.m);
+        T lrz = T(0), lrr = T(0);
         for (int c = 0; c < 3; ++c) {
-            v2[0] += wgt * ((double)rv[c].x * z[c].x + (double)rv[c].y * z[c].y);
-            v2[1] += wgt * ((double)rv[c].x * rv[c].x + (double)rv[c].y * rv[c].y);
+            lrz += rv[c].x * z[c].x + rv[c].y * z[c].y;
+            lrr += rv[c].x * rv[c].x + rv[c].y * rv[c].y;
         }
+        v2[0] = (double)wgt * (double)lrz;
+        v2[1] = (double)wgt * (double)lrr;
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         for (int k = 0; k < d.ne; ++k) {
@@ -594,13 +604,14 @@ __global__ void k_cg_init(CgInitArgs<T> a) {
         cs.done = (srr == 0.0) ? 1 : 0;
         if (!(srr == srr)) { cs.done = 1; cs.flags |= 2; }
         // first direction's macro part: p_e = z_e (beta = 0)
-        for (int q = 0; q < 9; ++q) { a.p_e[b * 9 + q] = 0.0; a.macroW[b * 9 + q] = 0.0; }
+        for (int q = 0; q < 9; ++q) { a.p_e[b * 9 + q] = 0.0; a.macroW[b * 9 + q] = 0.0; a.macroWf[b * 9 + q] = 0.f; }
         for (int k = 0; k < d.ne; ++k) {
             double ze = 0.0;
             for (int l = 0; l < d.ne; ++l) ze += pd.Me[k][l] * a.r_e[b * 9 + d.active[l]];
             const int m = d.active[k];
             a.p_e[b * 9 + m] = ze;
             a.macroW[b * 9 + m] = (d.nc == 6 && m >= 3 ? 0.70710678118654752440084436210485 : 1.0) * ze;
+            a.macroWf[b * 9 + m] = (float)a.macroW[b * 9 + m];
         }
         a.counters[b] = 0u;
     }
