@@ -242,6 +242,44 @@ dbfft_status dbfft_profile(dbfft_ctx* ctx, int enable);
 int dbfft_profile_read(dbfft_ctx* ctx, dbfft_profile_entry* out, int max_entries);
 long long dbfft_launch_count(const dbfft_ctx* ctx);
 
+/*
+ * Operator application that allocates nothing (no counterpart in the paper;
+ * this is a deployment aid). Some callers cannot let a library call
+ * cudaMalloc: a host application whose device memory is owned by a caching
+ * pool (a deep-learning framework that has reserved most of the GPU, where
+ * an extra driver allocation can fail or fragment the pool), or a caller
+ * that must not pay the latency and implicit device synchronisation of an
+ * allocation on its critical path (e.g. a solver calling the operator many
+ * times inside its own iteration). This entry point needs no context: it
+ * computes out = K u_hat exactly as dbfft_apply does for FP64, small strain,
+ * linear isotropic phases and full strain control (no macro unknowns), and
+ * keeps its work buffer and its frequency / twiddle tables in static device
+ * arrays inside the library.
+ *
+ * n[3]: grid, powers of two in [8, 256]; L[3]: box lengths (NULL: all 1);
+ * batch: right-hand sides, each with its own material map;
+ * phase_id: device uint16 [batch][n1][n2][n3]; lam, mu: device double
+ * [n_phases] Lame constants indexed by phase_id; u_hat, out: device
+ * complex128 [batch][3][n1][n2][n3/2+1] (out may not alias u_hat); stream: a
+ * cudaStream_t (NULL: legacy default stream). Returns after the work is done.
+ *
+ * Limit: the static work buffer holds 16 MiB, i.e.
+ * batch * 6 * n1 * n2 * (n3/2 + 1) * 16 bytes <= 16 MiB (one 64^3 field, or
+ * seven 32^3 fields) and batch <= 1024; larger requests return DBFFT_E_ARG
+ * with a message on stderr and touch no device memory.
+ * The buffer is shared by every call in the process and keeps the last
+ * call's contents; nothing in it needs to start at zero (each call
+ * overwrites what it reads). Calls that overlap on the GPU (from several
+ * streams or threads at once) race on it and must be serialised by the
+ * caller. The first call on a device looks up the device addresses of the
+ * static arrays; every GPU on which the library's device code is loaded
+ * holds the 16 MiB (plus the small tables) until the process exits.
+ * Errors: E_ARG, E_UNSUPPORTED_GRID, E_CUDA.
+ */
+dbfft_status dbfft_apply_iso_noalloc(const int n[3], const double L[3], int batch, const uint16_t* phase_id,
+                                     const double* lam, const double* mu, const void* u_hat, void* out,
+                                     void* stream);
+
 /* Device bytes held by the context. */
 size_t dbfft_device_bytes(const dbfft_ctx* ctx);
 

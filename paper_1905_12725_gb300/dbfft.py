@@ -73,7 +73,7 @@ class dbfft_profile_entry(C.Structure):
 EXPORTS = ["dbfft_create", "dbfft_apply", "dbfft_solve_increment", "dbfft_homogenized_stress",
            "dbfft_homogenized_tangent", "dbfft_adjoint", "dbfft_get_solution", "dbfft_device_bytes",
            "dbfft_destroy", "dbfft_last_error", "dbfft_status_string", "dbfft_profile",
-           "dbfft_profile_read", "dbfft_launch_count"]
+           "dbfft_profile_read", "dbfft_launch_count", "dbfft_apply_iso_noalloc"]
 
 _LIB = None
 
@@ -123,6 +123,8 @@ def load_library(build_if_missing: bool = True):
     lib.dbfft_profile_read.restype = ip
     lib.dbfft_launch_count.argtypes = [vp]
     lib.dbfft_launch_count.restype = C.c_longlong
+    lib.dbfft_apply_iso_noalloc.argtypes = [C.POINTER(C.c_int), dp, ip, vp, vp, vp, vp, vp, vp]
+    lib.dbfft_apply_iso_noalloc.restype = ip
     _LIB = lib
     return lib
 
@@ -334,6 +336,28 @@ class Solver:
         e = np.zeros((self.batch, 9))
         self._check(self.lib.dbfft_get_solution(self.ctx, C.c_void_p(u.data_ptr()), _dptr(e)))
         return u, e
+
+
+def apply_iso_noalloc(shape, phase_id, lam, mu, u_hat, out, L=None, stream=None):
+    """out = K u_hat through dbfft_apply_iso_noalloc (no device allocation in the call).
+
+    phase_id: torch uint16-compatible device tensor [B, n1, n2, n3] (int16 view is fine);
+    lam, mu: float64 device tensors [n_phases]; u_hat, out: complex128 device tensors
+    [B, 3, n1, n2, n3//2 + 1]. Returns the status code (0 on success).
+    """
+    import torch
+
+    lib = load_library()
+    n = (C.c_int * 3)(*[int(v) for v in shape])
+    Lh = None
+    if L is not None:
+        Larr = np.ascontiguousarray(L, dtype=np.float64)
+        Lh = _dptr(Larr)
+    st = stream if stream is not None else torch.cuda.current_stream()
+    return lib.dbfft_apply_iso_noalloc(n, Lh, int(u_hat.shape[0]), C.c_void_p(phase_id.data_ptr()),
+                                       C.c_void_p(lam.data_ptr()), C.c_void_p(mu.data_ptr()),
+                                       C.c_void_p(u_hat.data_ptr()), C.c_void_p(out.data_ptr()),
+                                       C.c_void_p(st.cuda_stream))
 
 
 # ---------------------------------------------------------------- autograd
