@@ -134,6 +134,11 @@ struct dbfft_ctx {
     std::vector<long long> prof_n;
     std::vector<double> prof_ms, prof_bytes;
     int active_b = 0;  // right-hand sides still iterating (bytes accounting)
+
+    // ---- inner PCG as one CUDA graph (WHILE node), per inner precision
+    bool use_graphs = true;
+    bool graph_warm[2] = {false, false};
+    cudaGraphExec_t cg_exec[2] = {nullptr, nullptr};
 };
 
 namespace {
@@ -660,6 +665,64 @@ dbfft_status chain_residual(dbfft_ctx* ctx, const cplx<double>* x, const double*
     return DBFFT_OK;
 }
 
+// Loop condition of the inner-PCG graph: keep iterating while any
+// right-hand side is still active (each stops by tolerance or iteration cap).
+__global__ void k_cg_continue(cudaGraphConditionalHandle h, const CgState* cg, int B) {
+    int any = 0;
+    for (int b = threadIdx.x; b < B; b += 32) any |= (cg[b].done == 0);
+    any = __any_sync(0xffffffffu, any);
+    if (threadIdx.x == 0) cudaGraphSetConditional(h, any ? 1u : 0u);
+}
+
+// Capture one PCG iteration (passes 1-5 + the loop condition) as the body of
+// a WHILE conditional node: one graph launch runs the whole inner solve.
+template <typename T>
+dbfft_status build_cg_graph(dbfft_ctx* ctx, const Ax1InvArgs<T>& a1, const Ax2Args<T>& a2, const Ax3Args<T>& a3,
+                            const Ax1FwdArgs<T>& a5, int opk, cudaGraphExec_t* out) {
+    cudaGraph_t g = nullptr;
+    CK(cudaGraphCreate(&g, 0));
+    cudaGraphConditionalHandle h;
+    CK(cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault));
+    alignas(cudaGraphNodeParams) unsigned char npbuf[sizeof(cudaGraphNodeParams)];
+    std::memset(npbuf, 0, sizeof(npbuf));
+    cudaGraphNodeParams& np = *reinterpret_cast<cudaGraphNodeParams*>(npbuf);
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = h;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    cudaGraphNode_t node;
+    CK(cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np));
+    cudaGraph_t body = np.conditional.phGraph_out[0];
+    // capture on a private stream (the context's stream may be the legacy
+    // default stream, which cannot capture); the graph runs on the context's stream
+    cudaStream_t cs = nullptr;
+    CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    cudaError_t e = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        e = launch_ax1_inv<T>(AX1_CG, a1, cs);
+        if (e == cudaSuccess) e = launch_ax2<T>(+1, a2, cs);
+        if (e == cudaSuccess) e = launch_ax3<T>(opk, a3, cs);
+        if (e == cudaSuccess) e = launch_ax2<T>(-1, a2, cs);
+        if (e == cudaSuccess) e = launch_ax1_fwd<T>(AX5_CG, a5, cs);
+        if (e == cudaSuccess) {
+            k_cg_continue<<<1, 32, 0, cs>>>(h, ctx->cg, ctx->B);
+            e = cudaGetLastError();
+        }
+        cudaGraph_t captured = nullptr;
+        cudaError_t e2 = cudaStreamEndCapture(cs, &captured);
+        if (e == cudaSuccess) e = e2;
+    }
+    cudaStreamDestroy(cs);
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(g);
+        CK(e);
+    }
+    cudaError_t e3 = cudaGraphInstantiate(out, g, 0);
+    cudaGraphDestroy(g);
+    CK(e3);
+    return DBFFT_OK;
+}
+
 // Inner PCG in precision T on K d = ri (already scaled), x = xi.
 template <typename T>
 dbfft_status inner_cg(dbfft_ctx* ctx, double tol, long long& it_sum, int& it_max) {
@@ -718,6 +781,24 @@ dbfft_status inner_cg(dbfft_ctx* ctx, double tol, long long& it_sum, int& it_max
     a5.counters = ctx->counters;
     const int opk = opk_apply(ctx);
 
+    const int pi_ = dbl ? 1 : 0;
+    if (ctx->use_graphs && !ctx->prof && ctx->graph_warm[pi_]) {
+        // the whole inner solve as one graph launch (kernels already configured by a warm run)
+        if (!ctx->cg_exec[pi_]) TRY(build_cg_graph<T>(ctx, a1, a2, a3, a5, opk_apply(ctx), &ctx->cg_exec[pi_]));
+        CK(cudaGraphLaunch(ctx->cg_exec[pi_], ctx->stream));
+        CK(cudaMemcpyAsync(ctx->cg_h, ctx->cg, ctx->B * sizeof(CgState), cudaMemcpyDeviceToHost, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+        int mx = 1;
+        for (int b = 0; b < ctx->B; ++b) mx = std::max(mx, ctx->cg_h[b].iter);
+        ctx->launches += 6LL * mx;
+        it_max = 0;
+        for (int b = 0; b < ctx->B; ++b) {
+            it_sum += ctx->cg_h[b].iter;
+            if (ctx->cg_h[b].iter > it_max) it_max = ctx->cg_h[b].iter;
+            if (ctx->cg_h[b].flags & 2) return fail(ctx, DBFFT_E_NONFINITE, "non-finite value in the inner CG");
+        }
+        return DBFFT_OK;
+    }
     int launched = 0;
     int chunk = 4;
     const int nc = ctx->nc;
@@ -748,6 +829,7 @@ dbfft_status inner_cg(dbfft_ctx* ctx, double tol, long long& it_sum, int& it_max
         if (all || launched >= ctx->grid.max_iter + 1) break;
         chunk = chunk < 16 ? chunk * 2 : 16;
     }
+    ctx->graph_warm[pi_] = true;
     it_max = 0;
     for (int b = 0; b < ctx->B; ++b) {
         it_sum += ctx->cg_h[b].iter;
@@ -961,6 +1043,8 @@ void dbfft_destroy(dbfft_ctx* ctx) {
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
     prof_flush(ctx);
     for (cudaEvent_t e : ctx->pool) cudaEventDestroy(e);
+    for (int k = 0; k < 2; ++k)
+        if (ctx->cg_exec[k]) cudaGraphExecDestroy(ctx->cg_exec[k]);
     for (auto& b : ctx->bufs) {
         if (ctx->use_cb) ctx->alloc.free(b.p, ctx->alloc.user);
         else cudaFree(b.p);

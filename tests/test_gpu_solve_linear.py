@@ -87,3 +87,27 @@ def test_zero_load_returns_zero_without_iterations():
     rep = s.solve_increment(0)
     assert rep["cg_iters"] == 0
     assert np.abs(s.homogenized_stress()).max() == 0.0
+
+
+def test_graph_and_launch_by_launch_inner_solves_agree():
+    """The inner PCG runs as one CUDA graph (WHILE node) after a warm solve; with
+    profiling on it is launched kernel by kernel. Both give the same iterates."""
+    shape = (16, 16, 32)
+    g = np.random.default_rng(23)
+    phase = (g.random(shape) < 0.3).astype(np.uint16)
+    E, nu = [1.0, 30.0], [0.3, 0.3]
+    tgt = np.zeros((2, 3, 3))
+    tgt[0, 0, 0] = 1e-3
+    tgt[1, 0, 1] = tgt[1, 1, 0] = 5e-4
+    dbfft = _dbfft()
+    s = dbfft.Solver(shape, phase, dbfft.iso_phases(E, nu), tgt, batch=2, tol=1e-10, precision=1, eta_inner=1e-3)
+    r0 = s.solve_increment(0)           # first inner solve launch by launch, later ones as graphs
+    sig_graph = s.homogenized_stress()
+    n0 = s.launch_count()
+    s.profile(True)                      # profiling forces launch-by-launch execution
+    r1 = s.solve_increment(0)
+    sig_plain = s.homogenized_stress()
+    s.profile(False)
+    assert r0["cg_iters"] == r1["cg_iters"]
+    assert np.abs(sig_graph - sig_plain).max() <= 1e-14 * np.abs(sig_plain).max()
+    assert s.launch_count() > n0
