@@ -208,7 +208,7 @@ def operator_256(torch, dbfft, peak, iters=40):
     prof = s.profile_read()
     s.profile(False)
     s.close()
-    names = ["axis1_inv_cg_f32", "axis2_f32", "axis3_apply_f32", "axis1_fwd_cg_f32"]
+    names = ["pass1_grad_cg_f32", "fft_ax2_f32", "fft_ax1_f32", "pass3_tangent_f32", "pass5_div_cg_f32"]
     rows = {}
     it_ms = 0.0
     it_bytes = 0.0

@@ -577,17 +577,19 @@ dbfft_status chain_apply(dbfft_ctx* ctx, const cplx<T>* u, const T* macroW, cplx
     const bool dbl = sizeof(T) == 8;
     const double cp = cpass(ctx, dbl, ctx->B);
     const int nc = ctx->nc;
-    Ax1InvArgs<T> a1{ctx->dims, freq<T>(ctx), twid<T>(ctx), u, nullptr, W, nullptr, ctx->pre};
-    TRY(run(ctx, dbl ? "axis1_inv_f64" : "axis1_inv_f32", (3 + nc) * cp,
-            [&] { return launch_ax1_inv<T>(AX1_PLAIN, a1, ctx->stream); }));
+    Ax1InvArgs<T> a1{ctx->dims, freq<T>(ctx), twid<T>(ctx), u, nullptr, nullptr, W, nullptr, ctx->pre};
     Ax2Args<T> a2{ctx->dims, twid<T>(ctx), W, nullptr};
-    TRY(run(ctx, dbl ? "axis2_f64" : "axis2_f32", 2 * nc * cp, [&] { return launch_ax2<T>(+1, a2, ctx->stream); }));
+    TRY(run(ctx, dbl ? "pass1_grad_f64" : "pass1_grad_f32", (3 + nc) * cp,
+            [&] { return launch_grad<T>(AX1_PLAIN, a1, ctx->stream); }));
+    TRY(run(ctx, dbl ? "fft_ax2_f64" : "fft_ax2_f32", 2 * nc * cp, [&] { return launch_fft_ax2<T>(+1, a2, ctx->stream); }));
+    TRY(run(ctx, dbl ? "fft_ax1_f64" : "fft_ax1_f32", 2 * nc * cp, [&] { return launch_fft_ax1<T>(+1, a2, ctx->stream); }));
     Ax3Args<T> a3 = ax3_base<T>(ctx, W);
     a3.macroW = macroW;
     a3.tan_in = reinterpret_cast<const T*>(ctx->tan);
-    TRY(run(ctx, dbl ? "axis3_apply_f64" : "axis3_apply_f32", 2 * nc * cp + mat_bytes(ctx, dbl, false),
+    TRY(run(ctx, dbl ? "pass3_tangent_f64" : "pass3_tangent_f32", 2 * nc * cp + mat_bytes(ctx, dbl, false),
             [&] { return launch_ax3<T>(opk_apply(ctx), a3, ctx->stream); }));
-    TRY(run(ctx, dbl ? "axis2_f64" : "axis2_f32", 2 * nc * cp, [&] { return launch_ax2<T>(-1, a2, ctx->stream); }));
+    TRY(run(ctx, dbl ? "fft_ax1_f64" : "fft_ax1_f32", 2 * nc * cp, [&] { return launch_fft_ax1<T>(-1, a2, ctx->stream); }));
+    TRY(run(ctx, dbl ? "fft_ax2_f64" : "fft_ax2_f32", 2 * nc * cp, [&] { return launch_fft_ax2<T>(-1, a2, ctx->stream); }));
     Ax1FwdArgs<T> a5;
     std::memset(&a5, 0, sizeof(a5));
     a5.d = ctx->dims;
@@ -596,8 +598,8 @@ dbfft_status chain_apply(dbfft_ctx* ctx, const cplx<T>* u, const T* macroW, cplx
     a5.W = W;
     a5.out = out;
     a5.e_out = e_out;
-    TRY(run(ctx, dbl ? "axis1_fwd_f64" : "axis1_fwd_f32", (3 + nc) * cp,
-            [&] { return launch_ax1_fwd<T>(AX5_PLAIN, a5, ctx->stream); }));
+    TRY(run(ctx, dbl ? "pass5_div_f64" : "pass5_div_f32", (3 + nc) * cp,
+            [&] { return launch_div<T>(AX5_PLAIN, a5, ctx->stream); }));
     return DBFFT_OK;
 }
 
@@ -611,10 +613,11 @@ dbfft_status chain_residual(dbfft_ctx* ctx, const cplx<double>* x, const double*
     const int nc = ctx->nc;
     TRY(run(ctx, "macro", 0.0,
             [&] { return launch_macro(ctx->B, ctx->nc, ctx->activeflag, ctx->fU, xe, ctx->macroW, ctx->macroWf, ctx->stream); }));
-    Ax1InvArgs<double> a1{ctx->dims, freq<double>(ctx), twid<double>(ctx), x, nullptr, W, nullptr, ctx->pre};
-    TRY(run(ctx, "axis1_inv_f64", (3 + nc) * cp, [&] { return launch_ax1_inv<double>(AX1_PLAIN, a1, ctx->stream); }));
+    Ax1InvArgs<double> a1{ctx->dims, freq<double>(ctx), twid<double>(ctx), x, nullptr, nullptr, W, nullptr, ctx->pre};
     Ax2Args<double> a2{ctx->dims, twid<double>(ctx), W, nullptr};
-    TRY(run(ctx, "axis2_f64", 2 * nc * cp, [&] { return launch_ax2<double>(+1, a2, ctx->stream); }));
+    TRY(run(ctx, "pass1_grad_f64", (3 + nc) * cp, [&] { return launch_grad<double>(AX1_PLAIN, a1, ctx->stream); }));
+    TRY(run(ctx, "fft_ax2_f64", 2 * nc * cp, [&] { return launch_fft_ax2<double>(+1, a2, ctx->stream); }));
+    TRY(run(ctx, "fft_ax1_f64", 2 * nc * cp, [&] { return launch_fft_ax1<double>(+1, a2, ctx->stream); }));
     Ax3Args<double> a3 = ax3_base<double>(ctx, W);
     a3.macroW = ctx->macroW;
     if (ctx->model != DBFFT_ISO_ELASTIC) {
@@ -626,9 +629,10 @@ dbfft_status chain_residual(dbfft_ctx* ctx, const cplx<double>* x, const double*
         a3.sig_t = ctx->sig_t;
     }
     CK(cudaMemsetAsync(ctx->errw, 0, sizeof(unsigned), ctx->stream));
-    TRY(run(ctx, "axis3_update_f64", 2 * nc * cp + mat_bytes(ctx, true, true),
+    TRY(run(ctx, "pass3_update_f64", 2 * nc * cp + mat_bytes(ctx, true, true),
             [&] { return launch_ax3<double>(opk_update(ctx), a3, ctx->stream); }));
-    TRY(run(ctx, "axis2_f64", 2 * nc * cp, [&] { return launch_ax2<double>(-1, a2, ctx->stream); }));
+    TRY(run(ctx, "fft_ax1_f64", 2 * nc * cp, [&] { return launch_fft_ax1<double>(-1, a2, ctx->stream); }));
+    TRY(run(ctx, "fft_ax2_f64", 2 * nc * cp, [&] { return launch_fft_ax2<double>(-1, a2, ctx->stream); }));
     Ax1FwdArgs<double> a5;
     std::memset(&a5, 0, sizeof(a5));
     a5.d = ctx->dims;
@@ -640,12 +644,11 @@ dbfft_status chain_residual(dbfft_ctx* ctx, const cplx<double>* x, const double*
     a5.sig_f = ctx->sigf;
     a5.r_e = ctx->re64;
     a5.partials = ctx->partials;
-    TRY(run(ctx, "axis1_fwd_resid_f64", (3 + nc) * cp,
-            [&] { return launch_ax1_fwd<double>(AX5_RESID, a5, ctx->stream); }));
+    TRY(run(ctx, "pass5_div_resid_f64", (3 + nc) * cp,
+            [&] { return launch_div<double>(AX5_RESID, a5, ctx->stream); }));
     // the unknowns are Hermitian-consistent spectra: drop the round-off that breaks it
     TRY(run(ctx, "hermitian_planes", 0.0, [&] { return launch_herm_planes<double>(ctx->dims, ctx->r64, ctx->stream); }));
-    const int TW = ax1_tile(ctx->n1, true);
-    const int nblk = (int)((ctx->dims.plane + TW - 1) / TW);
+    const int nblk = (int)pw_blocks(ctx->H);
     CK(cudaMemcpyAsync(ctx->part_h, ctx->partials, (size_t)ctx->B * nblk * 2 * sizeof(double),
                        cudaMemcpyDeviceToHost, ctx->stream));
     unsigned* errh = reinterpret_cast<unsigned*>(ctx->small_h + ctx->B * 10);
@@ -699,11 +702,13 @@ dbfft_status build_cg_graph(dbfft_ctx* ctx, const Ax1InvArgs<T>& a1, const Ax2Ar
     CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
     cudaError_t e = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
-        e = launch_ax1_inv<T>(AX1_CG, a1, cs);
-        if (e == cudaSuccess) e = launch_ax2<T>(+1, a2, cs);
+        e = launch_grad<T>(AX1_CG, a1, cs);
+        if (e == cudaSuccess) e = launch_fft_ax2<T>(+1, a2, cs);
+        if (e == cudaSuccess) e = launch_fft_ax1<T>(+1, a2, cs);
         if (e == cudaSuccess) e = launch_ax3<T>(opk, a3, cs);
-        if (e == cudaSuccess) e = launch_ax2<T>(-1, a2, cs);
-        if (e == cudaSuccess) e = launch_ax1_fwd<T>(AX5_CG, a5, cs);
+        if (e == cudaSuccess) e = launch_fft_ax1<T>(-1, a2, cs);
+        if (e == cudaSuccess) e = launch_fft_ax2<T>(-1, a2, cs);
+        if (e == cudaSuccess) e = launch_div<T>(AX5_CG, a5, cs);
         if (e == cudaSuccess) {
             k_cg_continue<<<1, 32, 0, cs>>>(h, ctx->cg, ctx->B);
             e = cudaGetLastError();
@@ -752,7 +757,7 @@ dbfft_status inner_cg(dbfft_ctx* ctx, double tol, long long& it_sum, int& it_max
         return cudaGetLastError();
     }));
 
-    Ax1InvArgs<T> a1{ctx->dims, freq<T>(ctx), twid<T>(ctx), ri, pi, W, ctx->cg, ctx->pre};
+    Ax1InvArgs<T> a1{ctx->dims, freq<T>(ctx), twid<T>(ctx), ri, pi, xi, W, ctx->cg, ctx->pre};
     Ax2Args<T> a2{ctx->dims, twid<T>(ctx), W, ctx->cg};
     Ax3Args<T> a3 = ax3_base<T>(ctx, W);
     if constexpr (sizeof(T) == 4) a3.macroW = ctx->macroWf;
@@ -790,7 +795,7 @@ dbfft_status inner_cg(dbfft_ctx* ctx, double tol, long long& it_sum, int& it_max
         CK(cudaStreamSynchronize(ctx->stream));
         int mx = 1;
         for (int b = 0; b < ctx->B; ++b) mx = std::max(mx, ctx->cg_h[b].iter);
-        ctx->launches += 6LL * mx;
+        ctx->launches += 8LL * mx;
         it_max = 0;
         for (int b = 0; b < ctx->B; ++b) {
             it_sum += ctx->cg_h[b].iter;
@@ -807,14 +812,16 @@ dbfft_status inner_cg(dbfft_ctx* ctx, double tol, long long& it_sum, int& it_max
         const double cp = cpass(ctx, dbl, nact);
         const double mb = mat_bytes(ctx, dbl, false) * (ctx->model == DBFFT_ISO_ELASTIC ? 1.0 : (double)nact / ctx->B);
         for (int k = 0; k < chunk; ++k) {
-            TRY(run(ctx, dbl ? "axis1_inv_cg_f64" : "axis1_inv_cg_f32", (9 + nc) * cp,
-                    [&] { return launch_ax1_inv<T>(AX1_CG, a1, ctx->stream); }));
-            TRY(run(ctx, dbl ? "axis2_f64" : "axis2_f32", 2 * nc * cp, [&] { return launch_ax2<T>(+1, a2, ctx->stream); }));
-            TRY(run(ctx, dbl ? "axis3_apply_f64" : "axis3_apply_f32", 2 * nc * cp + mb,
+            TRY(run(ctx, dbl ? "pass1_grad_cg_f64" : "pass1_grad_cg_f32", (15 + nc) * cp,
+                    [&] { return launch_grad<T>(AX1_CG, a1, ctx->stream); }));
+            TRY(run(ctx, dbl ? "fft_ax2_f64" : "fft_ax2_f32", 2 * nc * cp, [&] { return launch_fft_ax2<T>(+1, a2, ctx->stream); }));
+            TRY(run(ctx, dbl ? "fft_ax1_f64" : "fft_ax1_f32", 2 * nc * cp, [&] { return launch_fft_ax1<T>(+1, a2, ctx->stream); }));
+            TRY(run(ctx, dbl ? "pass3_tangent_f64" : "pass3_tangent_f32", 2 * nc * cp + mb,
                     [&] { return launch_ax3<T>(opk, a3, ctx->stream); }));
-            TRY(run(ctx, dbl ? "axis2_f64" : "axis2_f32", 2 * nc * cp, [&] { return launch_ax2<T>(-1, a2, ctx->stream); }));
-            TRY(run(ctx, dbl ? "axis1_fwd_cg_f64" : "axis1_fwd_cg_f32", (15 + nc) * cp,
-                    [&] { return launch_ax1_fwd<T>(AX5_CG, a5, ctx->stream); }));
+            TRY(run(ctx, dbl ? "fft_ax1_f64" : "fft_ax1_f32", 2 * nc * cp, [&] { return launch_fft_ax1<T>(-1, a2, ctx->stream); }));
+            TRY(run(ctx, dbl ? "fft_ax2_f64" : "fft_ax2_f32", 2 * nc * cp, [&] { return launch_fft_ax2<T>(-1, a2, ctx->stream); }));
+            TRY(run(ctx, dbl ? "pass5_div_cg_f64" : "pass5_div_cg_f32", (6 + nc) * cp,
+                    [&] { return launch_div<T>(AX5_CG, a5, ctx->stream); }));
         }
         launched += chunk;
         CK(cudaMemcpyAsync(ctx->cg_h, ctx->cg, ctx->B * sizeof(CgState), cudaMemcpyDeviceToHost, ctx->stream));
@@ -953,11 +960,13 @@ dbfft_status solve_current(dbfft_ctx* ctx, dbfft_report* rep) {
         }
         it_max_all += itm;
         TRY(set_scales(ctx, sb));
-        TRY(run(ctx, "from_inner", 3 * (2 * c64 + ci), [&] {
+        TRY(run(ctx, "from_inner", 3 * (2 * c64 + 2 * ci), [&] {
             if (inner64)
-                return launch_from_inner<double>(ctx->dims, reinterpret_cast<const cplx<double>*>(ctx->xi), ctx->xe_i,
+                return launch_from_inner<double>(ctx->dims, reinterpret_cast<const cplx<double>*>(ctx->xi),
+                                                 reinterpret_cast<const cplx<double>*>(ctx->pi), ctx->cg, ctx->xe_i,
                                                  ctx->scal, ctx->x64, ctx->xe64, ctx->stream);
-            return launch_from_inner<float>(ctx->dims, reinterpret_cast<const cplx<float>*>(ctx->xi), ctx->xe_i,
+            return launch_from_inner<float>(ctx->dims, reinterpret_cast<const cplx<float>*>(ctx->xi),
+                                            reinterpret_cast<const cplx<float>*>(ctx->pi), ctx->cg, ctx->xe_i,
                                             ctx->scal, ctx->x64, ctx->xe64, ctx->stream);
         }));
         ++steps;
@@ -1285,8 +1294,8 @@ static dbfft_status create_impl(dbfft_ctx* ctx, const dbfft_grid* grid, const db
     CK(cudaMemsetAsync(ctx->macroW2, 0, ctx->B * 9 * sizeof(double), ctx->stream));
     // reduction partials: the largest grid of any reducing kernel
     {
-        const long long nb1 = (ctx->dims.plane + ax1_tile(ctx->n1, false) - 1) / ax1_tile(ctx->n1, false);
-        const long long nb1d = (ctx->dims.plane + ax1_tile(ctx->n1, true) - 1) / ax1_tile(ctx->n1, true);
+        const long long nb1 = pw_blocks(ctx->H);  // element-wise kernels of passes 1 and 5
+        const long long nb1d = nb1;
         const long long nlines = (long long)ctx->n1 * ctx->n2;
         const long long nb3 = (nlines + ax3_lines(ctx->n3, ctx->nc, ctx->RB, false) - 1) /
                               ax3_lines(ctx->n3, ctx->nc, ctx->RB, false);
@@ -1507,14 +1516,16 @@ dbfft_status dbfft_adjoint(dbfft_ctx* ctx, const double* dJ_dsigma, double* dJ_d
     CK(cudaMemcpyAsync(ctx->macroW, fUfwd.data(), ctx->B * 9 * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
     cplx<double>* W = reinterpret_cast<cplx<double>*>(ctx->W);
     cplx<double>* W2 = reinterpret_cast<cplx<double>*>(ctx->W2);
-    Ax1InvArgs<double> a1{ctx->dims, freq<double>(ctx), twid<double>(ctx), ctx->xfwd, nullptr, W, nullptr, ctx->pre};
-    TRY(run(ctx, "axis1_inv_f64", 0.0, [&] { return launch_ax1_inv<double>(AX1_PLAIN, a1, ctx->stream); }));
+    Ax1InvArgs<double> a1{ctx->dims, freq<double>(ctx), twid<double>(ctx), ctx->xfwd, nullptr, nullptr, W, nullptr, ctx->pre};
     Ax2Args<double> a2{ctx->dims, twid<double>(ctx), W, nullptr};
-    TRY(run(ctx, "axis2_f64", 0.0, [&] { return launch_ax2<double>(+1, a2, ctx->stream); }));
-    Ax1InvArgs<double> b1{ctx->dims, freq<double>(ctx), twid<double>(ctx), ctx->x64, nullptr, W2, nullptr, ctx->pre};
-    TRY(run(ctx, "axis1_inv_f64", 0.0, [&] { return launch_ax1_inv<double>(AX1_PLAIN, b1, ctx->stream); }));
+    TRY(run(ctx, "pass1_grad_f64", 0.0, [&] { return launch_grad<double>(AX1_PLAIN, a1, ctx->stream); }));
+    TRY(run(ctx, "fft_ax2_f64", 0.0, [&] { return launch_fft_ax2<double>(+1, a2, ctx->stream); }));
+    TRY(run(ctx, "fft_ax1_f64", 0.0, [&] { return launch_fft_ax1<double>(+1, a2, ctx->stream); }));
+    Ax1InvArgs<double> b1{ctx->dims, freq<double>(ctx), twid<double>(ctx), ctx->x64, nullptr, nullptr, W2, nullptr, ctx->pre};
     Ax2Args<double> b2{ctx->dims, twid<double>(ctx), W2, nullptr};
-    TRY(run(ctx, "axis2_f64", 0.0, [&] { return launch_ax2<double>(+1, b2, ctx->stream); }));
+    TRY(run(ctx, "pass1_grad_f64", 0.0, [&] { return launch_grad<double>(AX1_PLAIN, b1, ctx->stream); }));
+    TRY(run(ctx, "fft_ax2_f64", 0.0, [&] { return launch_fft_ax2<double>(+1, b2, ctx->stream); }));
+    TRY(run(ctx, "fft_ax1_f64", 0.0, [&] { return launch_fft_ax1<double>(+1, b2, ctx->stream); }));
     Ax3Args<double> a3 = ax3_base<double>(ctx, W);
     a3.L = ax3_lines(ctx->n3, ctx->nc, ctx->RB, true, 2);
     a3.W2 = W2;
@@ -1524,7 +1535,7 @@ dbfft_status dbfft_adjoint(dbfft_ctx* ctx, const double* dJ_dsigma, double* dJ_d
     a3.mu = ctx->mu1;
     a3.scale = nullptr;
     a3.dJdE = dJ_dE;
-    TRY(run(ctx, "axis3_adjoint_f64", 0.0, [&] { return launch_ax3<double>(OP_ADJ, a3, ctx->stream); }));
+    TRY(run(ctx, "pass3_adjoint_f64", 0.0, [&] { return launch_ax3<double>(OP_ADJ, a3, ctx->stream); }));
     // restore the forward state
     CK(cudaMemcpyAsync(ctx->x64, ctx->xfwd, nU * sizeof(cplx<double>), cudaMemcpyDeviceToDevice, ctx->stream));
     TRY(set_load(ctx, 0, ctx->target.data()));

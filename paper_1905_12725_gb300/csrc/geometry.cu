@@ -7,10 +7,11 @@ bool supported_len(int n) { return n == 8 || n == 16 || n == 32 || n == 64 || n 
 
 static int radix_for(int n, bool dbl) { return radix_ax2(n, dbl); }
 
-int ax1_tile(int n1, bool dbl) {
-    const int P = n1 / radix_ax1(n1, dbl);  // threads per column; the block is tw x P = AX1_THREADS
-    return AX1_THREADS / P;
+long long pw_blocks(long long H) {
+    const long long nb = (H + PW_THREADS - 1) / PW_THREADS;
+    return nb < 2048 ? nb : 2048;  // grid-stride loops beyond 2048 blocks per right-hand side
 }
+
 int ax2_tile(int n2, bool dbl) {
     const int P = n2 / radix_ax2(n2, dbl);
     int tw = 256 / P;

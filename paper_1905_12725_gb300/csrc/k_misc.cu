@@ -46,17 +46,21 @@ __global__ void k_to_inner(long long n3H, int B, const cplx<double>* r64, const 
     }
 }
 
+// x64 += s (x_i + alpha p_i): the inner PCG applies each iterate update one
+// iteration late (in the next pass 1), so the last alpha p is added here.
 template <typename Ti>
-__global__ void k_from_inner(long long n3H, int B, const cplx<Ti>* xi, const double* xe_i, const double* sb,
-                             cplx<double>* x64, double* xe64) {
+__global__ void k_from_inner(long long n3H, int B, const cplx<Ti>* xi, const cplx<Ti>* pi, const CgState* cg,
+                             const double* xe_i, const double* sb, cplx<double>* x64, double* xe64) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const int b = blockIdx.y;
     const double s = sb[b];
+    const Ti al = (Ti)cg[b].alpha;
     if (i < n3H) {
         cplx<double> v = x64[(long long)b * n3H + i];
-        const cplx<Ti> d = xi[(long long)b * n3H + i];
-        v.x += s * (double)d.x;
-        v.y += s * (double)d.y;
+        const cplx<Ti> dx = xi[(long long)b * n3H + i];
+        const cplx<Ti> dp = pi[(long long)b * n3H + i];
+        v.x += s * (double)(dx.x + al * dp.x);
+        v.y += s * (double)(dx.y + al * dp.y);
         x64[(long long)b * n3H + i] = v;
     }
     if (blockIdx.x == 0 && threadIdx.x < 9) xe64[b * 9 + threadIdx.x] += s * xe_i[b * 9 + threadIdx.x];
@@ -70,20 +74,20 @@ cudaError_t launch_to_inner(const Dims& d, const cplx<double>* r64, const double
     return cudaGetLastError();
 }
 template <typename Ti>
-cudaError_t launch_from_inner(const Dims& d, const cplx<Ti>* xi, const double* xe_i, const double* sb,
-                              cplx<double>* x64, double* xe64, cudaStream_t s) {
+cudaError_t launch_from_inner(const Dims& d, const cplx<Ti>* xi, const cplx<Ti>* pi, const CgState* cg,
+                              const double* xe_i, const double* sb, cplx<double>* x64, double* xe64, cudaStream_t s) {
     const long long n = 3 * d.H;
-    k_from_inner<Ti><<<dim3((unsigned)((n + 255) / 256), d.B), 256, 0, s>>>(n, d.B, xi, xe_i, sb, x64, xe64);
+    k_from_inner<Ti><<<dim3((unsigned)((n + 255) / 256), d.B), 256, 0, s>>>(n, d.B, xi, pi, cg, xe_i, sb, x64, xe64);
     return cudaGetLastError();
 }
 template cudaError_t launch_to_inner<float>(const Dims&, const cplx<double>*, const double*, const double*,
                                             cplx<float>*, double*, cplx<float>*, double*, cudaStream_t);
 template cudaError_t launch_to_inner<double>(const Dims&, const cplx<double>*, const double*, const double*,
                                              cplx<double>*, double*, cplx<double>*, double*, cudaStream_t);
-template cudaError_t launch_from_inner<float>(const Dims&, const cplx<float>*, const double*, const double*,
-                                              cplx<double>*, double*, cudaStream_t);
-template cudaError_t launch_from_inner<double>(const Dims&, const cplx<double>*, const double*, const double*,
-                                               cplx<double>*, double*, cudaStream_t);
+template cudaError_t launch_from_inner<float>(const Dims&, const cplx<float>*, const cplx<float>*, const CgState*,
+                                              const double*, const double*, cplx<double>*, double*, cudaStream_t);
+template cudaError_t launch_from_inner<double>(const Dims&, const cplx<double>*, const cplx<double>*, const CgState*,
+                                               const double*, const double*, cplx<double>*, double*, cudaStream_t);
 
 // out = M u: N Q(xi)^-1 u per frequency (zero on the null set), macro block Me e.
 template <typename T>

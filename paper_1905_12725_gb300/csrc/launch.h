@@ -7,16 +7,17 @@
 namespace dbfft {
 
 // Launch geometry shared by the launchers and the buffer sizing.
-int ax1_tile(int n1, bool dbl);                      // columns per CTA of passes 1 and 5
-int ax2_tile(int n2, bool dbl);                      // columns per CTA of passes 2 and 4
+long long pw_blocks(long long H);                    // grid (per right-hand side) of the element-wise kernels
+int ax2_tile(int n, bool dbl);                       // columns per CTA of the strided transforms
 int ax3_lines(int n3, int nc, int rb, bool dbl, int nfields = 1);  // grid lines per CTA of pass 3
 int ax3_threads_per_line(int n3, int nc, int rb, bool dbl);
 size_t ax3_smem(int n3, int nc, int rb, int lines, bool dbl, bool two_fields);
 bool supported_len(int n);
 
-template <typename T> cudaError_t launch_ax1_inv(int mode, const Ax1InvArgs<T>& a, cudaStream_t s);
-template <typename T> cudaError_t launch_ax1_fwd(int mode, const Ax1FwdArgs<T>& a, cudaStream_t s);
-template <typename T> cudaError_t launch_ax2(int dir, const Ax2Args<T>& a, cudaStream_t s);
+template <typename T> cudaError_t launch_grad(int mode, const Ax1InvArgs<T>& a, cudaStream_t s);
+template <typename T> cudaError_t launch_div(int mode, const Ax1FwdArgs<T>& a, cudaStream_t s);
+template <typename T> cudaError_t launch_fft_ax1(int dir, const Ax2Args<T>& a, cudaStream_t s);
+template <typename T> cudaError_t launch_fft_ax2(int dir, const Ax2Args<T>& a, cudaStream_t s);
 template <typename T> cudaError_t launch_ax3(int opk, const Ax3Args<T>& a, cudaStream_t s);
 
 }  // namespace dbfft

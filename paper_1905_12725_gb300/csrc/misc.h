@@ -9,8 +9,8 @@ template <typename Ti>
 cudaError_t launch_to_inner(const Dims& d, const cplx<double>* r64, const double* re64, const double* sc, cplx<Ti>* ri,
                             double* re_i, cplx<Ti>* xi, double* xe_i, cudaStream_t s);
 template <typename Ti>
-cudaError_t launch_from_inner(const Dims& d, const cplx<Ti>* xi, const double* xe_i, const double* sb,
-                              cplx<double>* x64, double* xe64, cudaStream_t s);
+cudaError_t launch_from_inner(const Dims& d, const cplx<Ti>* xi, const cplx<Ti>* pi, const CgState* cg,
+                              const double* xe_i, const double* sb, cplx<double>* x64, double* xe64, cudaStream_t s);
 template <typename T>
 cudaError_t launch_precond_field(const Dims& d, const Freq<T>& f, const PrecondData* pre, const cplx<T>* u,
                                  cplx<T>* out, const double* e_in, double* e_out, cudaStream_t s);

@@ -114,10 +114,11 @@ extern "C" dbfft_status dbfft_apply_iso_noalloc(const int n[3], const double L[3
     const Twiddles<double> twd{sym->tw, sym->tw + kMaxLen, sym->tw + 2 * kMaxLen, sym->tw + 3 * kMaxLen};
     cplx<double>* W = reinterpret_cast<cplx<double>*>(sym->scratch);  // fully overwritten by pass 1
 
-    Ax1InvArgs<double> a1{d, f, twd, reinterpret_cast<const cplx<double>*>(u_hat), nullptr, W, nullptr, nullptr};
-    if (launch_ax1_inv<double>(AX1_PLAIN, a1, s) != cudaSuccess) return DBFFT_E_CUDA;
+    Ax1InvArgs<double> a1{d, f, twd, reinterpret_cast<const cplx<double>*>(u_hat), nullptr, nullptr, W, nullptr, nullptr};
     Ax2Args<double> a2{d, twd, W, nullptr};
-    if (launch_ax2<double>(+1, a2, s) != cudaSuccess) return DBFFT_E_CUDA;
+    if (launch_grad<double>(AX1_PLAIN, a1, s) != cudaSuccess) return DBFFT_E_CUDA;
+    if (launch_fft_ax2<double>(+1, a2, s) != cudaSuccess) return DBFFT_E_CUDA;
+    if (launch_fft_ax1<double>(+1, a2, s) != cudaSuccess) return DBFFT_E_CUDA;
     Ax3Args<double> a3{};
     a3.d = d;
     a3.tw = twd;
@@ -129,14 +130,15 @@ extern "C" dbfft_status dbfft_apply_iso_noalloc(const int n[3], const double L[3
     a3.lam = lam;
     a3.mu = mu;
     if (launch_ax3<double>(OP_ISO, a3, s) != cudaSuccess) return DBFFT_E_CUDA;
-    if (launch_ax2<double>(-1, a2, s) != cudaSuccess) return DBFFT_E_CUDA;
+    if (launch_fft_ax1<double>(-1, a2, s) != cudaSuccess) return DBFFT_E_CUDA;
+    if (launch_fft_ax2<double>(-1, a2, s) != cudaSuccess) return DBFFT_E_CUDA;
     Ax1FwdArgs<double> a5{};
     a5.d = d;
     a5.f = f;
     a5.tw = twd;
     a5.W = W;
     a5.out = reinterpret_cast<cplx<double>*>(out);
-    if (launch_ax1_fwd<double>(AX5_PLAIN, a5, s) != cudaSuccess) return DBFFT_E_CUDA;
+    if (launch_div<double>(AX5_PLAIN, a5, s) != cudaSuccess) return DBFFT_E_CUDA;
     if (cudaStreamSynchronize(s) != cudaSuccess) return DBFFT_E_CUDA;
     return DBFFT_OK;
 }

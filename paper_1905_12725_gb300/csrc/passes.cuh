@@ -5,11 +5,15 @@
 // h = n3/2 + 1 (nc = 6 strain components 11,22,33,23,13,12 at small strain,
 // nc = 9 components 3i+j of the displacement gradient at finite strain).
 //
-//   pass 1  axis 1, inverse : u (3 comps) -> s.u or g.u (nc comps), C2C   [k_axis1_inv]
-//   pass 2  axis 2, inverse : C2C                                         [k_axis2]
+//   pass 1  axis 2, inverse : u (3 comps) -> s.u or g.u (nc comps), C2C   [k_pass1]
+//   pass 2  axis 1, inverse : C2C                                         [k_fft_strided]
 //   pass 3  axis 3          : C2R, per-voxel tangent / constitutive, R2C  [k_axis3]
-//   pass 4  axis 2, forward : C2C                                         [k_axis2]
-//   pass 5  axis 1, forward : C2C, divergence d:sigma, null mask, CG      [k_axis1_fwd]
+//   pass 4  axis 1, forward : C2C                                         [k_fft_strided]
+//   pass 5  axis 2, forward : C2C, divergence d:sigma, null mask, CG      [k_pass5]
+//
+// The fused passes run along axis 2, whose stride (n3/2 + 1 entries) keeps a
+// column tile inside one compact region; the pure transforms run along
+// axis 1 (stride n2 (n3/2 + 1)) with wide tiles.
 //
 // Inside CG, pass 1 also forms the new search direction p = M r + beta p
 // (the preconditioner of Sec. 2.5 evaluated on the fly from the frequency),
@@ -152,134 +156,129 @@ struct Ax1InvArgs {
     Twiddles<T> tw;
     const cplx<T>* in;   // PLAIN: u [B][3][H]; CG: r [B][3][H]
     cplx<T>* p;          // CG: search direction [B][3][H], updated in place
+    cplx<T>* x;          // CG: iterate [B][3][H]; x += alpha_prev p_old is applied here
     cplx<T>* W;          // [B][nc][H]
     const CgState* cg;   // CG (beta, done)
     const PrecondData* pre;  // [B / Rm] per material group
 };
 
-// Threads per CTA of passes 1 and 5 (TW columns x P threads per column).
-constexpr int AX1_THREADS = 128;
+// Threads per CTA of the element-wise kernels of passes 1 and 5.
+constexpr int PW_THREADS = 256;
 
-// Pass 1. Shared memory: the FFT exchange tile [N1][TW] and, per thread, the
-// three displacement components of its R frequencies ([3][R][threads],
-// thread-private, so no synchronisation is needed around them).
-template <typename T, int N1, int NC, int MODE>
-__global__ void __launch_bounds__(AX1_THREADS, (sizeof(T) == 4 ? 8 : 4)) k_axis1_inv(Ax1InvArgs<T> a) {
-    constexpr int R = RadixAx1<T, N1>::value;
-    constexpr int P = N1 / R;
-    constexpr int TW = AX1_THREADS / P;
-    extern __shared__ __align__(16) unsigned char smraw[];
-    cplx<T>* sm = reinterpret_cast<cplx<T>*>(smraw);
-    cplx<T>* su = sm + N1 * TW;  // [3][R][AX1_THREADS]
-    const int w = threadIdx.x, p = threadIdx.y;
-    const int tid = w + p * TW;
+// Frequency indices of half-spectrum entry i (k3 fastest).
+struct FreqIdx {
+    int k1, k2, k3;
+};
+__device__ __forceinline__ FreqIdx freq_idx(const Dims& d, long long i) {
+    FreqIdx f;
+    const long long k1 = i / d.plane;
+    const long long rem = i - k1 * d.plane;
+    f.k1 = (int)k1;
+    f.k2 = (int)(rem / d.h);
+    f.k3 = (int)(rem - (long long)f.k2 * d.h);
+    return f;
+}
+
+// Pass 1a, element-wise over frequencies: the Fourier (symmetric) gradient of
+// u scaled by 1/N (the inverse transforms that follow are unnormalised).
+// In CG mode u is the new search direction p = M r + beta p_old, formed here
+// from r, together with the deferred iterate update x += alpha_prev p_old.
+template <typename T, int NC, int MODE>
+__global__ void __launch_bounds__(PW_THREADS) k_grad(Ax1InvArgs<T> a) {
     const int b = blockIdx.y;
     if (MODE == AX1_CG && a.cg[b].done) return;
     const Dims& d = a.d;
-    const long long j = (long long)blockIdx.x * TW + w;
-    const bool valid = j < d.plane;
-    const int k2 = valid ? (int)(j / d.h) : 0;
-    const int k3 = valid ? (int)(j - (long long)k2 * d.h) : 0;
-    const T x2 = a.f.xi2[k2], x3 = a.f.xi3[k3];
-    auto U = [&](int c, int r) -> cplx<T>& { return su[(c * R + r) * AX1_THREADS + tid]; };
-
-#pragma unroll
-    for (int c = 0; c < 3; ++c)
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-            const long long idx = ((long long)(b * 3 + c) * N1 + (p + r * P)) * d.plane + j;
-            U(c, r) = valid ? ldc(a.in + idx) : zero_c<T>();
-        }
+    const T s = (T)d.invN;
+    T beta = T(0), alpha = T(0), N = T(0);
+    const PrecondData* pd = nullptr;
     if constexpr (MODE == AX1_CG) {
-        const T beta = (T)a.cg[b].beta;
-        const PrecondData& pd = a.pre[b / d.Rm];
-        const T N = (T)(1.0 / d.invN);
+        beta = (T)a.cg[b].beta;
+        alpha = (T)a.cg[b].alpha;
+        N = (T)(1.0 / d.invN);
+        pd = a.pre + b / d.Rm;
+    }
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < d.H; i += (long long)gridDim.x * blockDim.x) {
+        const FreqIdx fi = freq_idx(d, i);
+        const T x1 = a.f.xi1[fi.k1], x2 = a.f.xi2[fi.k2], x3 = a.f.xi3[fi.k3];
+        cplx<T> u[3];
 #pragma unroll
-        for (int r = 0; r < R; ++r) {
-            const int k1 = p + r * P;
-            cplx<T> rr[3] = {U(0, r), U(1, r), U(2, r)};
-            cplx<T> z[3];
-            precond_apply<T>(pcoef<T>(pd), a.f.xi1[k1], x2, x3, N, rr, z);
+        for (int c = 0; c < 3; ++c) u[c] = ldc(a.in + (long long)(b * 3 + c) * d.H + i);
+        if constexpr (MODE == AX1_CG) {
+            cplx<T> z[3], po[3], xo[3];
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
-                const long long idx = ((long long)(b * 3 + c) * N1 + k1) * d.plane + j;
-                cplx<T> po = valid ? ldc(a.p + idx) : zero_c<T>();
-                cplx<T> pn = z[c] + po * beta;
-                if (valid) stc(a.p + idx, pn);
-                U(c, r) = pn;
+                po[c] = ldc(a.p + (long long)(b * 3 + c) * d.H + i);
+                xo[c] = ldc(a.x + (long long)(b * 3 + c) * d.H + i);
+            }
+            precond_apply<T>(pcoef<T>(*pd), x1, x2, x3, N, u, z);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                u[c] = z[c] + po[c] * beta;
+                stc(a.p + (long long)(b * 3 + c) * d.H + i, u[c]);
+                stc(a.x + (long long)(b * 3 + c) * d.H + i, xo[c] + po[c] * alpha);
             }
         }
-    }
-    const T s = (T)d.invN;
-    auto emit = [&](auto mc) {
-        constexpr int M = decltype(mc)::value;
-        cplx<T> v[R];
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-            cplx<T> uu[3] = {U(0, r), U(1, r), U(2, r)};
-            v[r] = grad_comp<T, NC, M>(uu, a.f.xi1[p + r * P], x2, x3, s);
+        cplx<T>* Wb = a.W + (long long)b * NC * d.H + i;
+        stc(Wb + 0 * d.H, grad_comp<T, NC, 0>(u, x1, x2, x3, s));
+        stc(Wb + 1 * d.H, grad_comp<T, NC, 1>(u, x1, x2, x3, s));
+        stc(Wb + 2 * d.H, grad_comp<T, NC, 2>(u, x1, x2, x3, s));
+        stc(Wb + 3 * d.H, grad_comp<T, NC, 3>(u, x1, x2, x3, s));
+        stc(Wb + 4 * d.H, grad_comp<T, NC, 4>(u, x1, x2, x3, s));
+        stc(Wb + 5 * d.H, grad_comp<T, NC, 5>(u, x1, x2, x3, s));
+        if constexpr (NC == 9) {
+            stc(Wb + 6 * d.H, grad_comp<T, NC, 6>(u, x1, x2, x3, s));
+            stc(Wb + 7 * d.H, grad_comp<T, NC, 7>(u, x1, x2, x3, s));
+            stc(Wb + 8 * d.H, grad_comp<T, NC, 8>(u, x1, x2, x3, s));
         }
-        ColFFT<T, N1, R, +1>::run(v, sm + w, TW, p, a.tw.t1);
-        if (valid) {
-#pragma unroll
-            for (int r = 0; r < R; ++r)
-                stc(a.W + ((long long)(b * NC + M) * N1 + (p + r * P)) * d.plane + j, v[r]);
-        }
-    };
-    emit(std::integral_constant<int, 0>());
-    emit(std::integral_constant<int, 1>());
-    emit(std::integral_constant<int, 2>());
-    emit(std::integral_constant<int, 3>());
-    emit(std::integral_constant<int, 4>());
-    emit(std::integral_constant<int, 5>());
-    if constexpr (NC == 9) {
-        emit(std::integral_constant<int, 6>());
-        emit(std::integral_constant<int, 7>());
-        emit(std::integral_constant<int, 8>());
     }
 }
 
 // ------------------------------------------------------------------ pass 2/4
+// Pure C2C transform of length N along a strided axis: column col = outer *
+// inner + in (in < inner), element t at outer * N * inner + t * inner + in.
+// Axis 1: inner = n2 h, outer = b * nc + c. A warp covers consecutive
+// columns, so every row segment of a tile is contiguous.
 template <typename T>
 struct Ax2Args {
     Dims d;
     Twiddles<T> tw;
     cplx<T>* W;
-    const CgState* cg;  // may be null
+    const CgState* cg;  // may be null: right-hand sides with done set are skipped
+    const cplx<T>* tab; // twiddle table of this axis (length N)
+    long long inner;    // stride of the transformed axis (in entries)
+    long long ncols;    // columns in total
+    long long cols_per_b;
 };
 
-template <typename T, int N2, int DIR>
-__global__ void __launch_bounds__(256) k_axis2(Ax2Args<T> a) {
-    constexpr int R = RadixFor<T, N2>::value;
-    constexpr int P = N2 / R;
+template <typename T, int N, int DIR>
+__global__ void __launch_bounds__(256) k_fft_strided(Ax2Args<T> a) {
+    constexpr int R = RadixFor<T, N>::value;
+    constexpr int P = N / R;
     extern __shared__ __align__(16) unsigned char smraw[];
     cplx<T>* sm = reinterpret_cast<cplx<T>*>(smraw);
-    const Dims& d = a.d;
     const int TW = blockDim.x;
     const int w = threadIdx.x, p = threadIdx.y;
-    const long long ncols = (long long)d.B * d.nc * d.n1 * d.h;
     const long long c0 = (long long)blockIdx.x * TW;
     if (a.cg) {  // skip tiles whose right-hand sides are all finished
-        const long long per_b = (long long)d.nc * d.n1 * d.h;
-        const int bfirst = (int)(c0 / per_b);
-        const long long clast = min(c0 + TW, ncols) - 1;
-        const int blast = (int)(clast / per_b);
+        const int bfirst = (int)(c0 / a.cols_per_b);
+        const long long clast = min(c0 + TW, a.ncols) - 1;
+        const int blast = (int)(clast / a.cols_per_b);
         bool all_done = true;
         for (int bb = bfirst; bb <= blast; ++bb) all_done &= (a.cg[bb].done != 0);
         if (all_done) return;
     }
     const long long col = c0 + w;
-    const bool valid = col < ncols;
-    const long long outer = valid ? col / d.h : 0;
-    const long long k3 = valid ? col - outer * d.h : 0;
-    const long long base = outer * (long long)N2 * d.h + k3;
+    const bool valid = col < a.ncols;
+    const long long outer = valid ? col / a.inner : 0;
+    const long long in = valid ? col - outer * a.inner : 0;
+    const long long base = outer * (long long)N * a.inner + in;
     cplx<T> v[R];
 #pragma unroll
-    for (int r = 0; r < R; ++r) v[r] = valid ? ldc(a.W + base + (long long)(p + r * P) * d.h) : zero_c<T>();
-    ColFFT<T, N2, R, DIR>::run(v, sm + w, TW, p, a.tw.t2);
+    for (int r = 0; r < R; ++r) v[r] = valid ? ldc(a.W + base + (long long)(p + r * P) * a.inner) : zero_c<T>();
+    ColFFT<T, N, R, DIR>::run(v, sm + w, TW, p, a.tab);
     if (valid) {
 #pragma unroll
-        for (int r = 0; r < R; ++r) stc(a.W + base + (long long)(p + r * P) * d.h, v[r]);
+        for (int r = 0; r < R; ++r) stc(a.W + base + (long long)(p + r * P) * a.inner, v[r]);
     }
 }
 
@@ -310,111 +309,100 @@ struct Ax1FwdArgs {
     unsigned* counters;  // [B]
 };
 
-// Pass 5. Shared memory: the FFT exchange tile and, per thread, the three
-// divergence accumulators of its R frequencies ([3][R][threads], private).
-template <typename T, int N1, int NC, int MODE>
-__global__ void __launch_bounds__(AX1_THREADS, (sizeof(T) == 4 ? 8 : 4)) k_axis1_fwd(Ax1FwdArgs<T> a) {
-    constexpr int R = RadixAx1<T, N1>::value;
-    constexpr int P = N1 / R;
-    constexpr int TW = AX1_THREADS / P;
-    extern __shared__ __align__(16) unsigned char smraw[];
-    cplx<T>* sm = reinterpret_cast<cplx<T>*>(smraw);
-    cplx<T>* sq = sm + N1 * TW;  // [3][R][AX1_THREADS]
+// Pass 5b, element-wise over frequencies, after the forward transforms:
+// q = B^H sigma = -(i/N) xi_j sigma-hat_ij (zero on the null set), then
+//  PLAIN: out = q (and E^T sigma-hat(0) into e_out);
+//  RESID: out = -q, the mean stress and the macro residual, ||r||^2 partials;
+//  CG:    r -= alpha q (the iterate update is deferred to the next pass 1),
+//         <r, M r> and ||r||^2; the last block sets beta and the stop flag.
+template <typename T, int NC, int MODE>
+__global__ void __launch_bounds__(PW_THREADS) k_div(Ax1FwdArgs<T> a) {
     __shared__ double red[32 * 2];
-    __shared__ double s0[9][2];
     __shared__ bool is_last;
-    const int w = threadIdx.x, p = threadIdx.y;
-    const int tid = w + p * TW;
     const int b = blockIdx.y;
+    const int tid = threadIdx.x;
     const Dims& d = a.d;
     if (MODE == AX5_CG && a.cg[b].done) return;
-    const long long j = (long long)blockIdx.x * TW + w;
-    const bool valid = j < d.plane;
-    const int k2 = valid ? (int)(j / d.h) : 0;
-    const int k3 = valid ? (int)(j - (long long)k2 * d.h) : 0;
-    const T x2 = a.f.xi2[k2], x3 = a.f.xi3[k3];
-    const bool has0 = valid && j == 0 && p == 0;  // holds k = (0,0,0) in register 0
-    auto Q = [&](int c, int r) -> cplx<T>& { return sq[(c * R + r) * AX1_THREADS + tid]; };
-
-#pragma unroll
-    for (int c = 0; c < 3; ++c)
-#pragma unroll
-        for (int r = 0; r < R; ++r) Q(c, r) = zero_c<T>();
-
-    auto take = [&](auto mc) {
-        constexpr int M = decltype(mc)::value;
-        cplx<T> v[R];
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-            const long long idx = ((long long)(b * NC + M) * N1 + (p + r * P)) * d.plane + j;
-            v[r] = valid ? ldc(a.W + idx) : zero_c<T>();
-        }
-        ColFFT<T, N1, R, -1>::run(v, sm + w, TW, p, a.tw.t1);
-        if (has0) { s0[M][0] = (double)v[0].x; s0[M][1] = (double)v[0].y; }
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-            cplx<T> ac[3] = {Q(0, r), Q(1, r), Q(2, r)};
-            div_acc<T, NC, M>(ac, v[r], a.f.xi1[p + r * P], x2, x3);
-            Q(0, r) = ac[0]; Q(1, r) = ac[1]; Q(2, r) = ac[2];
-        }
-    };
-    take(std::integral_constant<int, 0>());
-    take(std::integral_constant<int, 1>());
-    take(std::integral_constant<int, 2>());
-    take(std::integral_constant<int, 3>());
-    take(std::integral_constant<int, 4>());
-    take(std::integral_constant<int, 5>());
-    if constexpr (NC == 9) {
-        take(std::integral_constant<int, 6>());
-        take(std::integral_constant<int, 7>());
-        take(std::integral_constant<int, 8>());
-    }
-    // q = B^H sigma = -(i / N) xi_j sigma_ij, zero on the null set
     const T ms = -(T)d.invN;
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-        const bool z = (a.f.xi1[p + r * P] == T(0)) && (x2 == T(0)) && (x3 == T(0));
-#pragma unroll
-        for (int c = 0; c < 3; ++c) Q(c, r) = z ? zero_c<T>() : mul_i(ms, Q(c, r));
+    T alpha = T(0), N = T(0);
+    const PrecondData* pd = a.pre ? a.pre + b / d.Rm : nullptr;
+    if constexpr (MODE == AX5_CG) {
+        alpha = (T)a.cg[b].alpha;
+        N = (T)(1.0 / d.invN);
     }
-    const int wgt = hweight(k3, d.m);
+    T acc0 = T(0), acc1 = T(0);  // CG: <r, M r>, ||r||^2 ; RESID: ||r_u||^2
+    const cplx<T>* Wb = a.W + (long long)b * NC * d.H;
+    for (long long i = (long long)blockIdx.x * blockDim.x + tid; i < d.H; i += (long long)gridDim.x * blockDim.x) {
+        const FreqIdx fi = freq_idx(d, i);
+        const T x1 = a.f.xi1[fi.k1], x2 = a.f.xi2[fi.k2], x3 = a.f.xi3[fi.k3];
+        cplx<T> q[3] = {zero_c<T>(), zero_c<T>(), zero_c<T>()};
+        div_acc<T, NC, 0>(q, ldc(Wb + 0 * d.H + i), x1, x2, x3);
+        div_acc<T, NC, 1>(q, ldc(Wb + 1 * d.H + i), x1, x2, x3);
+        div_acc<T, NC, 2>(q, ldc(Wb + 2 * d.H + i), x1, x2, x3);
+        div_acc<T, NC, 3>(q, ldc(Wb + 3 * d.H + i), x1, x2, x3);
+        div_acc<T, NC, 4>(q, ldc(Wb + 4 * d.H + i), x1, x2, x3);
+        div_acc<T, NC, 5>(q, ldc(Wb + 5 * d.H + i), x1, x2, x3);
+        if constexpr (NC == 9) {
+            div_acc<T, NC, 6>(q, ldc(Wb + 6 * d.H + i), x1, x2, x3);
+            div_acc<T, NC, 7>(q, ldc(Wb + 7 * d.H + i), x1, x2, x3);
+            div_acc<T, NC, 8>(q, ldc(Wb + 8 * d.H + i), x1, x2, x3);
+        }
+        const bool zmode = (x1 == T(0)) && (x2 == T(0)) && (x3 == T(0));
+#pragma unroll
+        for (int c = 0; c < 3; ++c) q[c] = zmode ? zero_c<T>() : mul_i(ms, q[c]);
+        const T wgt = (T)hweight(fi.k3, d.m);
+        if constexpr (MODE == AX5_PLAIN) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) stc(a.out + (long long)(b * 3 + c) * d.H + i, q[c]);
+        } else if constexpr (MODE == AX5_RESID) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const cplx<T> v = mk(-q[c].x, -q[c].y);
+                stc(a.out + (long long)(b * 3 + c) * d.H + i, v);
+                acc0 += wgt * (v.x * v.x + v.y * v.y);
+            }
+        } else {
+            cplx<T> rv[3], z[3];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const long long idx = (long long)(b * 3 + c) * d.H + i;
+                rv[c] = ldc(a.r + idx) - q[c] * alpha;
+                stc(a.r + idx, rv[c]);
+            }
+            precond_apply<T>(pcoef<T>(*pd), x1, x2, x3, N, rv, z);
+            T lrz = T(0), lrr = T(0);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                lrz += rv[c].x * z[c].x + rv[c].y * z[c].y;
+                lrr += rv[c].x * rv[c].x + rv[c].y * rv[c].y;
+            }
+            acc0 += wgt * lrz;
+            acc1 += wgt * lrr;
+        }
+    }
+    const bool has0 = blockIdx.x == 0 && tid == 0;  // k = (0,0,0) is entry 0
+    // sigma-hat(0) of the nc components, W components (mean stress = this / N)
+    auto s0 = [&](int m) { return (double)ldc(Wb + (long long)m * d.H).x; };
 
     if constexpr (MODE == AX5_PLAIN) {
-        if (valid) {
-#pragma unroll
-            for (int c = 0; c < 3; ++c)
-#pragma unroll
-                for (int r = 0; r < R; ++r)
-                    stc(a.out + ((long long)(b * 3 + c) * N1 + (p + r * P)) * d.plane + j, Q(c, r));
-        }
         if (has0 && a.e_out) {
             for (int q = 0; q < 9; ++q) a.e_out[b * 9 + q] = 0.0;
             for (int k = 0; k < d.ne; ++k) {
                 const int m = d.active[k];
-                a.e_out[b * 9 + m] = w_to_macro<NC>(m) * s0[m][0];
+                a.e_out[b * 9 + m] = w_to_macro<NC>(m) * s0(m);
             }
         }
         return;
     }
     if constexpr (MODE == AX5_RESID) {
-        double v2[2] = {0.0, 0.0};  // ||r_u||^2 and ||r_e||^2
-        if (valid) {
-#pragma unroll
-            for (int c = 0; c < 3; ++c)
-#pragma unroll
-                for (int r = 0; r < R; ++r) {
-                    cplx<T> v = mk(-Q(c, r).x, -Q(c, r).y);
-                    stc(a.out + ((long long)(b * 3 + c) * N1 + (p + r * P)) * d.plane + j, v);
-                    v2[0] += (double)wgt * ((double)v.x * v.x + (double)v.y * v.y);
-                }
-        }
+        double v2[2] = {(double)acc0, 0.0};  // ||r_u||^2 and ||r_e||^2
         if (has0) {
-            const double N = 1.0 / d.invN;
-            for (int q = 0; q < 9; ++q) a.sig0[b * 9 + q] = q < NC ? s0[q][0] * d.invN : 0.0;
+            const double Nd = 1.0 / d.invN;
+            for (int q = 0; q < 9; ++q) a.sig0[b * 9 + q] = q < NC ? s0(q) * d.invN : 0.0;
             for (int q = 0; q < 9; ++q) a.r_e[b * 9 + q] = 0.0;
             for (int k = 0; k < d.ne; ++k) {
                 const int m = d.active[k];
-                const double re = N * a.sig_f[b * 9 + m] - w_to_macro<NC>(m) * s0[m][0];
+                const double re = Nd * a.sig_f[b * 9 + m] - w_to_macro<NC>(m) * s0(m);
                 a.r_e[b * 9 + m] = re;
                 v2[1] += re * re;
             }
@@ -427,47 +415,18 @@ __global__ void __launch_bounds__(AX1_THREADS, (sizeof(T) == 4 ? 8 : 4)) k_axis1
         return;
     }
     if constexpr (MODE == AX5_CG) {
-        const T alpha = (T)a.cg[b].alpha;
-        const PrecondData& pd = a.pre[b / d.Rm];
-        const T N = (T)(1.0 / d.invN);
-        T rz = T(0), rr = T(0);
-        if (valid) {
-#pragma unroll
-            for (int r = 0; r < R; ++r) {
-                cplx<T> rv[3], z[3];
-#pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    const long long idx = ((long long)(b * 3 + c) * N1 + (p + r * P)) * d.plane + j;
-                    cplx<T> xv = ldc(a.x + idx), pv = ldc(a.p + idx), rvv = ldc(a.r + idx);
-                    xv = xv + pv * alpha;
-                    rvv = rvv - Q(c, r) * alpha;
-                    stc(a.x + idx, xv);
-                    stc(a.r + idx, rvv);
-                    rv[c] = rvv;
-                }
-                precond_apply<T>(pcoef<T>(pd), a.f.xi1[p + r * P], x2, x3, N, rv, z);
-                T lrz = T(0), lrr = T(0);
-#pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    lrz += rv[c].x * z[c].x + rv[c].y * z[c].y;
-                    lrr += rv[c].x * rv[c].x + rv[c].y * rv[c].y;
-                }
-                rz += lrz;
-                rr += lrr;
-            }
-        }
-        double v2[2] = {(double)wgt * (double)rz, (double)wgt * (double)rr};
+        double v2[2] = {(double)acc0, (double)acc1};
         if (has0) {  // macro part: q_e = E^T sigma-hat(0); x_e += alpha p_e; r_e -= alpha q_e
             const double al = a.cg[b].alpha;
             double re[9];
             for (int k = 0; k < d.ne; ++k) {
                 const int m = d.active[k];
-                const double qe = w_to_macro<NC>(m) * s0[m][0];
+                const double qe = w_to_macro<NC>(m) * s0(m);
                 a.x_e[b * 9 + m] += al * a.p_e[b * 9 + m];
                 re[k] = a.r_e[b * 9 + m] - al * qe;
                 a.r_e[b * 9 + m] = re[k];
             }
-            const double(*Me)[9] = pd.Me;
+            const double(*Me)[9] = pd->Me;
             for (int k = 0; k < d.ne; ++k) {
                 double ze = 0.0;
                 for (int l = 0; l < d.ne; ++l) ze += Me[k][l] * re[l];
@@ -485,38 +444,43 @@ __global__ void __launch_bounds__(AX1_THREADS, (sizeof(T) == 4 ? 8 : 4)) k_axis1
             is_last = (prev == (unsigned)nblk - 1);
         }
         __syncthreads();
-        if (is_last && tid == 0) {
+        if (is_last) {
             __threadfence();
-            double srz = 0.0, srr = 0.0;
-            for (int k = 0; k < nblk; ++k) {
-                srz += __ldcg(a.partials + ((long long)b * nblk + k) * 2 + 0);
-                srr += __ldcg(a.partials + ((long long)b * nblk + k) * 2 + 1);
+            // the whole last block reduces the partials (fixed order: deterministic)
+            double t2[2] = {0.0, 0.0};
+            for (int k = tid; k < nblk; k += blockDim.x) {
+                t2[0] += __ldcg(a.partials + ((long long)b * nblk + k) * 2 + 0);
+                t2[1] += __ldcg(a.partials + ((long long)b * nblk + k) * 2 + 1);
             }
-            CgState& cs = a.cg[b];
-            cs.iter += 1;
-            cs.rnorm2 = srr;
-            const double beta = srz / cs.rho;
-            cs.rho = srz;
-            cs.beta = beta;
-            if (!(srr == srr) || !(srz == srz)) { cs.flags |= 2; cs.done = 1; }
-            if (srr <= cs.tol2 * cs.bnorm2 || cs.iter >= cs.max_iter) cs.done = 1;
-            if (!cs.done) {  // p_e = z_e + beta p_e, and E p_e for the next pass 3
-                const double(*Me)[9] = pd.Me;
-                double pe[9];
-                for (int k = 0; k < d.ne; ++k) {
-                    double ze = 0.0;
-                    for (int l = 0; l < d.ne; ++l) ze += Me[k][l] * a.r_e[b * 9 + d.active[l]];
-                    pe[k] = ze + beta * a.p_e[b * 9 + d.active[k]];
+            block_sum<2>(t2, red);
+            if (tid == 0) {
+                const double srz = t2[0], srr = t2[1];
+                CgState& cs = a.cg[b];
+                cs.iter += 1;
+                cs.rnorm2 = srr;
+                const double beta = srz / cs.rho;
+                cs.rho = srz;
+                cs.beta = beta;
+                if (!(srr == srr) || !(srz == srz)) { cs.flags |= 2; cs.done = 1; }
+                if (srr <= cs.tol2 * cs.bnorm2 || cs.iter >= cs.max_iter) cs.done = 1;
+                if (!cs.done) {  // p_e = z_e + beta p_e, and E p_e for the next pass 3
+                    const double(*Me)[9] = pd->Me;
+                    double pe[9];
+                    for (int k = 0; k < d.ne; ++k) {
+                        double ze = 0.0;
+                        for (int l = 0; l < d.ne; ++l) ze += Me[k][l] * a.r_e[b * 9 + d.active[l]];
+                        pe[k] = ze + beta * a.p_e[b * 9 + d.active[k]];
+                    }
+                    for (int q = 0; q < 9; ++q) { a.macroW[b * 9 + q] = 0.0; a.macroWf[b * 9 + q] = 0.f; }
+                    for (int k = 0; k < d.ne; ++k) {
+                        const int m = d.active[k];
+                        a.p_e[b * 9 + m] = pe[k];
+                        a.macroW[b * 9 + m] = macro_to_w<NC>(m) * pe[k];
+                        a.macroWf[b * 9 + m] = (float)a.macroW[b * 9 + m];
+                    }
                 }
-                for (int q = 0; q < 9; ++q) { a.macroW[b * 9 + q] = 0.0; a.macroWf[b * 9 + q] = 0.f; }
-                for (int k = 0; k < d.ne; ++k) {
-                    const int m = d.active[k];
-                    a.p_e[b * 9 + m] = pe[k];
-                    a.macroW[b * 9 + m] = macro_to_w<NC>(m) * pe[k];
-                    a.macroWf[b * 9 + m] = (float)a.macroW[b * 9 + m];
-                }
+                a.counters[b] = 0u;
             }
-            a.counters[b] = 0u;
         }
     }
 }
