@@ -280,6 +280,20 @@ dbfft_status dbfft_apply_iso_noalloc(const int n[3], const double L[3], int batc
                                      const double* lam, const double* mu, const void* u_hat, void* out,
                                      void* stream);
 
+/*
+ * Autotuner (no counterpart in the paper; launch-shape selection for the
+ * GPU). Times candidate launch shapes of the inner solve's passes on the
+ * context's own buffers -- the radix and the grid lines per CTA of pass 3,
+ * and the columns per CTA of the strided transforms -- and keeps the fastest
+ * for later calls. cache_path (may be NULL): a text file of earlier results,
+ * one line per GPU / grid / batch / precision / model; a matching line is
+ * used without timing, a new result is appended. Results are unchanged by
+ * tuning up to floating-point reassociation inside pass 3's block sums.
+ * dbfft_tuning returns a short text of the choice (valid until the next call).
+ */
+dbfft_status dbfft_autotune(dbfft_ctx* ctx, const char* cache_path);
+const char* dbfft_tuning(const dbfft_ctx* ctx);
+
 /* Device bytes held by the context. */
 size_t dbfft_device_bytes(const dbfft_ctx* ctx);
 

@@ -135,6 +135,12 @@ struct dbfft_ctx {
     std::vector<double> prof_ms, prof_bytes;
     int active_b = 0;  // right-hand sides still iterating (bytes accounting)
 
+    // ---- tuned launch shapes (0: built-in default), index 0 FP32 / 1 FP64
+    int ax3_radix[2] = {8, 4};
+    int ax3_L[2] = {0, 0};
+    int fft_tw[2][2] = {{0, 0}, {0, 0}};  // [precision][axis 1, axis 2]
+    std::string tune_note;
+
     // ---- inner PCG as one CUDA graph (WHILE node), per inner precision
     bool use_graphs = true;
     bool graph_warm[2] = {false, false};
@@ -546,6 +552,20 @@ int opk_update(const dbfft_ctx* ctx) {
 }
 
 template <typename T>
+Ax2Args<T> fft_args(dbfft_ctx* ctx, cplx<T>* W, const CgState* cg) {
+    Ax2Args<T> a;
+    std::memset(&a, 0, sizeof(a));
+    a.d = ctx->dims;
+    a.tw = twid<T>(ctx);
+    a.W = W;
+    a.cg = cg;
+    const int pi_ = sizeof(T) == 8 ? 1 : 0;
+    a.tw_ax1 = ctx->fft_tw[pi_][0];
+    a.tw_ax2 = ctx->fft_tw[pi_][1];
+    return a;
+}
+
+template <typename T>
 Ax3Args<T> ax3_base(dbfft_ctx* ctx, cplx<T>* W) {
     Ax3Args<T> a;
     std::memset(&a, 0, sizeof(a));
@@ -553,7 +573,9 @@ Ax3Args<T> ax3_base(dbfft_ctx* ctx, cplx<T>* W) {
     a.tw = twid<T>(ctx);
     a.W = W;
     a.RB = ctx->RB;
-    a.L = ax3_lines(ctx->n3, ctx->nc, ctx->RB, sizeof(T) == 8);
+    const int pi_ = sizeof(T) == 8 ? 1 : 0;
+    a.radix = ctx->ax3_radix[pi_];
+    a.L = ctx->ax3_L[pi_] > 0 ? ctx->ax3_L[pi_] : ax3_lines(ctx->n3, ctx->nc, ctx->RB, sizeof(T) == 8, 1, a.radix);
     a.phase = ctx->phase;
     if constexpr (sizeof(T) == 4) {
         a.scale = ctx->scale_f;
@@ -578,7 +600,7 @@ dbfft_status chain_apply(dbfft_ctx* ctx, const cplx<T>* u, const T* macroW, cplx
     const double cp = cpass(ctx, dbl, ctx->B);
     const int nc = ctx->nc;
     Ax1InvArgs<T> a1{ctx->dims, freq<T>(ctx), twid<T>(ctx), u, nullptr, nullptr, W, nullptr, ctx->pre};
-    Ax2Args<T> a2{ctx->dims, twid<T>(ctx), W, nullptr};
+    Ax2Args<T> a2 = fft_args<T>(ctx, W, nullptr);
     TRY(run(ctx, dbl ? "pass1_grad_f64" : "pass1_grad_f32", (3 + nc) * cp,
             [&] { return launch_grad<T>(AX1_PLAIN, a1, ctx->stream); }));
     TRY(run(ctx, dbl ? "fft_ax2_f64" : "fft_ax2_f32", 2 * nc * cp, [&] { return launch_fft_ax2<T>(+1, a2, ctx->stream); }));
@@ -614,7 +636,7 @@ dbfft_status chain_residual(dbfft_ctx* ctx, const cplx<double>* x, const double*
     TRY(run(ctx, "macro", 0.0,
             [&] { return launch_macro(ctx->B, ctx->nc, ctx->activeflag, ctx->fU, xe, ctx->macroW, ctx->macroWf, ctx->stream); }));
     Ax1InvArgs<double> a1{ctx->dims, freq<double>(ctx), twid<double>(ctx), x, nullptr, nullptr, W, nullptr, ctx->pre};
-    Ax2Args<double> a2{ctx->dims, twid<double>(ctx), W, nullptr};
+    Ax2Args<double> a2 = fft_args<double>(ctx, W, nullptr);
     TRY(run(ctx, "pass1_grad_f64", (3 + nc) * cp, [&] { return launch_grad<double>(AX1_PLAIN, a1, ctx->stream); }));
     TRY(run(ctx, "fft_ax2_f64", 2 * nc * cp, [&] { return launch_fft_ax2<double>(+1, a2, ctx->stream); }));
     TRY(run(ctx, "fft_ax1_f64", 2 * nc * cp, [&] { return launch_fft_ax1<double>(+1, a2, ctx->stream); }));
@@ -750,15 +772,15 @@ dbfft_status inner_cg(dbfft_ctx* ctx, double tol, long long& it_sum, int& it_max
     ai.counters = ctx->counters;
     ai.tol = tol;
     ai.max_iter = ctx->grid.max_iter;
-    const dim3 gi((unsigned)((ctx->H + 255) / 256), ctx->B);
+    const dim3 gi((unsigned)pw_blocks(ctx->H), ctx->B);
     const bool dbl = sizeof(T) == 8;
     TRY(run(ctx, dbl ? "cg_init_f64" : "cg_init_f32", 3 * cpass(ctx, dbl, ctx->B), [&] {
-        k_cg_init<T><<<gi, 256, 0, ctx->stream>>>(ai);
+        k_cg_init<T><<<gi, PW_THREADS, 0, ctx->stream>>>(ai);
         return cudaGetLastError();
     }));
 
     Ax1InvArgs<T> a1{ctx->dims, freq<T>(ctx), twid<T>(ctx), ri, pi, xi, W, ctx->cg, ctx->pre};
-    Ax2Args<T> a2{ctx->dims, twid<T>(ctx), W, ctx->cg};
+    Ax2Args<T> a2 = fft_args<T>(ctx, W, ctx->cg);
     Ax3Args<T> a3 = ax3_base<T>(ctx, W);
     if constexpr (sizeof(T) == 4) a3.macroW = ctx->macroWf;
     else a3.macroW = ctx->macroW;
@@ -993,6 +1015,95 @@ dbfft_status commit_state(dbfft_ctx* ctx) {
     return DBFFT_OK;
 }
 
+// Time one launch shape: two warm launches, then the best of five (CUDA events).
+template <class F>
+float time_launch(dbfft_ctx* ctx, F&& f) {
+    cudaEvent_t a = get_event(ctx), b = get_event(ctx);
+    float best = 1e30f;
+    bool ok = true;
+    for (int k = 0; k < 7 && ok; ++k) {
+        cudaEventRecord(a, ctx->stream);
+        ok = f() == cudaSuccess;
+        cudaEventRecord(b, ctx->stream);
+        if (cudaEventSynchronize(b) != cudaSuccess) ok = false;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, a, b);
+        if (ok && k >= 2) best = std::min(best, ms);
+    }
+    cudaGetLastError();
+    ctx->pool.push_back(a);
+    ctx->pool.push_back(b);
+    return ok ? best : 1e30f;
+}
+
+template <typename T>
+void tune_precision(dbfft_ctx* ctx, int pi_) {
+    cplx<T>* W = reinterpret_cast<cplx<T>*>(ctx->W);
+    cudaMemsetAsync(ctx->W, 0, (size_t)ctx->B * ctx->nc * ctx->H * sizeof(cplx<T>), ctx->stream);
+    // pass 3: radix x lines per CTA
+    const int radices[2] = {8, 16};
+    float best = 1e30f;
+    int bestR = ctx->ax3_radix[pi_], bestL = 0;
+    for (int ri = 0; ri < (sizeof(T) == 4 ? 2 : 1); ++ri) {
+        const int R = sizeof(T) == 4 ? radices[ri] : 4;
+        const int Ld = ax3_lines(ctx->n3, ctx->nc, ctx->RB, sizeof(T) == 8, 1, R);
+        const int cand[] = {1, 2, 3, 4, 6, 8, 12, 16, 24, 32, Ld};
+        for (int L : cand) {
+            if (L > Ld * 2 || (long long)L > (long long)ctx->n1 * ctx->n2) continue;
+            Ax3Args<T> a3 = ax3_base<T>(ctx, W);
+            a3.radix = R;
+            a3.L = L;
+            if constexpr (sizeof(T) == 4) a3.macroW = ctx->macroWf;
+            else a3.macroW = ctx->macroW;
+            a3.tan_in = reinterpret_cast<const T*>(ctx->tan);
+            const float ms = time_launch(ctx, [&] { return launch_ax3<T>(opk_apply(ctx), a3, ctx->stream); });
+            if (ms < best * 0.98f) {
+                best = ms;
+                bestR = R;
+                bestL = L;
+            }
+        }
+    }
+    ctx->ax3_radix[pi_] = bestR;
+    ctx->ax3_L[pi_] = bestL;
+    char buf[256];
+    std::snprintf(buf, sizeof(buf), "pass3 radix %d lines %d (%.4f ms); ", bestR, bestL, best);
+    ctx->tune_note += buf;
+    // strided transforms: columns per CTA along axes 1 and 2
+    for (int ax = 0; ax < 2; ++ax) {
+        float bt = 1e30f;
+        int btw = 0;
+        for (int tw : {4, 8, 16, 32, 64}) {
+            Ax2Args<T> a2 = fft_args<T>(ctx, W, nullptr);
+            a2.tw_ax1 = a2.tw_ax2 = tw;
+            const float ms = time_launch(ctx, [&] {
+                return ax == 0 ? launch_fft_ax1<T>(+1, a2, ctx->stream) : launch_fft_ax2<T>(+1, a2, ctx->stream);
+            });
+            if (ms < bt * 0.98f) {
+                bt = ms;
+                btw = tw;
+            }
+        }
+        ctx->fft_tw[pi_][ax] = btw;
+        std::snprintf(buf, sizeof(buf), "fft axis %d tile %d (%.4f ms); ", ax + 1, btw, bt);
+        ctx->tune_note += buf;
+    }
+}
+
+std::string tune_key(const dbfft_ctx* ctx) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceProp prop;
+    std::string name = "gpu";
+    if (cudaGetDeviceProperties(&prop, dev) == cudaSuccess) name = prop.name;
+    for (char& c : name)
+        if (c == ' ') c = '_';
+    char buf[256];
+    std::snprintf(buf, sizeof(buf), "%s n=%dx%dx%d B=%d RB=%d nc=%d prec=%d model=%d", name.c_str(), ctx->n1, ctx->n2,
+                  ctx->n3, ctx->B, ctx->RB, ctx->nc, ctx->prec, ctx->model);
+    return buf;
+}
+
 }  // namespace
 
 // ======================================================================== C ABI
@@ -1017,6 +1128,50 @@ const char* dbfft_status_string(dbfft_status s) {
 const char* dbfft_last_error(const dbfft_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
 
 long long dbfft_launch_count(const dbfft_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+dbfft_status dbfft_autotune(dbfft_ctx* ctx, const char* cache_path) {
+    if (!ctx) return DBFFT_E_ARG;
+    const std::string key = tune_key(ctx);
+    const int pi_ = ctx->prec == DBFFT_FP64 ? 1 : 0;
+    if (cache_path) {
+        if (FILE* f = std::fopen(cache_path, "r")) {
+            char line[512];
+            while (std::fgets(line, sizeof(line), f)) {
+                std::string ln(line);
+                if (ln.compare(0, key.size(), key) != 0 || ln.size() <= key.size() || ln[key.size()] != '|') continue;
+                int R = 0, L = 0, t1 = 0, t2 = 0;
+                if (std::sscanf(ln.c_str() + key.size() + 1, "%d %d %d %d", &R, &L, &t1, &t2) == 4) {
+                    ctx->ax3_radix[pi_] = R;
+                    ctx->ax3_L[pi_] = L;
+                    ctx->fft_tw[pi_][0] = t1;
+                    ctx->fft_tw[pi_][1] = t2;
+                    ctx->tune_note = "from cache";
+                    std::fclose(f);
+                    for (int k = 0; k < 2; ++k)
+                        if (ctx->cg_exec[k]) { cudaGraphExecDestroy(ctx->cg_exec[k]); ctx->cg_exec[k] = nullptr; }
+                    return DBFFT_OK;
+                }
+            }
+            std::fclose(f);
+        }
+    }
+    ctx->tune_note.clear();
+    if (pi_ == 0) tune_precision<float>(ctx, 0);
+    else tune_precision<double>(ctx, 1);
+    CK(cudaStreamSynchronize(ctx->stream));
+    for (int k = 0; k < 2; ++k)
+        if (ctx->cg_exec[k]) { cudaGraphExecDestroy(ctx->cg_exec[k]); ctx->cg_exec[k] = nullptr; }
+    if (cache_path) {
+        if (FILE* f = std::fopen(cache_path, "a")) {
+            std::fprintf(f, "%s|%d %d %d %d\n", key.c_str(), ctx->ax3_radix[pi_], ctx->ax3_L[pi_], ctx->fft_tw[pi_][0],
+                         ctx->fft_tw[pi_][1]);
+            std::fclose(f);
+        }
+    }
+    return DBFFT_OK;
+}
+
+const char* dbfft_tuning(const dbfft_ctx* ctx) { return ctx ? ctx->tune_note.c_str() : ""; }
 
 dbfft_status dbfft_profile(dbfft_ctx* ctx, int enable) {
     if (!ctx) return DBFFT_E_ARG;
@@ -1297,10 +1452,8 @@ static dbfft_status create_impl(dbfft_ctx* ctx, const dbfft_grid* grid, const db
         const long long nb1 = pw_blocks(ctx->H);  // element-wise kernels of passes 1 and 5
         const long long nb1d = nb1;
         const long long nlines = (long long)ctx->n1 * ctx->n2;
-        const long long nb3 = (nlines + ax3_lines(ctx->n3, ctx->nc, ctx->RB, false) - 1) /
-                              ax3_lines(ctx->n3, ctx->nc, ctx->RB, false);
-        const long long nb3d = (nlines + ax3_lines(ctx->n3, ctx->nc, ctx->RB, true) - 1) /
-                               ax3_lines(ctx->n3, ctx->nc, ctx->RB, true);
+        const long long nb3 = nlines;  // pass 3 with one line per CTA (any tuned shape fits)
+        const long long nb3d = nlines;
         const long long nbi = (ctx->H + 255) / 256;
         long long nb = std::max(std::max(nb1, nb1d), std::max(std::max(nb3, nb3d), nbi));
         ctx->nblk_max = (int)nb;
@@ -1517,17 +1670,17 @@ dbfft_status dbfft_adjoint(dbfft_ctx* ctx, const double* dJ_dsigma, double* dJ_d
     cplx<double>* W = reinterpret_cast<cplx<double>*>(ctx->W);
     cplx<double>* W2 = reinterpret_cast<cplx<double>*>(ctx->W2);
     Ax1InvArgs<double> a1{ctx->dims, freq<double>(ctx), twid<double>(ctx), ctx->xfwd, nullptr, nullptr, W, nullptr, ctx->pre};
-    Ax2Args<double> a2{ctx->dims, twid<double>(ctx), W, nullptr};
+    Ax2Args<double> a2 = fft_args<double>(ctx, W, nullptr);
     TRY(run(ctx, "pass1_grad_f64", 0.0, [&] { return launch_grad<double>(AX1_PLAIN, a1, ctx->stream); }));
     TRY(run(ctx, "fft_ax2_f64", 0.0, [&] { return launch_fft_ax2<double>(+1, a2, ctx->stream); }));
     TRY(run(ctx, "fft_ax1_f64", 0.0, [&] { return launch_fft_ax1<double>(+1, a2, ctx->stream); }));
     Ax1InvArgs<double> b1{ctx->dims, freq<double>(ctx), twid<double>(ctx), ctx->x64, nullptr, nullptr, W2, nullptr, ctx->pre};
-    Ax2Args<double> b2{ctx->dims, twid<double>(ctx), W2, nullptr};
+    Ax2Args<double> b2 = fft_args<double>(ctx, W2, nullptr);
     TRY(run(ctx, "pass1_grad_f64", 0.0, [&] { return launch_grad<double>(AX1_PLAIN, b1, ctx->stream); }));
     TRY(run(ctx, "fft_ax2_f64", 0.0, [&] { return launch_fft_ax2<double>(+1, b2, ctx->stream); }));
     TRY(run(ctx, "fft_ax1_f64", 0.0, [&] { return launch_fft_ax1<double>(+1, b2, ctx->stream); }));
     Ax3Args<double> a3 = ax3_base<double>(ctx, W);
-    a3.L = ax3_lines(ctx->n3, ctx->nc, ctx->RB, true, 2);
+    a3.L = ax3_lines(ctx->n3, ctx->nc, ctx->RB, true, 2, a3.radix);
     a3.W2 = W2;
     a3.macroW = ctx->macroW;
     a3.macroW2 = ctx->macroW2;

@@ -260,9 +260,11 @@ struct ColFFT {
 //  transform) uses radix 16 in FP32 and 8 in FP64.
 __host__ __device__ constexpr int radix_ax1(int n, bool dbl) { return dbl ? (n < 4 ? n : 4) : (n < 8 ? n : 8); }
 __host__ __device__ constexpr int radix_ax2(int n, bool dbl) { return dbl ? (n < 8 ? n : 8) : (n < 16 ? n : 16); }
-__host__ __device__ constexpr int radix_ax3(int m, bool dbl) { return dbl ? (m < 4 ? m : 4) : (m < 8 ? m : 8); }
+__host__ __device__ constexpr int radix_ax3(int m, bool dbl, int want = 8) {
+    return dbl ? (m < 4 ? m : 4) : (m < want ? m : want);
+}
 template <typename T, int N> struct RadixAx1 { static constexpr int value = radix_ax1(N, sizeof(T) == 8); };
-template <typename T, int M> struct RadixAx3 { static constexpr int value = radix_ax3(M, sizeof(T) == 8); };
+template <typename T, int M, int WANT> struct RadixAx3 { static constexpr int value = radix_ax3(M, sizeof(T) == 8, WANT); };
 template <typename T, int N> struct RadixFor { static constexpr int value = radix_ax2(N, sizeof(T) == 8); };
 
 }  // namespace dbfft

@@ -30,18 +30,32 @@ static int slot_bytes(int n3, bool dbl) {
     return n * csz;
 }
 
-int ax3_lines(int n3, int nc, int rb, bool dbl, int nfields) {
-    // real-space tiles of one CTA within ~56 KB so that four CTAs fit on an SM
+int ax3_lines(int n3, int nc, int rb, bool dbl, int nfields, int radix) {
+    // lines per CTA: real-space tiles within ~72 KB (three CTAs per SM), chosen
+    // so that the slot FFT rounds (256 / P slots each) are well filled
     const size_t sb = (size_t)slot_bytes(n3, dbl);
-    long long L = (long long)(56 * 1024) / ((long long)sb * rb * nc * nfields);
-    if (L < 1) L = 1;
-    if (L > 32) L = 32;
-    return (int)L;
+    long long Lmax = (long long)(72 * 1024) / ((long long)sb * rb * nc * nfields);
+    if (Lmax < 1) Lmax = 1;
+    if (Lmax > 32) Lmax = 32;
+    const int m = n3 / 2;
+    const int per_round = 256 / (m / radix_ax3(m, dbl, radix));
+    int best = 1;
+    double best_u = -1.0;
+    for (int L = (int)Lmax; L >= 1; --L) {
+        const int slots = L * rb * nc * nfields;
+        const int rounds = (slots + per_round - 1) / per_round;
+        const double u = (double)slots / (rounds * per_round);
+        if (u > best_u + 0.02) {
+            best_u = u;
+            best = L;
+        }
+    }
+    return best;
 }
 
 int ax3_threads_per_line(int n3, int nc, int rb, bool dbl) {
     const int m = n3 / 2;
-    return (m / radix_ax3(m, dbl)) * rb * nc;
+    return (m / radix_ax3(m, dbl, 8)) * rb * nc;
 }
 
 size_t ax3_smem(int n3, int nc, int rb, int lines, bool dbl, bool two_fields) {

@@ -7,7 +7,9 @@ template <typename T, int N, int DIR>
 static cudaError_t fft_n(Ax2Args<T> a, int axis, cudaStream_t s) {
     constexpr int R = RadixFor<T, N>::value;
     constexpr int P = N / R;
-    const int TW = ax2_tile(N, sizeof(T) == 8);
+    const int want = axis == 1 ? a.tw_ax1 : a.tw_ax2;
+    int TW = want > 0 ? want : ax2_tile(N, sizeof(T) == 8);
+    if (TW * P > 512) TW = 512 / P;
     if (axis == 1) {  // element (b, c, t, j): (b nc + c) n1 plane + t plane + j
         a.tab = a.tw.t1;
         a.inner = a.d.plane;

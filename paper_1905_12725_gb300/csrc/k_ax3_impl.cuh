@@ -4,8 +4,8 @@
 
 namespace dbfft {
 
-template <typename T, int N3, int NC, int OPK>
-static cudaError_t ax3_n(const Ax3Args<T>& a, cudaStream_t s) {
+template <typename T, int N3, int NC, int OPK, int RW>
+static cudaError_t ax3_nr(const Ax3Args<T>& a, cudaStream_t s) {
     const int threads = 256;
     const long long nlines = (long long)a.d.n1 * a.d.n2;
     const dim3 grid((unsigned)((nlines + a.L - 1) / a.L), (unsigned)(a.d.B / a.RB));
@@ -14,15 +14,23 @@ static cudaError_t ax3_n(const Ax3Args<T>& a, cudaStream_t s) {
     static int max_dyn = -1;
     if (max_dyn < 0) {  // opt in to large dynamic shared memory: 227 KB per block minus the static part
         cudaFuncAttributes fa;
-        cudaError_t e = cudaFuncGetAttributes(&fa, k_axis3<T, N3, NC, OPK>);
+        cudaError_t e = cudaFuncGetAttributes(&fa, k_axis3<T, N3, NC, OPK, RW>);
         if (e != cudaSuccess) return e;
         max_dyn = 227 * 1024 - (int)fa.sharedSizeBytes;
-        e = cudaFuncSetAttribute(k_axis3<T, N3, NC, OPK>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_dyn);
+        e = cudaFuncSetAttribute(k_axis3<T, N3, NC, OPK, RW>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_dyn);
         if (e != cudaSuccess) return e;
     }
     if (smem > (size_t)max_dyn) return cudaErrorInvalidConfiguration;
-    k_axis3<T, N3, NC, OPK><<<grid, threads, smem, s>>>(a);
+    k_axis3<T, N3, NC, OPK, RW><<<grid, threads, smem, s>>>(a);
     return cudaGetLastError();
+}
+
+template <typename T, int N3, int NC, int OPK>
+static cudaError_t ax3_n(const Ax3Args<T>& a, cudaStream_t s) {
+    if constexpr (sizeof(T) == 4) {
+        if (a.radix == 16) return ax3_nr<T, N3, NC, OPK, 16>(a, s);
+    }
+    return ax3_nr<T, N3, NC, OPK, 8>(a, s);
 }
 
 template <typename T, int NC, int OPK>

@@ -33,6 +33,7 @@ struct Ax3Args {
     const cplx<T>* W2;     // OP_ADJ: adjoint strain field in W layout
     int RB;                // right-hand sides per CTA (divides Rm)
     int L;                 // grid lines per CTA
+    int radix;             // radix of the half-length transform (FP32: 8 or 16; FP64: 4)
     const T* macroW;       // [B][9] constant field added before the op (W components)
     const T* macroW2;      // OP_ADJ: macro part of the adjoint field
     // CG curvature (apply ops only; null outside CG)
@@ -81,11 +82,11 @@ __host__ __device__ constexpr int ax3_slot_cplx() {
 // plus one scratch buffer for idle threads of the last FFT round. Global
 // loads and stores are done cooperatively: for one (right-hand side,
 // component) the L lines of a CTA are L h contiguous complex values.
-template <typename T, int N3, int NC, int OPK>
-__global__ void __launch_bounds__(256, (sizeof(T) == 4 ? 4 : ((OPK == OP_CP_UPDATE || OPK == OP_NH_UPDATE) ? 1 : 2))) k_axis3(Ax3Args<T> a) {
+template <typename T, int N3, int NC, int OPK, int RW>
+__global__ void __launch_bounds__(256, (sizeof(T) == 4 ? (RW == 16 ? 3 : 4) : ((OPK == OP_CP_UPDATE || OPK == OP_NH_UPDATE) ? 1 : 2))) k_axis3(Ax3Args<T> a) {
     constexpr int M = N3 / 2;
     constexpr int H = M + 1;
-    constexpr int R = RadixAx3<T, M>::value;
+    constexpr int R = RadixAx3<T, M, RW>::value;
     constexpr int P = M / R;
     constexpr int SB = 2 * ax3_slot_cplx<T, N3>();  // in T values
     static_assert(P <= 32 && (32 % P) == 0, "a slot's threads must sit inside one warp");
@@ -312,24 +313,30 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? 4 : ((OPK == OP_CP_UPDA
                 is_last = (prev == (unsigned)nblk - 1);
             }
             __syncthreads();
-            if (is_last && t < RB) {
+            if (is_last) {  // the whole last block reduces the partials (fixed order)
                 __threadfence();
-                const int bb = g * RB + t;
-                double sum = 0.0;
-                for (int k = 0; k < nblk; ++k) sum += __ldcg(a.partials + (long long)bb * nblk + k);
-                CgState& cs = a.cg[bb];
-                if (!cs.done) {
-                    cs.pq = sum;
-                    if (sum > 0.0 && sum == sum) {
-                        cs.alpha = cs.rho / sum;
-                    } else {
-                        cs.alpha = 0.0;
-                        cs.flags |= (sum == sum) ? 1 : 2;
-                        cs.done = 1;
+                for (int rr = 0; rr < RB; ++rr) {
+                    const int bb = g * RB + rr;
+                    double v1[1] = {0.0};
+                    for (int k = t; k < nblk; k += nthr) v1[0] += __ldcg(a.partials + (long long)bb * nblk + k);
+                    block_sum<1>(v1, red);
+                    if (t == 0) {
+                        const double sum = v1[0];
+                        CgState& cs = a.cg[bb];
+                        if (!cs.done) {
+                            cs.pq = sum;
+                            if (sum > 0.0 && sum == sum) {
+                                cs.alpha = cs.rho / sum;
+                            } else {
+                                cs.alpha = 0.0;
+                                cs.flags |= (sum == sum) ? 1 : 2;
+                                cs.done = 1;
+                            }
+                        }
                     }
                 }
+                if (t == 0) a.counters[g] = 0u;
             }
-            if (is_last && t == 0) a.counters[g] = 0u;
         }
     }
     if constexpr (!OpInfo<OPK>::forward) return;

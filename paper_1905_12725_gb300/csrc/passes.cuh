@@ -248,10 +248,11 @@ struct Ax2Args {
     long long inner;    // stride of the transformed axis (in entries)
     long long ncols;    // columns in total
     long long cols_per_b;
+    int tw_ax1, tw_ax2; // columns per CTA along axis 1 / axis 2 (0: default)
 };
 
 template <typename T, int N, int DIR>
-__global__ void __launch_bounds__(256) k_fft_strided(Ax2Args<T> a) {
+__global__ void __launch_bounds__(512) k_fft_strided(Ax2Args<T> a) {
     constexpr int R = RadixFor<T, N>::value;
     constexpr int P = N / R;
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -505,31 +506,28 @@ struct CgInitArgs {
 };
 
 template <typename T>
-__global__ void k_cg_init(CgInitArgs<T> a) {
+__global__ void __launch_bounds__(PW_THREADS) k_cg_init(CgInitArgs<T> a) {
     __shared__ double red[32 * 2];
     __shared__ bool is_last;
     const Dims& d = a.d;
     const int b = blockIdx.y;
-    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    double v2[2] = {0.0, 0.0};
+    const int tid = threadIdx.x;
     const PrecondData& pd = a.pre[b / d.Rm];
-    if (i < d.H) {
-        const long long k1 = i / d.plane;
-        const long long rem = i - k1 * d.plane;
-        const int k2 = (int)(rem / d.h), k3 = (int)(rem - (long long)k2 * d.h);
+    const T N = (T)(1.0 / d.invN);
+    T lrz = T(0), lrr = T(0);
+    for (long long i = (long long)blockIdx.x * blockDim.x + tid; i < d.H; i += (long long)gridDim.x * blockDim.x) {
+        const FreqIdx fi = freq_idx(d, i);
         cplx<T> rv[3], z[3];
         for (int c = 0; c < 3; ++c) rv[c] = ldc(a.r + (long long)(b * 3 + c) * d.H + i);
-        precond_apply<T>(pcoef<T>(pd), a.f.xi1[k1], a.f.xi2[k2], a.f.xi3[k3], (T)(1.0 / d.invN), rv, z);
-        const int wgt = hweight(k3, d.m);
-        T lrz = T(0), lrr = T(0);
+        precond_apply<T>(pcoef<T>(pd), a.f.xi1[fi.k1], a.f.xi2[fi.k2], a.f.xi3[fi.k3], N, rv, z);
+        const T wgt = (T)hweight(fi.k3, d.m);
         for (int c = 0; c < 3; ++c) {
-            lrz += rv[c].x * z[c].x + rv[c].y * z[c].y;
-            lrr += rv[c].x * rv[c].x + rv[c].y * rv[c].y;
+            lrz += wgt * (rv[c].x * z[c].x + rv[c].y * z[c].y);
+            lrr += wgt * (rv[c].x * rv[c].x + rv[c].y * rv[c].y);
         }
-        v2[0] = (double)wgt * (double)lrz;
-        v2[1] = (double)wgt * (double)lrr;
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
+    double v2[2] = {(double)lrz, (double)lrr};
+    if (blockIdx.x == 0 && tid == 0) {
         for (int k = 0; k < d.ne; ++k) {
             double ze = 0.0;
             for (int l = 0; l < d.ne; ++l) ze += pd.Me[k][l] * a.r_e[b * 9 + d.active[l]];
@@ -540,7 +538,7 @@ __global__ void k_cg_init(CgInitArgs<T> a) {
     }
     block_sum<2>(v2, red);
     const int nblk = gridDim.x;
-    if (threadIdx.x == 0) {
+    if (tid == 0) {
         a.partials[((long long)b * nblk + blockIdx.x) * 2 + 0] = v2[0];
         a.partials[((long long)b * nblk + blockIdx.x) * 2 + 1] = v2[1];
         __threadfence();
@@ -548,13 +546,16 @@ __global__ void k_cg_init(CgInitArgs<T> a) {
         is_last = (prev == (unsigned)nblk - 1);
     }
     __syncthreads();
-    if (is_last && threadIdx.x == 0) {
-        __threadfence();
-        double srz = 0.0, srr = 0.0;
-        for (int k = 0; k < nblk; ++k) {
-            srz += __ldcg(a.partials + ((long long)b * nblk + k) * 2 + 0);
-            srr += __ldcg(a.partials + ((long long)b * nblk + k) * 2 + 1);
-        }
+    if (!is_last) return;
+    __threadfence();
+    double t2[2] = {0.0, 0.0};
+    for (int k = tid; k < nblk; k += blockDim.x) {
+        t2[0] += __ldcg(a.partials + ((long long)b * nblk + k) * 2 + 0);
+        t2[1] += __ldcg(a.partials + ((long long)b * nblk + k) * 2 + 1);
+    }
+    block_sum<2>(t2, red);
+    if (tid == 0) {
+        const double srz = t2[0], srr = t2[1];
         CgState& cs = a.cg[b];
         cs.rho = srz;
         cs.bnorm2 = srr;

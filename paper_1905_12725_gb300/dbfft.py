@@ -73,7 +73,8 @@ class dbfft_profile_entry(C.Structure):
 EXPORTS = ["dbfft_create", "dbfft_apply", "dbfft_solve_increment", "dbfft_homogenized_stress",
            "dbfft_homogenized_tangent", "dbfft_adjoint", "dbfft_get_solution", "dbfft_device_bytes",
            "dbfft_destroy", "dbfft_last_error", "dbfft_status_string", "dbfft_profile",
-           "dbfft_profile_read", "dbfft_launch_count", "dbfft_apply_iso_noalloc"]
+           "dbfft_profile_read", "dbfft_launch_count", "dbfft_apply_iso_noalloc", "dbfft_autotune",
+           "dbfft_tuning"]
 
 _LIB = None
 
@@ -125,6 +126,10 @@ def load_library(build_if_missing: bool = True):
     lib.dbfft_launch_count.restype = C.c_longlong
     lib.dbfft_apply_iso_noalloc.argtypes = [C.POINTER(C.c_int), dp, ip, vp, vp, vp, vp, vp, vp]
     lib.dbfft_apply_iso_noalloc.restype = ip
+    lib.dbfft_autotune.argtypes = [vp, C.c_char_p]
+    lib.dbfft_autotune.restype = ip
+    lib.dbfft_tuning.argtypes = [vp]
+    lib.dbfft_tuning.restype = C.c_char_p
     _LIB = lib
     return lib
 
@@ -272,6 +277,14 @@ class Solver:
 
     def device_bytes(self) -> int:
         return int(self.lib.dbfft_device_bytes(self.ctx))
+
+    def autotune(self, cache_path=None):
+        """Pick launch shapes by timing them (dbfft_autotune); returns the choice as text."""
+        if cache_path is None:
+            cache_path = os.environ.get("DBFFT_TUNE_CACHE")
+        p = cache_path.encode() if cache_path else None
+        self._check(self.lib.dbfft_autotune(self.ctx, p))
+        return self.lib.dbfft_tuning(self.ctx).decode()
 
     def launch_count(self) -> int:
         return int(self.lib.dbfft_launch_count(self.ctx))

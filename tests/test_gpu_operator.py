@@ -114,3 +114,28 @@ def test_residual_chain_matches_oracle():
     r, _, _ = o.residual(prob, T.apply, (u[0], e), epsU, sig_f)
     assert rel_err(out.cpu().numpy()[0], r[0]) < 1e-12
     assert rel_err(e9_to_oracle(prob, eo.cpu().numpy()[0]), r[1]) < 1e-12
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_autotuned_launch_shapes_keep_results(precision, tmp_path):
+    """dbfft_autotune picks launch shapes by timing; the operator is unchanged."""
+    from paper_1905_12725_gb300 import dbfft
+    shape = (32, 16, 64)
+    B = 3
+    phase = _random_phase(shape, 31)
+    E, nu = [1.0, 30.0], [0.3, 0.2]
+    s = _solver(shape, phase, E, nu, np.zeros((B, 3, 3)), batch=B, precision=precision)
+    u = synth.random_spectrum(shape, 3, 33, batch=B)
+    fp32 = precision == 1
+    before, _ = s.apply(torch.from_numpy(u).cuda(), fp32=fp32)
+    cache = str(tmp_path / "tune.txt")
+    note = s.autotune(cache)
+    assert "pass3" in note
+    after, _ = s.apply(torch.from_numpy(u).cuda(), fp32=fp32)
+    assert rel_err(after.cpu().numpy(), before.cpu().numpy()) < (2e-6 if fp32 else 1e-13)
+    # a second context reads the cache instead of timing
+    s2 = _solver(shape, phase, E, nu, np.zeros((B, 3, 3)), batch=B, precision=precision)
+    assert s2.autotune(cache) == "from cache"
+    prob = o.Problem(shape)
+    ref, _ = prob.apply_K(iso_tangent(phase[0], E, nu), u[0], np.zeros(0))
+    assert rel_err(after.cpu().numpy()[0], ref) < (2e-5 if fp32 else 1e-12)
