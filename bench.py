@@ -236,6 +236,142 @@ def operator_256(torch, dbfft, peak, iters=40):
             "passes": rows, "wall_s": wall}
 
 
+# ------------------------------------------------------------------ other configurations
+def _timed(fn):
+    import torch
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    out = fn()
+    torch.cuda.synchronize()
+    return out, time.perf_counter() - t0
+
+
+def case_c1():
+    """16^3 centred sphere, E 1 / 10, nu 0.3, eps_xx = 1e-3, FP64 PCG to 1e-8."""
+    from paper_1905_12725_gb300 import dbfft, synth
+    c = synth.config1()
+    s = dbfft.Solver((16,) * 3, c["phase"], dbfft.iso_phases(c["E"], c["nu"]), c["eps_bar"][None], tol=1e-8)
+    s.solve_increment(0)
+    rep, dt = _timed(lambda: s.solve_increment(0))
+    return {"case": "c1 16^3 sphere FP64", "wall_ms": dt * 1e3, "report": rep,
+            "sigma_bar": s.homogenized_stress()[0].tolist()}
+
+
+NH_MASK_BITS = [(0, 1), (0, 2), (1, 2), (1, 1), (2, 2)]
+
+
+def case_c3(precision, n=128, n_inc=20):
+    """128^3 Neo-Hookean fibres (mu 1 / 20), F11 -> 1.2 in 20 increments, other macro stresses zero."""
+    from paper_1905_12725_gb300 import dbfft, synth
+    c = synth.config3(n=n)
+    mask = np.zeros((3, 3), bool)
+    for i, j in NH_MASK_BITS:
+        mask[i, j] = True
+    tgt = np.eye(3)
+    tgt[0, 0] = 1.2
+    tgt[mask] = 0.0
+    s = dbfft.Solver((n,) * 3, c["phase"], dbfft.neo_hooke_phases(c["mu"], c["lam"]), tgt[None],
+                     kinematics=dbfft.DBFFT_FINITE, precision=precision, stress_mask=mask.reshape(-1),
+                     n_increments=n_inc, newton_tol=1e-8, load_tol=1e-10, eta_inner=1e-4, max_newton=30,
+                     max_iter=5000)
+    s.autotune(TUNE_CACHE)
+    incs = []
+    t_all = 0.0
+    cg_all = 0
+    for k in range(n_inc):
+        rep, dt = _timed(lambda: s.solve_increment(k))
+        t_all += dt
+        cg_all += rep["cg_iters"]
+        P = s.homogenized_stress()[0]
+        incs.append({"inc": k, "newton": rep["newton_iters"], "cg": rep["cg_iters"], "eps_eq": rep["eps_eq"],
+                     "load_res": rep["load_res"], "P11": P[0, 0], "ms": dt * 1e3})
+    return {"case": f"c3 {n}^3 Neo-Hooke fibres vf {float(c['phase'].mean()):.3f}, n_fibres {c['n_fibres']}",
+            "precision": "mixed" if precision else "fp64", "wall_s": t_all, "cg_iters": cg_all,
+            "voxel_cg_iters_per_s": n ** 3 * cg_all / t_all, "increments": incs,
+            "P_bar_final": s.homogenized_stress()[0].tolist(), "phase_sha256": synth.sha256(c["phase"])}
+
+
+def case_c4(precision, n=256, n_inc=40, only=None):
+    """256^3 Voronoi polycrystal (500 grains), power-law CP, eps_xx to 2% at 1e-3/s in 40 increments."""
+    from paper_1905_12725_gb300 import dbfft, synth
+    t0 = time.perf_counter()
+    c = synth.config4(n=n)
+    t_gen = time.perf_counter() - t0
+    mask = np.ones((3, 3), bool)
+    mask[0, 0] = False
+    tgt = np.zeros((3, 3))
+    tgt[0, 0] = 0.02
+    s = dbfft.Solver((n,) * 3, c["phase"], dbfft.cp_phases(c["quat"]), tgt[None], precision=precision,
+                     stress_mask=mask.reshape(-1), n_increments=n_inc, total_time=20.0, newton_tol=1e-8,
+                     load_tol=1e-10, eta_inner=1e-4, max_newton=40, max_iter=5000)
+    s.autotune(TUNE_CACHE)
+    incs = []
+    t_all = 0.0
+    cg_all = 0
+    for k in range(n_inc if only is None else only):
+        rep, dt = _timed(lambda: s.solve_increment(k))
+        t_all += dt
+        cg_all += rep["cg_iters"]
+        sg = s.homogenized_stress()[0]
+        incs.append({"inc": k, "newton": rep["newton_iters"], "cg": rep["cg_iters"], "eps_eq": rep["eps_eq"],
+                     "sigma_xx": sg[0, 0], "ms": dt * 1e3})
+    return {"case": f"c4 {n}^3 polycrystal 500 grains", "precision": "mixed" if precision else "fp64",
+            "generate_s": t_gen, "wall_s": t_all, "cg_iters": cg_all,
+            "voxel_cg_iters_per_s": n ** 3 * cg_all / t_all, "increments": incs,
+            "phase_sha256": synth.sha256(c["phase"])}
+
+
+def case_c5(n=64, n_rve=32, n_fd=20):
+    """32 RVEs of 64^3: d sigma_xx / dE(x) by the adjoint, checked by central differences on 20 voxels each."""
+    from paper_1905_12725_gb300 import dbfft, synth
+    c = synth.config5(n=n, n_rve=n_rve)
+    E = c["E"][np.arange(n_rve)[:, None, None, None], c["phase"]]  # per-voxel Young's modulus
+    ph = np.zeros_like(c["phase"])
+    eps = np.zeros((n_rve, 3, 3))
+    eps[:, 0, 0] = 1e-3
+    g = np.zeros((n_rve, 9))
+    g[:, 0] = 1.0
+    out = {"case": f"c5 {n_rve} x {n}^3 adjoint", "vf_target": c["vf_target"].tolist()}
+    for prec, name in [(dbfft.DBFFT_MIXED, "mixed"), (dbfft.DBFFT_FP64, "fp64")]:
+        s = dbfft.Solver((n,) * 3, ph, dbfft.iso_phases([1.0], [0.3]), eps, E_scale=E, precision=prec,
+                         tol=1e-10 if prec == dbfft.DBFFT_FP64 else 1e-6, eta_inner=1e-3)
+        s.autotune(TUNE_CACHE)
+        s.adjoint(g)
+        (dJ, rep), dt = _timed(lambda: s.adjoint(g))
+        out[name] = {"wall_ms": dt * 1e3, "report": rep, "dJdE": dJ}
+        s.close()
+    dJ64 = out["fp64"]["dJdE"].cpu().numpy()
+    dJmx = out["mixed"]["dJdE"].cpu().numpy()
+    out["mixed_vs_fp64_rel"] = float(np.abs(dJmx - dJ64).max() / np.abs(dJ64).max())
+    # central differences, delta = 1e-3 E(x), batched over the RVEs (one voxel per RVE per solve pair)
+    rng = synth.Xoshiro256ss(synth.SEED_BASE + 55)
+    vox = np.array([synth.random_voxels(n ** 3, n_fd, rng) for _ in range(n_rve)])
+    errs = []
+    t0 = time.perf_counter()
+    for k in range(n_fd):
+        Js = []
+        for sgn in (+1.0, -1.0):
+            Ep = E.copy().reshape(n_rve, -1)
+            d = 1e-3 * Ep[np.arange(n_rve), vox[:, k]]
+            Ep[np.arange(n_rve), vox[:, k]] += sgn * d
+            sp = dbfft.Solver((n,) * 3, ph, dbfft.iso_phases([1.0], [0.3]), eps, E_scale=Ep.reshape(E.shape),
+                              precision=dbfft.DBFFT_MIXED, tol=1e-12, eta_inner=1e-3)
+            sp.autotune(TUNE_CACHE)
+            sp.solve_increment(0)
+            Js.append(sp.homogenized_stress()[:, 0, 0])
+            sp.close()
+        d = 1e-3 * E.reshape(n_rve, -1)[np.arange(n_rve), vox[:, k]]
+        fd = (Js[0] - Js[1]) / (2 * d)
+        adj = dJ64.reshape(n_rve, -1)[np.arange(n_rve), vox[:, k]]
+        errs.append(np.abs(fd - adj) / np.abs(adj))
+    errs = np.array(errs)
+    out["fd_check"] = {"voxels_per_rve": n_fd, "max_rel_err": float(errs.max()), "median_rel_err": float(np.median(errs)),
+                       "pass_1e-4": bool(errs.max() < 1e-4), "wall_s": time.perf_counter() - t0}
+    for name in ["mixed", "fp64"]:
+        out[name].pop("dJdE")
+    return out
+
+
 def our_arm(args, rank, world, local_rank):
     import torch
     from paper_1905_12725_gb300 import dbfft
@@ -414,9 +550,11 @@ def main():
     ap.add_argument("--ref-iters", type=int, default=40)
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-256", action="store_true")
-    ap.add_argument("--case", default="", choices=["", "op256", "c2"],
-                    help="run one sub-measurement only (for profiler captures): op256 = 256^3 FP32 CG "
-                         "pass chain, c2 = one mixed batched 64^3 solve")
+    ap.add_argument("--case", default="",
+                    choices=["", "op256", "c2", "c1", "c3", "c3fp64", "c4", "c4fp64", "c5"],
+                    help="run one sub-measurement only: op256 = 256^3 FP32 CG pass chain, c2 = one mixed "
+                         "batched 64^3 solve (profiler captures); c1, c3[fp64], c4[fp64], c5 = the other "
+                         "configurations at full size")
     args = ap.parse_args()
     if args.case:
         import torch
@@ -424,6 +562,12 @@ def main():
         torch.cuda.set_device(0)
         if args.case == "op256":
             print(json.dumps(operator_256(torch, dbfft, _peaks()[0], iters=args.steps)), flush=True)
+        elif args.case in ("c1", "c3", "c3fp64", "c4", "c4fp64", "c5"):
+            prec = dbfft.DBFFT_FP64 if args.case.endswith("fp64") else dbfft.DBFFT_MIXED
+            res = {"c1": lambda: case_c1(), "c3": lambda: case_c3(prec), "c3fp64": lambda: case_c3(prec),
+                   "c4": lambda: case_c4(prec), "c4fp64": lambda: case_c4(prec, only=args.steps),
+                   "c5": lambda: case_c5()}[args.case]()
+            print(json.dumps(res, default=float), flush=True)
         else:
             s = make_solver(workload_inputs(), dbfft.DBFFT_MIXED, 6)
             for _ in range(max(args.steps, 1)):
