@@ -189,6 +189,10 @@ dbfft_status dbfft_apply(dbfft_ctx* ctx, int flags, const void* u_hat, const voi
  * newton_tol and load_tol; the preconditioner uses the mean tangent at the
  * first iterate of the increment. rep may be NULL. Returns E_NOT_CONVERGED
  * when a cap is hit (the state and report are still written).
+ * From the second inner solve of a context on, an inner PCG runs as one
+ * CUDA graph launch (a WHILE node around one iteration); with the
+ * environment variable DBFFT_CUDA_GRAPHS=0 at dbfft_create it runs launch
+ * by launch instead (same kernels and results; for kernel profilers).
  */
 dbfft_status dbfft_solve_increment(dbfft_ctx* ctx, int inc, dbfft_report* rep);
 
@@ -293,6 +297,20 @@ dbfft_status dbfft_apply_iso_noalloc(const int n[3], const double L[3], int batc
  */
 dbfft_status dbfft_autotune(dbfft_ctx* ctx, const char* cache_path);
 const char* dbfft_tuning(const dbfft_ctx* ctx);
+
+/*
+ * Set the launch shape of pass 3 for the operator applications of one inner
+ * precision by hand (no counterpart in the paper), in place of the
+ * autotuner's choice. fp64: 0 for the FP32 applications, 1 for FP64.
+ * pipelined: 0 = one CTA per group of grid lines, loads staged by cp.async;
+ * 1 = persistent CTAs looping over tiles of `lines` grid lines with two
+ * shared-memory stages filled and drained by bulk copies. radix: 8 or 16
+ * (FP32) / 4 (FP64); lines: grid lines per CTA (per tile when pipelined;
+ * then even and dividing n1 * n2). Returns DBFFT_E_ARG for a shape that does
+ * not exist or does not fit in shared memory; the results of the operator do
+ * not depend on the shape beyond floating-point reassociation.
+ */
+dbfft_status dbfft_set_pass3_shape(dbfft_ctx* ctx, int fp64, int pipelined, int radix, int lines);
 
 /* Device bytes held by the context. */
 size_t dbfft_device_bytes(const dbfft_ctx* ctx);

@@ -12,6 +12,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -73,6 +74,8 @@ struct dbfft_ctx {
     float* scale_f = nullptr;
     std::vector<double> lam_h, mu_h, E_h;
     CpGrain* grains = nullptr;
+    CpGrainF* grains_f = nullptr;
+    int cp_guess_trial = 0;  // next CP update starts from the trial stress
     CpParams cp{};
     PrecondData* pre = nullptr;
     std::vector<PrecondData> pre_h;
@@ -139,6 +142,8 @@ struct dbfft_ctx {
     int ax3_radix[2] = {8, 4};
     int ax3_L[2] = {0, 0};
     int fft_tw[2][2] = {{0, 0}, {0, 0}};  // [precision][axis 1, axis 2]
+    // pipelined pass 3 for the CG applications: [precision] on/off, radix, lines per tile
+    int pipe_on[2] = {0, 0}, pipe_R[2] = {8, 4}, pipe_L[2] = {0, 0};
     std::string tune_note;
 
     // ---- inner PCG as one CUDA graph (WHILE node), per inner precision
@@ -587,9 +592,21 @@ Ax3Args<T> ax3_base(dbfft_ctx* ctx, cplx<T>* W) {
         a.mu = ctx->mu;
     }
     a.grains = ctx->grains;
+    a.grains_f = ctx->grains_f;
     a.cp = ctx->cp;
     a.err = ctx->errw;
     return a;
+}
+
+// Launch shape of the CG applications of pass 3 (the pipelined kernel when tuned in).
+template <typename T>
+void apply_shape(const dbfft_ctx* ctx, Ax3Args<T>& a) {
+    const int pi_ = sizeof(T) == 8 ? 1 : 0;
+    if (ctx->pipe_on[pi_]) {
+        a.pipe = 1;
+        a.radix = ctx->pipe_R[pi_];
+        a.L = ctx->pipe_L[pi_];
+    }
 }
 
 // One operator application in precision T: out = K u (flags: macro e_in/e_out).
@@ -606,6 +623,7 @@ dbfft_status chain_apply(dbfft_ctx* ctx, const cplx<T>* u, const T* macroW, cplx
     TRY(run(ctx, dbl ? "fft_ax2_f64" : "fft_ax2_f32", 2 * nc * cp, [&] { return launch_fft_ax2<T>(+1, a2, ctx->stream); }));
     TRY(run(ctx, dbl ? "fft_ax1_f64" : "fft_ax1_f32", 2 * nc * cp, [&] { return launch_fft_ax1<T>(+1, a2, ctx->stream); }));
     Ax3Args<T> a3 = ax3_base<T>(ctx, W);
+    apply_shape<T>(ctx, a3);
     a3.macroW = macroW;
     a3.tan_in = reinterpret_cast<const T*>(ctx->tan);
     TRY(run(ctx, dbl ? "pass3_tangent_f64" : "pass3_tangent_f32", 2 * nc * cp + mat_bytes(ctx, dbl, false),
@@ -649,6 +667,7 @@ dbfft_status chain_residual(dbfft_ctx* ctx, const cplx<double>* x, const double*
         a3.sig_prev = ctx->sig_prev;
         a3.eps_p_t = ctx->eps_p_t;
         a3.sig_t = ctx->sig_t;
+        a3.guess_trial = ctx->cp_guess_trial;
     }
     CK(cudaMemsetAsync(ctx->errw, 0, sizeof(unsigned), ctx->stream));
     TRY(run(ctx, "pass3_update_f64", 2 * nc * cp + mat_bytes(ctx, true, true),
@@ -684,6 +703,7 @@ dbfft_status chain_residual(dbfft_ctx* ctx, const cplx<double>* x, const double*
             ru2[b] += ctx->part_h[((size_t)b * nblk + k) * 2 + 0];
             re2[b] += ctx->part_h[((size_t)b * nblk + k) * 2 + 1];
         }
+    if (*errh & 2u) return fail(ctx, DBFFT_E_TIMEOUT, "a device wait gave up (pass 3 copy pipeline)");
     if (*errh) return fail(ctx, DBFFT_E_MATERIAL, "local constitutive update failed (non-positive J or local Newton)");
     for (int b = 0; b < ctx->B; ++b)
         if (!std::isfinite(ru2[b]) || !std::isfinite(re2[b])) return fail(ctx, DBFFT_E_NONFINITE, "non-finite residual");
@@ -782,6 +802,7 @@ dbfft_status inner_cg(dbfft_ctx* ctx, double tol, long long& it_sum, int& it_max
     Ax1InvArgs<T> a1{ctx->dims, freq<T>(ctx), twid<T>(ctx), ri, pi, xi, W, ctx->cg, ctx->pre};
     Ax2Args<T> a2 = fft_args<T>(ctx, W, ctx->cg);
     Ax3Args<T> a3 = ax3_base<T>(ctx, W);
+    apply_shape<T>(ctx, a3);
     if constexpr (sizeof(T) == 4) a3.macroW = ctx->macroWf;
     else a3.macroW = ctx->macroW;
     a3.cg = ctx->cg;
@@ -814,7 +835,10 @@ dbfft_status inner_cg(dbfft_ctx* ctx, double tol, long long& it_sum, int& it_max
         if (!ctx->cg_exec[pi_]) TRY(build_cg_graph<T>(ctx, a1, a2, a3, a5, opk_apply(ctx), &ctx->cg_exec[pi_]));
         CK(cudaGraphLaunch(ctx->cg_exec[pi_], ctx->stream));
         CK(cudaMemcpyAsync(ctx->cg_h, ctx->cg, ctx->B * sizeof(CgState), cudaMemcpyDeviceToHost, ctx->stream));
+        unsigned* errh = reinterpret_cast<unsigned*>(ctx->small_h + ctx->B * 10);
+        CK(cudaMemcpyAsync(errh, ctx->errw, sizeof(unsigned), cudaMemcpyDeviceToHost, ctx->stream));
         CK(cudaStreamSynchronize(ctx->stream));
+        if (*errh & 2u) return fail(ctx, DBFFT_E_TIMEOUT, "a device wait gave up (pass 3 copy pipeline)");
         int mx = 1;
         for (int b = 0; b < ctx->B; ++b) mx = std::max(mx, ctx->cg_h[b].iter);
         ctx->launches += 8LL * mx;
@@ -829,31 +853,55 @@ dbfft_status inner_cg(dbfft_ctx* ctx, double tol, long long& it_sum, int& it_max
     int launched = 0;
     int chunk = 4;
     const int nc = ctx->nc;
-    int nact = ctx->B;
+    const char* n_p1 = dbl ? "pass1_grad_cg_f64" : "pass1_grad_cg_f32";
+    const char* n_a2 = dbl ? "fft_ax2_f64" : "fft_ax2_f32";
+    const char* n_a1 = dbl ? "fft_ax1_f64" : "fft_ax1_f32";
+    const char* n_p3 = dbl ? "pass3_tangent_f64" : "pass3_tangent_f32";
+    const char* n_p5 = dbl ? "pass5_div_cg_f64" : "pass5_div_cg_f32";
+    std::vector<int> it_before(ctx->B, 0);
     while (true) {
-        const double cp = cpass(ctx, dbl, nact);
-        const double mb = mat_bytes(ctx, dbl, false) * (ctx->model == DBFFT_ISO_ELASTIC ? 1.0 : (double)nact / ctx->B);
+        // launches are timed here; their algorithmic bytes are credited after
+        // the chunk, from the iterations each right-hand side really made (a
+        // right-hand side that stops inside a chunk skips the later launches)
         for (int k = 0; k < chunk; ++k) {
-            TRY(run(ctx, dbl ? "pass1_grad_cg_f64" : "pass1_grad_cg_f32", (15 + nc) * cp,
-                    [&] { return launch_grad<T>(AX1_CG, a1, ctx->stream); }));
-            TRY(run(ctx, dbl ? "fft_ax2_f64" : "fft_ax2_f32", 2 * nc * cp, [&] { return launch_fft_ax2<T>(+1, a2, ctx->stream); }));
-            TRY(run(ctx, dbl ? "fft_ax1_f64" : "fft_ax1_f32", 2 * nc * cp, [&] { return launch_fft_ax1<T>(+1, a2, ctx->stream); }));
-            TRY(run(ctx, dbl ? "pass3_tangent_f64" : "pass3_tangent_f32", 2 * nc * cp + mb,
-                    [&] { return launch_ax3<T>(opk, a3, ctx->stream); }));
-            TRY(run(ctx, dbl ? "fft_ax1_f64" : "fft_ax1_f32", 2 * nc * cp, [&] { return launch_fft_ax1<T>(-1, a2, ctx->stream); }));
-            TRY(run(ctx, dbl ? "fft_ax2_f64" : "fft_ax2_f32", 2 * nc * cp, [&] { return launch_fft_ax2<T>(-1, a2, ctx->stream); }));
-            TRY(run(ctx, dbl ? "pass5_div_cg_f64" : "pass5_div_cg_f32", (6 + nc) * cp,
-                    [&] { return launch_div<T>(AX5_CG, a5, ctx->stream); }));
+            TRY(run(ctx, n_p1, 0.0, [&] { return launch_grad<T>(AX1_CG, a1, ctx->stream); }));
+            TRY(run(ctx, n_a2, 0.0, [&] { return launch_fft_ax2<T>(+1, a2, ctx->stream); }));
+            TRY(run(ctx, n_a1, 0.0, [&] { return launch_fft_ax1<T>(+1, a2, ctx->stream); }));
+            TRY(run(ctx, n_p3, 0.0, [&] { return launch_ax3<T>(opk, a3, ctx->stream); }));
+            TRY(run(ctx, n_a1, 0.0, [&] { return launch_fft_ax1<T>(-1, a2, ctx->stream); }));
+            TRY(run(ctx, n_a2, 0.0, [&] { return launch_fft_ax2<T>(-1, a2, ctx->stream); }));
+            TRY(run(ctx, n_p5, 0.0, [&] { return launch_div<T>(AX5_CG, a5, ctx->stream); }));
         }
         launched += chunk;
         CK(cudaMemcpyAsync(ctx->cg_h, ctx->cg, ctx->B * sizeof(CgState), cudaMemcpyDeviceToHost, ctx->stream));
+        unsigned* errh = reinterpret_cast<unsigned*>(ctx->small_h + ctx->B * 10);
+        CK(cudaMemcpyAsync(errh, ctx->errw, sizeof(unsigned), cudaMemcpyDeviceToHost, ctx->stream));
         CK(cudaStreamSynchronize(ctx->stream));
         prof_flush(ctx);
+        if (*errh & 2u) return fail(ctx, DBFFT_E_TIMEOUT, "a device wait gave up (pass 3 copy pipeline)");
+        if (ctx->prof) {
+            const double cp1 = cpass(ctx, dbl, 1);
+            double sum_it = 0.0, mat = 0.0;
+            for (int g = 0; g < ctx->Bm; ++g) {  // material tables: once per launch in which a group iterates
+                int mx = 0;
+                for (int r = 0; r < ctx->Rm; ++r) {
+                    const int b = g * ctx->Rm + r;
+                    mx = std::max(mx, ctx->cg_h[b].iter - it_before[b]);
+                    sum_it += ctx->cg_h[b].iter - it_before[b];
+                }
+                mat += (ctx->model == DBFFT_ISO_ELASTIC ? (double)mx : 0.0) * mat_bytes(ctx, dbl, false) / ctx->Bm;
+            }
+            if (ctx->model != DBFFT_ISO_ELASTIC) mat = sum_it * mat_bytes(ctx, dbl, false) / ctx->B;
+            ctx->prof_bytes[prof_slot(ctx, n_p1)] += sum_it * (15 + nc) * cp1;
+            ctx->prof_bytes[prof_slot(ctx, n_a2)] += sum_it * 2 * (2 * nc * cp1);
+            ctx->prof_bytes[prof_slot(ctx, n_a1)] += sum_it * 2 * (2 * nc * cp1);
+            ctx->prof_bytes[prof_slot(ctx, n_p3)] += sum_it * 2 * nc * cp1 + mat;
+            ctx->prof_bytes[prof_slot(ctx, n_p5)] += sum_it * (6 + nc) * cp1;
+        }
         bool all = true;
-        nact = 0;
         for (int b = 0; b < ctx->B; ++b) {
             all &= (ctx->cg_h[b].done != 0);
-            nact += ctx->cg_h[b].done ? 0 : 1;
+            it_before[b] = ctx->cg_h[b].iter;
         }
         if (all || launched >= ctx->grid.max_iter + 1) break;
         chunk = chunk < 16 ? chunk * 2 : 16;
@@ -922,7 +970,10 @@ dbfft_status solve_current(dbfft_ctx* ctx, dbfft_report* rep) {
     }
     const int max_steps = ctx->grid.max_newton > 0 ? ctx->grid.max_newton : 50;
     for (int step = 0; step <= max_steps; ++step) {
-        TRY(chain_residual(ctx, ctx->x64, ctx->xe64, ru2, re2));
+        ctx->cp_guess_trial = step > 0;  // later Newton steps start the local solves from the last trial stress
+        const dbfft_status rs = chain_residual(ctx, ctx->x64, ctx->xe64, ru2, re2);
+        ctx->cp_guess_trial = 0;
+        TRY(rs);
         ++outer;
         // convergence per right-hand side
         CK(cudaMemcpyAsync(ctx->small_h, ctx->sig0, ctx->B * 9 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
@@ -1069,6 +1120,39 @@ void tune_precision(dbfft_ctx* ctx, int pi_) {
     char buf[256];
     std::snprintf(buf, sizeof(buf), "pass3 radix %d lines %d (%.4f ms); ", bestR, bestL, best);
     ctx->tune_note += buf;
+    // the pipelined pass for the CG applications: radix x lines per tile
+    {
+        const long long nlines = (long long)ctx->n1 * ctx->n2;
+        float bp = 1e30f;
+        int bpR = 0, bpL = 0;
+        for (int ri = 0; ri < (sizeof(T) == 4 ? 2 : 1); ++ri) {
+            const int R = sizeof(T) == 4 ? radices[ri] : 4;
+            for (int L : {2, 4, 6, 8, 12, 16, 24, 32}) {
+                const long long sm = ax3_pipe_smem(ctx->n3, ctx->nc, ctx->RB, sizeof(T) == 8, ctx->scale != nullptr, R,
+                                                   L, nlines);
+                if (sm < 0 || sm > 200 * 1024) continue;
+                Ax3Args<T> a3 = ax3_base<T>(ctx, W);
+                a3.pipe = 1;
+                a3.radix = R;
+                a3.L = L;
+                if constexpr (sizeof(T) == 4) a3.macroW = ctx->macroWf;
+                else a3.macroW = ctx->macroW;
+                a3.tan_in = reinterpret_cast<const T*>(ctx->tan);
+                const float ms = time_launch(ctx, [&] { return launch_ax3<T>(opk_apply(ctx), a3, ctx->stream); });
+                if (ms < bp * 0.98f) {
+                    bp = ms;
+                    bpR = R;
+                    bpL = L;
+                }
+            }
+        }
+        ctx->pipe_on[pi_] = (bpL > 0 && bp < best) ? 1 : 0;
+        ctx->pipe_R[pi_] = bpR;
+        ctx->pipe_L[pi_] = bpL;
+        std::snprintf(buf, sizeof(buf), "pass3 pipelined radix %d lines %d (%.4f ms)%s; ", bpR, bpL, bp,
+                      ctx->pipe_on[pi_] ? " used" : "");
+        ctx->tune_note += buf;
+    }
     // strided transforms: columns per CTA along axes 1 and 2
     for (int ax = 0; ax < 2; ++ax) {
         float bt = 1e30f;
@@ -1099,8 +1183,8 @@ std::string tune_key(const dbfft_ctx* ctx) {
     for (char& c : name)
         if (c == ' ') c = '_';
     char buf[256];
-    std::snprintf(buf, sizeof(buf), "%s n=%dx%dx%d B=%d RB=%d nc=%d prec=%d model=%d", name.c_str(), ctx->n1, ctx->n2,
-                  ctx->n3, ctx->B, ctx->RB, ctx->nc, ctx->prec, ctx->model);
+    std::snprintf(buf, sizeof(buf), "%s n=%dx%dx%d B=%d RB=%d nc=%d prec=%d model=%d scale=%d", name.c_str(), ctx->n1,
+                  ctx->n2, ctx->n3, ctx->B, ctx->RB, ctx->nc, ctx->prec, ctx->model, ctx->scale != nullptr ? 1 : 0);
     return buf;
 }
 
@@ -1139,12 +1223,16 @@ dbfft_status dbfft_autotune(dbfft_ctx* ctx, const char* cache_path) {
             while (std::fgets(line, sizeof(line), f)) {
                 std::string ln(line);
                 if (ln.compare(0, key.size(), key) != 0 || ln.size() <= key.size() || ln[key.size()] != '|') continue;
-                int R = 0, L = 0, t1 = 0, t2 = 0;
-                if (std::sscanf(ln.c_str() + key.size() + 1, "%d %d %d %d", &R, &L, &t1, &t2) == 4) {
+                int R = 0, L = 0, t1 = 0, t2 = 0, pon = 0, pR = 0, pL = 0;
+                if (std::sscanf(ln.c_str() + key.size() + 1, "%d %d %d %d %d %d %d", &R, &L, &t1, &t2, &pon, &pR,
+                                &pL) == 7) {
                     ctx->ax3_radix[pi_] = R;
                     ctx->ax3_L[pi_] = L;
                     ctx->fft_tw[pi_][0] = t1;
                     ctx->fft_tw[pi_][1] = t2;
+                    ctx->pipe_on[pi_] = pon;
+                    ctx->pipe_R[pi_] = pR;
+                    ctx->pipe_L[pi_] = pL;
                     ctx->tune_note = "from cache";
                     std::fclose(f);
                     for (int k = 0; k < 2; ++k)
@@ -1163,8 +1251,9 @@ dbfft_status dbfft_autotune(dbfft_ctx* ctx, const char* cache_path) {
         if (ctx->cg_exec[k]) { cudaGraphExecDestroy(ctx->cg_exec[k]); ctx->cg_exec[k] = nullptr; }
     if (cache_path) {
         if (FILE* f = std::fopen(cache_path, "a")) {
-            std::fprintf(f, "%s|%d %d %d %d\n", key.c_str(), ctx->ax3_radix[pi_], ctx->ax3_L[pi_], ctx->fft_tw[pi_][0],
-                         ctx->fft_tw[pi_][1]);
+            std::fprintf(f, "%s|%d %d %d %d %d %d %d\n", key.c_str(), ctx->ax3_radix[pi_], ctx->ax3_L[pi_],
+                         ctx->fft_tw[pi_][0], ctx->fft_tw[pi_][1], ctx->pipe_on[pi_], ctx->pipe_R[pi_],
+                         ctx->pipe_L[pi_]);
             std::fclose(f);
         }
     }
@@ -1172,6 +1261,30 @@ dbfft_status dbfft_autotune(dbfft_ctx* ctx, const char* cache_path) {
 }
 
 const char* dbfft_tuning(const dbfft_ctx* ctx) { return ctx ? ctx->tune_note.c_str() : ""; }
+
+dbfft_status dbfft_set_pass3_shape(dbfft_ctx* ctx, int fp64, int pipelined, int radix, int lines) {
+    if (!ctx || (fp64 != 0 && fp64 != 1) || lines < 1) return DBFFT_E_ARG;
+    const bool dbl = fp64 == 1;
+    if (dbl ? radix != 4 : (radix != 8 && radix != 16)) return fail(ctx, DBFFT_E_ARG, "radix: 8 or 16 (FP32), 4 (FP64)");
+    const long long nlines = (long long)ctx->n1 * ctx->n2;
+    if (lines > nlines) return fail(ctx, DBFFT_E_ARG, "more lines per CTA than grid lines");
+    const int pi_ = dbl ? 1 : 0;
+    if (pipelined) {
+        const long long sm = ax3_pipe_smem(ctx->n3, ctx->nc, ctx->RB, dbl, ctx->scale != nullptr, radix, lines, nlines);
+        if (sm < 0 || sm > 200 * 1024)
+            return fail(ctx, DBFFT_E_ARG, "pipelined pass 3: lines must be even, divide n1*n2 and fit in shared memory");
+        ctx->pipe_on[pi_] = 1;
+        ctx->pipe_R[pi_] = radix;
+        ctx->pipe_L[pi_] = lines;
+    } else {
+        ctx->pipe_on[pi_] = 0;
+        ctx->ax3_radix[pi_] = radix;
+        ctx->ax3_L[pi_] = lines;
+    }
+    for (int k = 0; k < 2; ++k)  // graphs captured with the old shape
+        if (ctx->cg_exec[k]) { cudaGraphExecDestroy(ctx->cg_exec[k]); ctx->cg_exec[k] = nullptr; }
+    return DBFFT_OK;
+}
 
 dbfft_status dbfft_profile(dbfft_ctx* ctx, int enable) {
     if (!ctx) return DBFFT_E_ARG;
@@ -1222,6 +1335,9 @@ void dbfft_destroy(dbfft_ctx* ctx) {
 static dbfft_status create_impl(dbfft_ctx* ctx, const dbfft_grid* grid, const dbfft_materials* mat,
                                 const dbfft_load* load) {
     ctx->grid = *grid;
+    // DBFFT_CUDA_GRAPHS=0 runs every inner PCG launch by launch (same kernels,
+    // same order), e.g. for profilers that cannot look inside conditional graphs
+    if (const char* g = std::getenv("DBFFT_CUDA_GRAPHS")) ctx->use_graphs = g[0] != '0';
     ctx->n1 = grid->n[0];
     ctx->n2 = grid->n[1];
     ctx->n3 = grid->n[2];
@@ -1362,14 +1478,38 @@ static dbfft_status create_impl(dbfft_ctx* ctx, const dbfft_grid* grid, const db
         std::vector<CpGrain> gr(np);
         for (int p = 0; p < np; ++p)
             if (!cp_grain(mat->phases[p], gr[p])) return fail(ctx, DBFFT_E_ARG, "singular crystal stiffness");
+        std::vector<CpGrainF> grf(np);
+        for (int p = 0; p < np; ++p) {
+            for (int q = 0; q < 21; ++q) grf[p].S[q] = (float)gr[p].S[q];
+            for (int a = 0; a < 12; ++a)
+                for (int q = 0; q < 6; ++q) grf[p].P[a][q] = (float)gr[p].P[a][q];
+        }
         TRY(dalloc_t(ctx, np, &ctx->grains));
+        TRY(dalloc_t(ctx, np, &ctx->grains_f));
         CK(cudaMemcpyAsync(ctx->grains, gr.data(), np * sizeof(CpGrain), cudaMemcpyHostToDevice, ctx->stream));
+        CK(cudaMemcpyAsync(ctx->grains_f, grf.data(), np * sizeof(CpGrainF), cudaMemcpyHostToDevice, ctx->stream));
         CK(cudaStreamSynchronize(ctx->stream));
         const dbfft_phase& p0 = mat->phases[0];
-        ctx->cp.gdot0 = p0.gdot0;
-        ctx->cp.inv_m = 1.0 / p0.m;
-        ctx->cp.tau_c = p0.tau_c;
-        ctx->cp.dt = ctx->total_time / ctx->n_inc;
+        CpScalars<double>& c = ctx->cp.d;
+        c.gdot0 = p0.gdot0;
+        c.inv_m = 1.0 / p0.m;
+        c.tau_c = p0.tau_c;
+        c.dt = ctx->total_time / ctx->n_inc;
+        c.inv_tc = 1.0 / c.tau_c;
+        c.dtg = c.dt * c.gdot0;
+        c.dtg_n_tc = c.dtg * c.inv_m / c.tau_c;
+        c.dtk = c.dtg * c.tau_c * p0.m / (1.0 + p0.m);
+        CpScalars<float>& cf = ctx->cp.f;
+        cf.gdot0 = (float)c.gdot0;
+        cf.inv_m = (float)c.inv_m;
+        cf.tau_c = (float)c.tau_c;
+        cf.dt = (float)c.dt;
+        cf.inv_tc = (float)c.inv_tc;
+        cf.dtg = (float)c.dtg;
+        cf.dtg_n_tc = (float)c.dtg_n_tc;
+        cf.dtk = (float)c.dtk;
+        const double ni = std::round(c.inv_m);
+        ctx->cp.n_int = (ni >= 1.0 && ni <= 127.0 && std::fabs(c.inv_m - ni) <= 1e-12 * ni) ? (int)ni : 0;
         ctx->cp.rtol = 1e-12;
         ctx->cp.max_it = 100;
     }
@@ -1443,6 +1583,7 @@ static dbfft_status create_impl(dbfft_ctx* ctx, const dbfft_grid* grid, const db
     TRY(dalloc_t(ctx, (size_t)ctx->B, &ctx->cg));
     TRY(dalloc_t(ctx, (size_t)ctx->B, &ctx->counters));
     TRY(dalloc_t(ctx, 1, &ctx->errw));
+    CK(cudaMemsetAsync(ctx->errw, 0, sizeof(unsigned), ctx->stream));
     CK(cudaMemsetAsync(ctx->counters, 0, ctx->B * sizeof(unsigned), ctx->stream));
     CK(cudaMemsetAsync(ctx->x64, 0, nU * sizeof(cplx<double>), ctx->stream));
     CK(cudaMemsetAsync(ctx->xe64, 0, ctx->B * 9 * sizeof(double), ctx->stream));

@@ -10,9 +10,12 @@
 //    solved by Newton (stopped on the full Newton step) with backtracking,
 //    far from the solution, on the convex potential whose gradient R is;
 //    consistent tangent (S + dt sum_a gdot'_a P_a P_a^T)^-1.
-// The stress-side math runs in FP64.
+// The converged stress is FP64; a mixed-precision context runs the first
+// Newton iterations in FP32.
 #pragma once
 #include <cuda_runtime.h>
+
+#include <type_traits>
 
 namespace dbfft {
 
@@ -21,12 +24,29 @@ struct CpGrain {
     double P[12][6];  // Schmid tensors sym(s x n), Mandel, sample frame
 };
 
-struct CpParams {
-    double gdot0, inv_m, tau_c, dt, rtol;
-    int max_it;
+struct CpGrainF {  // the same in FP32
+    float S[21];
+    float P[12][6];
 };
 
-__host__ __device__ __forceinline__ int sym6(int i, int j) {
+template <typename R>
+struct CpScalars {
+    R gdot0, inv_m, tau_c, dt;
+    R inv_tc;    // 1 / tau_c
+    R dtg;       // dt gdot0
+    R dtg_n_tc;  // dt gdot0 (1/m) / tau_c
+    R dtk;       // dt gdot0 tau_c m / (1 + m): potential coefficient
+};
+
+struct CpParams {
+    CpScalars<double> d;
+    CpScalars<float> f;
+    double rtol;
+    int max_it;
+    int n_int;  // 1/m when it is an integer in [1, 127] (powers by products), else 0
+};
+
+__host__ __device__ __forceinline__ constexpr int sym6(int i, int j) {
     if (i > j) { int t = i; i = j; j = t; }
     return i * 6 - (i * (i - 1)) / 2 + (j - i);
 }
@@ -119,144 +139,272 @@ __device__ __forceinline__ void cp_apply(const T* tn, const T* e, T* s) {
     s[3] = ir2 * sm[3]; s[4] = ir2 * sm[4]; s[5] = ir2 * sm[5];
 }
 
-// Cholesky solve / inverse of a 6x6 SPD matrix (full storage).
-__device__ __forceinline__ bool chol6(double (*A)[6], double (*L)[6]) {
-    for (int j = 0; j < 6; ++j) {
-        double s = A[j][j];
-        for (int k = 0; k < j; ++k) s -= L[j][k] * L[j][k];
-        if (!(s > 0.0)) return false;
-        const double ljj = sqrt(s);
-        L[j][j] = ljj;
-        for (int i = j + 1; i < 6; ++i) {
-            double t = A[i][j];
-            for (int k = 0; k < j; ++k) t -= L[i][k] * L[j][k];
-            L[i][j] = t / ljj;
-        }
-    }
-    return true;
+// ---- crystal plasticity, local problem
+// Index of (i, j), i > j, in a strictly lower 6x6 triangle stored by rows.
+__host__ __device__ __forceinline__ constexpr int lo6(int i, int j) { return i * (i - 1) / 2 + j; }
+
+template <typename R> struct CpGrainOf;
+template <> struct CpGrainOf<double> { using type = CpGrain; };
+template <> struct CpGrainOf<float> { using type = CpGrainF; };
+
+template <typename R>
+__device__ __forceinline__ const CpScalars<R>& cp_scalars(const CpParams& cp) {
+    if constexpr (sizeof(R) == 8) return cp.d;
+    else return cp.f;
 }
-__device__ __forceinline__ void chol6_solve(double (*L)[6], const double* b, double* x) {
-    double y[6];
-    for (int i = 0; i < 6; ++i) {
-        double t = b[i];
-        for (int k = 0; k < i; ++k) t -= L[i][k] * y[k];
-        y[i] = t / L[i][i];
+
+// x^k, 0 <= k < 128, by binary powering (exact products, no pow call).
+template <typename R>
+__device__ __forceinline__ R ipow(R x, int k) {
+    R r = R(1), b = x;
+#pragma unroll
+    for (int bit = 0; bit < 7; ++bit) {
+        if (k & (1 << bit)) r *= b;
+        if ((k >> (bit + 1)) == 0) break;
+        b *= b;
     }
-    for (int i = 5; i >= 0; --i) {
-        double t = y[i];
-        for (int k = i + 1; k < 6; ++k) t -= L[k][i] * x[k];
-        x[i] = t / L[i][i];
+    return r;
+}
+
+// xn = x^(1/m) and xn1 = x^(1/m - 1) for x = |tau| / tau_c >= 0.
+template <typename R>
+__device__ __forceinline__ void cp_powers(const CpParams& cp, R x, R& xn, R& xn1) {
+    if (cp.n_int > 0) {
+        xn1 = ipow<R>(x, cp.n_int - 1);
+        xn = xn1 * x;
+    } else {
+        const CpScalars<R>& c = cp_scalars<R>(cp);
+        xn = pow(x, c.inv_m);
+        xn1 = x > R(0) ? xn / x : pow(x, c.inv_m - R(1));
     }
 }
 
-struct CpEval {
-    double R[6];
-    double Jm[6][6];
-};
-
-__device__ __forceinline__ void cp_residual(const CpGrain& G, const CpParams& cp, const double* s,
-                                            const double* target, double* R, double (*Jm)[6], double* gd_out) {
+// Residual R(s) = S s + dt sum_a gdot_a(s) P_a - tg, optionally its Jacobian
+// J = S + dt sum_a gdot'_a P_a P_a^T (21 packed entries, symmetric) and the
+// convex potential phi(s) = 1/2 s.S.s - s.tg + dt sum_a k |tau_a / tau_c|^(1+1/m)
+// whose gradient R is. All in precision R.
+template <typename R, bool JAC, bool POT>
+__device__ __forceinline__ void cp_eval(const typename CpGrainOf<R>::type& G, const CpParams& cp, const R (&s)[6],
+                                        const R (&tg)[6], R (&Rv)[6], R (&J)[21], R& pot) {
+    const CpScalars<R>& c = cp_scalars<R>(cp);
+    if (POT) pot = R(0);
+#pragma unroll
     for (int i = 0; i < 6; ++i) {
-        double acc = 0.0;
+        R acc = R(0);
+#pragma unroll
         for (int j = 0; j < 6; ++j) acc += G.S[sym6(i, j)] * s[j];
-        R[i] = acc - target[i];
-        if (Jm)
-            for (int j = 0; j < 6; ++j) Jm[i][j] = G.S[sym6(i, j)];
+        Rv[i] = acc - tg[i];
+        if (POT) pot += s[i] * (R(0.5) * acc - tg[i]);
     }
+    if (JAC) {
+#pragma unroll
+        for (int q = 0; q < 21; ++q) J[q] = G.S[q];
+    }
+    R ppot = R(0);
+#pragma unroll 1
     for (int al = 0; al < 12; ++al) {
-        double tau = 0.0;
-        for (int j = 0; j < 6; ++j) tau += G.P[al][j] * s[j];
-        const double x = fabs(tau) / cp.tau_c;
-        const double pw = pow(x, cp.inv_m);
-        const double gd = cp.gdot0 * pw * (tau > 0.0 ? 1.0 : (tau < 0.0 ? -1.0 : 0.0));
-        if (gd_out) gd_out[al] = gd;
-        for (int i = 0; i < 6; ++i) R[i] += cp.dt * gd * G.P[al][i];
-        if (Jm) {
-            const double dgd = cp.gdot0 * cp.inv_m / cp.tau_c * pow(x, cp.inv_m - 1.0);
-            const double f = cp.dt * dgd;
-            for (int i = 0; i < 6; ++i)
-                for (int j = 0; j < 6; ++j) Jm[i][j] += f * G.P[al][i] * G.P[al][j];
-        }
-    }
-}
-
-__device__ __forceinline__ double cp_potential(const CpGrain& G, const CpParams& cp, const double* s,
-                                               const double* target) {
-    double v = 0.0;
-    for (int i = 0; i < 6; ++i) {
-        double acc = 0.0;
-        for (int j = 0; j < 6; ++j) acc += G.S[sym6(i, j)] * s[j];
-        v += 0.5 * s[i] * acc - s[i] * target[i];
-    }
-    const double m = 1.0 / cp.inv_m;
-    const double k = cp.gdot0 * cp.tau_c * m / (1.0 + m);
-    double pot = 0.0;
-    for (int al = 0; al < 12; ++al) {
-        double tau = 0.0;
-        for (int j = 0; j < 6; ++j) tau += G.P[al][j] * s[j];
-        pot += k * pow(fabs(tau) / cp.tau_c, 1.0 + cp.inv_m);
-    }
-    return v + cp.dt * pot;
-}
-
-// eps_w: total strain in W components (11,22,33,23,13,12); ep_old, s_guess,
-// s_out, ep_new: Mandel; tan: 21-entry Mandel tangent. Returns false when
-// the local Newton fails.
-__device__ __forceinline__ bool cp_update(const CpGrain& G, const CpParams& cp, const double* eps_w,
-                                          const double* ep_old, const double* s_guess, double* s_out,
-                                          double* tan, double* ep_new) {
-    const double r2 = 1.41421356237309504880168872420970;
-    double target[6];
-    const double em[6] = {eps_w[0], eps_w[1], eps_w[2], r2 * eps_w[3], r2 * eps_w[4], r2 * eps_w[5]};
-    for (int i = 0; i < 6; ++i) target[i] = em[i] - ep_old[i];
-    double s[6];
-    for (int i = 0; i < 6; ++i) s[i] = s_guess[i];
-    bool conv = false;
-    double R[6], Jm[6][6], L[6][6], step[6];
-    for (int it = 0; it < cp.max_it; ++it) {
-        cp_residual(G, cp, s, target, R, Jm, nullptr);
-        if (!chol6(Jm, L)) return false;
-        double mR[6];
-        for (int i = 0; i < 6; ++i) mR[i] = -R[i];
-        chol6_solve(L, mR, step);
-        double slope = 0.0, ns = 0.0, sn = 0.0;
-        for (int i = 0; i < 6; ++i) {
-            slope += R[i] * step[i];
-            ns += step[i] * step[i];
-            sn += s[i] * s[i];
-        }
-        const double scale = sqrt(sn) + cp.tau_c;
-        ns = sqrt(ns);
-        double t = 1.0;
-        if (ns > 1e-3 * scale) {  // backtracking on the convex potential, far from the solution only
-            const double f0 = cp_potential(G, cp, s, target);
-            for (int ls = 0; ls < 60; ++ls) {
-                double trial[6];
-                for (int i = 0; i < 6; ++i) trial[i] = s[i] + t * step[i];
-                if (!(cp_potential(G, cp, trial, target) > f0 + 1e-4 * t * slope + 1e-13 * fabs(f0))) break;
-                t *= 0.5;
+        R Pa[6];
+#pragma unroll
+        for (int j = 0; j < 6; ++j) Pa[j] = G.P[al][j];
+        R tau = R(0);
+#pragma unroll
+        for (int j = 0; j < 6; ++j) tau += Pa[j] * s[j];
+        const R x = fabs(tau) * c.inv_tc;
+        R xn, xn1;
+        cp_powers<R>(cp, x, xn, xn1);
+        const R g = tau < R(0) ? -c.dtg * xn : c.dtg * xn;  // dt gdot_a (0 at tau = 0)
+#pragma unroll
+        for (int i = 0; i < 6; ++i) Rv[i] += g * Pa[i];
+        if (JAC) {
+            const R f = c.dtg_n_tc * xn1;  // dt d gdot_a / d tau
+#pragma unroll
+            for (int i = 0; i < 6; ++i) {
+                const R fi = f * Pa[i];
+#pragma unroll
+                for (int j = i; j < 6; ++j) J[sym6(i, j)] += fi * Pa[j];
             }
         }
-        for (int i = 0; i < 6; ++i) s[i] += t * step[i];
-        if (ns <= cp.rtol * scale) { conv = true; break; }  // full Newton step below tolerance
+        if (POT) ppot += xn * x;
     }
-    double gd[12];
-    cp_residual(G, cp, s, target, R, Jm, gd);
-    if (!chol6(Jm, L)) return false;
-    // tangent = Jm^-1 (symmetric), column by column
-    for (int j = 0; j < 6; ++j) {
-        double e[6] = {0, 0, 0, 0, 0, 0}, col[6];
-        e[j] = 1.0;
-        chol6_solve(L, e, col);
-        for (int i = 0; i <= j; ++i) tan[sym6(i, j)] = col[i];
+    if (POT) pot += c.dtk * ppot;
+}
+
+// Compile-time loop: f(std::integral_constant<int, k>) for k = B .. E-1, so
+// that every array index below is a constant and the arrays stay in registers.
+template <int B, int E, typename F>
+__device__ __forceinline__ void sfor(F&& f) {
+    if constexpr (B < E) {
+        f(std::integral_constant<int, B>{});
+        sfor<B + 1, E>(f);
     }
+}
+
+// L D L^T factorisation of a packed symmetric 6x6 matrix; false unless
+// positive definite (or on a non-finite entry).
+template <typename R>
+__device__ __forceinline__ bool ldl6(const R (&A)[21], R (&L)[15], R (&Di)[6]) {
+    R D[6];
+    bool ok = true;
+    sfor<0, 6>([&](auto jc) {
+        constexpr int j = decltype(jc)::value;
+        R d = A[sym6(j, j)];
+        sfor<0, j>([&](auto kc) {
+            constexpr int k = decltype(kc)::value;
+            d -= L[lo6(j, k)] * L[lo6(j, k)] * D[k];
+        });
+        ok = ok && (d > R(0));
+        D[j] = d;
+        Di[j] = R(1) / d;
+        sfor<j + 1, 6>([&](auto ic) {
+            constexpr int i = decltype(ic)::value;
+            R t = A[sym6(j, i)];
+            sfor<0, j>([&](auto kc) {
+                constexpr int k = decltype(kc)::value;
+                t -= L[lo6(i, k)] * L[lo6(j, k)] * D[k];
+            });
+            L[lo6(i, j)] = t * Di[j];
+        });
+    });
+    return ok;
+}
+
+template <typename R>
+__device__ __forceinline__ void ldl6_solve(const R (&L)[15], const R (&Di)[6], const R (&b)[6], R (&x)[6]) {
+    R y[6];
+    sfor<0, 6>([&](auto ic) {
+        constexpr int i = decltype(ic)::value;
+        R t = b[i];
+        sfor<0, i>([&](auto kc) {
+            constexpr int k = decltype(kc)::value;
+            t -= L[lo6(i, k)] * y[k];
+        });
+        y[i] = t;
+    });
+    sfor<0, 6>([&](auto rc) {
+        constexpr int i = 5 - decltype(rc)::value;
+        R t = y[i] * Di[i];
+        sfor<i + 1, 6>([&](auto kc) {
+            constexpr int k = decltype(kc)::value;
+            t -= L[lo6(k, i)] * x[k];
+        });
+        x[i] = t;
+    });
+}
+
+// Newton on R(s) = 0 in precision R, from s (in/out). Stops once the full
+// Newton step is below rtol (|s| + tau_c) (the step is then applied).
+// Far from the solution (step > 1e-3 scale) the step is backtracked on the
+// convex potential, with an allowance armijo |phi| for its round-off.
+// Returns 1 when converged, 0 at the iteration cap, -1 on a non-SPD
+// Jacobian or a non-finite step.
+template <typename R>
+__device__ __forceinline__ int cp_newton(const typename CpGrainOf<R>::type& G, const CpParams& cp, const R (&tg)[6],
+                                         R (&s)[6], R rtol, R armijo, int max_it) {
+    const R tau_c = cp_scalars<R>(cp).tau_c;
+    for (int it = 0; it < max_it; ++it) {
+        R Rv[6], J[21], L[15], Di[6], st[6], unused;
+        cp_eval<R, true, false>(G, cp, s, tg, Rv, J, unused);
+        if (!ldl6<R>(J, L, Di)) return -1;
+        R mR[6];
+#pragma unroll
+        for (int i = 0; i < 6; ++i) mR[i] = -Rv[i];
+        ldl6_solve<R>(L, Di, mR, st);
+        R slope = R(0), ns = R(0), sn = R(0);
+#pragma unroll
+        for (int i = 0; i < 6; ++i) {
+            slope += Rv[i] * st[i];
+            ns += st[i] * st[i];
+            sn += s[i] * s[i];
+        }
+        if (!(ns <= R(3e38))) return -1;  // NaN or overflow
+        const R scale = sqrt(sn) + tau_c;
+        ns = sqrt(ns);
+        R t = R(1);
+        if (ns > R(1e-3) * scale) {
+            R f0, Rj[6], Jj[21];
+            cp_eval<R, false, true>(G, cp, s, tg, Rj, Jj, f0);
+            for (int ls = 0; ls < 60; ++ls) {
+                R trial[6], f;
+#pragma unroll
+                for (int i = 0; i < 6; ++i) trial[i] = s[i] + t * st[i];
+                cp_eval<R, false, true>(G, cp, trial, tg, Rj, Jj, f);
+                if (!(f > f0 + R(1e-4) * t * slope + armijo * fabs(f0))) break;
+                t *= R(0.5);
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < 6; ++i) s[i] += t * st[i];
+        if (ns <= rtol * scale) return 1;
+    }
+    return 0;
+}
+
+// Backward-Euler update of one voxel. eps_w: total strain in W components
+// (11,22,33,23,13,12); ep_old, s_guess, s_out, ep_new: Mandel 6-vectors;
+// tan: 21-entry Mandel tangent (J^-1 at the solution) in precision TT.
+// With TT = float (the FP32 inner-CG mode) Newton first runs in FP32 from
+// s_guess and FP64 Newton finishes from there, so the FP64 iterations are
+// the last two or three of the quadratic phase; the stored FP32 tangent is
+// built in FP32. With TT = double everything runs in FP64. Both stop on the
+// same FP64 criterion, so both return the same stress to that tolerance.
+// Returns false when the local Newton fails (outputs stay finite).
+template <typename TT>
+__device__ __forceinline__ bool cp_update(const CpGrain& G, const CpGrainF& Gf, const CpParams& cp,
+                                          const double* eps_w, const double* ep_old, const double* s_guess,
+                                          double* s_out, TT* tan, double* ep_new) {
+    const double r2 = 1.41421356237309504880168872420970;
+    const double em[6] = {eps_w[0], eps_w[1], eps_w[2], r2 * eps_w[3], r2 * eps_w[4], r2 * eps_w[5]};
+    double tg[6], s[6];
+#pragma unroll
     for (int i = 0; i < 6; ++i) {
-        double acc = ep_old[i];
-        for (int al = 0; al < 12; ++al) acc += cp.dt * gd[al] * G.P[al][i];
-        ep_new[i] = acc;
+        tg[i] = em[i] - ep_old[i];
+        s[i] = s_guess[i];
     }
-    for (int i = 0; i < 6; ++i) s_out[i] = s[i];
-    return conv;
+    if constexpr (sizeof(TT) == 4) {
+        float tgf[6], sf[6];
+#pragma unroll
+        for (int i = 0; i < 6; ++i) {
+            tgf[i] = (float)tg[i];
+            sf[i] = (float)s[i];
+        }
+        if (cp_newton<float>(Gf, cp, tgf, sf, 1e-5f, 1e-6f, 40) >= 0) {
+#pragma unroll
+            for (int i = 0; i < 6; ++i) s[i] = sf[i];
+        }
+    }
+    const int r = cp_newton<double>(G, cp, tg, s, cp.rtol, 1e-13, cp.max_it);
+    bool ok = r == 1;
+    // plastic strain from the converged residual: eps_p = eps - S s
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+        double acc = em[i];
+#pragma unroll
+        for (int j = 0; j < 6; ++j) acc -= G.S[sym6(i, j)] * s[j];
+        ep_new[i] = acc;
+        s_out[i] = s[i];
+    }
+    // consistent tangent J^-1 at the solution, column by column
+    using RT = TT;
+    RT sT[6], tgT[6], Rv[6], J[21], L[15], Di[6], unused;
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+        sT[i] = (RT)s[i];
+        tgT[i] = (RT)tg[i];
+    }
+    if constexpr (sizeof(TT) == 4) cp_eval<float, true, false>(Gf, cp, sT, tgT, Rv, J, unused);
+    else cp_eval<double, true, false>(G, cp, sT, tgT, Rv, J, unused);
+    const bool spd = ldl6<RT>(J, L, Di);
+    ok = ok && spd;
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+        RT e[6], col[6];
+#pragma unroll
+        for (int i = 0; i < 6; ++i) e[i] = RT(i == j ? 1 : 0);
+        ldl6_solve<RT>(L, Di, e, col);
+#pragma unroll
+        for (int i = 0; i <= j; ++i) tan[sym6(i, j)] = spd ? col[i] : RT(0);
+    }
+    return ok;
 }
 
 }  // namespace dbfft

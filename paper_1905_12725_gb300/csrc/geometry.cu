@@ -1,5 +1,6 @@
 // geometry.cu -- launch geometry of the passes (shared by host code).
 #include "launch.h"
+#include "pass3_pipe.cuh"
 
 namespace dbfft {
 
@@ -60,6 +61,37 @@ int ax3_threads_per_line(int n3, int nc, int rb, bool dbl) {
 
 size_t ax3_smem(int n3, int nc, int rb, int lines, bool dbl, bool two_fields) {
     return (size_t)lines * rb * nc * n3 * (dbl ? 8 : 4) * (two_fields ? 2 : 1);
+}
+
+}  // namespace dbfft
+
+namespace dbfft {
+
+namespace {
+template <typename T, int N3>
+long long pipe_smem_t(int nc, int rb, bool scale, int radix, int L) {
+    constexpr int M = N3 / 2;
+    const int R = radix_ax3(M, sizeof(T) == 8, radix);
+    const int P = M / R;
+    return PipePlan<T, N3>::total_bytes(L, rb, nc, scale, P, 256 / 32);
+}
+template <typename T>
+long long pipe_smem_n(int n3, int nc, int rb, bool scale, int radix, int L) {
+    switch (n3) {
+        case 8: return pipe_smem_t<T, 8>(nc, rb, scale, radix, L);
+        case 16: return pipe_smem_t<T, 16>(nc, rb, scale, radix, L);
+        case 32: return pipe_smem_t<T, 32>(nc, rb, scale, radix, L);
+        case 64: return pipe_smem_t<T, 64>(nc, rb, scale, radix, L);
+        case 128: return pipe_smem_t<T, 128>(nc, rb, scale, radix, L);
+        case 256: return pipe_smem_t<T, 256>(nc, rb, scale, radix, L);
+        default: return -1;
+    }
+}
+}  // namespace
+
+long long ax3_pipe_smem(int n3, int nc, int rb, bool dbl, bool scale, int radix, int L, long long nlines) {
+    if (L < 2 || (L & 1) || nlines % L != 0 || rb < 1 || rb > 8) return -1;
+    return dbl ? pipe_smem_n<double>(n3, nc, rb, scale, radix, L) : pipe_smem_n<float>(n3, nc, rb, scale, radix, L);
 }
 
 }  // namespace dbfft

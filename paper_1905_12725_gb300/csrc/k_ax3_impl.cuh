@@ -6,6 +6,9 @@ namespace dbfft {
 
 template <typename T, int N3, int NC, int OPK, int RW>
 static cudaError_t ax3_nr(const Ax3Args<T>& a, cudaStream_t s) {
+    if constexpr (OpInfo<OPK>::apply) {
+        if (a.pipe) return launch_ax3_pipe<T>(OPK, a, s);
+    }
     const int threads = 256;
     const long long nlines = (long long)a.d.n1 * a.d.n2;
     const dim3 grid((unsigned)((nlines + a.L - 1) / a.L), (unsigned)(a.d.B / a.RB));

@@ -32,7 +32,8 @@ struct Ax3Args {
     cplx<T>* W;            // [B][nc][H]
     const cplx<T>* W2;     // OP_ADJ: adjoint strain field in W layout
     int RB;                // right-hand sides per CTA (divides Rm)
-    int L;                 // grid lines per CTA
+    int L;                 // grid lines per CTA (per tile for the pipelined pass)
+    int pipe;              // CG applications: 1 = pipelined pass (k_axis3_pipe), 0 = k_axis3
     int radix;             // radix of the half-length transform (FP32: 8 or 16; FP64: 4)
     const T* macroW;       // [B][9] constant field added before the op (W components)
     const T* macroW2;      // OP_ADJ: macro part of the adjoint field
@@ -50,7 +51,9 @@ struct Ax3Args {
     float* tan_out_f;      // update ops: tangent written in FP32 (or null)
     double* tan_out_d;     // update ops: tangent written in FP64 (or null)
     const CpGrain* grains; // CP per-grain data
+    const CpGrainF* grains_f; // the same in FP32
     CpParams cp;
+    int guess_trial;       // CP: start the local Newton from the trial stress (not the committed one)
     const double* eps_p;   // [B][V][6] committed plastic strain
     const double* sig_prev;// [B][V][6] committed stress (Newton start)
     double* eps_p_t;       // trial plastic strain
@@ -278,17 +281,25 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? (RW == 16 ? 3 : 4) : ((
 #pragma unroll
                 for (int q = 0; q < 6; ++q) e[q] = (double)f[q * SB] + a.macroW[bb * 9 + q];
                 const long long so = ((long long)bb * d.V + vox) * 6;
-                double sg[6], tn[21], ep[6];
-                const bool ok = cp_update(a.grains[gr], a.cp, e, a.eps_p + so, a.sig_prev + so, sg, tn, ep);
+                double sg[6], ep[6], guess[6];
+#pragma unroll
+                for (int q = 0; q < 6; ++q) guess[q] = (a.guess_trial ? a.sig_t : a.sig_prev)[so + q];
+                const long long to = ((long long)bb * d.V + vox) * 21;
+                bool ok;
+                if (a.tan_out_f) {
+                    float tn[21];
+                    ok = cp_update<float>(a.grains[gr], a.grains_f[gr], a.cp, e, a.eps_p + so, guess, sg, tn, ep);
+#pragma unroll
+                    for (int q = 0; q < 21; ++q) a.tan_out_f[to + q] = tn[q];
+                } else {
+                    double tn[21];
+                    ok = cp_update<double>(a.grains[gr], a.grains_f[gr], a.cp, e, a.eps_p + so, guess, sg, tn, ep);
+#pragma unroll
+                    for (int q = 0; q < 21; ++q) a.tan_out_d[to + q] = tn[q];
+                }
                 if (!ok) atomicOr(a.err, 1u);
 #pragma unroll
                 for (int q = 0; q < 6; ++q) { a.eps_p_t[so + q] = ep[q]; a.sig_t[so + q] = sg[q]; }
-                const long long to = ((long long)bb * d.V + vox) * 21;
-#pragma unroll
-                for (int q = 0; q < 21; ++q) {
-                    if (a.tan_out_f) a.tan_out_f[to + q] = (float)tn[q];
-                    if (a.tan_out_d) a.tan_out_d[to + q] = tn[q];
-                }
                 const double ir2 = 0.70710678118654752440084436210485;
 #pragma unroll
                 for (int q = 0; q < 6; ++q) f[q * SB] = (T)(q < 3 ? sg[q] : ir2 * sg[q]);

@@ -74,7 +74,7 @@ EXPORTS = ["dbfft_create", "dbfft_apply", "dbfft_solve_increment", "dbfft_homoge
            "dbfft_homogenized_tangent", "dbfft_adjoint", "dbfft_get_solution", "dbfft_device_bytes",
            "dbfft_destroy", "dbfft_last_error", "dbfft_status_string", "dbfft_profile",
            "dbfft_profile_read", "dbfft_launch_count", "dbfft_apply_iso_noalloc", "dbfft_autotune",
-           "dbfft_tuning"]
+           "dbfft_tuning", "dbfft_set_pass3_shape"]
 
 _LIB = None
 
@@ -130,6 +130,8 @@ def load_library(build_if_missing: bool = True):
     lib.dbfft_autotune.restype = ip
     lib.dbfft_tuning.argtypes = [vp]
     lib.dbfft_tuning.restype = C.c_char_p
+    lib.dbfft_set_pass3_shape.argtypes = [vp, ip, ip, ip, ip]
+    lib.dbfft_set_pass3_shape.restype = ip
     _LIB = lib
     return lib
 
@@ -285,6 +287,10 @@ class Solver:
         p = cache_path.encode() if cache_path else None
         self._check(self.lib.dbfft_autotune(self.ctx, p))
         return self.lib.dbfft_tuning(self.ctx).decode()
+
+    def set_pass3_shape(self, fp64, pipelined, radix, lines):
+        """Fix pass 3's launch shape for one inner precision (dbfft_set_pass3_shape)."""
+        self._check(self.lib.dbfft_set_pass3_shape(self.ctx, int(fp64), int(pipelined), int(radix), int(lines)))
 
     def launch_count(self) -> int:
         return int(self.lib.dbfft_launch_count(self.ctx))

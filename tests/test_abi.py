@@ -9,7 +9,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 def _declared():
     txt = open(os.path.join(ROOT, "include", "dbfft.h")).read()
     txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
-    return sorted(set(re.findall(r"\b(dbfft_[a-z_]+)\s*\(", txt)))
+    return sorted(set(re.findall(r"\b(dbfft_[a-z0-9_]+)\s*\(", txt)))
 
 
 def test_header_declares_the_entry_points():
