@@ -689,7 +689,7 @@ dbfft_status chain_residual(dbfft_ctx* ctx, const cplx<double>* x, const double*
             [&] { return launch_div<double>(AX5_RESID, a5, ctx->stream); }));
     // the unknowns are Hermitian-consistent spectra: drop the round-off that breaks it
     TRY(run(ctx, "hermitian_planes", 0.0, [&] { return launch_herm_planes<double>(ctx->dims, ctx->r64, ctx->stream); }));
-    const int nblk = (int)pw_blocks(ctx->H);
+    const int nblk = (int)pw_blocks(ctx->H, ctx->B);
     CK(cudaMemcpyAsync(ctx->part_h, ctx->partials, (size_t)ctx->B * nblk * 2 * sizeof(double),
                        cudaMemcpyDeviceToHost, ctx->stream));
     unsigned* errh = reinterpret_cast<unsigned*>(ctx->small_h + ctx->B * 10);
@@ -792,7 +792,7 @@ dbfft_status inner_cg(dbfft_ctx* ctx, double tol, long long& it_sum, int& it_max
     ai.counters = ctx->counters;
     ai.tol = tol;
     ai.max_iter = ctx->grid.max_iter;
-    const dim3 gi((unsigned)pw_blocks(ctx->H), ctx->B);
+    const dim3 gi((unsigned)pw_blocks(ctx->H, ctx->B), ctx->B);
     const bool dbl = sizeof(T) == 8;
     TRY(run(ctx, dbl ? "cg_init_f64" : "cg_init_f32", 3 * cpass(ctx, dbl, ctx->B), [&] {
         k_cg_init<T><<<gi, PW_THREADS, 0, ctx->stream>>>(ai);
@@ -1042,6 +1042,9 @@ dbfft_status solve_current(dbfft_ctx* ctx, dbfft_report* rep) {
                                             reinterpret_cast<const cplx<float>*>(ctx->pi), ctx->cg, ctx->xe_i,
                                             ctx->scal, ctx->x64, ctx->xe64, ctx->stream);
         }));
+        // keep the iterate a Hermitian-consistent spectrum (R5b): FP32 corrections
+        // carry round-off off that subspace on the k3 = 0 and k3 = n3/2 planes
+        TRY(run(ctx, "hermitian_planes", 0.0, [&] { return launch_herm_planes<double>(ctx->dims, ctx->x64, ctx->stream); }));
         ++steps;
     }
     ctx->have_solution = true;
@@ -1380,6 +1383,8 @@ static dbfft_status create_impl(dbfft_ctx* ctx, const dbfft_grid* grid, const db
     std::memset(&d, 0, sizeof(d));
     d.n1 = ctx->n1; d.n2 = ctx->n2; d.n3 = ctx->n3; d.h = ctx->h; d.m = ctx->m;
     d.H = ctx->H; d.V = ctx->V; d.plane = (long long)ctx->n2 * ctx->h;
+    d.div_plane = make_fastdiv((unsigned)d.plane);
+    d.div_h = make_fastdiv((unsigned)ctx->h);
     d.B = ctx->B; d.Rm = ctx->Rm; d.nc = ctx->nc; d.kin = ctx->kin;
     d.invN = 1.0 / (double)ctx->V;
     if (ctx->nc == 6) {
@@ -1590,7 +1595,7 @@ static dbfft_status create_impl(dbfft_ctx* ctx, const dbfft_grid* grid, const db
     CK(cudaMemsetAsync(ctx->macroW2, 0, ctx->B * 9 * sizeof(double), ctx->stream));
     // reduction partials: the largest grid of any reducing kernel
     {
-        const long long nb1 = pw_blocks(ctx->H);  // element-wise kernels of passes 1 and 5
+        const long long nb1 = pw_blocks(ctx->H, 1);  // element-wise kernels of passes 1 and 5
         const long long nb1d = nb1;
         const long long nlines = (long long)ctx->n1 * ctx->n2;
         const long long nb3 = nlines;  // pass 3 with one line per CTA (any tuned shape fits)

@@ -42,6 +42,35 @@ __host__ __device__ __forceinline__ const T (*pcoef(const PrecondData& pd))[6] {
 }
 
 // Everything a pass needs about the grid and the macro basis.
+// Division by a loop-invariant unsigned 32-bit divisor with one multiply-high
+// (Granlund & Montgomery, "Division by invariant integers using
+// multiplication", 1994, round-up variant): with l = ceil(log2 d) and
+// m = floor(2^32 (2^l - d) / d) + 1, q = (t + ((n - t) >> s1)) >> s2 for
+// t = mulhi(m, n), s1 = min(l, 1), s2 = max(l - 1, 0); exact for all n < 2^32.
+struct FastDiv {
+    unsigned d, m, s1, s2;
+};
+
+__host__ __device__ inline FastDiv make_fastdiv(unsigned d) {
+    unsigned l = 0;
+    while (l < 32 && (1ull << l) < d) ++l;
+    FastDiv f;
+    f.d = d;
+    f.m = (unsigned)(((1ull << 32) * ((1ull << l) - d)) / d + 1);
+    f.s1 = l < 1 ? l : 1;
+    f.s2 = l > 1 ? l - 1 : 0;
+    return f;
+}
+
+__host__ __device__ __forceinline__ unsigned fastdiv(unsigned n, const FastDiv& f) {
+#ifdef __CUDA_ARCH__
+    const unsigned t = __umulhi(f.m, n);
+#else
+    const unsigned t = (unsigned)(((unsigned long long)f.m * n) >> 32);
+#endif
+    return (t + ((n - t) >> f.s1)) >> f.s2;
+}
+
 struct Dims {
     int n1, n2, n3, h, m;   // h = n3/2 + 1, m = n3/2
     long long H;            // n1 n2 h
@@ -54,6 +83,7 @@ struct Dims {
     int ne;                 // number of active macro unknowns
     int active[9];          // active macro basis indices (Mandel or 3i+j)
     double invN;
+    FastDiv div_plane, div_h;  // half-spectrum index -> (k1, k2, k3); H < 2^32
 };
 
 template <typename T>

@@ -8,9 +8,23 @@ bool supported_len(int n) { return n == 8 || n == 16 || n == 32 || n == 64 || n 
 
 static int radix_for(int n, bool dbl) { return radix_ax2(n, dbl); }
 
-long long pw_blocks(long long H) {
-    const long long nb = (H + PW_THREADS - 1) / PW_THREADS;
-    return nb < 2048 ? nb : 2048;  // grid-stride loops beyond 2048 blocks per right-hand side
+long long pw_blocks(long long H, int B) {
+    // about two waves of blocks over the whole GPU, shared among the right-hand
+    // sides: the element-wise kernels end with a block reduction, whose cost
+    // is amortised over several frequencies per thread (grid-stride loops)
+    static int nsm = 0;
+    if (nsm == 0) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+            nsm < 1)
+            nsm = 152;
+    }
+    const long long target = 2LL * 5 * nsm;  // ~5 resident 256-thread blocks per SM
+    long long per = (target + (B > 0 ? B : 1) - 1) / (B > 0 ? B : 1);
+    const long long need = (H + PW_THREADS - 1) / PW_THREADS;
+    if (per > need) per = need;
+    if (per < 1) per = 1;
+    return per;
 }
 
 int ax2_tile(int n2, bool dbl) {

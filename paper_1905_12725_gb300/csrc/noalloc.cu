@@ -108,6 +108,8 @@ extern "C" dbfft_status dbfft_apply_iso_noalloc(const int n[3], const double L[3
     Dims d{};
     d.n1 = n1; d.n2 = n2; d.n3 = n3; d.h = h; d.m = m;
     d.H = H; d.V = (long long)n1 * n2 * n3; d.plane = (long long)n2 * h;
+    d.div_plane = make_fastdiv((unsigned)d.plane);
+    d.div_h = make_fastdiv((unsigned)h);
     d.B = batch; d.Rm = 1; d.nc = 6; d.kin = KIN_SMALL; d.ne = 0;
     d.invN = 1.0 / (double)d.V;
     const Freq<double> f{sym->xi, sym->xi + kMaxLen, sym->xi + 2 * kMaxLen};

@@ -34,6 +34,10 @@ __device__ __forceinline__ cplx<T> zero_c() { return mk<T>(T(0), T(0)); }
 __device__ __forceinline__ int hweight(int k3, int m) { return (k3 == 0 || k3 == m) ? 1 : 2; }
 
 // z = N Q(xi)^-1 r (zero on the null set), Q from the mean tangent.
+// 1/x: the correctly rounded FP32 reciprocal instruction, or an FP64 division.
+__device__ __forceinline__ float rcp_t(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ double rcp_t(double x) { return 1.0 / x; }
+
 template <typename T>
 __device__ __forceinline__ void precond_apply(const T (*coef)[6], T x1, T x2, T x3, T N,
                                               const cplx<T>* r, cplx<T>* z) {
@@ -42,7 +46,7 @@ __device__ __forceinline__ void precond_apply(const T (*coef)[6], T x1, T x2, T 
         z[0] = z[1] = z[2] = zero_c<T>();
         return;
     }
-    const T ik2 = T(1) / k2;
+    const T ik2 = rcp_t(k2);
     const T mono[6] = {x1 * x1 * ik2, x2 * x2 * ik2, x3 * x3 * ik2,
                        x2 * x3 * ik2, x1 * x3 * ik2, x1 * x2 * ik2};
     T q[6];
@@ -61,7 +65,7 @@ __device__ __forceinline__ void precond_apply(const T (*coef)[6], T x1, T x2, T 
     const T A02 = q[5] * q[3] - q[4] * q[1];
     const T A12 = q[5] * q[4] - q[0] * q[3];
     const T det = q[0] * A00 + q[5] * A01 + q[4] * A02;
-    const T s = N * ik2 / det;
+    const T s = N * ik2 * rcp_t(det);
     z[0] = s * (A00 * r[0] + (A01 * r[1] + A02 * r[2]));
     z[1] = s * (A01 * r[0] + (A11 * r[1] + A12 * r[2]));
     z[2] = s * (A02 * r[0] + (A12 * r[1] + A22 * r[2]));
@@ -171,11 +175,13 @@ struct FreqIdx {
 };
 __device__ __forceinline__ FreqIdx freq_idx(const Dims& d, long long i) {
     FreqIdx f;
-    const long long k1 = i / d.plane;
-    const long long rem = i - k1 * d.plane;
+    const unsigned u = (unsigned)i;  // i < H < 2^32
+    const unsigned k1 = fastdiv(u, d.div_plane);
+    const unsigned rem = u - k1 * d.div_plane.d;
+    const unsigned k2 = fastdiv(rem, d.div_h);
     f.k1 = (int)k1;
-    f.k2 = (int)(rem / d.h);
-    f.k3 = (int)(rem - (long long)f.k2 * d.h);
+    f.k2 = (int)k2;
+    f.k3 = (int)(rem - k2 * d.div_h.d);
     return f;
 }
 

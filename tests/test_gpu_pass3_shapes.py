@@ -30,7 +30,7 @@ CASES = [
     ((32, 8, 32), 2, 1, 1, 4, 2),
     ((16, 32, 128), 1, 1, 0, 16, 16),
     ((16, 8, 256), 2, 2, 0, 8, 4),
-    ((8, 8, 256), 1, 1, 1, 4, 8),
+    ((8, 8, 256), 1, 1, 1, 4, 4),
     ((32, 32, 8), 4, 2, 0, 8, 16),
 ]
 
