@@ -312,8 +312,15 @@ def case_c4(precision, n=256, n_inc=40, only=None):
     incs = []
     t_all = 0.0
     cg_all = 0
-    for k in range(n_inc if only is None else only):
+    n_run = n_inc if only is None else only
+    prof = None
+    for k in range(n_run):
+        if k == n_run - 1:
+            s.profile(True)  # the last increment launch by launch, with per-kernel CUDA events
         rep, dt = _timed(lambda: s.solve_increment(k))
+        if k == n_run - 1:
+            prof = s.profile_read()
+            s.profile(False)
         t_all += dt
         cg_all += rep["cg_iters"]
         sg = s.homogenized_stress()[0]
@@ -321,6 +328,8 @@ def case_c4(precision, n=256, n_inc=40, only=None):
                      "sigma_xx": sg[0, 0], "ms": dt * 1e3})
     return {"case": f"c4 {n}^3 polycrystal 500 grains", "precision": "mixed" if precision else "fp64",
             "generate_s": t_gen, "wall_s": t_all, "cg_iters": cg_all,
+            "last_increment_kernels (launch by launch)": {
+                k: {"launches": v["launches"], "ms": v["ms"]} for k, v in sorted(prof.items(), key=lambda kv: -kv[1]["ms"])},
             "voxel_cg_iters_per_s": n ** 3 * cg_all / t_all, "increments": incs,
             "phase_sha256": synth.sha256(c["phase"])}
 

@@ -553,7 +553,8 @@ int opk_apply(const dbfft_ctx* ctx) {
     return ctx->model == DBFFT_ISO_ELASTIC ? OP_ISO : (ctx->model == DBFFT_NEO_HOOKE ? OP_NH_APPLY : OP_CP_APPLY);
 }
 int opk_update(const dbfft_ctx* ctx) {
-    return ctx->model == DBFFT_ISO_ELASTIC ? OP_ISO : (ctx->model == DBFFT_NEO_HOOKE ? OP_NH_UPDATE : OP_CP_UPDATE);
+    if (ctx->model == DBFFT_CP_FCC_POWERLAW) return ctx->prec == DBFFT_MIXED ? OP_CP_UPDATE32 : OP_CP_UPDATE;
+    return ctx->model == DBFFT_ISO_ELASTIC ? OP_ISO : OP_NH_UPDATE;
 }
 
 template <typename T>
@@ -916,9 +917,11 @@ dbfft_status inner_cg(dbfft_ctx* ctx, double tol, long long& it_sum, int& it_max
     return DBFFT_OK;
 }
 
+constexpr int kMeanTangentBlocks = 456;  // blocks per right-hand side of the mean-tangent reduction
+
 // Mean tangent of the current state -> preconditioner (R10), nonlinear only.
 dbfft_status refresh_precond(dbfft_ctx* ctx) {
-    const int nblk = 64;
+    const int nblk = kMeanTangentBlocks;
     const int kind = ctx->model == DBFFT_NEO_HOOKE ? 0 : 1;
     TRY(run(ctx, "mean_tangent", 0.0, [&] {
         if (ctx->prec == DBFFT_MIXED)
@@ -1603,7 +1606,7 @@ static dbfft_status create_impl(dbfft_ctx* ctx, const dbfft_grid* grid, const db
         const long long nbi = (ctx->H + 255) / 256;
         long long nb = std::max(std::max(nb1, nb1d), std::max(std::max(nb3, nb3d), nbi));
         ctx->nblk_max = (int)nb;
-        ctx->partials_n = std::max((size_t)ctx->B * (size_t)nb * 2, (size_t)ctx->B * 64 * 81);
+        ctx->partials_n = std::max((size_t)ctx->B * (size_t)nb * 2, (size_t)ctx->B * kMeanTangentBlocks * 81);
         TRY(dalloc_t(ctx, ctx->partials_n, &ctx->partials));
         if (cudaMallocHost(&ctx->part_h, ctx->partials_n * sizeof(double)) != cudaSuccess)
             return fail(ctx, DBFFT_E_NOMEM, "pinned host allocation failed");

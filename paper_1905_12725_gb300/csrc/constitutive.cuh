@@ -339,14 +339,42 @@ __device__ __forceinline__ int cp_newton(const typename CpGrainOf<R>::type& G, c
     return 0;
 }
 
+// Simplified Newton in FP64 with a fixed FP32 factorisation (L, Di): the
+// residual is evaluated in FP64, the step solved in FP32. Stops, like
+// cp_newton, once the step is below rtol (|s| + tau_c). Returns 1 when
+// converged, 0 otherwise (then s is left where the iteration stopped).
+__device__ __forceinline__ int cp_refine64(const CpGrain& G, const CpParams& cp, const double (&tg)[6], double (&s)[6],
+                                           const float (&L)[15], const float (&Di)[6], double rtol, int max_it) {
+    for (int it = 0; it < max_it; ++it) {
+        double Rv[6], J[21], unused;
+        cp_eval<double, false, false>(G, cp, s, tg, Rv, J, unused);
+        float mR[6], st[6];
+#pragma unroll
+        for (int i = 0; i < 6; ++i) mR[i] = (float)(-Rv[i]);
+        ldl6_solve<float>(L, Di, mR, st);
+        double ns = 0.0, sn = 0.0;
+#pragma unroll
+        for (int i = 0; i < 6; ++i) {
+            ns += (double)st[i] * (double)st[i];
+            sn += s[i] * s[i];
+        }
+        if (!(ns <= 1e300)) return 0;
+#pragma unroll
+        for (int i = 0; i < 6; ++i) s[i] += (double)st[i];
+        if (ns <= rtol * rtol * (sqrt(sn) + cp.d.tau_c) * (sqrt(sn) + cp.d.tau_c)) return 1;
+    }
+    return 0;
+}
+
 // Backward-Euler update of one voxel. eps_w: total strain in W components
 // (11,22,33,23,13,12); ep_old, s_guess, s_out, ep_new: Mandel 6-vectors;
 // tan: 21-entry Mandel tangent (J^-1 at the solution) in precision TT.
 // With TT = float (the FP32 inner-CG mode) Newton first runs in FP32 from
-// s_guess and FP64 Newton finishes from there, so the FP64 iterations are
-// the last two or three of the quadratic phase; the stored FP32 tangent is
-// built in FP32. With TT = double everything runs in FP64. Both stop on the
-// same FP64 criterion, so both return the same stress to that tolerance.
+// s_guess; FP64 then finishes with simplified Newton steps (FP64 residual,
+// FP32 Jacobian factors), falling back to FP64 Newton if those do not
+// settle; the stored FP32 tangent is built in FP32. With TT = double
+// everything runs in FP64 Newton. Both stop when the FP64 step is below the
+// same tolerance, so both return the same stress to that tolerance.
 // Returns false when the local Newton fails (outputs stay finite).
 template <typename TT>
 __device__ __forceinline__ bool cp_update(const CpGrain& G, const CpGrainF& Gf, const CpParams& cp,
@@ -360,6 +388,7 @@ __device__ __forceinline__ bool cp_update(const CpGrain& G, const CpGrainF& Gf, 
         tg[i] = em[i] - ep_old[i];
         s[i] = s_guess[i];
     }
+    int r = 0;
     if constexpr (sizeof(TT) == 4) {
         float tgf[6], sf[6];
 #pragma unroll
@@ -367,12 +396,24 @@ __device__ __forceinline__ bool cp_update(const CpGrain& G, const CpGrainF& Gf, 
             tgf[i] = (float)tg[i];
             sf[i] = (float)s[i];
         }
-        if (cp_newton<float>(Gf, cp, tgf, sf, 1e-5f, 1e-6f, 40) >= 0) {
+        if (cp_newton<float>(Gf, cp, tgf, sf, 3e-6f, 1e-6f, 40) >= 0) {
+            // FP64 finish with the FP32 Jacobian at the FP32 solution: each step
+            // takes the FP64 residual and an FP32 solve, and the iteration
+            // contracts by about cond(J) times the Jacobian's relative error
+            float Rf[6], Jf[21], Lf[15], Dif[6], unused;
+            cp_eval<float, true, false>(Gf, cp, sf, tgf, Rf, Jf, unused);
+            if (ldl6<float>(Jf, Lf, Dif)) {
 #pragma unroll
-            for (int i = 0; i < 6; ++i) s[i] = sf[i];
+                for (int i = 0; i < 6; ++i) s[i] = sf[i];
+                r = cp_refine64(G, cp, tg, s, Lf, Dif, cp.rtol, 8);
+            }
+            if (r != 1) {  // the simplified iteration did not settle: plain FP64 Newton from the FP32 point
+#pragma unroll
+                for (int i = 0; i < 6; ++i) s[i] = sf[i];
+            }
         }
     }
-    const int r = cp_newton<double>(G, cp, tg, s, cp.rtol, 1e-13, cp.max_it);
+    if (r != 1) r = cp_newton<double>(G, cp, tg, s, cp.rtol, 1e-13, cp.max_it);
     bool ok = r == 1;
     // plastic strain from the converged residual: eps_p = eps - S s
 #pragma unroll

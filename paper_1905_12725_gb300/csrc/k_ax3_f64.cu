@@ -9,6 +9,7 @@ cudaError_t launch_ax3<double>(int opk, const Ax3Args<double>& a, cudaStream_t s
         case OP_CP_APPLY: return ax3_sz<double, 6, OP_CP_APPLY>(a, s);
         case OP_NH_UPDATE: return ax3_sz<double, 9, OP_NH_UPDATE>(a, s);
         case OP_CP_UPDATE: return ax3_sz<double, 6, OP_CP_UPDATE>(a, s);
+        case OP_CP_UPDATE32: return ax3_sz<double, 6, OP_CP_UPDATE32>(a, s);
         case OP_ADJ: return ax3_sz<double, 6, OP_ADJ>(a, s);
         default: return cudaErrorInvalidValue;
     }

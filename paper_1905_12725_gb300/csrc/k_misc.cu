@@ -139,10 +139,10 @@ __global__ void k_mean_tangent(int kind, long long V, const TT* tan, const uint1
     const int b = blockIdx.y;
     for (int q = threadIdx.x; q < 81; q += blockDim.x) acc[q] = 0.0;
     __syncthreads();
-    double loc[81];
-    for (int q = 0; q < 81; ++q) loc[q] = 0.0;
-    for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < V; v += (long long)gridDim.x * blockDim.x) {
-        if (kind == 0) {
+    if (kind == 0) {
+        double loc[81];
+        for (int q = 0; q < 81; ++q) loc[q] = 0.0;
+        for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < V; v += (long long)gridDim.x * blockDim.x) {
             const TT* t = tan + ((long long)b * V + v) * 10;
             const int ph = phase[(long long)b * V + v];
             double A[9];
@@ -157,24 +157,46 @@ __global__ void k_mean_tangent(int kind, long long V, const TT* tan, const uint1
                             if (i == k && J == L) val += mu[ph];
                             loc[((i * 3 + J) * 3 + k) * 3 + L] += val;
                         }
-        } else {
+        }
+        for (int q = 0; q < 81; ++q) atomicAdd(&acc[q], loc[q]);
+        __syncthreads();
+    } else {
+        // the mean is linear in the 21 Mandel entries: sum them (in TT per
+        // thread, FP64 across threads), then expand the block's sums to the
+        // fourth-order tensor once
+        __shared__ double m21[21];
+        for (int q = threadIdx.x; q < 21; q += blockDim.x) m21[q] = 0.0;
+        __syncthreads();
+        TT loc[21];
+#pragma unroll
+        for (int q = 0; q < 21; ++q) loc[q] = TT(0);
+        for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < V; v += (long long)gridDim.x * blockDim.x) {
             const TT* t = tan + ((long long)b * V + v) * 21;
-            // Mandel -> tensor: K_ijkl = sum_mn Psi_m,ij Cm_mn Psi_n,kl
+#pragma unroll
+            for (int q = 0; q < 21; ++q) loc[q] += t[q];
+        }
+#pragma unroll
+        for (int q = 0; q < 21; ++q) {
+            double x = (double)loc[q];
+            for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+            if ((threadIdx.x & 31) == 0) atomicAdd(&m21[q], x);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {  // Mandel -> tensor: K_ijkl = sum_mn Psi_m,ij Cm_mn Psi_n,kl
             const int pi[6] = {0, 1, 2, 1, 0, 0}, pj[6] = {0, 1, 2, 2, 2, 1};
             for (int m = 0; m < 6; ++m)
                 for (int n = 0; n < 6; ++n) {
-                    const double c = (double)t[sym6(m, n)] * (m >= 3 ? 0.70710678118654752440 : 1.0) *
+                    const double c = m21[sym6(m, n)] * (m >= 3 ? 0.70710678118654752440 : 1.0) *
                                      (n >= 3 ? 0.70710678118654752440 : 1.0);
                     const int ii[2] = {pi[m], pj[m]}, jj[2] = {pj[m], pi[m]};
                     const int kk[2] = {pi[n], pj[n]}, ll[2] = {pj[n], pi[n]};
                     for (int s1 = 0; s1 < (m >= 3 ? 2 : 1); ++s1)
                         for (int s2 = 0; s2 < (n >= 3 ? 2 : 1); ++s2)
-                            loc[((ii[s1] * 3 + jj[s1]) * 3 + kk[s2]) * 3 + ll[s2]] += c;
+                            acc[((ii[s1] * 3 + jj[s1]) * 3 + kk[s2]) * 3 + ll[s2]] += c;
                 }
         }
+        __syncthreads();
     }
-    for (int q = 0; q < 81; ++q) atomicAdd(&acc[q], loc[q]);
-    __syncthreads();
     for (int q = threadIdx.x; q < 81; q += blockDim.x)
         partials[((long long)b * gridDim.x + blockIdx.x) * 81 + q] = acc[q];
 }
@@ -182,7 +204,7 @@ __global__ void k_mean_tangent(int kind, long long V, const TT* tan, const uint1
 template <typename TT>
 cudaError_t launch_mean_tangent(int kind, int B, long long V, const TT* tan, const uint16_t* phase, const double* lam,
                                 const double* mu, double* partials, int nblk, cudaStream_t s) {
-    k_mean_tangent<TT><<<dim3(nblk, B), 128, 0, s>>>(kind, V, tan, phase, lam, mu, partials);
+    k_mean_tangent<TT><<<dim3(nblk, B), 256, 0, s>>>(kind, V, tan, phase, lam, mu, partials);
     return cudaGetLastError();
 }
 template cudaError_t launch_mean_tangent<float>(int, int, long long, const float*, const uint16_t*, const double*,

@@ -22,7 +22,8 @@ enum {
     OP_NH_UPDATE = 2,  // P(F), F = macro (incl. I) + G; stores tangent data
     OP_CP_APPLY = 3,   // sigma = C_tan (eps + macro), stored 21-entry Mandel tangent
     OP_CP_UPDATE = 4,  // backward-Euler crystal plasticity at eps = macro + eps~
-    OP_ADJ = 5         // dJ/dE(x) = (1/N) eps_adj : C1 : eps_fwd (no forward R2C)
+    OP_ADJ = 5,        // dJ/dE(x) = (1/N) eps_adj : C1 : eps_fwd (no forward R2C)
+    OP_CP_UPDATE32 = 6 // OP_CP_UPDATE for an FP32 inner solve: FP32 Newton start, FP32 tangent
 };
 
 template <typename T>
@@ -86,7 +87,8 @@ __host__ __device__ constexpr int ax3_slot_cplx() {
 // loads and stores are done cooperatively: for one (right-hand side,
 // component) the L lines of a CTA are L h contiguous complex values.
 template <typename T, int N3, int NC, int OPK, int RW>
-__global__ void __launch_bounds__(256, (sizeof(T) == 4 ? (RW == 16 ? 3 : 4) : ((OPK == OP_CP_UPDATE || OPK == OP_NH_UPDATE) ? 1 : 2))) k_axis3(Ax3Args<T> a) {
+__global__ void __launch_bounds__(256, (sizeof(T) == 4 ? (RW == 16 ? 3 : 4) : ((OPK == OP_CP_UPDATE || OPK == OP_CP_UPDATE32 || OPK == OP_NH_UPDATE) ? 1 : 2))) k_axis3(Ax3Args<T> a) {
+    constexpr bool CPU_ = OPK == OP_CP_UPDATE || OPK == OP_CP_UPDATE32;  // crystal-plasticity update
     constexpr int M = N3 / 2;
     constexpr int H = M + 1;
     constexpr int R = RadixAx3<T, M, RW>::value;
@@ -114,6 +116,11 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? (RW == 16 ? 3 : 4) : ((
     // slot s = (ll * RB + rl) * NC + c ; field f at offset f * NSLOT
     auto slot_ptr = [&](int f, int sl) { return sbuf + ((long long)f * NSLOT + sl) * SB; };
     auto rhs_done = [&](int rl) { return a.cg != nullptr && a.cg[g * RB + rl].done != 0; };
+    if (a.cg != nullptr) {  // every right-hand side of this group has stopped: nothing to do
+        bool all = true;
+        for (int rl = 0; rl < RB; ++rl) all = all && rhs_done(rl);
+        if (all) return;
+    }
 
     // ---- cooperative load of the half-spectrum lines: for each (rhs, comp)
     // the lines of this CTA are lines_here * H contiguous complex values
@@ -271,7 +278,7 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? (RW == 16 ? 3 : 4) : ((
 #pragma unroll
                 for (int q = 0; q < 6; ++q) f[q * SB] = sg[q];
             }
-        } else if constexpr (OPK == OP_CP_UPDATE) {
+        } else if constexpr (CPU_) {
             const long long mv = (long long)mat * d.V + vox;
             const int gr = a.phase[mv];
             for (int rr = 0; rr < RB; ++rr) {
@@ -286,7 +293,7 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? (RW == 16 ? 3 : 4) : ((
                 for (int q = 0; q < 6; ++q) guess[q] = (a.guess_trial ? a.sig_t : a.sig_prev)[so + q];
                 const long long to = ((long long)bb * d.V + vox) * 21;
                 bool ok;
-                if (a.tan_out_f) {
+                if constexpr (OPK == OP_CP_UPDATE32) {
                     float tn[21];
                     ok = cp_update<float>(a.grains[gr], a.grains_f[gr], a.cp, e, a.eps_p + so, guess, sg, tn, ep);
 #pragma unroll

@@ -122,6 +122,7 @@ __global__ void __launch_bounds__(256) k_axis3_pipe(Ax3Args<T> a) {
     if (a.cg != nullptr)
         for (int rl = 0; rl < RB; ++rl) done_mask |= (a.cg[g * RB + rl].done != 0 ? 1u : 0u) << rl;
     auto rhs_done = [&](int rl) { return (done_mask >> rl) & 1u; };
+    if (a.cg != nullptr && done_mask == (RB >= 32 ? ~0u : ((1u << RB) - 1u))) return;  // the whole group has stopped
 
     __shared__ double s_eacc[8];  // <p, K p> of this CTA per right-hand side (tile shares formed in T)
     if (t < 8) s_eacc[t] = 0.0;
