@@ -304,7 +304,8 @@ const char* dbfft_tuning(const dbfft_ctx* ctx);
  * autotuner's choice. fp64: 0 for the FP32 applications, 1 for FP64.
  * pipelined: 0 = one CTA per group of grid lines, loads staged by cp.async;
  * 1 = persistent CTAs looping over tiles of `lines` grid lines with two
- * shared-memory stages filled and drained by bulk copies. radix: 8 or 16
+ * shared-memory stages filled and drained by bulk copies; 2 = the same with
+ * one stage (half the shared memory per CTA). radix: 8 or 16
  * (FP32) / 4 (FP64); lines: grid lines per CTA (per tile when pipelined;
  * then even and dividing n1 * n2). Returns DBFFT_E_ARG for a shape that does
  * not exist or does not fit in shared memory; the results of the operator do

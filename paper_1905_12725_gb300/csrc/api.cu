@@ -604,7 +604,7 @@ template <typename T>
 void apply_shape(const dbfft_ctx* ctx, Ax3Args<T>& a) {
     const int pi_ = sizeof(T) == 8 ? 1 : 0;
     if (ctx->pipe_on[pi_]) {
-        a.pipe = 1;
+        a.pipe = ctx->pipe_on[pi_];
         a.radix = ctx->pipe_R[pi_];
         a.L = ctx->pipe_L[pi_];
     }
@@ -1130,15 +1130,16 @@ void tune_precision(dbfft_ctx* ctx, int pi_) {
     {
         const long long nlines = (long long)ctx->n1 * ctx->n2;
         float bp = 1e30f;
-        int bpR = 0, bpL = 0;
+        int bpR = 0, bpL = 0, bpS = 0;
+        for (int ps : {1, 2})
         for (int ri = 0; ri < (sizeof(T) == 4 ? 2 : 1); ++ri) {
             const int R = sizeof(T) == 4 ? radices[ri] : 4;
             for (int L : {2, 4, 6, 8, 12, 16, 24, 32}) {
                 const long long sm = ax3_pipe_smem(ctx->n3, ctx->nc, ctx->RB, sizeof(T) == 8, ctx->scale != nullptr, R,
-                                                   L, nlines);
+                                                   L, nlines, ps);
                 if (sm < 0 || sm > 200 * 1024) continue;
                 Ax3Args<T> a3 = ax3_base<T>(ctx, W);
-                a3.pipe = 1;
+                a3.pipe = ps;
                 a3.radix = R;
                 a3.L = L;
                 if constexpr (sizeof(T) == 4) a3.macroW = ctx->macroWf;
@@ -1149,14 +1150,15 @@ void tune_precision(dbfft_ctx* ctx, int pi_) {
                     bp = ms;
                     bpR = R;
                     bpL = L;
+                    bpS = ps;
                 }
             }
         }
-        ctx->pipe_on[pi_] = (bpL > 0 && bp < best) ? 1 : 0;
+        ctx->pipe_on[pi_] = (bpL > 0 && bp < best) ? bpS : 0;
         ctx->pipe_R[pi_] = bpR;
         ctx->pipe_L[pi_] = bpL;
-        std::snprintf(buf, sizeof(buf), "pass3 pipelined radix %d lines %d (%.4f ms)%s; ", bpR, bpL, bp,
-                      ctx->pipe_on[pi_] ? " used" : "");
+        std::snprintf(buf, sizeof(buf), "pass3 bulk-copy %s radix %d lines %d (%.4f ms)%s; ",
+                      bpS == 2 ? "one-stage" : "two-stage", bpR, bpL, bp, ctx->pipe_on[pi_] ? " used" : "");
         ctx->tune_note += buf;
     }
     // strided transforms: columns per CTA along axes 1 and 2
@@ -1276,10 +1278,11 @@ dbfft_status dbfft_set_pass3_shape(dbfft_ctx* ctx, int fp64, int pipelined, int 
     if (lines > nlines) return fail(ctx, DBFFT_E_ARG, "more lines per CTA than grid lines");
     const int pi_ = dbl ? 1 : 0;
     if (pipelined) {
-        const long long sm = ax3_pipe_smem(ctx->n3, ctx->nc, ctx->RB, dbl, ctx->scale != nullptr, radix, lines, nlines);
+        const long long sm =
+            ax3_pipe_smem(ctx->n3, ctx->nc, ctx->RB, dbl, ctx->scale != nullptr, radix, lines, nlines, pipelined);
         if (sm < 0 || sm > 200 * 1024)
             return fail(ctx, DBFFT_E_ARG, "pipelined pass 3: lines must be even, divide n1*n2 and fit in shared memory");
-        ctx->pipe_on[pi_] = 1;
+        ctx->pipe_on[pi_] = pipelined;
         ctx->pipe_R[pi_] = radix;
         ctx->pipe_L[pi_] = lines;
     } else {

@@ -83,29 +83,30 @@ namespace dbfft {
 
 namespace {
 template <typename T, int N3>
-long long pipe_smem_t(int nc, int rb, bool scale, int radix, int L) {
+long long pipe_smem_t(int nc, int rb, bool scale, int radix, int L, int nstage) {
     constexpr int M = N3 / 2;
     const int R = radix_ax3(M, sizeof(T) == 8, radix);
     const int P = M / R;
-    return PipePlan<T, N3>::total_bytes(L, rb, nc, scale, P, 256 / 32);
+    return PipePlan<T, N3>::total_bytes(L, rb, nc, scale, P, 256 / 32, nstage);
 }
 template <typename T>
-long long pipe_smem_n(int n3, int nc, int rb, bool scale, int radix, int L) {
+long long pipe_smem_n(int n3, int nc, int rb, bool scale, int radix, int L, int ns) {
     switch (n3) {
-        case 8: return pipe_smem_t<T, 8>(nc, rb, scale, radix, L);
-        case 16: return pipe_smem_t<T, 16>(nc, rb, scale, radix, L);
-        case 32: return pipe_smem_t<T, 32>(nc, rb, scale, radix, L);
-        case 64: return pipe_smem_t<T, 64>(nc, rb, scale, radix, L);
-        case 128: return pipe_smem_t<T, 128>(nc, rb, scale, radix, L);
-        case 256: return pipe_smem_t<T, 256>(nc, rb, scale, radix, L);
+        case 8: return pipe_smem_t<T, 8>(nc, rb, scale, radix, L, ns);
+        case 16: return pipe_smem_t<T, 16>(nc, rb, scale, radix, L, ns);
+        case 32: return pipe_smem_t<T, 32>(nc, rb, scale, radix, L, ns);
+        case 64: return pipe_smem_t<T, 64>(nc, rb, scale, radix, L, ns);
+        case 128: return pipe_smem_t<T, 128>(nc, rb, scale, radix, L, ns);
+        case 256: return pipe_smem_t<T, 256>(nc, rb, scale, radix, L, ns);
         default: return -1;
     }
 }
 }  // namespace
 
-long long ax3_pipe_smem(int n3, int nc, int rb, bool dbl, bool scale, int radix, int L, long long nlines) {
-    if (L < 2 || (L & 1) || nlines % L != 0 || rb < 1 || rb > 8) return -1;
-    return dbl ? pipe_smem_n<double>(n3, nc, rb, scale, radix, L) : pipe_smem_n<float>(n3, nc, rb, scale, radix, L);
+long long ax3_pipe_smem(int n3, int nc, int rb, bool dbl, bool scale, int radix, int L, long long nlines, int pipe) {
+    if (L < 2 || (L & 1) || nlines % L != 0 || rb < 1 || rb > 8 || (pipe != 1 && pipe != 2)) return -1;
+    const int ns = pipe == 2 ? 1 : 2;
+    return dbl ? pipe_smem_n<double>(n3, nc, rb, scale, radix, L, ns) : pipe_smem_n<float>(n3, nc, rb, scale, radix, L, ns);
 }
 
 }  // namespace dbfft

@@ -5,8 +5,8 @@
 
 namespace dbfft {
 
-template <typename T, int N3, int NC, int OPK, int RW>
-static cudaError_t pipe_nr(const Ax3Args<T>& a, cudaStream_t s) {
+template <typename T, int N3, int NC, int OPK, int RW, int NS>
+static cudaError_t pipe_nrs(const Ax3Args<T>& a, cudaStream_t s) {
     using Plan = PipePlan<T, N3>;
     constexpr int M = N3 / 2;
     constexpr int R = RadixAx3<T, M, RW>::value;
@@ -15,8 +15,8 @@ static cudaError_t pipe_nr(const Ax3Args<T>& a, cudaStream_t s) {
     const long long nlines = (long long)a.d.n1 * a.d.n2;
     if (a.L < 2 || (a.L & 1) || nlines % a.L != 0 || a.RB < 1 || a.RB > 8 || a.d.B % a.RB != 0)
         return cudaErrorInvalidConfiguration;
-    const long long smem = Plan::total_bytes(a.L, a.RB, NC, a.scale != nullptr, P, threads / 32);
-    auto kern = k_axis3_pipe<T, N3, NC, OPK, RW>;
+    const long long smem = Plan::total_bytes(a.L, a.RB, NC, a.scale != nullptr, P, threads / 32, NS);
+    auto kern = k_axis3_pipe<T, N3, NC, OPK, RW, NS>;
     static int max_dyn = -1;
     if (max_dyn < 0) {  // opt in to large dynamic shared memory: 227 KB per block minus the static part
         cudaFuncAttributes fa;
@@ -48,6 +48,13 @@ static cudaError_t pipe_nr(const Ax3Args<T>& a, cudaStream_t s) {
     if (per_group < 1) per_group = 1;
     kern<<<dim3((unsigned)per_group, (unsigned)ngroups), threads, (size_t)smem, s>>>(a);
     return cudaGetLastError();
+}
+
+// a.pipe: 1 = two shared-memory stages, 2 = one stage
+template <typename T, int N3, int NC, int OPK, int RW>
+static cudaError_t pipe_nr(const Ax3Args<T>& a, cudaStream_t s) {
+    if (a.pipe == 2) return pipe_nrs<T, N3, NC, OPK, RW, 1>(a, s);
+    return pipe_nrs<T, N3, NC, OPK, RW, 2>(a, s);
 }
 
 template <typename T, int N3, int NC, int OPK>

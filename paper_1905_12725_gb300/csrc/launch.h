@@ -21,7 +21,7 @@ template <typename T> cudaError_t launch_fft_ax2(int dir, const Ax2Args<T>& a, c
 template <typename T> cudaError_t launch_ax3(int opk, const Ax3Args<T>& a, cudaStream_t s);
 // the pipelined pass 3 of the CG applications (OP_ISO, OP_NH_APPLY, OP_CP_APPLY)
 template <typename T> cudaError_t launch_ax3_pipe(int opk, const Ax3Args<T>& a, cudaStream_t s);
-// shared memory of one pipelined CTA, or -1 when (n3, L) is not a valid tile
-long long ax3_pipe_smem(int n3, int nc, int rb, bool dbl, bool scale, int radix, int L, long long nlines);
+// shared memory of one pipelined CTA (pipe 1: two stages, 2: one stage), or -1 when (n3, L) is not a valid tile
+long long ax3_pipe_smem(int n3, int nc, int rb, bool dbl, bool scale, int radix, int L, long long nlines, int pipe);
 
 }  // namespace dbfft

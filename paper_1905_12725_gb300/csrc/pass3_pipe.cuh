@@ -86,12 +86,16 @@ struct PipePlan {
     __host__ __device__ static constexpr long long scratch_bytes(int P, int nwarps) {
         return (long long)nwarps * (32 / P) * padded_len<T>(M) * (long long)sizeof(cplx<T>);
     }
-    __host__ __device__ static constexpr long long total_bytes(int L, int RB, int NC, bool sc, int P, int nwarps) {
-        return 2 * stage_bytes(L, RB, NC, sc) + scratch_bytes(P, nwarps) + 16;  // + 2 mbarriers
+    __host__ __device__ static constexpr long long total_bytes(int L, int RB, int NC, bool sc, int P, int nwarps,
+                                                               int nstage) {
+        return nstage * stage_bytes(L, RB, NC, sc) + scratch_bytes(P, nwarps) + 16;  // + 2 mbarriers
     }
 };
 
-template <typename T, int N3, int NC, int OPK, int RW>
+// NS = 2: two stages, the loads of the next tile overlap this tile's work;
+// NS = 1: one stage (half the shared memory, so more CTAs per SM overlap
+// each other instead).
+template <typename T, int N3, int NC, int OPK, int RW, int NS>
 __global__ void __launch_bounds__(256) k_axis3_pipe(Ax3Args<T> a) {
     static_assert(OpInfo<OPK>::apply, "the pipelined pass serves the CG applications");
     constexpr int M = N3 / 2;
@@ -114,8 +118,8 @@ __global__ void __launch_bounds__(256) k_axis3_pipe(Ax3Args<T> a) {
     const long long ntiles = nlines / L;
     const bool has_scale = a.scale != nullptr;
     const long long sbytes = Plan::stage_bytes(L, RB, NC, has_scale);
-    cplx<T>* scratch = reinterpret_cast<cplx<T>*>(smpipe + 2 * sbytes) + (long long)warp * LPW * padded_len<T>(M);
-    uint64_t* bars = reinterpret_cast<uint64_t*>(smpipe + 2 * sbytes + Plan::scratch_bytes(P, nthr / 32));
+    cplx<T>* scratch = reinterpret_cast<cplx<T>*>(smpipe + NS * sbytes) + (long long)warp * LPW * padded_len<T>(M);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smpipe + NS * sbytes + Plan::scratch_bytes(P, nthr / 32));
     const int mat = (g * RB) / d.Rm;
     // right-hand sides of this group that have stopped (the flags do not change while the pass runs)
     unsigned done_mask = 0;
@@ -159,18 +163,23 @@ __global__ void __launch_bounds__(256) k_axis3_pipe(Ax3Args<T> a) {
 
 
     long long tile = blockIdx.x;
-    if (t == 0 && tile < ntiles) issue_loads(tile, 0);
+    if (NS == 2 && t == 0 && tile < ntiles) issue_loads(tile, 0);
     const int nslot = L * RB * NC;  // (line, rhs, component) lines of a tile
     const int rounds = (nslot + LPW * (nthr / 32) - 1) / (LPW * (nthr / 32));
     int ab_it = -1;  // iteration at which a wait gave up (then the pass stops early)
     for (int it = 0; tile < ntiles; ++it, tile += gridDim.x) {
-        const int s = it & 1;
+        const int s = NS == 2 ? (it & 1) : 0;
         const long long next = tile + gridDim.x;
-        if (t == 0 && next < ntiles) {
-            bulk_wait_read_all();  // the stores of the other stage have left shared memory
-            issue_loads(next, s ^ 1);
+        if (t == 0) {
+            if (NS == 2 && next < ntiles) {
+                bulk_wait_read_all();  // the stores of the other stage have left shared memory
+                issue_loads(next, s ^ 1);
+            } else if (NS == 1) {
+                bulk_wait_read_all();  // the previous tile's stores have left the stage
+                issue_loads(tile, 0);
+            }
         }
-        if (!mbar_wait_bounded(&bars[s], (uint32_t)((it >> 1) & 1))) {
+        if (!mbar_wait_bounded(&bars[s], (uint32_t)(NS == 2 ? ((it >> 1) & 1) : (it & 1)))) {
             if (a.err) atomicOr(a.err, 2u);
             abort_flag = 1;
         }
@@ -296,9 +305,13 @@ __global__ void __launch_bounds__(256) k_axis3_pipe(Ax3Args<T> a) {
     }
     if (t == 0) {
         if (ab_it >= 0) {  // give the loads still in flight a bounded time to land before the CTA exits
-            mbar_wait_bounded(&bars[ab_it & 1], (uint32_t)((ab_it >> 1) & 1));
-            if (blockIdx.x + (long long)(ab_it + 1) * gridDim.x < ntiles)
-                mbar_wait_bounded(&bars[(ab_it + 1) & 1], (uint32_t)(((ab_it + 1) >> 1) & 1));
+            if (NS == 1) {
+                mbar_wait_bounded(&bars[0], (uint32_t)(ab_it & 1));
+            } else {
+                mbar_wait_bounded(&bars[ab_it & 1], (uint32_t)((ab_it >> 1) & 1));
+                if (blockIdx.x + (long long)(ab_it + 1) * gridDim.x < ntiles)
+                    mbar_wait_bounded(&bars[(ab_it + 1) & 1], (uint32_t)(((ab_it + 1) >> 1) & 1));
+            }
         }
         bulk_wait_all();
     }

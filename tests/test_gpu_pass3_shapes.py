@@ -45,16 +45,17 @@ def test_pipelined_pass3_matches_oracle(shape, B, nmat, fp64, radix, lines, scal
     scale = 0.5 + g.random((nmat,) + shape) if scaled else None
     s = dbfft.Solver(shape, phase, dbfft.iso_phases(E, nu), np.zeros((B, 3, 3)), batch=B, E_scale=scale,
                      precision=dbfft.DBFFT_FP64 if fp64 else dbfft.DBFFT_MIXED)
-    s.set_pass3_shape(fp64, 1, radix, lines)
     u = synth.random_spectrum(shape, 3, 500 + lines, batch=B)
-    out, _ = s.apply(torch.from_numpy(u).cuda(), fp32=not fp64)
-    out = out.cpu().numpy()
     prob = o.Problem(shape)
     Rm = B // nmat
-    for b in range(B):
-        m = b // Rm
-        ref, _ = prob.apply_K(iso_tangent(phase[m], E, nu, None if scale is None else scale[m]), u[b], np.zeros(0))
-        assert rel_err(out[b], ref) < (1e-12 if fp64 else 2e-5), b
+    refs = [prob.apply_K(iso_tangent(phase[b // Rm], E, nu, None if scale is None else scale[b // Rm]), u[b],
+                         np.zeros(0))[0] for b in range(B)]
+    for pipelined in (1, 2):  # two shared-memory stages, one stage
+        s.set_pass3_shape(fp64, pipelined, radix, lines)
+        out, _ = s.apply(torch.from_numpy(u).cuda(), fp32=not fp64)
+        out = out.cpu().numpy()
+        for b in range(B):
+            assert rel_err(out[b], refs[b]) < (1e-12 if fp64 else 2e-5), (pipelined, b)
     s.close()
 
 
@@ -62,7 +63,7 @@ def test_invalid_pipelined_shapes_are_refused():
     dbfft = _dbfft()
     shape = (8, 8, 16)
     s = dbfft.Solver(shape, np.zeros(shape, np.uint16), dbfft.iso_phases([1.0], [0.3]), np.zeros((1, 3, 3)))
-    for args in [(0, 1, 8, 3), (0, 1, 8, 5), (0, 1, 32, 4), (1, 1, 8, 4), (0, 1, 8, 128), (1, 0, 4, 0)]:
+    for args in [(0, 1, 8, 3), (0, 1, 8, 5), (0, 1, 32, 4), (1, 1, 8, 4), (0, 1, 8, 128), (1, 0, 4, 0), (0, 3, 8, 4)]:
         with pytest.raises(dbfft.DbfftError):
             s.set_pass3_shape(*args)
     s.set_pass3_shape(0, 1, 8, 4)
@@ -83,7 +84,7 @@ def test_pcg_with_pipelined_pass3_equals_plain(precision):
     tgt[0, 0, 0] = 1e-3
     tgt[1, 0, 1] = tgt[1, 1, 0] = 5e-4
     sig = []
-    for pipelined in (0, 1):
+    for pipelined in (0, 1, 2):
         s = dbfft.Solver(shape, phase, dbfft.iso_phases(E, nu), tgt, batch=2, stress_mask=mask.reshape(-1),
                          precision=precision, tol=1e-11 if precision == 0 else 1e-9, eta_inner=1e-3)
         fp64 = 1 if precision == 0 else 0
@@ -96,5 +97,5 @@ def test_pcg_with_pipelined_pass3_equals_plain(precision):
     T = iso_tangent(phase, E, nu)
     for b in range(2):
         ref = o.solve_linear(prob, T, tgt[b], tol=1e-12)["sig_bar"]
-        for k in range(2):
+        for k in range(3):
             assert rel_err(sig[k][b], ref) < (1e-10 if precision == 0 else 1e-7)
