@@ -1094,9 +1094,8 @@ float time_launch(dbfft_ctx* ctx, F&& f) {
 }
 
 template <typename T>
-void tune_precision(dbfft_ctx* ctx, int pi_) {
-    cplx<T>* W = reinterpret_cast<cplx<T>*>(ctx->W);
-    cudaMemsetAsync(ctx->W, 0, (size_t)ctx->B * ctx->nc * ctx->H * sizeof(cplx<T>), ctx->stream);
+void tune_pass3(dbfft_ctx* ctx, int pi_, cplx<T>* W) {
+    char buf[256];
     // pass 3: radix x lines per CTA
     const int radices[2] = {8, 16};
     float best = 1e30f;
@@ -1123,7 +1122,6 @@ void tune_precision(dbfft_ctx* ctx, int pi_) {
     }
     ctx->ax3_radix[pi_] = bestR;
     ctx->ax3_L[pi_] = bestL;
-    char buf[256];
     std::snprintf(buf, sizeof(buf), "pass3 radix %d lines %d (%.4f ms); ", bestR, bestL, best);
     ctx->tune_note += buf;
     // the pipelined pass for the CG applications: radix x lines per tile
@@ -1161,6 +1159,14 @@ void tune_precision(dbfft_ctx* ctx, int pi_) {
                       bpS == 2 ? "one-stage" : "two-stage", bpR, bpL, bp, ctx->pipe_on[pi_] ? " used" : "");
         ctx->tune_note += buf;
     }
+}
+
+template <typename T>
+void tune_precision(dbfft_ctx* ctx, int pi_, bool pass3) {
+    cplx<T>* W = reinterpret_cast<cplx<T>*>(ctx->W);
+    cudaMemsetAsync(ctx->W, 0, (size_t)ctx->B * ctx->nc * ctx->H * sizeof(cplx<T>), ctx->stream);
+    char buf[256];
+    if (pass3) tune_pass3<T>(ctx, pi_, W);
     // strided transforms: columns per CTA along axes 1 and 2
     for (int ax = 0; ax < 2; ++ax) {
         float bt = 1e30f;
@@ -1224,44 +1230,73 @@ long long dbfft_launch_count(const dbfft_ctx* ctx) { return ctx ? ctx->launches 
 dbfft_status dbfft_autotune(dbfft_ctx* ctx, const char* cache_path) {
     if (!ctx) return DBFFT_E_ARG;
     const std::string key = tune_key(ctx);
-    const int pi_ = ctx->prec == DBFFT_FP64 ? 1 : 0;
+    // precisions to tune: the inner solve's, and in the MIXED mode also the
+    // FP64 passes of the outer residual chain
+    std::vector<int> pis;
+    if (ctx->prec == DBFFT_FP64) pis = {1};
+    else pis = {0, 1};
+    auto drop_graphs = [&] {
+        for (int k = 0; k < 2; ++k)
+            if (ctx->cg_exec[k]) { cudaGraphExecDestroy(ctx->cg_exec[k]); ctx->cg_exec[k] = nullptr; }
+    };
     if (cache_path) {
         if (FILE* f = std::fopen(cache_path, "r")) {
             char line[512];
             while (std::fgets(line, sizeof(line), f)) {
                 std::string ln(line);
                 if (ln.compare(0, key.size(), key) != 0 || ln.size() <= key.size() || ln[key.size()] != '|') continue;
-                int R = 0, L = 0, t1 = 0, t2 = 0, pon = 0, pR = 0, pL = 0;
-                if (std::sscanf(ln.c_str() + key.size() + 1, "%d %d %d %d %d %d %d", &R, &L, &t1, &t2, &pon, &pR,
-                                &pL) == 7) {
-                    ctx->ax3_radix[pi_] = R;
-                    ctx->ax3_L[pi_] = L;
-                    ctx->fft_tw[pi_][0] = t1;
-                    ctx->fft_tw[pi_][1] = t2;
-                    ctx->pipe_on[pi_] = pon;
-                    ctx->pipe_R[pi_] = pR;
-                    ctx->pipe_L[pi_] = pL;
-                    ctx->tune_note = "from cache";
-                    std::fclose(f);
-                    for (int k = 0; k < 2; ++k)
-                        if (ctx->cg_exec[k]) { cudaGraphExecDestroy(ctx->cg_exec[k]); ctx->cg_exec[k] = nullptr; }
-                    return DBFFT_OK;
+                const char* p = ln.c_str() + key.size() + 1;
+                int v[2][7];
+                int n = 0;
+                for (size_t k = 0; k < pis.size(); ++k) {
+                    int used = 0;
+                    if (std::sscanf(p, "%d %d %d %d %d %d %d%n", &v[k][0], &v[k][1], &v[k][2], &v[k][3], &v[k][4],
+                                    &v[k][5], &v[k][6], &used) != 7)
+                        break;
+                    p += used;
+                    ++n;
                 }
+                if (n != (int)pis.size()) continue;
+                for (size_t k = 0; k < pis.size(); ++k) {
+                    const int pi_ = pis[k];
+                    ctx->ax3_radix[pi_] = v[k][0];
+                    ctx->ax3_L[pi_] = v[k][1];
+                    ctx->fft_tw[pi_][0] = v[k][2];
+                    ctx->fft_tw[pi_][1] = v[k][3];
+                    ctx->pipe_on[pi_] = v[k][4];
+                    ctx->pipe_R[pi_] = v[k][5];
+                    ctx->pipe_L[pi_] = v[k][6];
+                }
+                ctx->tune_note = "from cache";
+                std::fclose(f);
+                drop_graphs();
+                return DBFFT_OK;
             }
             std::fclose(f);
         }
     }
     ctx->tune_note.clear();
-    if (pi_ == 0) tune_precision<float>(ctx, 0);
-    else tune_precision<double>(ctx, 1);
+    for (int pi_ : pis) {
+        if (pi_ == 0) {
+            tune_precision<float>(ctx, 0, true);
+        } else {
+            // the FP64 operator application of pass 3 reads an FP64 tangent, which a
+            // MIXED context of a nonlinear model does not hold: there only the
+            // strided transforms are tuned for FP64
+            const bool p3 = ctx->prec == DBFFT_FP64 || ctx->model == DBFFT_ISO_ELASTIC;
+            if (ctx->prec != DBFFT_FP64) ctx->tune_note += "[FP64 residual chain] ";
+            tune_precision<double>(ctx, 1, p3);
+        }
+    }
     CK(cudaStreamSynchronize(ctx->stream));
-    for (int k = 0; k < 2; ++k)
-        if (ctx->cg_exec[k]) { cudaGraphExecDestroy(ctx->cg_exec[k]); ctx->cg_exec[k] = nullptr; }
+    drop_graphs();
     if (cache_path) {
         if (FILE* f = std::fopen(cache_path, "a")) {
-            std::fprintf(f, "%s|%d %d %d %d %d %d %d\n", key.c_str(), ctx->ax3_radix[pi_], ctx->ax3_L[pi_],
-                         ctx->fft_tw[pi_][0], ctx->fft_tw[pi_][1], ctx->pipe_on[pi_], ctx->pipe_R[pi_],
-                         ctx->pipe_L[pi_]);
+            std::fprintf(f, "%s|", key.c_str());
+            for (int pi_ : pis)
+                std::fprintf(f, " %d %d %d %d %d %d %d", ctx->ax3_radix[pi_], ctx->ax3_L[pi_], ctx->fft_tw[pi_][0],
+                             ctx->fft_tw[pi_][1], ctx->pipe_on[pi_], ctx->pipe_R[pi_], ctx->pipe_L[pi_]);
+            std::fprintf(f, "\n");
             std::fclose(f);
         }
     }

@@ -318,8 +318,9 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? (RW == 16 ? 3 : 4) : ((
     if constexpr (OpInfo<OPK>::apply) {
         if (a.cg) {
             for (int rr = 0; rr < RB; ++rr) {
-                double v1[1] = {(double)eacc[rr]};
-                block_sum<1>(v1, red);
+                double v1[1];
+                const T in1[1] = {eacc[rr]};
+                block_sum_t<T, 1>(in1, v1, red);
                 if (t == 0) ecc[rr] = v1[0];
             }
             const int nblk = gridDim.x;

@@ -102,6 +102,35 @@ __device__ __forceinline__ void block_sum(double* v, double* scratch /* >= 32*NV
     (void)lane;
 }
 
+// Block-wide sum of NV values held in precision T: warp sums in T, the
+// per-warp partials combined in FP64 by thread 0 (result valid there).
+template <typename T, int NV>
+__device__ __forceinline__ void block_sum_t(const T* vin, double* out, double* scratch /* >= 32*NV */) {
+    T v[NV];
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+        v[k] = vin[k];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
+    }
+    const int tid = threadIdx.x + threadIdx.y * blockDim.x;
+    const int warp = tid / 32;
+    const int nwarps = (blockDim.x * blockDim.y + 31) / 32;
+    __syncthreads();
+    if ((tid & 31) == 0) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) scratch[warp * NV + k] = (double)v[k];
+    }
+    __syncthreads();
+    if (tid == 0) {
+        for (int k = 0; k < NV; ++k) {
+            double s = 0.0;
+            for (int w = 0; w < nwarps; ++w) s += scratch[w * NV + k];
+            out[k] = s;
+        }
+    }
+}
+
 // Symmetric-gradient / gradient component m of u at xi, times (i * invN).
 template <typename T, int NC, int M>
 __device__ __forceinline__ cplx<T> grad_comp(const cplx<T>* u, T x1, T x2, T x3, T s) {
@@ -402,7 +431,11 @@ __global__ void __launch_bounds__(PW_THREADS) k_div(Ax1FwdArgs<T> a) {
         return;
     }
     if constexpr (MODE == AX5_RESID) {
-        double v2[2] = {(double)acc0, 0.0};  // ||r_u||^2 and ||r_e||^2
+        double v2[2];  // ||r_u||^2 and ||r_e||^2
+        {
+            const T in2[2] = {acc0, T(0)};
+            block_sum_t<T, 2>(in2, v2, red);
+        }
         if (has0) {
             const double Nd = 1.0 / d.invN;
             for (int q = 0; q < 9; ++q) a.sig0[b * 9 + q] = q < NC ? s0(q) * d.invN : 0.0;
@@ -414,7 +447,6 @@ __global__ void __launch_bounds__(PW_THREADS) k_div(Ax1FwdArgs<T> a) {
                 v2[1] += re * re;
             }
         }
-        block_sum<2>(v2, red);
         if (tid == 0) {
             a.partials[((long long)b * gridDim.x + blockIdx.x) * 2 + 0] = v2[0];
             a.partials[((long long)b * gridDim.x + blockIdx.x) * 2 + 1] = v2[1];
@@ -422,7 +454,11 @@ __global__ void __launch_bounds__(PW_THREADS) k_div(Ax1FwdArgs<T> a) {
         return;
     }
     if constexpr (MODE == AX5_CG) {
-        double v2[2] = {(double)acc0, (double)acc1};
+        double v2[2];
+        {
+            const T in2[2] = {acc0, acc1};
+            block_sum_t<T, 2>(in2, v2, red);
+        }
         if (has0) {  // macro part: q_e = E^T sigma-hat(0); x_e += alpha p_e; r_e -= alpha q_e
             const double al = a.cg[b].alpha;
             double re[9];
@@ -441,7 +477,6 @@ __global__ void __launch_bounds__(PW_THREADS) k_div(Ax1FwdArgs<T> a) {
                 v2[1] += re[k] * re[k];
             }
         }
-        block_sum<2>(v2, red);
         const int nblk = gridDim.x;
         if (tid == 0) {
             a.partials[((long long)b * nblk + blockIdx.x) * 2 + 0] = v2[0];
