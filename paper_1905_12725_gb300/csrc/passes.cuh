@@ -219,7 +219,7 @@ __device__ __forceinline__ FreqIdx freq_idx(const Dims& d, long long i) {
 // In CG mode u is the new search direction p = M r + beta p_old, formed here
 // from r, together with the deferred iterate update x += alpha_prev p_old.
 template <typename T, int NC, int MODE>
-__global__ void __launch_bounds__(PW_THREADS, (sizeof(T) == 4 ? 3 : 2)) k_grad(Ax1InvArgs<T> a) {
+__global__ void __launch_bounds__(PW_THREADS) k_grad(Ax1InvArgs<T> a) {
     const int b = blockIdx.y;
     if (MODE == AX1_CG && a.cg[b].done) return;
     const Dims& d = a.d;
@@ -232,40 +232,27 @@ __global__ void __launch_bounds__(PW_THREADS, (sizeof(T) == 4 ? 3 : 2)) k_grad(A
         N = (T)(1.0 / d.invN);
         pd = a.pre + b / d.Rm;
     }
-    // two frequencies per step: both sets of loads are issued before either
-    // set of stores (the loads of one may not wait behind the other's stores)
-    struct In {
-        cplx<T> u[3], po[3], xo[3];
-        T x1, x2, x3;
-    };
-    auto load = [&](long long i, In& g) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < d.H; i += (long long)gridDim.x * blockDim.x) {
         const FreqIdx fi = freq_idx(d, i);
-        g.x1 = a.f.xi1[fi.k1];
-        g.x2 = a.f.xi2[fi.k2];
-        g.x3 = a.f.xi3[fi.k3];
+        const T x1 = a.f.xi1[fi.k1], x2 = a.f.xi2[fi.k2], x3 = a.f.xi3[fi.k3];
+        cplx<T> u[3];
 #pragma unroll
-        for (int c = 0; c < 3; ++c) g.u[c] = ldc(a.in + (long long)(b * 3 + c) * d.H + i);
+        for (int c = 0; c < 3; ++c) u[c] = ldc(a.in + (long long)(b * 3 + c) * d.H + i);
         if constexpr (MODE == AX1_CG) {
+            cplx<T> z[3], po[3], xo[3];
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
-                g.po[c] = ldc(a.p + (long long)(b * 3 + c) * d.H + i);
-                g.xo[c] = ldc(a.x + (long long)(b * 3 + c) * d.H + i);
+                po[c] = ldc(a.p + (long long)(b * 3 + c) * d.H + i);
+                xo[c] = ldc(a.x + (long long)(b * 3 + c) * d.H + i);
             }
-        }
-    };
-    auto finish = [&](long long i, In& g) {
-        cplx<T>* u = g.u;
-        if constexpr (MODE == AX1_CG) {
-            cplx<T> z[3];
-            precond_apply<T>(pcoef<T>(*pd), g.x1, g.x2, g.x3, N, u, z);
+            precond_apply<T>(pcoef<T>(*pd), x1, x2, x3, N, u, z);
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
-                u[c] = z[c] + g.po[c] * beta;
+                u[c] = z[c] + po[c] * beta;
                 stc(a.p + (long long)(b * 3 + c) * d.H + i, u[c]);
-                stc(a.x + (long long)(b * 3 + c) * d.H + i, g.xo[c] + g.po[c] * alpha);
+                stc(a.x + (long long)(b * 3 + c) * d.H + i, xo[c] + po[c] * alpha);
             }
         }
-        const T x1 = g.x1, x2 = g.x2, x3 = g.x3;
         cplx<T>* Wb = a.W + (long long)b * NC * d.H + i;
         stc(Wb + 0 * d.H, grad_comp<T, NC, 0>(u, x1, x2, x3, s));
         stc(Wb + 1 * d.H, grad_comp<T, NC, 1>(u, x1, x2, x3, s));
@@ -278,15 +265,6 @@ __global__ void __launch_bounds__(PW_THREADS, (sizeof(T) == 4 ? 3 : 2)) k_grad(A
             stc(Wb + 7 * d.H, grad_comp<T, NC, 7>(u, x1, x2, x3, s));
             stc(Wb + 8 * d.H, grad_comp<T, NC, 8>(u, x1, x2, x3, s));
         }
-    };
-    const long long st = (long long)gridDim.x * blockDim.x;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < d.H; i += 2 * st) {
-        const long long j = i + st;
-        In A, Bv;
-        load(i, A);
-        if (j < d.H) load(j, Bv);
-        finish(i, A);
-        if (j < d.H) finish(j, Bv);
     }
 }
 
@@ -374,7 +352,7 @@ struct Ax1FwdArgs {
 //  CG:    r -= alpha q (the iterate update is deferred to the next pass 1),
 //         <r, M r> and ||r||^2; the last block sets beta and the stop flag.
 template <typename T, int NC, int MODE>
-__global__ void __launch_bounds__(PW_THREADS, (sizeof(T) == 4 ? 3 : 2)) k_div(Ax1FwdArgs<T> a) {
+__global__ void __launch_bounds__(PW_THREADS) k_div(Ax1FwdArgs<T> a) {
     __shared__ double red[32 * 2];
     __shared__ bool is_last;
     const int b = blockIdx.y;
@@ -390,44 +368,25 @@ __global__ void __launch_bounds__(PW_THREADS, (sizeof(T) == 4 ? 3 : 2)) k_div(Ax
     }
     T acc0 = T(0), acc1 = T(0);  // CG: <r, M r>, ||r||^2 ; RESID: ||r_u||^2
     const cplx<T>* Wb = a.W + (long long)b * NC * d.H;
-    // two frequencies per step: both sets of loads are issued before either
-    // set of stores (the loads of one may not wait behind the other's stores)
-    struct In {
-        cplx<T> w[NC], r[3];
-        T x1, x2, x3;
-        int k3;
-    };
-    auto load = [&](long long i, In& g) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + tid; i < d.H; i += (long long)gridDim.x * blockDim.x) {
         const FreqIdx fi = freq_idx(d, i);
-        g.x1 = a.f.xi1[fi.k1];
-        g.x2 = a.f.xi2[fi.k2];
-        g.x3 = a.f.xi3[fi.k3];
-        g.k3 = fi.k3;
-#pragma unroll
-        for (int m = 0; m < NC; ++m) g.w[m] = ldc(Wb + (long long)m * d.H + i);
-        if constexpr (MODE == AX5_CG) {
-#pragma unroll
-            for (int c = 0; c < 3; ++c) g.r[c] = ldc(a.r + (long long)(b * 3 + c) * d.H + i);
-        }
-    };
-    auto finish = [&](long long i, In& g) {
-        const T x1 = g.x1, x2 = g.x2, x3 = g.x3;
+        const T x1 = a.f.xi1[fi.k1], x2 = a.f.xi2[fi.k2], x3 = a.f.xi3[fi.k3];
         cplx<T> q[3] = {zero_c<T>(), zero_c<T>(), zero_c<T>()};
-        div_acc<T, NC, 0>(q, g.w[0], x1, x2, x3);
-        div_acc<T, NC, 1>(q, g.w[1], x1, x2, x3);
-        div_acc<T, NC, 2>(q, g.w[2], x1, x2, x3);
-        div_acc<T, NC, 3>(q, g.w[3], x1, x2, x3);
-        div_acc<T, NC, 4>(q, g.w[4], x1, x2, x3);
-        div_acc<T, NC, 5>(q, g.w[5], x1, x2, x3);
+        div_acc<T, NC, 0>(q, ldc(Wb + 0 * d.H + i), x1, x2, x3);
+        div_acc<T, NC, 1>(q, ldc(Wb + 1 * d.H + i), x1, x2, x3);
+        div_acc<T, NC, 2>(q, ldc(Wb + 2 * d.H + i), x1, x2, x3);
+        div_acc<T, NC, 3>(q, ldc(Wb + 3 * d.H + i), x1, x2, x3);
+        div_acc<T, NC, 4>(q, ldc(Wb + 4 * d.H + i), x1, x2, x3);
+        div_acc<T, NC, 5>(q, ldc(Wb + 5 * d.H + i), x1, x2, x3);
         if constexpr (NC == 9) {
-            div_acc<T, NC, 6>(q, g.w[6], x1, x2, x3);
-            div_acc<T, NC, 7>(q, g.w[7], x1, x2, x3);
-            div_acc<T, NC, 8>(q, g.w[8], x1, x2, x3);
+            div_acc<T, NC, 6>(q, ldc(Wb + 6 * d.H + i), x1, x2, x3);
+            div_acc<T, NC, 7>(q, ldc(Wb + 7 * d.H + i), x1, x2, x3);
+            div_acc<T, NC, 8>(q, ldc(Wb + 8 * d.H + i), x1, x2, x3);
         }
         const bool zmode = (x1 == T(0)) && (x2 == T(0)) && (x3 == T(0));
 #pragma unroll
         for (int c = 0; c < 3; ++c) q[c] = zmode ? zero_c<T>() : mul_i(ms, q[c]);
-        const T wgt = (T)hweight(g.k3, d.m);
+        const T wgt = (T)hweight(fi.k3, d.m);
         if constexpr (MODE == AX5_PLAIN) {
 #pragma unroll
             for (int c = 0; c < 3; ++c) stc(a.out + (long long)(b * 3 + c) * d.H + i, q[c]);
@@ -442,8 +401,9 @@ __global__ void __launch_bounds__(PW_THREADS, (sizeof(T) == 4 ? 3 : 2)) k_div(Ax
             cplx<T> rv[3], z[3];
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
-                rv[c] = g.r[c] - q[c] * alpha;
-                stc(a.r + (long long)(b * 3 + c) * d.H + i, rv[c]);
+                const long long idx = (long long)(b * 3 + c) * d.H + i;
+                rv[c] = ldc(a.r + idx) - q[c] * alpha;
+                stc(a.r + idx, rv[c]);
             }
             precond_apply<T>(pcoef<T>(*pd), x1, x2, x3, N, rv, z);
             T lrz = T(0), lrr = T(0);
@@ -455,15 +415,6 @@ __global__ void __launch_bounds__(PW_THREADS, (sizeof(T) == 4 ? 3 : 2)) k_div(Ax
             acc0 += wgt * lrz;
             acc1 += wgt * lrr;
         }
-    };
-    const long long st = (long long)gridDim.x * blockDim.x;
-    for (long long i = (long long)blockIdx.x * blockDim.x + tid; i < d.H; i += 2 * st) {
-        const long long j = i + st;
-        In A, Bv;
-        load(i, A);
-        if (j < d.H) load(j, Bv);
-        finish(i, A);
-        if (j < d.H) finish(j, Bv);
     }
     const bool has0 = blockIdx.x == 0 && tid == 0;  // k = (0,0,0) is entry 0
     // sigma-hat(0) of the nc components, W components (mean stress = this / N)
