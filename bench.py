@@ -81,10 +81,14 @@ class ClockSampler:
     def start(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
+            t0 = time.time()  # the timed region starts once sampling runs
+            while not self.lines and time.time() - t0 < 3.0 and self.proc.poll() is None:
+                time.sleep(0.01)
+            self.first = len(self.lines)
         except Exception:
             self.proc = None
 
@@ -95,6 +99,10 @@ class ClockSampler:
     def stop(self):
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        n_end = len(self.lines)
+        t0 = time.time()  # one more sample after the region ends
+        while len(self.lines) <= n_end and time.time() - t0 < 1.0:
+            time.sleep(0.01)
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
@@ -210,7 +218,35 @@ def operator_256(torch, dbfft, peak, iters=40):
     s = dbfft.Solver((n, n, n), phase, dbfft.iso_phases([1.0, 100.0], [0.3, 0.3]), eps,
                      precision=dbfft.DBFFT_MIXED, tol=1e-30, eta_inner=1e-30, max_iter=iters, max_newton=1)
     tuning = s.autotune(TUNE_CACHE)
-    s.solve_increment(0, allow_not_converged=True)  # warm-up
+    s.solve_increment(0, allow_not_converged=True)  # warm-up (the next inner solves run as CUDA graphs)
+    s.close()
+
+    # graph-mode cost of one CG iteration: difference of two solves that differ only in the cap
+    def graph_solve_ms(cap):
+        sg = dbfft.Solver((n, n, n), phase, dbfft.iso_phases([1.0, 100.0], [0.3, 0.3]), eps,
+                          precision=dbfft.DBFFT_MIXED, tol=1e-30, eta_inner=1e-30, max_iter=cap, max_newton=1)
+        sg.autotune(TUNE_CACHE)
+        sg.solve_increment(0, allow_not_converged=True)
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(3):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(sg.stream)
+            sg.solve_increment(0, allow_not_converged=True)
+            e1.record(sg.stream)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        sg.close()
+        return min(ts)
+
+    t_lo, t_hi = graph_solve_ms(iters // 2), graph_solve_ms(iters + iters // 2)
+    graph_ms_it = (t_hi - t_lo) / iters
+
+    s = dbfft.Solver((n, n, n), phase, dbfft.iso_phases([1.0, 100.0], [0.3, 0.3]), eps,
+                     precision=dbfft.DBFFT_MIXED, tol=1e-30, eta_inner=1e-30, max_iter=iters, max_newton=1)
+    s.autotune(TUNE_CACHE)
+    s.solve_increment(0, allow_not_converged=True)
     s.profile(True)
     t0 = time.perf_counter()
     rep = s.solve_increment(0, allow_not_converged=True)
@@ -232,7 +268,12 @@ def operator_256(torch, dbfft, peak, iters=40):
         it_ms += e["ms"]
         it_bytes += e["bytes"]
     iters = rep["cg_iters"]
+    bytes_it = it_bytes / max(iters, 1)
     return {"grid": "256^3, 1 RHS, FP32 inner CG, iso two-phase (vf 0.3, contrast 100)", "tuning": tuning,
+            "graph_ms_per_cg_iter": graph_ms_it,
+            "graph_voxel_cg_iters_per_s": n ** 3 / (graph_ms_it * 1e-3),
+            "graph_chain_GBps": bytes_it / (graph_ms_it * 1e-3) / 1e9,
+            "graph_chain_frac": bytes_it / (graph_ms_it * 1e-3) / 1e9 / peak,
             "cg_iters": iters, "ms_per_cg_iter": it_ms / max(iters, 1),
             "voxel_cg_iters_per_s": n ** 3 * iters / (it_ms * 1e-3) if it_ms else None,
             "chain_GBps": it_bytes / (it_ms * 1e-3) / 1e9 if it_ms else None,
@@ -555,7 +596,7 @@ def our_arm(args, rank, world, local_rank):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--ref-iters", type=int, default=40)

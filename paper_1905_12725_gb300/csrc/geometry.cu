@@ -35,10 +35,17 @@ int ax2_tile(int n2, bool dbl) {
     return tw;
 }
 
-static int slot_bytes(int n3, bool dbl) {
-    // mirrors ax3_slot_cplx<T, N3>() in pass3.cuh
+static int slot_bytes(int n3, bool dbl, int radix) {
+    // mirrors ax3_slot_cplx<T, N3, RW>() in pass3.cuh
     const int m = n3 / 2;
     const int csz = dbl ? 16 : 8;
+    const int r = radix_ax3(m, dbl, radix);
+    if (r == m) {  // one thread per line: an odd number of words of the element size
+        const int words = csz / 4;
+        int n = m + 1;
+        while (((n * words) & 31) != words) ++n;
+        return n * csz;
+    }
     const int pl = m + (m >> (dbl ? 3 : 4)) + 1;
     int n = pl > m + 1 ? pl : m + 1;
     while (((n * csz / 4) & 31) != 16) ++n;
@@ -48,7 +55,7 @@ static int slot_bytes(int n3, bool dbl) {
 int ax3_lines(int n3, int nc, int rb, bool dbl, int nfields, int radix) {
     // lines per CTA: real-space tiles within ~72 KB (three CTAs per SM), chosen
     // so that the slot FFT rounds (256 / P slots each) are well filled
-    const size_t sb = (size_t)slot_bytes(n3, dbl);
+    const size_t sb = (size_t)slot_bytes(n3, dbl, radix);
     long long Lmax = (long long)(72 * 1024) / ((long long)sb * rb * nc * nfields);
     if (Lmax < 1) Lmax = 1;
     if (Lmax > 32) Lmax = 32;

@@ -13,7 +13,7 @@ static cudaError_t ax3_nr(const Ax3Args<T>& a, cudaStream_t s) {
     const long long nlines = (long long)a.d.n1 * a.d.n2;
     const dim3 grid((unsigned)((nlines + a.L - 1) / a.L), (unsigned)(a.d.B / a.RB));
     const int nf = OPK == OP_ADJ ? 2 : 1;
-    const size_t smem = ((size_t)nf * a.L * a.RB * NC + 1) * ax3_slot_cplx<T, N3>() * sizeof(cplx<T>);
+    const size_t smem = ((size_t)nf * a.L * a.RB * NC + 1) * ax3_slot_cplx<T, N3, RW>() * sizeof(cplx<T>);
     static int max_dyn = -1;
     if (max_dyn < 0) {  // opt in to large dynamic shared memory: 227 KB per block minus the static part
         cudaFuncAttributes fa;
@@ -32,6 +32,10 @@ template <typename T, int N3, int NC, int OPK>
 static cudaError_t ax3_n(const Ax3Args<T>& a, cudaStream_t s) {
     if constexpr (sizeof(T) == 4) {
         if (a.radix == 16) return ax3_nr<T, N3, NC, OPK, 16>(a, s);
+        // one thread per line (radix N3/2): lines of up to 32 complex values
+        if constexpr (N3 <= 64 && OpInfo<OPK>::apply) {
+            if (a.radix == 32 && !a.pipe) return ax3_nr<T, N3, NC, OPK, 32>(a, s);
+        }
     }
     return ax3_nr<T, N3, NC, OPK, 8>(a, s);
 }

@@ -69,15 +69,26 @@ template <int OPK> struct OpInfo {
 };
 
 // Complex entries per slot buffer: room for the half-spectrum line (M + 1),
-// the real line (M complex) and the padded FFT exchange, rounded so that the
-// slot stride is 16 banks modulo 32 (neighbouring slots of a half-warp then
-// use disjoint banks).
-template <typename T, int N3>
+// the real line (M complex) and, when a line's transform is shared among
+// threads, the padded FFT exchange. Several threads per line: the slot
+// stride is 16 banks modulo 32 (neighbouring slots of a half-warp then use
+// disjoint banks). One thread per line (radix = M, no exchange): the stride
+// is an odd number of 8- or 16-byte words, so the lanes of a warp, each on
+// its own line, read the same position of 32 lines without bank conflicts.
+template <typename T, int N3, int RW = 8>
 __host__ __device__ constexpr int ax3_slot_cplx() {
     constexpr int M = N3 / 2;
-    int n = padded_len<T>(M) > M + 1 ? padded_len<T>(M) : M + 1;
-    while (((n * (int)sizeof(cplx<T>) / 4) & 31) != 16) ++n;
-    return n;
+    constexpr int R = (sizeof(T) == 8) ? (M < 4 ? M : 4) : (M < RW ? M : RW);
+    if constexpr (R == M) {
+        int n = M + 1;
+        const int words = (int)sizeof(cplx<T>) / 4;  // 2 (FP32) or 4 (FP64)
+        while (((n * words) & 31) != words) ++n;
+        return n;
+    } else {
+        int n = padded_len<T>(M) > M + 1 ? padded_len<T>(M) : M + 1;
+        while (((n * (int)sizeof(cplx<T>) / 4) & 31) != 16) ++n;
+        return n;
+    }
 }
 
 // Shared-memory layout: one buffer of SB = N3 + 2 values per slot
@@ -87,13 +98,13 @@ __host__ __device__ constexpr int ax3_slot_cplx() {
 // loads and stores are done cooperatively: for one (right-hand side,
 // component) the L lines of a CTA are L h contiguous complex values.
 template <typename T, int N3, int NC, int OPK, int RW>
-__global__ void __launch_bounds__(256, (sizeof(T) == 4 ? (RW == 16 ? 3 : 4) : ((OPK == OP_CP_UPDATE || OPK == OP_CP_UPDATE32 || OPK == OP_NH_UPDATE) ? 1 : 2))) k_axis3(Ax3Args<T> a) {
+__global__ void __launch_bounds__(256, (sizeof(T) == 4 ? (RW == 32 ? 2 : (RW == 16 ? 3 : 4)) : ((OPK == OP_CP_UPDATE || OPK == OP_CP_UPDATE32 || OPK == OP_NH_UPDATE) ? 1 : 2))) k_axis3(Ax3Args<T> a) {
     constexpr bool CPU_ = OPK == OP_CP_UPDATE || OPK == OP_CP_UPDATE32;  // crystal-plasticity update
     constexpr int M = N3 / 2;
     constexpr int H = M + 1;
     constexpr int R = RadixAx3<T, M, RW>::value;
     constexpr int P = M / R;
-    constexpr int SB = 2 * ax3_slot_cplx<T, N3>();  // in T values
+    constexpr int SB = 2 * ax3_slot_cplx<T, N3, RW>();  // in T values
     static_assert(P <= 32 && (32 % P) == 0, "a slot's threads must sit inside one warp");
     extern __shared__ __align__(16) unsigned char smraw[];
     T* sbuf = reinterpret_cast<T*>(smraw);
@@ -374,6 +385,27 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? (RW == 16 ? 3 : 4) : ((
         __syncwarp();
         ColFFT<T, M, R, -1, true, true>::run(v, myc, 1, p, a.tw.tm);
         __syncwarp();
+        if constexpr (P == 1) {
+            // the whole line is in this thread's registers: X[k] and X[M-k] from
+            // Z[k] and Z[M-k] directly, written pairwise
+            const T half = T(0.5);
+#pragma unroll
+            for (int k = 0; k <= M / 2; ++k) {
+                const int kc = (M - k) & (M - 1);
+                const cplx<T> Zk = v[k], Zc = conjg(v[kc]);
+                const cplx<T> e = ldg_c(a.tw.t3 + k);
+                const cplx<T> dl = e * (Zk - Zc);
+                myc[k] = mk(half * (Zk.x + Zc.x) + half * dl.y, half * (Zk.y + Zc.y) - half * dl.x);
+                if (k != 0 && k != M - k) {
+                    const cplx<T> Zk2 = v[kc], Zc2 = conjg(v[k]);
+                    const cplx<T> e2 = ldg_c(a.tw.t3 + (M - k));
+                    const cplx<T> dl2 = e2 * (Zk2 - Zc2);
+                    myc[M - k] = mk(half * (Zk2.x + Zc2.x) + half * dl2.y, half * (Zk2.y + Zc2.y) - half * dl2.x);
+                }
+            }
+            myc[M] = mk(v[0].x - v[0].y, T(0));
+            continue;
+        }
 #pragma unroll
         for (int r = 0; r < R; ++r) myc[p + r * P] = v[r];
         __syncwarp();
