@@ -305,8 +305,9 @@ const char* dbfft_tuning(const dbfft_ctx* ctx);
  * pipelined: 0 = one CTA per group of grid lines, loads staged by cp.async;
  * 1 = persistent CTAs looping over tiles of `lines` grid lines with two
  * shared-memory stages filled and drained by bulk copies; 2 = the same with
- * one stage (half the shared memory per CTA). radix: 8 or 16, or 32 with
- * the plain kernel when n3 <= 64 (one thread per grid line)
+ * one stage (half the shared memory per CTA). radix: 8 or 16 (FP32), 4
+ * (FP64), or 32 with the plain kernel when n3 <= 128 (FP32) / 64 (FP64):
+ * one thread per grid line, or per half line when n3 = 128
  * (FP32) / 4 (FP64); lines: grid lines per CTA (per tile when pipelined;
  * then even and dividing n1 * n2). Returns DBFFT_E_ARG for a shape that does
  * not exist or does not fit in shared memory; the results of the operator do

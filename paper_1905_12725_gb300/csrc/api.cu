@@ -1098,11 +1098,13 @@ void tune_pass3(dbfft_ctx* ctx, int pi_, cplx<T>* W) {
     char buf[256];
     // pass 3: radix x lines per CTA (radix 32 = one thread per line, lines of up to 32 complex values)
     const int radices[3] = {8, 16, 32};
-    const int nrad = sizeof(T) == 4 ? (ctx->n3 <= 64 ? 3 : 2) : 1;
+    const int radices64[2] = {4, 32};
+    const bool r32 = sizeof(T) == 4 ? ctx->n3 <= 128 : ctx->n3 <= 64;
+    const int nrad = sizeof(T) == 4 ? (r32 ? 3 : 2) : (r32 ? 2 : 1);
     float best = 1e30f;
     int bestR = ctx->ax3_radix[pi_], bestL = 0;
     for (int ri = 0; ri < nrad; ++ri) {
-        const int R = sizeof(T) == 4 ? radices[ri] : 4;
+        const int R = sizeof(T) == 4 ? radices[ri] : radices64[ri];
         const int Ld = ax3_lines(ctx->n3, ctx->nc, ctx->RB, sizeof(T) == 8, 1, R);
         const int cand[] = {1, 2, 3, 4, 6, 8, 12, 16, 24, 32, Ld};
         for (int L : cand) {
@@ -1309,8 +1311,10 @@ const char* dbfft_tuning(const dbfft_ctx* ctx) { return ctx ? ctx->tune_note.c_s
 dbfft_status dbfft_set_pass3_shape(dbfft_ctx* ctx, int fp64, int pipelined, int radix, int lines) {
     if (!ctx || (fp64 != 0 && fp64 != 1) || lines < 1) return DBFFT_E_ARG;
     const bool dbl = fp64 == 1;
-    if (dbl ? radix != 4 : (radix != 8 && radix != 16 && !(radix == 32 && !pipelined && ctx->n3 <= 64)))
-        return fail(ctx, DBFFT_E_ARG, "radix: 8 or 16 (FP32; 32 with the plain kernel when n3 <= 64), 4 (FP64)");
+    const bool r32 = radix == 32 && !pipelined && ctx->n3 <= (dbl ? 64 : 128);
+    if (dbl ? (radix != 4 && !r32) : (radix != 8 && radix != 16 && !r32))
+        return fail(ctx, DBFFT_E_ARG,
+                    "radix: 8 or 16 (FP32), 4 (FP64), or 32 with the plain kernel (n3 <= 128 FP32, <= 64 FP64)");
     const long long nlines = (long long)ctx->n1 * ctx->n2;
     if (lines > nlines) return fail(ctx, DBFFT_E_ARG, "more lines per CTA than grid lines");
     const int pi_ = dbl ? 1 : 0;

@@ -261,7 +261,8 @@ struct ColFFT {
 __host__ __device__ constexpr int radix_ax1(int n, bool dbl) { return dbl ? (n < 4 ? n : 4) : (n < 8 ? n : 8); }
 __host__ __device__ constexpr int radix_ax2(int n, bool dbl) { return dbl ? (n < 8 ? n : 8) : (n < 16 ? n : 16); }
 __host__ __device__ constexpr int radix_ax3(int m, bool dbl, int want = 8) {
-    return dbl ? (m < 4 ? m : 4) : (m < want ? m : want);
+    // want = 32: whole lines (m <= 32) or halves of lines per thread, in either precision
+    return want == 32 ? (m < 32 ? m : 32) : dbl ? (m < 4 ? m : 4) : (m < want ? m : want);
 }
 template <typename T, int N> struct RadixAx1 { static constexpr int value = radix_ax1(N, sizeof(T) == 8); };
 template <typename T, int M, int WANT> struct RadixAx3 { static constexpr int value = radix_ax3(M, sizeof(T) == 8, WANT); };

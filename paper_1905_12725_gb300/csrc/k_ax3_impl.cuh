@@ -32,10 +32,11 @@ template <typename T, int N3, int NC, int OPK>
 static cudaError_t ax3_n(const Ax3Args<T>& a, cudaStream_t s) {
     if constexpr (sizeof(T) == 4) {
         if (a.radix == 16) return ax3_nr<T, N3, NC, OPK, 16>(a, s);
-        // one thread per line (radix N3/2): lines of up to 32 complex values
-        if constexpr (N3 <= 64 && OpInfo<OPK>::apply) {
-            if (a.radix == 32 && !a.pipe) return ax3_nr<T, N3, NC, OPK, 32>(a, s);
-        }
+    }
+    // radix 32: one thread per line (N3/2 <= 32) or per half line (N3 = 128, FP32);
+    // for the operator applications (and the linear residual chain in FP64)
+    if constexpr ((sizeof(T) == 4 ? N3 <= 128 : N3 <= 64) && (OpInfo<OPK>::apply)) {
+        if (a.radix == 32 && !a.pipe) return ax3_nr<T, N3, NC, OPK, 32>(a, s);
     }
     return ax3_nr<T, N3, NC, OPK, 8>(a, s);
 }

@@ -78,7 +78,7 @@ template <int OPK> struct OpInfo {
 template <typename T, int N3, int RW = 8>
 __host__ __device__ constexpr int ax3_slot_cplx() {
     constexpr int M = N3 / 2;
-    constexpr int R = (sizeof(T) == 8) ? (M < 4 ? M : 4) : (M < RW ? M : RW);
+    constexpr int R = radix_ax3(M, sizeof(T) == 8, RW);
     if constexpr (R == M) {
         int n = M + 1;
         const int words = (int)sizeof(cplx<T>) / 4;  // 2 (FP32) or 4 (FP64)
@@ -98,7 +98,7 @@ __host__ __device__ constexpr int ax3_slot_cplx() {
 // loads and stores are done cooperatively: for one (right-hand side,
 // component) the L lines of a CTA are L h contiguous complex values.
 template <typename T, int N3, int NC, int OPK, int RW>
-__global__ void __launch_bounds__(256, (sizeof(T) == 4 ? (RW == 32 ? 2 : (RW == 16 ? 3 : 4)) : ((OPK == OP_CP_UPDATE || OPK == OP_CP_UPDATE32 || OPK == OP_NH_UPDATE) ? 1 : 2))) k_axis3(Ax3Args<T> a) {
+__global__ void __launch_bounds__(256, (sizeof(T) == 4 ? (RW == 32 ? 2 : (RW == 16 ? 3 : 4)) : ((RW == 32 || OPK == OP_CP_UPDATE || OPK == OP_CP_UPDATE32 || OPK == OP_NH_UPDATE) ? 1 : 2))) k_axis3(Ax3Args<T> a) {
     constexpr bool CPU_ = OPK == OP_CP_UPDATE || OPK == OP_CP_UPDATE32;  // crystal-plasticity update
     constexpr int M = N3 / 2;
     constexpr int H = M + 1;

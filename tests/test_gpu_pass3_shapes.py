@@ -101,23 +101,26 @@ def test_pcg_with_pipelined_pass3_equals_plain(precision):
             assert rel_err(sig[k][b], ref) < (1e-10 if precision == 0 else 1e-7)
 
 
-@pytest.mark.parametrize("shape,B,nmat,lines", [((16, 16, 64), 1, 1, 8), ((8, 32, 32), 3, 3, 5),
-                                                ((32, 16, 16), 6, 1, 7), ((16, 8, 8), 2, 2, 3)])
-def test_one_thread_per_line_pass3_matches_oracle(shape, B, nmat, lines):
-    """Radix n3/2 (one thread holds a whole line; no exchange) for n3 <= 64, FP32."""
+@pytest.mark.parametrize("shape,B,nmat,lines,fp64", [((16, 16, 64), 1, 1, 8, 0), ((8, 32, 32), 3, 3, 5, 0),
+                                                     ((32, 16, 16), 6, 1, 7, 0), ((16, 8, 8), 2, 2, 3, 0),
+                                                     ((8, 8, 128), 2, 1, 4, 0), ((16, 8, 64), 2, 1, 3, 1),
+                                                     ((8, 16, 32), 1, 1, 6, 1)])
+def test_radix32_pass3_matches_oracle(shape, B, nmat, lines, fp64):
+    """Radix 32: one thread holds a whole line (no exchange) for n3 <= 64, or half a
+    line (one exchange) for n3 = 128; FP32 and FP64."""
     dbfft = _dbfft()
     g = np.random.default_rng(7 * lines + B)
     phase = (g.random((nmat,) + shape) < 0.4).astype(np.uint16)
     E, nu = [1.0, 25.0], [0.3, 0.2]
     s = dbfft.Solver(shape, phase, dbfft.iso_phases(E, nu), np.zeros((B, 3, 3)), batch=B,
-                     precision=dbfft.DBFFT_MIXED)
-    s.set_pass3_shape(0, 0, 32, lines)
+                     precision=dbfft.DBFFT_FP64 if fp64 else dbfft.DBFFT_MIXED)
+    s.set_pass3_shape(fp64, 0, 32, lines)
     u = synth.random_spectrum(shape, 3, 900 + lines, batch=B)
-    out, _ = s.apply(torch.from_numpy(u).cuda(), fp32=True)
+    out, _ = s.apply(torch.from_numpy(u).cuda(), fp32=not fp64)
     out = out.cpu().numpy()
     prob = o.Problem(shape)
     Rm = B // nmat
     for b in range(B):
         ref, _ = prob.apply_K(iso_tangent(phase[b // Rm], E, nu), u[b], np.zeros(0))
-        assert rel_err(out[b], ref) < 2e-5, b
+        assert rel_err(out[b], ref) < (1e-12 if fp64 else 2e-5), b
     s.close()
