@@ -35,6 +35,7 @@ struct Ax3Args {
     int RB;                // right-hand sides per CTA (divides Rm)
     int L;                 // grid lines per CTA (per tile for the pipelined pass)
     int pipe;              // CG applications: 1 = pipelined pass (k_axis3_pipe), 0 = k_axis3
+    int zero_in;           // the input field is known to be zero: no load, no C2R (real fields start at 0)
     int radix;             // radix of the half-length transform (FP32: 8 or 16; FP64: 4)
     const T* macroW;       // [B][9] constant field added before the op (W components)
     const T* macroW2;      // OP_ADJ: macro part of the adjoint field
@@ -133,6 +134,13 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? (RW == 32 ? 2 : (RW == 
         if (all) return;
     }
 
+    if (a.zero_in) {  // real-space input fields are zero: clear the real lines instead
+        for (int i = t; i < NF * NSLOT * N3; i += nthr) {
+            const int sl = i / N3, x3 = i - sl * N3;
+            sbuf[(long long)sl * SB + x3] = T(0);
+        }
+        __syncthreads();
+    } else {
     // ---- cooperative load of the half-spectrum lines: for each (rhs, comp)
     // the lines of this CTA are lines_here * H contiguous complex values
     for (int f = 0; f < NF; ++f) {
@@ -179,6 +187,7 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? (RW == 32 ? 2 : (RW == 
         }
     }
     __syncthreads();
+    }  // !zero_in
 
     // ---- per-voxel operation
     T eacc[8];
