@@ -281,6 +281,57 @@ def operator_256(torch, dbfft, peak, iters=40):
             "passes": rows, "wall_s": wall}
 
 
+def cufft_operator_256(torch, reps=10):
+    """Comparison only: the same small-strain operator application K u at 256^3
+    (FP32, one RHS, the two-phase map of operator_256) composed from torch
+    element-wise ops and torch.fft (cuFFT) -- Fourier gradient, inverse 3-D
+    real FFT of six components, isotropic stress, forward 3-D FFT,
+    divergence. No part of the library uses it."""
+    n = 256
+    dev = torch.device("cuda")
+    g = np.random.default_rng(7)
+    phase = torch.from_numpy((g.random((n, n, n)) < 0.3).astype(np.int64)).to(dev)
+    E = torch.tensor([1.0, 100.0], device=dev)
+    nu = 0.3
+    lam_t = (E * nu / ((1 + nu) * (1 - 2 * nu)))[phase].float()
+    mu_t = (E / (2 * (1 + nu)))[phase].float()
+    k = torch.fft.fftfreq(n, d=1.0 / n, device=dev).float() * 2 * math.pi
+    k[n // 2] = 0.0
+    kh = k[: n // 2 + 1].clone()
+    kh[n // 2] = 0.0
+    x1, x2, x3 = k[:, None, None], k[None, :, None], kh[None, None, :]
+    u = (torch.randn(3, n, n, n // 2 + 1, device=dev) + 1j * torch.randn(3, n, n, n // 2 + 1, device=dev)).to(
+        torch.complex64)
+    pairs = [(0, 0), (1, 1), (2, 2), (1, 2), (0, 2), (0, 1)]
+    xs = [x1, x2, x3]
+
+    def apply(u):
+        eh = torch.stack([0.5j * (xs[i] * u[j] + xs[j] * u[i]) for i, j in pairs])
+        e = torch.fft.irfftn(eh, s=(n, n, n), dim=(-3, -2, -1))
+        tr = e[0] + e[1] + e[2]
+        sig = torch.stack([lam_t * tr + 2 * mu_t * e[0], lam_t * tr + 2 * mu_t * e[1], lam_t * tr + 2 * mu_t * e[2],
+                           2 * mu_t * e[3], 2 * mu_t * e[4], 2 * mu_t * e[5]])
+        sh = torch.fft.rfftn(sig, dim=(-3, -2, -1))
+        q0 = xs[0] * sh[0] + xs[1] * sh[5] + xs[2] * sh[4]
+        q1 = xs[0] * sh[5] + xs[1] * sh[1] + xs[2] * sh[3]
+        q2 = xs[0] * sh[4] + xs[1] * sh[3] + xs[2] * sh[2]
+        return torch.stack([q0, q1, q2]) * (-1j / n ** 3)
+
+    for _ in range(3):
+        apply(u)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        apply(u)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    return {"what": "torch.fft (cuFFT) + torch element-wise ops, K u only (no CG vector work), FP32, 256^3, 1 RHS",
+            "ms_per_application": ms, "voxel_applications_per_s": n ** 3 / (ms * 1e-3)}
+
+
 # ------------------------------------------------------------------ other configurations
 def _timed(fn):
     import torch
@@ -551,6 +602,10 @@ def our_arm(args, rank, world, local_rank):
     op256 = None
     if rank == 0 and not args.skip_256:
         op256 = operator_256(torch, dbfft, peak)
+        try:
+            op256["cufft_comparison"] = cufft_operator_256(torch)
+        except Exception as exc:  # comparison only; never fails the benchmark
+            op256["cufft_comparison"] = {"error": str(exc)[:200]}
 
     cpu = None
     if rank == 0 and world == 1 and not args.skip_cpu:
@@ -613,7 +668,9 @@ def main():
         from paper_1905_12725_gb300 import dbfft
         torch.cuda.set_device(0)
         if args.case == "op256":
-            print(json.dumps(operator_256(torch, dbfft, _peaks()[0], iters=args.steps)), flush=True)
+            r = operator_256(torch, dbfft, _peaks()[0], iters=args.steps)
+            r["cufft_comparison"] = cufft_operator_256(torch)
+            print(json.dumps(r), flush=True)
         elif args.case in ("c1", "c3", "c3fp64", "c4", "c4fp64", "c5"):
             prec = dbfft.DBFFT_FP64 if args.case.endswith("fp64") else dbfft.DBFFT_MIXED
             res = {"c1": lambda: case_c1(), "c3": lambda: case_c3(prec), "c3fp64": lambda: case_c3(prec),

@@ -306,8 +306,8 @@ const char* dbfft_tuning(const dbfft_ctx* ctx);
  * 1 = persistent CTAs looping over tiles of `lines` grid lines with two
  * shared-memory stages filled and drained by bulk copies; 2 = the same with
  * one stage (half the shared memory per CTA). radix: 8 or 16 (FP32), 4
- * (FP64), or 32 with the plain kernel when n3 <= 128 (FP32) / 64 (FP64):
- * one thread per grid line, or per half line when n3 = 128
+ * (FP64), or 32 with the plain kernel when n3 <= 256 (FP32) / 64 (FP64):
+ * one thread per grid line, or 32 values of a line per thread beyond
  * (FP32) / 4 (FP64); lines: grid lines per CTA (per tile when pipelined;
  * then even and dividing n1 * n2). Returns DBFFT_E_ARG for a shape that does
  * not exist or does not fit in shared memory; the results of the operator do

@@ -1105,12 +1105,14 @@ void tune_pass3(dbfft_ctx* ctx, int pi_, cplx<T>* W) {
     // pass 3: radix x lines per CTA (radix 32 = one thread per line, lines of up to 32 complex values)
     const int radices[3] = {8, 16, 32};
     const int radices64[2] = {4, 32};
-    const bool r32 = sizeof(T) == 4 ? ctx->n3 <= 128 : ctx->n3 <= 64;
+    const bool r32 = sizeof(T) == 4 ? ctx->n3 <= 256 : ctx->n3 <= 64;
     const int nrad = sizeof(T) == 4 ? (r32 ? 3 : 2) : (r32 ? 2 : 1);
     float best = 1e30f;
     int bestR = ctx->ax3_radix[pi_], bestL = 0;
+    std::string per_radix;
     for (int ri = 0; ri < nrad; ++ri) {
         const int R = sizeof(T) == 4 ? radices[ri] : radices64[ri];
+        float bR = 1e30f;
         const int Ld = ax3_lines(ctx->n3, ctx->nc, ctx->RB, sizeof(T) == 8, 1, R);
         const int cand[] = {1, 2, 3, 4, 6, 8, 12, 16, 24, 32, Ld};
         for (int L : cand) {
@@ -1122,16 +1124,20 @@ void tune_pass3(dbfft_ctx* ctx, int pi_, cplx<T>* W) {
             else a3.macroW = ctx->macroW;
             a3.tan_in = reinterpret_cast<const T*>(ctx->tan);
             const float ms = time_launch(ctx, [&] { return launch_ax3<T>(opk_apply(ctx), a3, ctx->stream); });
+            bR = std::min(bR, ms);
             if (ms < best * 0.98f) {
                 best = ms;
                 bestR = R;
                 bestL = L;
             }
         }
+        std::snprintf(buf, sizeof(buf), "%s%d: %.4f", per_radix.empty() ? "" : ", ", R, bR);
+        per_radix += buf;
     }
     ctx->ax3_radix[pi_] = bestR;
     ctx->ax3_L[pi_] = bestL;
-    std::snprintf(buf, sizeof(buf), "pass3 radix %d lines %d (%.4f ms); ", bestR, bestL, best);
+    std::snprintf(buf, sizeof(buf), "pass3 radix %d lines %d (%.4f ms; best per radix %s); ", bestR, bestL, best,
+                  per_radix.c_str());
     ctx->tune_note += buf;
     // the pipelined pass for the CG applications: radix x lines per tile
     {
@@ -1317,7 +1323,7 @@ const char* dbfft_tuning(const dbfft_ctx* ctx) { return ctx ? ctx->tune_note.c_s
 dbfft_status dbfft_set_pass3_shape(dbfft_ctx* ctx, int fp64, int pipelined, int radix, int lines) {
     if (!ctx || (fp64 != 0 && fp64 != 1) || lines < 1) return DBFFT_E_ARG;
     const bool dbl = fp64 == 1;
-    const bool r32 = radix == 32 && !pipelined && ctx->n3 <= (dbl ? 64 : 128);
+    const bool r32 = radix == 32 && !pipelined && ctx->n3 <= (dbl ? 64 : 256);
     if (dbl ? (radix != 4 && !r32) : (radix != 8 && radix != 16 && !r32))
         return fail(ctx, DBFFT_E_ARG,
                     "radix: 8 or 16 (FP32), 4 (FP64), or 32 with the plain kernel (n3 <= 128 FP32, <= 64 FP64)");

@@ -33,9 +33,10 @@ static cudaError_t ax3_n(const Ax3Args<T>& a, cudaStream_t s) {
     if constexpr (sizeof(T) == 4) {
         if (a.radix == 16) return ax3_nr<T, N3, NC, OPK, 16>(a, s);
     }
-    // radix 32: one thread per line (N3/2 <= 32) or per half line (N3 = 128, FP32);
-    // for the operator applications (and the linear residual chain in FP64)
-    if constexpr ((sizeof(T) == 4 ? N3 <= 128 : N3 <= 64) && (OpInfo<OPK>::apply)) {
+    // radix 32: one thread per line (N3/2 <= 32), or 32 values of a line per
+    // thread (N3 = 128, 256; FP32); for the operator applications (and the
+    // linear residual chain in FP64)
+    if constexpr ((sizeof(T) == 4 ? N3 <= 256 : N3 <= 64) && (OpInfo<OPK>::apply)) {
         if (a.radix == 32 && !a.pipe) return ax3_nr<T, N3, NC, OPK, 32>(a, s);
     }
     return ax3_nr<T, N3, NC, OPK, 8>(a, s);

@@ -103,7 +103,8 @@ def test_pcg_with_pipelined_pass3_equals_plain(precision):
 
 @pytest.mark.parametrize("shape,B,nmat,lines,fp64", [((16, 16, 64), 1, 1, 8, 0), ((8, 32, 32), 3, 3, 5, 0),
                                                      ((32, 16, 16), 6, 1, 7, 0), ((16, 8, 8), 2, 2, 3, 0),
-                                                     ((8, 8, 128), 2, 1, 4, 0), ((16, 8, 64), 2, 1, 3, 1),
+                                                     ((8, 8, 128), 2, 1, 4, 0), ((8, 8, 256), 1, 1, 12, 0),
+                                                     ((16, 8, 64), 2, 1, 3, 1),
                                                      ((8, 16, 32), 1, 1, 6, 1)])
 def test_radix32_pass3_matches_oracle(shape, B, nmat, lines, fp64):
     """Radix 32: one thread holds a whole line (no exchange) for n3 <= 64, or half a
