@@ -43,8 +43,11 @@ WORKLOAD = "64^3 random-sphere composite (r=6 vox, vf 0.25, contrast 100, nu 0.3
 
 # DRAM traffic per launch of the dominant kernel from an ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum), keyed by kernel; valid only
-# for the kernel sources it was taken on.
-NCU_TRAFFIC = {}
+# for the kernel sources it was taken on (hash of KERNEL_SOURCES below).
+# pass3_tangent_f32: k_axis3<float, 64, 6, OP_ISO, 32> of the 64^3 x 6 RHS step,
+# `ncu --set full` with caches flushed before the launch (39.53 MB read +
+# 0.71 MB written; inside the timed step the fields are L2-resident).
+NCU_TRAFFIC = {"pass3_tangent_f32": {"bytes": 39525632 + 713472, "src": "fb0f092b495f17f2"}}
 
 
 def _peaks():
@@ -56,11 +59,18 @@ def _peaks():
         return 6800.0, "fallback"
 
 
-def _sources_hash():
+# sources that make up each profiled pass's kernels (a change invalidates its ncu counters)
+KERNEL_SOURCES = {
+    "pass3_tangent_f32": ["dbfft_dev.cuh", "fft.cuh", "passes.cuh", "constitutive.cuh", "pass3.cuh", "pass3_pipe.cuh",
+                          "tma.cuh", "launch.h", "k_ax3_impl.cuh", "k_ax3_f32.cu", "k_ax3p_impl.cuh", "k_ax3p_f32.cu"],
+}
+
+
+def _sources_hash(files=None):
     import hashlib
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_1905_12725_gb300", "csrc")
-    for n in sorted(os.listdir(d)):
+    for n in sorted(files if files is not None else os.listdir(d)):
         with open(os.path.join(d, n), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
@@ -551,9 +561,9 @@ def our_arm(args, rank, world, local_rank):
     per_launch_ms = de["ms"] / de["launches"]
     per_launch_bytes = de["bytes"] / de["launches"]
     achieved = per_launch_bytes / (per_launch_ms * 1e-3) / 1e9
-    src = _sources_hash()
     tr = NCU_TRAFFIC.get(dname)
-    traffic = tr["bytes"] if tr and tr.get("src") == src else None
+    traffic = (tr["bytes"] if tr and dname in KERNEL_SOURCES and tr.get("src") == _sources_hash(KERNEL_SOURCES[dname])
+               else None)
     kernels = {k: {"launches": v["launches"], "ms": v["ms"],
                    "GBps": (v["bytes"] / (v["ms"] * 1e-3) / 1e9) if v["ms"] > 0 and v["bytes"] > 0 else None}
                for k, v in sorted(prof.items(), key=lambda kv: -kv[1]["ms"])}

@@ -4,7 +4,7 @@
 // small strain, linear isotropic phases, full strain control) without a
 // context: the work buffer of the passes and the frequency / twiddle tables
 // live in file-scope static device arrays, so the call itself never asks
-// the driver (or any allocator) for memory. Host code never dereferences
+// the CUDA runtime (or any allocator) for memory. Host code never dereferences
 // those arrays: their device addresses are looked up once per device with
 // cudaGetSymbolAddress and passed to the kernels.
 #include <cmath>
