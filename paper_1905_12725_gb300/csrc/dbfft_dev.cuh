@@ -71,6 +71,21 @@ __host__ __device__ __forceinline__ unsigned fastdiv(unsigned n, const FastDiv& 
     return (t + ((n - t) >> f.s1)) >> f.s2;
 }
 
+// Programmatic dependent launch: a kernel launched with programmatic stream
+// serialisation may start while its predecessor finishes; it waits here,
+// before touching anything the predecessor wrote (a no-op otherwise).
+__device__ __forceinline__ void pdl_wait() {
+#if defined(__CUDA_ARCH__)
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+#endif
+}
+// Let the successor start launching (called once a block's main work is issued).
+__device__ __forceinline__ void pdl_trigger() {
+#if defined(__CUDA_ARCH__)
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+#endif
+}
+
 struct Dims {
     int n1, n2, n3, h, m;   // h = n3/2 + 1, m = n3/2
     long long H;            // n1 n2 h

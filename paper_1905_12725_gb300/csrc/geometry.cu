@@ -4,6 +4,8 @@
 
 namespace dbfft {
 
+thread_local bool g_pdl_launch = false;
+
 bool supported_len(int n) { return n == 8 || n == 16 || n == 32 || n == 64 || n == 128 || n == 256; }
 
 static int radix_for(int n, bool dbl) { return radix_ax2(n, dbl); }

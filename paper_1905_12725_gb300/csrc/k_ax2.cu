@@ -24,8 +24,7 @@ static cudaError_t fft_n(Ax2Args<T> a, int axis, cudaStream_t s) {
     const dim3 block(TW, P);
     const dim3 grid((unsigned)((a.ncols + TW - 1) / TW));
     const size_t smem = (ColFFT<T, N, R, DIR>::NST > 1) ? (size_t)N * TW * sizeof(cplx<T>) : 0;
-    k_fft_strided<T, N, DIR><<<grid, block, smem, s>>>(a);
-    return cudaGetLastError();
+    return launch_k(k_fft_strided<T, N, DIR>, grid, block, smem, s, a);
 }
 
 #define DBFFT_FFT(N, AX) case N: return dir > 0 ? fft_n<T, N, +1>(a, AX, s) : fft_n<T, N, -1>(a, AX, s);

@@ -24,8 +24,7 @@ static cudaError_t ax3_nr(const Ax3Args<T>& a, cudaStream_t s) {
         if (e != cudaSuccess) return e;
     }
     if (smem > (size_t)max_dyn) return cudaErrorInvalidConfiguration;
-    k_axis3<T, N3, NC, OPK, RW><<<grid, threads, smem, s>>>(a);
-    return cudaGetLastError();
+    return launch_k(k_axis3<T, N3, NC, OPK, RW>, grid, dim3(threads), smem, s, a);
 }
 
 template <typename T, int N3, int NC, int OPK>

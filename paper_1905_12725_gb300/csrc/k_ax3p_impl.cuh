@@ -46,8 +46,7 @@ static cudaError_t pipe_nrs(const Ax3Args<T>& a, cudaStream_t s) {
     long long per_group = ((long long)occ * nsm + ngroups - 1) / ngroups;
     if (per_group > ntiles) per_group = ntiles;
     if (per_group < 1) per_group = 1;
-    kern<<<dim3((unsigned)per_group, (unsigned)ngroups), threads, (size_t)smem, s>>>(a);
-    return cudaGetLastError();
+    return launch_k(kern, dim3((unsigned)per_group, (unsigned)ngroups), dim3(threads), (size_t)smem, s, a);
 }
 
 // a.pipe: 1 = two shared-memory stages, 2 = one stage

@@ -4,6 +4,31 @@
 #pragma once
 #include "pass3.cuh"
 
+#include <utility>
+
+namespace dbfft {
+// Kernels of the PCG loop are launched with programmatic stream serialisation
+// while this is set (the CG graph body is captured that way).
+extern thread_local bool g_pdl_launch;
+
+template <typename... KArgs, typename... Args>
+cudaError_t launch_k(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, Args&&... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    if (g_pdl_launch) {
+        attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr[0].val.programmaticStreamSerializationAllowed = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+    }
+    return cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
+}
+}  // namespace dbfft
+
 namespace dbfft {
 
 // Launch geometry shared by the launchers and the buffer sizing.

@@ -101,6 +101,8 @@ __host__ __device__ constexpr int ax3_slot_cplx() {
 template <typename T, int N3, int NC, int OPK, int RW>
 __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? (RW == 32 ? 2 : (RW == 16 ? 3 : 4)) : ((RW == 32 || OPK == OP_CP_UPDATE || OPK == OP_CP_UPDATE32 || OPK == OP_NH_UPDATE) ? 1 : 2))) k_axis3(Ax3Args<T> a) {
     constexpr bool CPU_ = OPK == OP_CP_UPDATE || OPK == OP_CP_UPDATE32;  // crystal-plasticity update
+    pdl_wait();
+    pdl_trigger();  // the successor may start launching; it waits for this grid to finish
     constexpr int M = N3 / 2;
     constexpr int H = M + 1;
     constexpr int R = RadixAx3<T, M, RW>::value;

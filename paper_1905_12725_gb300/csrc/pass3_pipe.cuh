@@ -98,6 +98,8 @@ struct PipePlan {
 template <typename T, int N3, int NC, int OPK, int RW, int NS>
 __global__ void __launch_bounds__(256) k_axis3_pipe(Ax3Args<T> a) {
     static_assert(OpInfo<OPK>::apply, "the pipelined pass serves the CG applications");
+    pdl_wait();
+    pdl_trigger();  // the successor may start launching; it waits for this grid to finish
     constexpr int M = N3 / 2;
     constexpr int H = M + 1;
     constexpr int R = RadixAx3<T, M, RW>::value;

@@ -220,6 +220,8 @@ __device__ __forceinline__ FreqIdx freq_idx(const Dims& d, long long i) {
 // from r, together with the deferred iterate update x += alpha_prev p_old.
 template <typename T, int NC, int MODE>
 __global__ void __launch_bounds__(PW_THREADS) k_grad(Ax1InvArgs<T> a) {
+    pdl_wait();
+    pdl_trigger();  // the successor may start launching; it waits for this grid to finish
     const int b = blockIdx.y;
     if (MODE == AX1_CG && a.cg[b].done) return;
     const Dims& d = a.d;
@@ -288,6 +290,8 @@ struct Ax2Args {
 
 template <typename T, int N, int DIR>
 __global__ void __launch_bounds__(512) k_fft_strided(Ax2Args<T> a) {
+    pdl_wait();
+    pdl_trigger();  // the successor may start launching; it waits for this grid to finish
     constexpr int R = RadixFor<T, N>::value;
     constexpr int P = N / R;
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -355,6 +359,8 @@ template <typename T, int NC, int MODE>
 __global__ void __launch_bounds__(PW_THREADS) k_div(Ax1FwdArgs<T> a) {
     __shared__ double red[32 * 2];
     __shared__ bool is_last;
+    pdl_wait();
+    pdl_trigger();  // the successor may start launching; it waits for this grid to finish
     const int b = blockIdx.y;
     const int tid = threadIdx.x;
     const Dims& d = a.d;
