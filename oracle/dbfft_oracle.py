@@ -49,7 +49,8 @@ R9  Newton stops when eps_eq = ||div P||_L2 / ||<P>|| <= newton_tol and the
 R10 Preconditioner refresh: linear problems use the mean stiffness; Newton
     uses the mean tangent at the first iterate of each increment.
 R13 Compressible Neo-Hookean (not in the paper): W = mu/2 (tr F^T F - 3) -
-    mu ln J + lam/2 (ln J)^2.
+    mu ln J + lam/2 (ln J)^2. St. Venant-Kirchhoff (the paper's porous-matrix
+    law): W = lam/2 (tr E)^2 + mu E:E, E = (F^T F - I)/2.
 R14 Small-strain power-law crystal plasticity (replaces the paper's model,
     whose parameters are not given): backward Euler on the stress.
 """
@@ -509,6 +510,38 @@ def neo_hooke_energy(F, mu, lam):
     return 0.5 * mu * (I1 - 3.0) - mu * lnJ + 0.5 * lam * lnJ ** 2
 
 
+def svk(F, mu, lam):
+    """St. Venant-Kirchhoff law (the matrix of the paper's porous hyperelastic
+    example, Sec. 3): W = lam/2 (tr E)^2 + mu E:E with E = (F^T F - I)/2.
+
+    P = F S, S = lam tr(E) I + 2 mu E;
+    K_iJkL = d_ik S_JL + lam F_iJ F_kL + mu (F_iL F_kJ + (F F^T)_ik d_JL).
+    F [3,3,...]; mu, lam broadcastable to F[0,0]. Returns P, K like neo_hooke.
+    """
+    Fm = np.moveaxis(F, (0, 1), (-2, -1))
+    d = np.eye(3)
+    E = 0.5 * (np.swapaxes(Fm, -1, -2) @ Fm - d)
+    mu_ = np.asarray(mu)[..., None, None]
+    lam_ = np.asarray(lam)[..., None, None]
+    S = lam_ * np.trace(E, axis1=-2, axis2=-1)[..., None, None] * d + 2.0 * mu_ * E
+    P = Fm @ S
+    B = Fm @ np.swapaxes(Fm, -1, -2)
+    lam4 = np.asarray(lam)[..., None, None, None, None]
+    mu4 = np.asarray(mu)[..., None, None, None, None]
+    K = (np.einsum("ik,...jl->...ijkl", d, S) + lam4 * np.einsum("...ij,...kl->...ijkl", Fm, Fm)
+         + mu4 * (np.einsum("...il,...kj->...ijkl", Fm, Fm) + np.einsum("...ik,jl->...ijkl", B, d)))
+    P = np.moveaxis(P, (-2, -1), (0, 1))
+    K = np.moveaxis(K, (-4, -3, -2, -1), (0, 1, 2, 3))
+    return P, K
+
+
+def svk_energy(F, mu, lam):
+    Fm = np.moveaxis(F, (0, 1), (-2, -1))
+    E = 0.5 * (np.swapaxes(Fm, -1, -2) @ Fm - np.eye(3))
+    trE = np.trace(E, axis1=-2, axis2=-1)
+    return 0.5 * lam * trE ** 2 + mu * np.einsum("...ij,...ij->...", E, E)
+
+
 # --------------------------------------------------------------------------
 # Small-strain power-law FCC crystal plasticity (R14)
 # --------------------------------------------------------------------------
@@ -716,6 +749,13 @@ def newton_increments(prob: Problem, material, targets, newton_tol=1e-8, load_to
 def neo_hooke_material(mu_field, lam_field):
     def material(F, state):
         P, K = neo_hooke(F, mu_field, lam_field)
+        return P, FullTangent(K), state
+    return material
+
+
+def svk_material(mu_field, lam_field):
+    def material(F, state):
+        P, K = svk(F, mu_field, lam_field)
         return P, FullTangent(K), state
     return material
 

@@ -369,13 +369,36 @@ def test_neo_hooke_stress_and_tangent_by_finite_differences():
     assert np.abs(K0 - o.iso_stiffness(lam, mu)).max() < 1e-14
 
 
-def _laminate_finite_reference(f, mu_p, lam_p, Fbar, mask_stress=None):
+def test_svk_stress_and_tangent_by_finite_differences():
+    g = np.random.default_rng(6)
+    F = np.eye(3) + 0.25 * g.standard_normal((3, 3))
+    mu, lam = 0.9, 1.7
+    P, K = o.svk(F, mu, lam)
+    h = 1e-6
+    for k in range(3):
+        for l in range(3):
+            dF = np.zeros((3, 3))
+            dF[k, l] = h
+            dW = (o.svk_energy(F + dF, mu, lam) - o.svk_energy(F - dF, mu, lam)) / (2 * h)
+            assert abs(dW - P[k, l]) < 1e-8
+            dP = (o.svk(F + dF, mu, lam)[0] - o.svk(F - dF, mu, lam)[0]) / (2 * h)
+            assert np.abs(dP - K[:, :, k, l]).max() < 1e-7
+    # major symmetry, objectivity, and the small-strain limit
+    assert np.abs(K - np.transpose(K, (2, 3, 0, 1))).max() < 1e-13
+    Q = o.quat_to_rot(np.array([0.3, -0.6, 0.2, 0.7]) / np.linalg.norm([0.3, -0.6, 0.2, 0.7]))
+    assert np.abs(o.svk(Q @ F, mu, lam)[0] - Q @ P).max() < 1e-13
+    _, K0 = o.svk(np.eye(3), mu, lam)
+    assert np.abs(K0 - o.iso_stiffness(lam, mu)).max() < 1e-14
+
+
+def _laminate_finite_reference(f, mu_p, lam_p, Fbar, mask_stress=None, law=None):
     """Rank-one laminate: F_p = Fbar + a_p x e1, P_p e1 = t, sum f_p a_p = 0 (Newton)."""
+    law = o.neo_hooke if law is None else law
     n = np.array([1.0, 0, 0])
     a = np.zeros((2, 3))
     for _ in range(50):
         Fs = [Fbar + np.outer(a[p], n) for p in range(2)]
-        PK = [o.neo_hooke(Fs[p], mu_p[p], lam_p[p]) for p in range(2)]
+        PK = [law(Fs[p], mu_p[p], lam_p[p]) for p in range(2)]
         # unknowns a_0, a_1 (6); equations: P_0 n - P_1 n = 0 (3), f0 a0 + f1 a1 = 0 (3)
         R = np.concatenate([PK[0][0] @ n - PK[1][0] @ n, f[0] * a[0] + f[1] * a[1]])
         A = [np.einsum("j,ijkl,l->ik", n, PK[p][1], n) for p in range(2)]
@@ -387,7 +410,7 @@ def _laminate_finite_reference(f, mu_p, lam_p, Fbar, mask_stress=None):
         if np.abs(d).max() < 1e-15:
             break
     Fs = [Fbar + np.outer(a[p], n) for p in range(2)]
-    return sum(f[p] * o.neo_hooke(Fs[p], mu_p[p], lam_p[p])[0] for p in range(2))
+    return sum(f[p] * law(Fs[p], mu_p[p], lam_p[p])[0] for p in range(2))
 
 
 def test_finite_strain_laminate_against_rank_one_solution():
@@ -403,6 +426,22 @@ def test_finite_strain_laminate_against_rank_one_solution():
     res, _ = o.newton_increments(prob, o.neo_hooke_material(mu, lam), targets,
                                  newton_tol=1e-12, load_tol=1e-12, eta=1e-6)
     ref = _laminate_finite_reference(f, mu_p, lam_p, Fbar)
+    assert np.abs(res[-1]["stress_bar"] - ref).max() < 1e-11 * np.abs(ref).max()
+
+
+def test_finite_strain_laminate_svk_against_rank_one_solution():
+    shape = (8, 4, 4)
+    mu_p, lam_p = [1.0, 15.0], [1.5, 20.0]
+    ph = (np.arange(8) >= 6).astype(int)  # even widths: the exact field has no Nyquist content
+    mu = np.broadcast_to(np.array(mu_p)[ph][:, None, None], shape)
+    lam = np.broadcast_to(np.array(lam_p)[ph][:, None, None], shape)
+    f = np.array([6, 2]) / 8.0
+    prob = o.Problem(shape, "finite")
+    Fbar = np.array([[1.08, 0.04, 0.0], [0.01, 0.98, 0.02], [0.0, -0.03, 1.01]])
+    targets = [np.eye(3) + (Fbar - np.eye(3)) * (k + 1) / 2 for k in range(2)]
+    res, _ = o.newton_increments(prob, o.svk_material(mu, lam), targets,
+                                 newton_tol=1e-12, load_tol=1e-12, eta=1e-6)
+    ref = _laminate_finite_reference(f, mu_p, lam_p, Fbar, law=o.svk)
     assert np.abs(res[-1]["stress_bar"] - ref).max() < 1e-11 * np.abs(ref).max()
 
 
