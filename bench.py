@@ -397,6 +397,34 @@ def case_c3(precision, n=128, n_inc=20):
             "P_bar_final": s.homogenized_stress()[0].tolist(), "phase_sha256": synth.sha256(c["phase"])}
 
 
+def case_porous(precision, n=64, n_inc=5, stretch=2.0):
+    """Porous St. Venant-Kirchhoff matrix (E 70, nu 0.3; 5 pores of total porosity 0.2 with 1/100 of the
+    stiffness), stretched to F11 = 2 in 5 increments with every other component of F held at its
+    undeformed value; Newton to 1e-6."""
+    from paper_1905_12725_gb300 import dbfft, synth
+    c = synth.porous_svk(n=n)
+    tgt = np.eye(3)
+    tgt[0, 0] = stretch
+    s = dbfft.Solver((n,) * 3, c["phase"], dbfft.svk_phases(c["mu"], c["lam"]), tgt[None],
+                     kinematics=dbfft.DBFFT_FINITE, precision=precision, n_increments=n_inc, newton_tol=1e-6,
+                     load_tol=1e-10, eta_inner=1e-3 if precision else 1e-4, max_newton=40, max_iter=20000)
+    s.autotune(TUNE_CACHE)
+    incs = []
+    t_all = 0.0
+    cg_all = 0
+    for k in range(n_inc):
+        rep, dt = _timed(lambda: s.solve_increment(k))
+        t_all += dt
+        cg_all += rep["cg_iters"]
+        P = s.homogenized_stress()[0]
+        incs.append({"inc": k, "newton": rep["newton_iters"], "cg": rep["cg_iters"], "eps_eq": rep["eps_eq"],
+                     "P11": P[0, 0], "ms": dt * 1e3})
+    return {"case": f"porous SVK {n}^3, 5 pores, porosity {float(c['phase'].mean()):.4f}, F11 -> {stretch}",
+            "precision": "mixed" if precision else "fp64", "wall_s": t_all, "cg_iters": cg_all,
+            "voxel_cg_iters_per_s": n ** 3 * cg_all / t_all, "increments": incs,
+            "P_bar_final": s.homogenized_stress()[0].tolist(), "phase_sha256": synth.sha256(c["phase"])}
+
+
 def case_c4(precision, n=256, n_inc=40, only=None):
     """256^3 Voronoi polycrystal (500 grains), power-law CP, eps_xx to 2% at 1e-3/s in 40 increments."""
     from paper_1905_12725_gb300 import dbfft, synth
@@ -668,10 +696,12 @@ def main():
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-256", action="store_true")
     ap.add_argument("--case", default="",
-                    choices=["", "op256", "c2", "c1", "c3", "c3fp64", "c4", "c4fp64", "c5"],
+                    choices=["", "op256", "c2", "c1", "c3", "c3fp64", "c4", "c4fp64", "c5", "porous",
+                             "porousfp64"],
                     help="run one sub-measurement only: op256 = 256^3 FP32 CG pass chain, c2 = one mixed "
                          "batched 64^3 solve (profiler captures); c1, c3[fp64], c4[fp64], c5 = the other "
-                         "configurations at full size")
+                         "configurations at full size; porous[fp64] = the porous St. Venant-Kirchhoff "
+                         "stretch (64^3)")
     args = ap.parse_args()
     if args.case:
         import torch
@@ -681,11 +711,12 @@ def main():
             r = operator_256(torch, dbfft, _peaks()[0], iters=args.steps)
             r["cufft_comparison"] = cufft_operator_256(torch)
             print(json.dumps(r), flush=True)
-        elif args.case in ("c1", "c3", "c3fp64", "c4", "c4fp64", "c5"):
+        elif args.case in ("c1", "c3", "c3fp64", "c4", "c4fp64", "c5", "porous", "porousfp64"):
             prec = dbfft.DBFFT_FP64 if args.case.endswith("fp64") else dbfft.DBFFT_MIXED
             res = {"c1": lambda: case_c1(), "c3": lambda: case_c3(prec), "c3fp64": lambda: case_c3(prec),
                    "c4": lambda: case_c4(prec), "c4fp64": lambda: case_c4(prec, only=args.steps),
-                   "c5": lambda: case_c5()}[args.case]()
+                   "c5": lambda: case_c5(), "porous": lambda: case_porous(prec),
+                   "porousfp64": lambda: case_porous(prec)}[args.case]()
             print(json.dumps(res, default=float), flush=True)
         else:
             s = make_solver(workload_inputs(), dbfft.DBFFT_MIXED, 6)

@@ -74,7 +74,10 @@ enum { DBFFT_FP64 = 0, DBFFT_MIXED = 1 };        /* precision of the solve      
 enum {                                           /* constitutive model of a phase    */
     DBFFT_ISO_ELASTIC = 0,     /* linear isotropic elasticity (E, nu), small strain     */
     DBFFT_NEO_HOOKE = 1,       /* compressible Neo-Hookean (mu, lambda), finite strain  */
-    DBFFT_CP_FCC_POWERLAW = 2  /* small-strain FCC crystal plasticity, power-law flow   */
+    DBFFT_CP_FCC_POWERLAW = 2, /* small-strain FCC crystal plasticity, power-law flow   */
+    DBFFT_SVK = 3              /* St. Venant-Kirchhoff (mu, lambda), finite strain: the
+                                  porous hyperelastic example of Sec. 3; needs mu > 0 and
+                                  3 lambda + 2 mu > 0                                   */
 };
 
 /* Problem size and solver settings. */
@@ -97,9 +100,10 @@ typedef struct {
 
 /* One phase. Only the fields of its model are read. */
 typedef struct {
-    int model;                /* DBFFT_ISO_ELASTIC, DBFFT_NEO_HOOKE, DBFFT_CP_FCC_POWERLAW */
+    int model;                /* DBFFT_ISO_ELASTIC, DBFFT_NEO_HOOKE, DBFFT_CP_FCC_POWERLAW,
+                                 DBFFT_SVK                                                 */
     double E, nu;             /* ISO_ELASTIC                                               */
-    double mu, lambda;        /* NEO_HOOKE                                                 */
+    double mu, lambda;        /* NEO_HOOKE and SVK: Lame constants                         */
     double C11, C12, C44;     /* CP: cubic stiffness in the crystal frame                  */
     double gdot0, m, tau_c;   /* CP: gdot = gdot0 |tau/tau_c|^(1/m) sign(tau)              */
     double quat[4];           /* CP: unit quaternion (w, x, y, z), crystal -> sample       */
@@ -162,7 +166,7 @@ enum {
  * tables. stream is a cudaStream_t (NULL: the legacy default stream).
  * Grid limits: see dbfft_grid.n. All phases must use one model kind, and
  * the kind must match the kinematics (ISO_ELASTIC and CP with SMALL,
- * NEO_HOOKE with FINITE). Errors: E_ARG, E_UNSUPPORTED_GRID, E_NOMEM,
+ * NEO_HOOKE and SVK with FINITE). Errors: E_ARG, E_UNSUPPORTED_GRID, E_NOMEM,
  * E_NONFINITE (a non-finite material parameter), E_CUDA.
  */
 dbfft_status dbfft_create(const dbfft_grid* grid, const dbfft_materials* mat,

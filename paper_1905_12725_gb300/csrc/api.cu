@@ -240,7 +240,7 @@ double mat_bytes(const dbfft_ctx* ctx, bool dbl, bool update) {
     const double t = dbl ? 8.0 : 4.0;
     if (!update) return (double)ctx->B * V * (2.0 + ctx->ntan * t);
     const double tw = ctx->prec == DBFFT_FP64 ? 8.0 : 4.0;
-    if (ctx->model == DBFFT_NEO_HOOKE) return (double)ctx->B * V * (2.0 + ctx->ntan * tw);
+    if (ctx->model != DBFFT_CP_FCC_POWERLAW) return (double)ctx->B * V * (2.0 + ctx->ntan * tw);
     return (double)ctx->B * V * (2.0 + ctx->ntan * tw + 4 * 6 * 8.0);
 }
 
@@ -551,10 +551,16 @@ template <typename T>
 Dims dims_of(dbfft_ctx* ctx) { return ctx->dims; }
 
 int opk_apply(const dbfft_ctx* ctx) {
-    return ctx->model == DBFFT_ISO_ELASTIC ? OP_ISO : (ctx->model == DBFFT_NEO_HOOKE ? OP_NH_APPLY : OP_CP_APPLY);
+    switch (ctx->model) {
+        case DBFFT_ISO_ELASTIC: return OP_ISO;
+        case DBFFT_NEO_HOOKE: return OP_NH_APPLY;
+        case DBFFT_SVK: return OP_SVK_APPLY;
+        default: return OP_CP_APPLY;
+    }
 }
 int opk_update(const dbfft_ctx* ctx) {
     if (ctx->model == DBFFT_CP_FCC_POWERLAW) return ctx->prec == DBFFT_MIXED ? OP_CP_UPDATE32 : OP_CP_UPDATE;
+    if (ctx->model == DBFFT_SVK) return OP_SVK_UPDATE;
     return ctx->model == DBFFT_ISO_ELASTIC ? OP_ISO : OP_NH_UPDATE;
 }
 
@@ -938,7 +944,7 @@ constexpr int kMeanTangentBlocks = 456;  // blocks per right-hand side of the me
 // Mean tangent of the current state -> preconditioner (R10), nonlinear only.
 dbfft_status refresh_precond(dbfft_ctx* ctx) {
     const int nblk = kMeanTangentBlocks;
-    const int kind = ctx->model == DBFFT_NEO_HOOKE ? 0 : 1;
+    const int kind = ctx->model == DBFFT_NEO_HOOKE ? 0 : (ctx->model == DBFFT_SVK ? 2 : 1);
     TRY(run(ctx, "mean_tangent", 0.0, [&] {
         if (ctx->prec == DBFFT_MIXED)
             return launch_mean_tangent<float>(kind, ctx->B, ctx->V, reinterpret_cast<const float*>(ctx->tan),
@@ -1441,8 +1447,8 @@ static dbfft_status create_impl(dbfft_ctx* ctx, const dbfft_grid* grid, const db
     ctx->model = mat->phases[0].model;
     for (int p = 0; p < mat->n_phases; ++p)
         if (mat->phases[p].model != ctx->model) return fail(ctx, DBFFT_E_ARG, "all phases must use one model kind");
-    if ((ctx->model == DBFFT_NEO_HOOKE) != (ctx->kin == DBFFT_FINITE))
-        return fail(ctx, DBFFT_E_ARG, "NEO_HOOKE needs FINITE kinematics; ISO_ELASTIC and CP need SMALL");
+    if ((ctx->model == DBFFT_NEO_HOOKE || ctx->model == DBFFT_SVK) != (ctx->kin == DBFFT_FINITE))
+        return fail(ctx, DBFFT_E_ARG, "NEO_HOOKE and SVK need FINITE kinematics; ISO_ELASTIC and CP need SMALL");
     if (ctx->model != DBFFT_ISO_ELASTIC && ctx->Rm != 1)
         return fail(ctx, DBFFT_E_ARG, "nonlinear models need one material map per right-hand side");
     if (!load || !load->target || load->n_increments < 1) return fail(ctx, DBFFT_E_ARG, "load");
@@ -1524,9 +1530,11 @@ static dbfft_status create_impl(dbfft_ctx* ctx, const dbfft_grid* grid, const db
             ctx->E_h[p] = ph.E;
             lam1[p] = ctx->lam_h[p] / ph.E;
             mu1[p] = ctx->mu_h[p] / ph.E;
-        } else if (ctx->model == DBFFT_NEO_HOOKE) {
+        } else if (ctx->model == DBFFT_NEO_HOOKE || ctx->model == DBFFT_SVK) {
             if (!std::isfinite(ph.mu) || !std::isfinite(ph.lambda)) return fail(ctx, DBFFT_E_NONFINITE, "non-finite mu or lambda");
             if (!(ph.mu > 0)) return fail(ctx, DBFFT_E_ARG, "mu > 0 required");
+            if (ctx->model == DBFFT_SVK && !(3.0 * ph.lambda + 2.0 * ph.mu > 0))
+                return fail(ctx, DBFFT_E_ARG, "3 lambda + 2 mu > 0 required");
             ctx->lam_h[p] = ph.lambda;
             ctx->mu_h[p] = ph.mu;
         } else if (ctx->model == DBFFT_CP_FCC_POWERLAW) {
@@ -1607,7 +1615,7 @@ static dbfft_status create_impl(dbfft_ctx* ctx, const dbfft_grid* grid, const db
                 sm += ctx->mu_h[p] * s;
             }
             iso_C(sl / ctx->V, sm / ctx->V, C);
-        } else if (ctx->model == DBFFT_NEO_HOOKE) {  // initial tangent K(I) = isotropic C
+        } else if (ctx->model == DBFFT_NEO_HOOKE || ctx->model == DBFFT_SVK) {  // initial tangent K(I) = isotropic C
             double sl = 0.0, sm = 0.0;
             for (long long v = 0; v < ctx->V; ++v) {
                 const int p = mat->phase_id[(size_t)g * ctx->V + v];
@@ -1688,7 +1696,7 @@ static dbfft_status create_impl(dbfft_ctx* ctx, const dbfft_grid* grid, const db
         return fail(ctx, DBFFT_E_NOMEM, "pinned host allocation failed");
     // nonlinear tangent and state
     if (ctx->model != DBFFT_ISO_ELASTIC) {
-        ctx->ntan = ctx->model == DBFFT_NEO_HOOKE ? 10 : 21;
+        ctx->ntan = ctx->model == DBFFT_NEO_HOOKE ? 10 : (ctx->model == DBFFT_SVK ? 15 : 21);
         const size_t tsz = ctx->prec == DBFFT_FP64 ? 8 : 4;
         TRY(dalloc(ctx, (size_t)ctx->B * ctx->V * ctx->ntan * tsz, &ctx->tan));
         if (ctx->model == DBFFT_CP_FCC_POWERLAW) {

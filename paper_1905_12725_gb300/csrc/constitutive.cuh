@@ -121,6 +121,62 @@ __device__ __forceinline__ void nh_apply(const T* tn, T mu, T lam, const T* G, T
         }
 }
 
+// St. Venant-Kirchhoff: E = (F^T F - I)/2, S = lam tr(E) I + 2 mu E,
+// P = F S. The tangent data are F (9) and S (6, order 11,22,33,23,13,12).
+// The law is defined for every F; a non-finite P is reported as a failure.
+__device__ __forceinline__ bool svk_stress(const double* F, double mu, double lam, double* P, double* tn) {
+    double C[6];  // F^T F, same component order as S
+    const int ci[6] = {0, 1, 2, 1, 0, 0}, cj[6] = {0, 1, 2, 2, 2, 1};
+#pragma unroll
+    for (int q = 0; q < 6; ++q)
+        C[q] = F[ci[q]] * F[cj[q]] + F[3 + ci[q]] * F[3 + cj[q]] + F[6 + ci[q]] * F[6 + cj[q]];
+    const double trE = 0.5 * (C[0] + C[1] + C[2] - 3.0);
+    double S[6];
+#pragma unroll
+    for (int q = 0; q < 6; ++q) S[q] = mu * (C[q] - (q < 3 ? 1.0 : 0.0)) + (q < 3 ? lam * trE : 0.0);
+    const double Sm[9] = {S[0], S[5], S[4], S[5], S[1], S[3], S[4], S[3], S[2]};
+    bool ok = true;
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            const double p = F[3 * i] * Sm[j] + F[3 * i + 1] * Sm[3 + j] + F[3 * i + 2] * Sm[6 + j];
+            ok = ok && isfinite(p);
+            P[3 * i + j] = p;
+        }
+#pragma unroll
+    for (int q = 0; q < 9; ++q) tn[q] = F[q];
+#pragma unroll
+    for (int q = 0; q < 6; ++q) tn[9 + q] = S[q];
+    return ok;
+}
+
+// dP = K(F) : G = G S + F dS with dS = lam tr(dE) I + 2 mu dE, dE = sym(F^T G).
+template <typename T>
+__device__ __forceinline__ void svk_apply(const T* tn, T mu, T lam, const T* G, T* out) {
+    T F[9];
+#pragma unroll
+    for (int q = 0; q < 9; ++q) F[q] = tn[q];
+    const T Sm[9] = {tn[9], tn[14], tn[13], tn[14], tn[10], tn[12], tn[13], tn[12], tn[11]};
+    T H[9];  // F^T G
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) H[3 * i + j] = F[i] * G[j] + F[3 + i] * G[3 + j] + F[6 + i] * G[6 + j];
+    const T tr = H[0] + H[4] + H[8];
+    T dS[9];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) dS[3 * i + j] = mu * (H[3 * i + j] + H[3 * j + i]) + (i == j ? lam * tr : T(0));
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+            out[3 * i + j] = G[3 * i] * Sm[j] + G[3 * i + 1] * Sm[3 + j] + G[3 * i + 2] * Sm[6 + j] +
+                             F[3 * i] * dS[j] + F[3 * i + 1] * dS[3 + j] + F[3 * i + 2] * dS[6 + j];
+}
+
 // sigma (W components 11,22,33,23,13,12) = C_mandel eps, 21-entry tangent.
 template <typename T>
 __device__ __forceinline__ void cp_apply(const T* tn, const T* e, T* s) {

@@ -11,6 +11,8 @@ cudaError_t launch_ax3<double>(int opk, const Ax3Args<double>& a, cudaStream_t s
         case OP_CP_UPDATE: return ax3_sz<double, 6, OP_CP_UPDATE>(a, s);
         case OP_CP_UPDATE32: return ax3_sz<double, 6, OP_CP_UPDATE32>(a, s);
         case OP_ADJ: return ax3_sz<double, 6, OP_ADJ>(a, s);
+        case OP_SVK_APPLY:
+        case OP_SVK_UPDATE: return launch_ax3_svk<double>(opk, a, s);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -131,7 +131,8 @@ template cudaError_t launch_precond_field<double>(const Dims&, const Freq<double
 // Mean of the fourth-order tangent K_ijkl over the voxels of one right-hand
 // side (81 components), from the stored tangent data:
 //   kind 0: Neo-Hookean data (F^-T, mu - lam ln J) with per-phase mu, lam;
-//   kind 1: 21-entry Mandel tangent.
+//   kind 1: 21-entry Mandel tangent;
+//   kind 2: St. Venant-Kirchhoff data (F, S) with per-phase mu, lam.
 template <typename TT>
 __global__ void k_mean_tangent(int kind, long long V, const TT* tan, const uint16_t* phase, const double* lam,
                                const double* mu, double* partials /* [B][gridDim.x][81] */) {
@@ -155,6 +156,30 @@ __global__ void k_mean_tangent(int kind, long long V, const TT* tan, const uint1
                         for (int L = 0; L < 3; ++L) {
                             double val = c1 * A[3 * i + L] * A[3 * k + J] + lam[ph] * A[3 * i + J] * A[3 * k + L];
                             if (i == k && J == L) val += mu[ph];
+                            loc[((i * 3 + J) * 3 + k) * 3 + L] += val;
+                        }
+        }
+        for (int q = 0; q < 81; ++q) atomicAdd(&acc[q], loc[q]);
+        __syncthreads();
+    } else if (kind == 2) {
+        // St. Venant-Kirchhoff, data (F, S):
+        // K_iJkL = d_ik S_JL + lam F_iJ F_kL + mu (F_iL F_kJ + (F F^T)_ik d_JL)
+        double loc[81];
+        for (int q = 0; q < 81; ++q) loc[q] = 0.0;
+        for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < V; v += (long long)gridDim.x * blockDim.x) {
+            const TT* t = tan + ((long long)b * V + v) * 15;
+            const int ph = phase[(long long)b * V + v];
+            double F[9];
+            for (int q = 0; q < 9; ++q) F[q] = (double)t[q];
+            const int sidx[9] = {0, 5, 4, 5, 1, 3, 4, 3, 2};
+            for (int i = 0; i < 3; ++i)
+                for (int J = 0; J < 3; ++J)
+                    for (int k = 0; k < 3; ++k)
+                        for (int L = 0; L < 3; ++L) {
+                            double val = lam[ph] * F[3 * i + J] * F[3 * k + L] + mu[ph] * F[3 * i + L] * F[3 * k + J];
+                            if (i == k) val += (double)t[9 + sidx[3 * J + L]];
+                            if (J == L)
+                                val += mu[ph] * (F[3 * i] * F[3 * k] + F[3 * i + 1] * F[3 * k + 1] + F[3 * i + 2] * F[3 * k + 2]);
                             loc[((i * 3 + J) * 3 + k) * 3 + L] += val;
                         }
         }

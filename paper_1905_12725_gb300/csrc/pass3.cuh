@@ -23,7 +23,9 @@ enum {
     OP_CP_APPLY = 3,   // sigma = C_tan (eps + macro), stored 21-entry Mandel tangent
     OP_CP_UPDATE = 4,  // backward-Euler crystal plasticity at eps = macro + eps~
     OP_ADJ = 5,        // dJ/dE(x) = (1/N) eps_adj : C1 : eps_fwd (no forward R2C)
-    OP_CP_UPDATE32 = 6 // OP_CP_UPDATE for an FP32 inner solve: FP32 Newton start, FP32 tangent
+    OP_CP_UPDATE32 = 6, // OP_CP_UPDATE for an FP32 inner solve: FP32 Newton start, FP32 tangent
+    OP_SVK_APPLY = 7,   // dP = K(F) : (G + macro) from the stored SVK tangent data (F, S)
+    OP_SVK_UPDATE = 8   // St. Venant-Kirchhoff P(F), F = macro (incl. I) + G; stores F and S
 };
 
 template <typename T>
@@ -66,7 +68,7 @@ struct Ax3Args {
 
 template <int OPK> struct OpInfo {
     static constexpr bool forward = OPK != OP_ADJ;
-    static constexpr bool apply = OPK == OP_ISO || OPK == OP_NH_APPLY || OPK == OP_CP_APPLY;
+    static constexpr bool apply = OPK == OP_ISO || OPK == OP_NH_APPLY || OPK == OP_CP_APPLY || OPK == OP_SVK_APPLY;
 };
 
 // Complex entries per slot buffer: room for the half-spectrum line (M + 1),
@@ -99,7 +101,7 @@ __host__ __device__ constexpr int ax3_slot_cplx() {
 // loads and stores are done cooperatively: for one (right-hand side,
 // component) the L lines of a CTA are L h contiguous complex values.
 template <typename T, int N3, int NC, int OPK, int RW>
-__global__ void __launch_bounds__(256, (sizeof(T) == 4 ? (RW == 32 ? 2 : (RW == 16 ? 3 : 4)) : ((RW == 32 || OPK == OP_CP_UPDATE || OPK == OP_CP_UPDATE32 || OPK == OP_NH_UPDATE) ? 1 : 2))) k_axis3(Ax3Args<T> a) {
+__global__ void __launch_bounds__(256, (sizeof(T) == 4 ? (RW == 32 ? 2 : (RW == 16 ? 2 : 3)) : ((RW == 32 || OPK == OP_CP_UPDATE || OPK == OP_CP_UPDATE32 || OPK == OP_NH_UPDATE || OPK == OP_SVK_UPDATE) ? 1 : 2))) k_axis3(Ax3Args<T> a) {
     constexpr bool CPU_ = OPK == OP_CP_UPDATE || OPK == OP_CP_UPDATE32;  // crystal-plasticity update
     pdl_wait();
     pdl_trigger();  // the successor may start launching; it waits for this grid to finish
@@ -129,12 +131,22 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? (RW == 32 ? 2 : (RW == 
     T* scratch = sbuf + (long long)NF * NSLOT * SB;
     // slot s = (ll * RB + rl) * NC + c ; field f at offset f * NSLOT
     auto slot_ptr = [&](int f, int sl) { return sbuf + ((long long)f * NSLOT + sl) * SB; };
-    auto rhs_done = [&](int rl) { return a.cg != nullptr && a.cg[g * RB + rl].done != 0; };
-    if (a.cg != nullptr) {  // every right-hand side of this group has stopped: nothing to do
-        bool all = true;
-        for (int rl = 0; rl < RB; ++rl) all = all && rhs_done(rl);
-        if (all) return;
+    // stopped right-hand sides of this group, read once (bit rl)
+    // (kept in shared memory, so that no register holds it through the kernel)
+    __shared__ unsigned s_done;
+    {
+        unsigned done_mask = 0;
+        if (a.cg != nullptr)
+            for (int rl = 0; rl < RB; ++rl) done_mask |= (a.cg[g * RB + rl].done != 0 ? 1u : 0u) << rl;
+        if (a.cg != nullptr && done_mask == (1u << RB) - 1u) return;  // the whole group has stopped
+        if (t == 0) s_done = done_mask;
+        __syncthreads();
     }
+    auto rhs_done = [&](int rl) { return (s_done >> rl) & 1u; };
+    // the macro parts of the group's right-hand sides, staged once per CTA
+    // (visible after the barrier that ends the load / C2R phase)
+    __shared__ T s_macro[8 * 9];
+    for (int i = t; i < RB * 9; i += nthr) s_macro[i] = a.macroW[(long long)g * RB * 9 + i];
 
     if (a.zero_in) {  // real-space input fields are zero: clear the real lines instead
         for (int i = t; i < NF * NSLOT * N3; i += nthr) {
@@ -210,7 +222,7 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? (RW == 32 ? 2 : (RW == 
                 T* f = slot_ptr(0, (lv * RB + rr) * NC) + x3;
                 T e[NC];
 #pragma unroll
-                for (int q = 0; q < NC; ++q) e[q] = f[q * SB] + a.macroW[bb * 9 + q];
+                for (int q = 0; q < NC; ++q) e[q] = f[q * SB] + s_macro[rr * 9 + q];
                 if constexpr (OPK == OP_ADJ) {
                     // dJ/dE = (1/N) eps_adj : C1 : eps_fwd, C1 = C / E: for this
                     // op the phase tables hold lam, mu per unit Young's modulus
@@ -237,7 +249,8 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? (RW == 32 ? 2 : (RW == 
                     for (int q = 0; q < NC; ++q) f[q * SB] = sg[q];
                 }
             }
-        } else if constexpr (OPK == OP_NH_APPLY) {
+        } else if constexpr (OPK == OP_NH_APPLY || OPK == OP_SVK_APPLY) {
+            constexpr int NT = OPK == OP_SVK_APPLY ? 15 : 10;  // tangent data per voxel
             const long long mv = (long long)mat * d.V + vox;
             const int ph = a.phase[mv];
             const T lam = a.lam[ph], mu = a.mu[ph];
@@ -247,10 +260,13 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? (RW == 32 ? 2 : (RW == 
                 T* f = slot_ptr(0, (lv * RB + rr) * NC) + x3;
                 T G[9];
 #pragma unroll
-                for (int q = 0; q < 9; ++q) G[q] = f[q * SB] + a.macroW[bb * 9 + q];
-                const T* tn = a.tan_in + ((long long)bb * d.V + vox) * 10;
+                for (int q = 0; q < 9; ++q) G[q] = f[q * SB] + s_macro[rr * 9 + q];
+                const T* tn = a.tan_in + ((long long)bb * d.V + vox) * NT;
                 T sg[9];
-                nh_apply<T>(tn, mu, lam, G, sg);
+                if constexpr (OPK == OP_SVK_APPLY)
+                    svk_apply<T>(tn, mu, lam, G, sg);
+                else
+                    nh_apply<T>(tn, mu, lam, G, sg);
                 if (a.cg) {
                     T en = T(0);
 #pragma unroll
@@ -260,20 +276,25 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? (RW == 32 ? 2 : (RW == 
 #pragma unroll
                 for (int q = 0; q < 9; ++q) f[q * SB] = sg[q];
             }
-        } else if constexpr (OPK == OP_NH_UPDATE) {
+        } else if constexpr (OPK == OP_NH_UPDATE || OPK == OP_SVK_UPDATE) {
+            constexpr int NT = OPK == OP_SVK_UPDATE ? 15 : 10;
             const long long mv = (long long)mat * d.V + vox;
             const int ph = a.phase[mv];
             for (int rr = 0; rr < RB; ++rr) {
                 const int bb = g * RB + rr;
                 T* f = slot_ptr(0, (lv * RB + rr) * NC) + x3;
-                double F[9], Pk[9], tn[10];
+                double F[9], Pk[9], tn[NT];
 #pragma unroll
-                for (int q = 0; q < 9; ++q) F[q] = (double)f[q * SB] + a.macroW[bb * 9 + q];
-                const bool ok = nh_stress(F, a.mu[ph], a.lam[ph], Pk, tn);
+                for (int q = 0; q < 9; ++q) F[q] = (double)f[q * SB] + s_macro[rr * 9 + q];
+                bool ok;
+                if constexpr (OPK == OP_SVK_UPDATE)
+                    ok = svk_stress(F, a.mu[ph], a.lam[ph], Pk, tn);
+                else
+                    ok = nh_stress(F, a.mu[ph], a.lam[ph], Pk, tn);
                 if (!ok) atomicOr(a.err, 1u);
-                const long long to = ((long long)bb * d.V + vox) * 10;
+                const long long to = ((long long)bb * d.V + vox) * NT;
 #pragma unroll
-                for (int q = 0; q < 10; ++q) {
+                for (int q = 0; q < NT; ++q) {
                     if (a.tan_out_f) a.tan_out_f[to + q] = (float)tn[q];
                     if (a.tan_out_d) a.tan_out_d[to + q] = tn[q];
                 }
@@ -287,7 +308,7 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? (RW == 32 ? 2 : (RW == 
                 T* f = slot_ptr(0, (lv * RB + rr) * NC) + x3;
                 T e[6];
 #pragma unroll
-                for (int q = 0; q < 6; ++q) e[q] = f[q * SB] + a.macroW[bb * 9 + q];
+                for (int q = 0; q < 6; ++q) e[q] = f[q * SB] + s_macro[rr * 9 + q];
                 const T* tn = a.tan_in + ((long long)bb * d.V + vox) * 21;
                 T sg[6];
                 cp_apply<T>(tn, e, sg);
@@ -308,7 +329,7 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? (RW == 32 ? 2 : (RW == 
                 T* f = slot_ptr(0, (lv * RB + rr) * NC) + x3;
                 double e[6];
 #pragma unroll
-                for (int q = 0; q < 6; ++q) e[q] = (double)f[q * SB] + a.macroW[bb * 9 + q];
+                for (int q = 0; q < 6; ++q) e[q] = (double)f[q * SB] + s_macro[rr * 9 + q];
                 const long long so = ((long long)bb * d.V + vox) * 6;
                 double sg[6], ep[6], guess[6];
 #pragma unroll

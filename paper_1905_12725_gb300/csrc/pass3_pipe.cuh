@@ -40,12 +40,15 @@ __device__ __forceinline__ T apply_voxel(const Ax3Args<T>& a, int bb, long long 
             en += (q >= 3 && NC == 6 ? T(2) : T(1)) * e[q] * sg[q];
             f[q * CS] = sg[q];
         }
-    } else if constexpr (OPK == OP_NH_APPLY) {
+    } else if constexpr (OPK == OP_NH_APPLY || OPK == OP_SVK_APPLY) {
         const T lam = a.lam[ph], mu = a.mu[ph];
         T G[9], sg[9];
 #pragma unroll
         for (int q = 0; q < 9; ++q) G[q] = f[q * CS] + a.macroW[bb * 9 + q];
-        nh_apply<T>(a.tan_in + ((long long)bb * a.d.V + vox) * 10, mu, lam, G, sg);
+        if constexpr (OPK == OP_SVK_APPLY)
+            svk_apply<T>(a.tan_in + ((long long)bb * a.d.V + vox) * 15, mu, lam, G, sg);
+        else
+            nh_apply<T>(a.tan_in + ((long long)bb * a.d.V + vox) * 10, mu, lam, G, sg);
 #pragma unroll
         for (int q = 0; q < 9; ++q) {
             en += G[q] * sg[q];

@@ -22,7 +22,7 @@ STATUS = {0: "DBFFT_OK", 1: "DBFFT_E_ARG", 2: "DBFFT_E_UNSUPPORTED_GRID", 3: "DB
           8: "DBFFT_E_MATERIAL", 9: "DBFFT_E_STATE"}
 DBFFT_SMALL, DBFFT_FINITE = 0, 1
 DBFFT_FP64, DBFFT_MIXED = 0, 1
-DBFFT_ISO_ELASTIC, DBFFT_NEO_HOOKE, DBFFT_CP_FCC_POWERLAW = 0, 1, 2
+DBFFT_ISO_ELASTIC, DBFFT_NEO_HOOKE, DBFFT_CP_FCC_POWERLAW, DBFFT_SVK = 0, 1, 2, 3
 DBFFT_APPLY_FP32, DBFFT_APPLY_PRECOND, DBFFT_APPLY_RESIDUAL = 1, 2, 4
 
 
@@ -165,6 +165,16 @@ def neo_hooke_phases(mu, lam):
     return out
 
 
+def svk_phases(mu, lam):
+    """St. Venant-Kirchhoff phases from Lame constants (finite strain)."""
+    out = (dbfft_phase * len(mu))()
+    for i, (m, l) in enumerate(zip(mu, lam)):
+        out[i].model = DBFFT_SVK
+        out[i].mu = float(m)
+        out[i].lambda_ = float(l)
+    return out
+
+
 def cp_phases(quats, C11=168000.0, C12=121000.0, C44=75000.0, gdot0=1e-3, m=0.05, tau_c=50.0):
     out = (dbfft_phase * len(quats))()
     for i, q in enumerate(quats):
@@ -190,7 +200,7 @@ class Solver:
     """One dbfft context on the current CUDA device and torch stream.
 
     phase: uint16 array [n_materials, n1, n2, n3] (or [n1, n2, n3]);
-    phases: ctypes array from iso_phases / neo_hooke_phases / cp_phases;
+    phases: ctypes array from iso_phases / neo_hooke_phases / svk_phases / cp_phases;
     target: [batch, 3, 3] end-of-ramp macro targets; stress_mask: 9 booleans.
     """
 

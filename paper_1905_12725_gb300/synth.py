@@ -273,6 +273,44 @@ def config5(n: int = 64, n_rve: int = 32, radius: float = 6.0, seed: int = SEED_
                 vf_target=np.array(vfs))
 
 
+def porous_svk(n: int = 64, n_pores: int = 5, porosity: float = 0.2, E: float = 70.0, nu: float = 0.3,
+               pore_ratio: float = 100.0, seed: int = SEED_BASE + 6, gap_vox: float = 1.0, max_tries: int = 100000):
+    """Porous St. Venant-Kirchhoff matrix (Sec. 3, third benchmark).
+
+    n_pores equal spherical pores of total volume fraction `porosity`, placed
+    by random sequential addition (periodic centre distance >= 2r + gap). The
+    pores are a compliant phase (stiffness E / pore_ratio, same nu), because
+    the Fourier operators act on the whole box. Returns the phase map
+    (0 matrix, 1 pore), the Lame constants per phase and the centres.
+    """
+    rng = Xoshiro256ss(seed)
+    r = n * (3.0 * porosity / (4.0 * math.pi * n_pores)) ** (1.0 / 3.0)
+    dmin = 2.0 * r + gap_vox
+    centres = []
+    tries = 0
+    while len(centres) < n_pores:
+        tries += 1
+        if tries > max_tries:
+            raise RuntimeError("could not place the pores without overlap")
+        c = np.array([rng.uniform() * n for _ in range(3)])
+        ok = True
+        for q in centres:
+            d = c - q
+            d -= n * np.round(d / n)
+            if float(d @ d) < dmin * dmin:
+                ok = False
+                break
+        if ok:
+            centres.append(c)
+    mask = np.zeros((n, n, n), dtype=bool)
+    for c in centres:
+        paint_sphere(mask, c, r)
+    Es = np.array([E, E / pore_ratio])
+    lam = Es * nu / ((1.0 + nu) * (1.0 - 2.0 * nu))
+    mu = Es / (2.0 * (1.0 + nu))
+    return dict(phase=mask.astype(np.uint16), mu=mu, lam=lam, radius=r, centres=np.array(centres))
+
+
 def random_voxels(n_vox: int, k: int, rng: Xoshiro256ss) -> np.ndarray:
     """k distinct voxel indices in [0, n_vox), drawn in order (for sampled checks)."""
     out = []

@@ -1,5 +1,6 @@
-"""GPU parity of the nonlinear paths: Neo-Hookean finite strain with mixed control
-(Sec. 2.4) and small-strain crystal plasticity, against the FP64 oracle.
+"""GPU parity of the nonlinear paths: Neo-Hookean and St. Venant-Kirchhoff finite
+strain with strain or mixed control (Sec. 2.4, Sec. 3) and small-strain crystal
+plasticity, against the FP64 oracle.
 
 Both sides run Newton to tight tolerances so that the difference is bounded by
 the solve error: bar 1e-10 relative on the homogenized stress per increment
@@ -88,6 +89,68 @@ def test_neo_hooke_tangent_operator_matches_oracle():
     out, _ = s.apply(torch.from_numpy(u).cuda())
     ref, _ = prob.apply_K(o.FullTangent(Kf), u[0], np.zeros(0))
     assert rel_err(out.cpu().numpy()[0], ref) < 1e-12
+
+
+# ------------------------------------------------------------------ St. Venant-Kirchhoff
+@pytest.mark.parametrize("fp32", [False, True])
+def test_svk_tangent_operator_matches_oracle(fp32):
+    """SVK: P(F) by a residual evaluation at a random F field, then K(F) applied to
+    random spectra (FP64 tangent, or the FP32 tangent of the mixed solve)."""
+    shape = (8, 16, 8)
+    c = synth.porous_svk(8, 1, 0.1, seed=11)
+    phase = np.resize(c["phase"], shape).astype(np.uint16)
+    mu, lam = c["mu"], c["lam"]
+    dbfft = _dbfft()
+    Fbar = np.array([[1.3, 0.05, 0.0], [0.02, 0.95, 0.04], [0.0, -0.03, 1.02]])
+    s = dbfft.Solver(shape, phase, dbfft.svk_phases(mu, lam), Fbar[None], kinematics=dbfft.DBFFT_FINITE,
+                     precision=dbfft.DBFFT_MIXED if fp32 else dbfft.DBFFT_FP64)
+    prob = o.Problem(shape, "finite")
+    x = synth.random_spectrum(shape, 3, 23) * 2e-3
+    r, _ = s.apply(torch.from_numpy(x).cuda(), residual=True)  # constitutive update at F(x)
+    F = prob.field_from(x[0], np.zeros(0)) + Fbar[:, :, None, None, None]
+    Pf, Kf = o.svk(F, mu[phase], lam[phase])
+    qu, _ = prob.adjoint(Pf)
+    assert rel_err(r.cpu().numpy()[0], -qu) < 1e-12
+    u = synth.random_spectrum(shape, 3, 24)
+    out, _ = s.apply(torch.from_numpy(u).cuda(), fp32=fp32)
+    ref, _ = prob.apply_K(o.FullTangent(Kf), u[0], np.zeros(0))
+    assert rel_err(out.cpu().numpy()[0], ref) < (2e-5 if fp32 else 1e-12)
+    s.close()
+
+
+@pytest.mark.parametrize("precision,control", [(0, "strain"), (1, "strain"), (0, "mixed"), (1, "mixed")])
+def test_svk_porous_increments(precision, control):
+    """Porous SVK matrix (compliant pores, 1/100 stiffness) stretched along x: every
+    component of F prescribed, or the lateral and shear stresses held at zero."""
+    c = synth.porous_svk(16, 2, 0.15, seed=5)
+    phase, mu, lam = c["phase"], c["mu"], c["lam"]
+    shape = phase.shape
+    n_inc, F11 = 3, 1.3
+    mask = NH_MASK if control == "mixed" else np.zeros((3, 3), bool)
+    targets = []
+    for k in range(n_inc):
+        t = np.eye(3)
+        t[0, 0] = 1.0 + (F11 - 1.0) * (k + 1) / n_inc
+        t[mask] = 0.0
+        targets.append(t)
+    dbfft = _dbfft()
+    s = dbfft.Solver(shape, phase, dbfft.svk_phases(mu, lam), targets[-1][None], kinematics=dbfft.DBFFT_FINITE,
+                     precision=precision, stress_mask=mask.reshape(-1) if control == "mixed" else None,
+                     n_increments=n_inc, newton_tol=1e-11 if precision == 0 else 1e-8,
+                     load_tol=1e-12 if precision == 0 else 1e-9, eta_inner=1e-6 if precision == 0 else 1e-3,
+                     tol=1e-12, max_newton=40)
+    prob = o.Problem(shape, "finite", mask.reshape(-1) if control == "mixed" else None)
+    ref, _ = o.newton_increments(prob, o.svk_material(mu[phase], lam[phase]), targets,
+                                 newton_tol=1e-12, load_tol=1e-13, eta=1e-8)
+    for k in range(n_inc):
+        rep = s.solve_increment(k)
+        P = s.homogenized_stress()[0]
+        assert rel_err(P, ref[k]["stress_bar"]) < (1e-10 if precision == 0 else 1e-6), (k, rep)
+        assert rep["eps_eq"] <= (1e-11 if precision == 0 else 1e-8)
+    if precision == 0:
+        u, _ = s.get_solution()
+        assert rel_err(u.cpu().numpy()[0], ref[-1]["x"][0]) < 1e-9
+    s.close()
 
 
 # ------------------------------------------------------------------ crystal plasticity
