@@ -10,7 +10,7 @@ step (forward unnormalised e^{-i xi.x}, inverse with 1/N); every other step is
 written out in the order of the paper's equations:
 
 * grid and frequencies ........................... Sec. 2.1 (frequency vectors)
-* displacement split, symmetric gradient s-hat ... Sec. 2.2, Eqs. symgrad, s-hat
+* displacement split, symmetric gradient s-hat ... Sec. 2.2, Eqs. disp_decomp, symgrad, s-hat
 * divergence d-hat ............................... Sec. 2.2, Eq. diver, d-hat
 * linear system (strain control) ................. Sec. 2.2, Eq. lineqf
 * stress / mixed control ......................... Sec. 2.3, final system
@@ -282,6 +282,7 @@ class Problem:
         self.shape = tuple(int(s) for s in shape)
         self.N = int(np.prod(self.shape))
         self.kind = kind
+        self.L = tuple(float(v) for v in L)
         self.xi = frequencies(self.shape, L)
         self.Z = null_mask(self.shape)
         m9 = np.zeros(9, dtype=bool) if stress_mask is None else np.asarray(stress_mask, dtype=bool)
@@ -408,6 +409,31 @@ def split_load(prob: Problem, target):
     fU = base + np.einsum("mij,m->ij", prob.basis_all[~prob.active], coeff[~prob.active])
     sig_f = np.einsum("mij,ij->m", prob.basis, target)
     return fU, sig_f
+
+
+def macro_field(prob: Problem, fieldU, e):
+    """The whole macroscopic strain (small) or deformation gradient (finite):
+    the prescribed part plus the solved stress-controlled unknowns E e."""
+    out = np.array(fieldU, dtype=np.float64)
+    if prob.ne:
+        out = out + np.einsum("mij,m->ij", prob.basis, e)
+    return out
+
+
+def displacement(prob: Problem, u_hat, macro):
+    """Total displacement at the voxel centres (Sec. 2.2, Eqs. disp_decomp and
+    decomp_displ; Sec. 2.4 with Fbar - I in place of the macro strain).
+
+    u(x) = Hbar x + u~(x): u~ is the inverse DFT of the unknown u-hat (the
+    periodic fluctuation, zero mean) and Hbar = macro (small strain) or
+    macro - I (finite strain), macro from macro_field. Voxel j of axis a sits
+    at x_a = (j + 1/2) L_a / n_a. Returns [3, n1, n2, n3].
+    """
+    Hbar = np.asarray(macro, dtype=np.float64) - (np.eye(3) if prob.kind == "finite" else 0.0)
+    ut = to_real(u_hat, prob.shape)
+    x = [(np.arange(n) + 0.5) * (L / n) for n, L in zip(prob.shape, prob.L)]
+    X = np.stack(np.meshgrid(*x, indexing="ij"))  # [3, n1, n2, n3]
+    return ut + np.einsum("ij,j...->i...", Hbar, X)
 
 
 def linear_rhs(prob: Problem, tangent, target):

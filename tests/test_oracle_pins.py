@@ -227,6 +227,51 @@ def test_homogeneous_medium_is_affine_with_zero_iterations():
     assert np.abs(sol["sig_bar"] - np.einsum("ijkl,kl->ij", C, eps)).max() < 1e-15
 
 
+# ---------------------------------------------------------------- displacement (Eqs. disp_decomp, decomp_displ)
+def test_displacement_of_an_affine_state_sits_at_voxel_centres():
+    """u~ = 0: u = Hbar x at x = (j + 1/2) L / n. A non-symmetric Fbar - I (finite
+    strain) catches a transposed Hbar; a stress-controlled shear (small strain)
+    checks the macro unknown's Mandel basis element (e_i e_j + e_j e_i)/sqrt 2."""
+    shape, L = (4, 6, 8), (1.0, 2.0, 0.5)
+    h = np.array(L) / np.array(shape)
+    mask = np.zeros((3, 3), bool)
+    mask[0, 2] = mask[2, 0] = True
+    prob = o.Problem(shape, "small", mask.reshape(-1), L=L)
+    fU = np.array([[1e-3, 2e-4, 0.0], [2e-4, -5e-4, 0.0], [0.0, 0.0, 3e-4]])
+    e = np.array([math.sqrt(2.0) * 7e-4])  # the 13 shear = 7e-4
+    macro = o.macro_field(prob, fU, e)
+    u = o.displacement(prob, prob.zeros()[0], macro)
+    H = fU.copy()
+    H[0, 2] = H[2, 0] = 7e-4
+    for j in [(0, 0, 0), (3, 5, 7), (1, 4, 2)]:
+        x = (np.array(j) + 0.5) * h
+        assert np.allclose(u[(slice(None),) + j], H @ x, rtol=0, atol=1e-18)
+    # finite strain: u_1(j2 + 1) - u_1(j2) = (F - I)_12 h_2, not (F - I)_21 h_2
+    probf = o.Problem(shape, "finite", L=L)
+    F = np.eye(3) + np.array([[0.1, 0.3, 0.0], [-0.2, 0.0, 0.05], [0.0, 0.0, -0.1]])
+    uf = o.displacement(probf, probf.zeros()[0], o.macro_field(probf, F, np.zeros(0)))
+    assert abs((uf[0, 0, 1, 0] - uf[0, 0, 0, 0]) - 0.3 * h[1]) < 1e-15
+    assert abs((uf[1, 1, 0, 0] - uf[1, 0, 0, 0]) - (-0.2) * h[0]) < 1e-15
+    assert np.allclose(uf[:, 0, 0, 0], (F - np.eye(3)) @ (0.5 * h), rtol=0, atol=1e-16)
+
+
+def test_displacement_of_one_fourier_mode_closed_form():
+    """One stored mode k = (1, 2, 3) off the k3 = 0, n3/2 planes: u~_c(j) =
+    (2/N) Re(u_c e^{2 pi i k.j/n}) (it and its conjugate partner)."""
+    shape = (4, 6, 8)
+    prob = o.Problem(shape, "small")
+    uh = prob.zeros()[0]
+    a = np.array([0.3 - 0.7j, -1.1 + 0.2j, 0.5 + 0.5j])
+    uh[:, 1, 2, 3] = a
+    u = o.displacement(prob, uh, np.zeros((3, 3)))
+    j1, j2, j3 = np.meshgrid(*[np.arange(n) for n in shape], indexing="ij")
+    th = 2 * np.pi * (1 * j1 / 4 + 2 * j2 / 6 + 3 * j3 / 8)
+    N = prob.N
+    for c in range(3):
+        ref = (2.0 / N) * (a[c].real * np.cos(th) - a[c].imag * np.sin(th))
+        assert np.abs(u[c] - ref).max() < 1e-15
+
+
 # ---------------------------------------------------------------- laminates (closed forms)
 def _laminate(shape, widths, lam_p, mu_p):
     ph = np.zeros(shape[0], int)
