@@ -230,6 +230,18 @@ dbfft_status dbfft_adjoint(dbfft_ctx* ctx, const double* dJ_dsigma, double* dJ_d
  * (may be NULL), e host [B][9] (may be NULL). */
 dbfft_status dbfft_get_solution(dbfft_ctx* ctx, void* u_hat, double* e);
 
+/*
+ * Total displacement of the current solution at the voxel centres
+ * (Sec. 2.2, Eqs. disp_decomp and decomp_displ; Sec. 2.4): u(x) = Hbar x +
+ * u~(x), u~ the inverse DFT of the unknown u-hat (the periodic fluctuation,
+ * zero mean), Hbar the whole macro strain (DBFFT_SMALL) or Fbar - I
+ * (DBFFT_FINITE), including the solved stress-controlled components.
+ * Voxel (i1, i2, i3) sits at x_a = (i_a + 1/2) L_a / n_a. out: device double
+ * [B][3][n1][n2][n3], written in full; the transforms run in FP64 on the
+ * context's stream. Errors: E_ARG (null pointer), E_CUDA.
+ */
+dbfft_status dbfft_displacement(dbfft_ctx* ctx, double* out);
+
 /* One row of the per-pass profile. */
 typedef struct {
     char name[40];       /* pass and precision, e.g. "axis3_apply_f32"                  */
@@ -318,6 +330,22 @@ const char* dbfft_tuning(const dbfft_ctx* ctx);
  * not depend on the shape beyond floating-point reassociation.
  */
 dbfft_status dbfft_set_pass3_shape(dbfft_ctx* ctx, int fp64, int pipelined, int radix, int lines);
+
+/*
+ * Refresh policy of the preconditioner's reference stiffness for the
+ * nonlinear models (Sec. 2.5 takes the volume average of the tangent; the
+ * paper computes it at the start of each increment, and its hyperelastic
+ * example keeps the initial tangent). DBFFT_PRECOND_PER_INCREMENT (default):
+ * the mean tangent at the first Newton iterate of each increment.
+ * DBFFT_PRECOND_INITIAL: the mean initial stiffness (K(I) for NEO_HOOKE and
+ * SVK, the elastic stiffness for CP), never refreshed.
+ * DBFFT_PRECOND_PER_NEWTON: the mean tangent at every Newton iterate. The
+ * converged solution does not depend on the policy; the number of CG
+ * iterations does. Takes effect at the next dbfft_solve_increment.
+ * Errors: E_ARG (unknown policy).
+ */
+enum { DBFFT_PRECOND_PER_INCREMENT = 0, DBFFT_PRECOND_INITIAL = 1, DBFFT_PRECOND_PER_NEWTON = 2 };
+dbfft_status dbfft_set_precond_refresh(dbfft_ctx* ctx, int policy);
 
 /* Device bytes held by the context. */
 size_t dbfft_device_bytes(const dbfft_ctx* ctx);

@@ -79,6 +79,9 @@ struct dbfft_ctx {
     CpParams cp{};
     PrecondData* pre = nullptr;
     std::vector<PrecondData> pre_h;
+    std::vector<PrecondData> pre_init_h;  // the preconditioner of the initial stiffness
+    int pre_refresh = DBFFT_PRECOND_PER_INCREMENT;
+    bool pre_is_init = true;  // the device holds pre_init_h
 
     // ---- vectors
     cplx<double>* x64 = nullptr;
@@ -95,6 +98,7 @@ struct dbfft_ctx {
     void* W2 = nullptr;  // adjoint assembly
     cplx<double>* xfwd = nullptr;
     double* fU = nullptr;
+    double* hbar = nullptr;  // [B][9] macro displacement gradient (displacement output)
     double* sigf = nullptr;
     double* sig0 = nullptr;
     double* macroW = nullptr;
@@ -969,6 +973,17 @@ dbfft_status refresh_precond(dbfft_ctx* ctx) {
     CK(cudaMemcpyAsync(ctx->pre, ctx->pre_h.data(), ctx->pre_h.size() * sizeof(PrecondData), cudaMemcpyHostToDevice,
                        ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
+    ctx->pre_is_init = false;
+    return DBFFT_OK;
+}
+
+// Back to the preconditioner of the initial stiffness (refresh policy INITIAL).
+dbfft_status restore_initial_precond(dbfft_ctx* ctx) {
+    ctx->pre_h = ctx->pre_init_h;
+    CK(cudaMemcpyAsync(ctx->pre, ctx->pre_h.data(), ctx->pre_h.size() * sizeof(PrecondData), cudaMemcpyHostToDevice,
+                       ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    ctx->pre_is_init = true;
     return DBFFT_OK;
 }
 
@@ -1029,7 +1044,13 @@ dbfft_status solve_current(dbfft_ctx* ctx, dbfft_report* rep) {
         }
         if (all) { converged = true; break; }
         if (step == max_steps) break;
-        if (!linear && step == 0) TRY(refresh_precond(ctx));
+        if (!linear) {  // reference stiffness of the preconditioner (R10 and its alternatives)
+            if (ctx->pre_refresh == DBFFT_PRECOND_INITIAL) {
+                if (!ctx->pre_is_init) TRY(restore_initial_precond(ctx));
+            } else if (step == 0 || ctx->pre_refresh == DBFFT_PRECOND_PER_NEWTON) {
+                TRY(refresh_precond(ctx));
+            }
+        }
         // inner solve on r / ||r||
         std::vector<double> sc(ctx->B), sb(ctx->B);
         for (int b = 0; b < ctx->B; ++b) {
@@ -1342,7 +1363,7 @@ dbfft_status dbfft_set_pass3_shape(dbfft_ctx* ctx, int fp64, int pipelined, int 
     const bool r32 = radix == 32 && !pipelined && ctx->n3 <= (dbl ? 64 : 256);
     if (dbl ? (radix != 4 && !r32) : (radix != 8 && radix != 16 && !r32))
         return fail(ctx, DBFFT_E_ARG,
-                    "radix: 8 or 16 (FP32), 4 (FP64), or 32 with the plain kernel (n3 <= 128 FP32, <= 64 FP64)");
+                    "radix: 8 or 16 (FP32), 4 (FP64), or 32 with the plain kernel (n3 <= 256 FP32, <= 64 FP64)");
     const long long nlines = (long long)ctx->n1 * ctx->n2;
     if (lines > nlines) return fail(ctx, DBFFT_E_ARG, "more lines per CTA than grid lines");
     const int pi_ = dbl ? 1 : 0;
@@ -1361,6 +1382,14 @@ dbfft_status dbfft_set_pass3_shape(dbfft_ctx* ctx, int fp64, int pipelined, int 
     }
     for (int k = 0; k < 2; ++k)  // graphs captured with the old shape
         if (ctx->cg_exec[k]) { cudaGraphExecDestroy(ctx->cg_exec[k]); ctx->cg_exec[k] = nullptr; }
+    return DBFFT_OK;
+}
+
+dbfft_status dbfft_set_precond_refresh(dbfft_ctx* ctx, int policy) {
+    if (!ctx) return DBFFT_E_ARG;
+    if (policy != DBFFT_PRECOND_PER_INCREMENT && policy != DBFFT_PRECOND_INITIAL && policy != DBFFT_PRECOND_PER_NEWTON)
+        return fail(ctx, DBFFT_E_ARG, "unknown preconditioner refresh policy");
+    ctx->pre_refresh = policy;
     return DBFFT_OK;
 }
 
@@ -1653,6 +1682,7 @@ static dbfft_status create_impl(dbfft_ctx* ctx, const dbfft_grid* grid, const db
     }
     TRY(dalloc_t(ctx, ctx->Bm, &ctx->pre));
     CK(cudaMemcpyAsync(ctx->pre, ctx->pre_h.data(), ctx->Bm * sizeof(PrecondData), cudaMemcpyHostToDevice, ctx->stream));
+    ctx->pre_init_h = ctx->pre_h;
 
     // vectors and work buffers
     const size_t nU = (size_t)ctx->B * 3 * ctx->H;
@@ -1664,7 +1694,7 @@ static dbfft_status create_impl(dbfft_ctx* ctx, const dbfft_grid* grid, const db
     TRY(dalloc(ctx, nU * isz, &ctx->pi));
     TRY(dalloc(ctx, (size_t)ctx->B * ctx->nc * ctx->H * sizeof(cplx<double>), &ctx->W));
     double** smalls[] = {&ctx->xe64, &ctx->re64, &ctx->xe_i, &ctx->re_i, &ctx->pe_i, &ctx->fU,
-                         &ctx->sigf, &ctx->sig0, &ctx->macroW, &ctx->macroW2};
+                         &ctx->sigf, &ctx->sig0, &ctx->macroW, &ctx->macroW2, &ctx->hbar};
     for (double** s : smalls) TRY(dalloc_t(ctx, (size_t)ctx->B * 9, s));
     TRY(dalloc_t(ctx, (size_t)ctx->B * 9, &ctx->macroWf));
     TRY(dalloc_t(ctx, (size_t)ctx->B, &ctx->scal));
@@ -1778,6 +1808,60 @@ dbfft_status dbfft_get_solution(dbfft_ctx* ctx, void* u_hat, double* e) {
         CK(cudaMemcpyAsync(u_hat, ctx->x64, (size_t)ctx->B * 3 * ctx->H * sizeof(cplx<double>),
                            cudaMemcpyDeviceToDevice, ctx->stream));
     if (e) CK(cudaMemcpyAsync(e, ctx->xe64, (size_t)ctx->B * 9 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return DBFFT_OK;
+}
+
+dbfft_status dbfft_displacement(dbfft_ctx* ctx, double* out) {
+    if (!ctx || !out) return DBFFT_E_ARG;
+    // Hbar = the whole macro strain (small) or Fbar - I (finite), row-major, from the
+    // prescribed part fU (W components) and the solved stress-controlled unknowns
+    std::vector<double> fU((size_t)ctx->B * 9), xe((size_t)ctx->B * 9), hb((size_t)ctx->B * 9);
+    CK(cudaMemcpyAsync(fU.data(), ctx->fU, fU.size() * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemcpyAsync(xe.data(), ctx->xe64, xe.size() * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    static const int pi[6] = {0, 1, 2, 1, 0, 0}, pj[6] = {0, 1, 2, 2, 2, 1};
+    for (int b = 0; b < ctx->B; ++b) {
+        double* H = &hb[(size_t)b * 9];
+        if (ctx->nc == 6) {
+            for (int mm = 0; mm < 6; ++mm) {
+                double v = fU[(size_t)b * 9 + mm];
+                if (ctx->activeflag_h[mm]) v += (mm >= 3 ? std::sqrt(0.5) : 1.0) * xe[(size_t)b * 9 + mm];
+                H[3 * pi[mm] + pj[mm]] = v;
+                H[3 * pj[mm] + pi[mm]] = v;
+            }
+        } else {
+            for (int q = 0; q < 9; ++q) {
+                double v = fU[(size_t)b * 9 + q];
+                if (ctx->activeflag_h[q]) v += xe[(size_t)b * 9 + q];
+                H[q] = v - ((q / 3 == q % 3) ? 1.0 : 0.0);
+            }
+        }
+    }
+    CK(cudaMemcpyAsync(ctx->hbar, hb.data(), hb.size() * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+    // the fluctuation: inverse transforms of the three components of u-hat
+    cplx<double>* W = reinterpret_cast<cplx<double>*>(ctx->W);
+    CK(cudaMemcpyAsync(W, ctx->x64, (size_t)ctx->B * 3 * ctx->H * sizeof(cplx<double>), cudaMemcpyDeviceToDevice,
+                       ctx->stream));
+    Ax2Args<double> a2 = fft_args<double>(ctx, W, nullptr);
+    a2.d.nc = 3;
+    const double cp = cpass(ctx, true, ctx->B);
+    TRY(run(ctx, "fft_ax2_f64", 2 * 3 * cp, [&] { return launch_fft_ax2<double>(+1, a2, ctx->stream); }));
+    TRY(run(ctx, "fft_ax1_f64", 2 * 3 * cp, [&] { return launch_fft_ax1<double>(+1, a2, ctx->stream); }));
+    Ax3Args<double> a3 = ax3_base<double>(ctx, W);
+    a3.d.nc = 3;
+    a3.radix = 4;
+    a3.L = ax3_lines(ctx->n3, 3, ctx->RB, true, 1, 4);
+    a3.pipe = 0;
+    a3.macroW = ctx->hbar;
+    a3.real_out = out;
+    const double Ls[3] = {ctx->grid.L[0] > 0 ? ctx->grid.L[0] : 1.0, ctx->grid.L[1] > 0 ? ctx->grid.L[1] : 1.0,
+                          ctx->grid.L[2] > 0 ? ctx->grid.L[2] : 1.0};
+    a3.hx[0] = Ls[0] / ctx->n1;
+    a3.hx[1] = Ls[1] / ctx->n2;
+    a3.hx[2] = Ls[2] / ctx->n3;
+    TRY(run(ctx, "pass3_displacement_f64", 3 * cp + (double)ctx->B * 3 * ctx->V * 8.0,
+            [&] { return launch_ax3_post<double>(OP_DISP, a3, ctx->stream); }));
     CK(cudaStreamSynchronize(ctx->stream));
     return DBFFT_OK;
 }

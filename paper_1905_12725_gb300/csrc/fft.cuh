@@ -88,6 +88,92 @@ __device__ __forceinline__ constexpr double cos32(int m) {
 }
 __device__ __forceinline__ constexpr double sin32(int m) { return cos32((m + 24) & 31); }
 
+// cos(2 pi m / 256) for m = 0..64 (first quadrant), mathematical constants
+// (34 decimals), for twiddles whose index is known at compile time.
+__host__ __device__ constexpr double c256(int m) {
+    switch (m) {
+        case 0: return 1.0000000000000000000000000000000000;
+        case 1: return 0.9996988186962042201157656496661722;
+        case 2: return 0.9987954562051723927147716047591007;
+        case 3: return 0.9972904566786902161355971401825678;
+        case 4: return 0.9951847266721968862448369531094799;
+        case 5: return 0.9924795345987099981567672516611178;
+        case 6: return 0.9891765099647809734516737380162431;
+        case 7: return 0.9852776423889412447740184331785478;
+        case 8: return 0.9807852804032304491261822361342390;
+        case 9: return 0.9757021300385285444603957664195280;
+        case 10: return 0.9700312531945439926039842072861003;
+        case 11: return 0.9637760657954398666864643555078352;
+        case 12: return 0.9569403357322088649357978869802700;
+        case 13: return 0.9495281805930366671959360741893450;
+        case 14: return 0.9415440651830207784125094025995024;
+        case 15: return 0.9329927988347388877116602555433025;
+        case 16: return 0.9238795325112867561281831893967883;
+        case 17: return 0.9142097557035306546350148293935774;
+        case 18: return 0.9039892931234433315862002972305370;
+        case 19: return 0.8932243011955153203424164474933980;
+        case 20: return 0.8819212643483550297127568636603883;
+        case 21: return 0.8700869911087114186522924044838488;
+        case 22: return 0.8577286100002720699022699842847701;
+        case 23: return 0.8448535652497070732595712051049571;
+        case 24: return 0.8314696123025452370787883776179058;
+        case 25: return 0.8175848131515836965049208841306338;
+        case 26: return 0.8032075314806449098066765129631419;
+        case 27: return 0.7883464276266062620091647053596893;
+        case 28: return 0.7730104533627369608109066097584698;
+        case 29: return 0.7572088465064845475754640536057845;
+        case 30: return 0.7409511253549590911756168974951627;
+        case 31: return 0.7242470829514669209410692432905532;
+        case 32: return 0.7071067811865475244008443621048490;
+        case 33: return 0.6895405447370669246167306299574847;
+        case 34: return 0.6715589548470184006253768504274218;
+        case 35: return 0.6531728429537767640842030136563054;
+        case 36: return 0.6343932841636454982151716132254934;
+        case 37: return 0.6152315905806268454849135634139843;
+        case 38: return 0.5956993044924333434670365288299699;
+        case 39: return 0.5758081914178453007459724538157308;
+        case 40: return 0.5555702330196022247428308139485329;
+        case 41: return 0.5349976198870972106630769046370179;
+        case 42: return 0.5141027441932217265936938389688158;
+        case 43: return 0.4928981922297840368730266887588093;
+        case 44: return 0.4713967368259976485563876259052544;
+        case 45: return 0.4496113296546066000462945794242271;
+        case 46: return 0.4275550934302820943209668568887985;
+        case 47: return 0.4052413140049898709084813055050525;
+        case 48: return 0.3826834323650897717284599840303989;
+        case 49: return 0.3598950365349881487751045723267564;
+        case 50: return 0.3368898533922200506892532126191476;
+        case 51: return 0.3136817403988914766564788459941003;
+        case 52: return 0.2902846772544623676361923758173953;
+        case 53: return 0.2667127574748983863252865151164364;
+        case 54: return 0.2429801799032638899482741620774711;
+        case 55: return 0.2191012401568697972277375474973578;
+        case 56: return 0.1950903220161282678482848684770222;
+        case 57: return 0.1709618887603012263636423572082635;
+        case 58: return 0.1467304744553617516588501296467178;
+        case 59: return 0.1224106751992161984987044741509458;
+        case 60: return 0.0980171403295606019941955638886418;
+        case 61: return 0.0735645635996674235294656215752343;
+        case 62: return 0.0490676743274180142549549769426827;
+        case 63: return 0.0245412285229122880317345294592829;
+        default: return 0.0;  // m = 64
+    }
+}
+// cos and sin of 2 pi m / 256 for any m in [0, 256)
+__host__ __device__ constexpr double cos256(int m) {
+    return m <= 64 ? c256(m) : m <= 128 ? -c256(128 - m) : m <= 192 ? -c256(m - 128) : c256(256 - m);
+}
+__host__ __device__ constexpr double sin256(int m) { return cos256((m + 192) & 255); }
+
+// exp(-2 pi i K / N) as compile-time constants (N a power of two <= 256): the
+// entry K of the forward twiddle table of length N.
+template <typename T, int N, int K>
+__device__ __forceinline__ cplx<T> tw_const() {
+    static_assert(N <= 256 && 256 % N == 0, "twiddle constants cover lengths dividing 256");
+    constexpr int m = ((K % N + N) % N) * (256 / N);
+    return mk((T)cos256(m), (T)(-sin256(m)));
+}
+
 // Multiply by exp(DIR * 2 pi i k / L) with k, L compile-time.
 template <int DIR, int L, int K, typename T>
 __device__ __forceinline__ cplx<T> rot(cplx<T> a) {

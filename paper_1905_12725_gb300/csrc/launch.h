@@ -49,6 +49,8 @@ template <typename T> cudaError_t launch_ax3_pipe(int opk, const Ax3Args<T>& a, 
 // pass 3 of the St. Venant-Kirchhoff law (OP_SVK_APPLY in both precisions, OP_SVK_UPDATE in FP64),
 // plain and pipelined; compiled in translation units of their own
 template <typename T> cudaError_t launch_ax3_svk(int opk, const Ax3Args<T>& a, cudaStream_t s);
+// pass 3 of the post-processing transforms (OP_DISP, FP64 only)
+template <typename T> cudaError_t launch_ax3_post(int opk, const Ax3Args<T>& a, cudaStream_t s);
 // shared memory of one pipelined CTA (pipe 1: two stages, 2: one stage), or -1 when (n3, L) is not a valid tile
 long long ax3_pipe_smem(int n3, int nc, int rb, bool dbl, bool scale, int radix, int L, long long nlines, int pipe);
 

@@ -25,7 +25,8 @@ enum {
     OP_ADJ = 5,        // dJ/dE(x) = (1/N) eps_adj : C1 : eps_fwd (no forward R2C)
     OP_CP_UPDATE32 = 6, // OP_CP_UPDATE for an FP32 inner solve: FP32 Newton start, FP32 tangent
     OP_SVK_APPLY = 7,   // dP = K(F) : (G + macro) from the stored SVK tangent data (F, S)
-    OP_SVK_UPDATE = 8   // St. Venant-Kirchhoff P(F), F = macro (incl. I) + G; stores F and S
+    OP_SVK_UPDATE = 8,  // St. Venant-Kirchhoff P(F), F = macro (incl. I) + G; stores F and S
+    OP_DISP = 9         // total displacement Hbar x + u~ from the 3 inverse-transformed components (no R2C)
 };
 
 template <typename T>
@@ -64,10 +65,12 @@ struct Ax3Args {
     double* sig_t;         // trial stress
     unsigned* err;         // error bits (bit 0: local Newton failure)
     double* dJdE;          // OP_ADJ output [B][V]
+    double* real_out;      // OP_DISP output [B][3][V]; macroW holds Hbar row-major [B][9]
+    double hx[3];          // OP_DISP: voxel edge lengths L_a / n_a
 };
 
 template <int OPK> struct OpInfo {
-    static constexpr bool forward = OPK != OP_ADJ;
+    static constexpr bool forward = OPK != OP_ADJ && OPK != OP_DISP;
     static constexpr bool apply = OPK == OP_ISO || OPK == OP_NH_APPLY || OPK == OP_CP_APPLY || OPK == OP_SVK_APPLY;
 };
 
@@ -183,14 +186,33 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? (RW == 32 ? 2 : (RW == 
             T* my = ok ? slot_ptr(f, sl) : scratch;
             cplx<T>* myc = reinterpret_cast<cplx<T>*>(my);
             cplx<T> v[R];
+            if constexpr (P == 1) {
+                // the whole line in this thread: X[k] and X[M-k] read once for both
+                // Z[k] and Z[M-k] (Z[M-k] = conj(A) - i e_{M-k}^* conj(B) with A, B of k),
+                // twiddles as compile-time constants
+                sfor<0, M / 2 + 1>([&](auto kc) {
+                    constexpr int k = decltype(kc)::value;
+                    constexpr int km = M - k;
+                    const cplx<T> X = myc[k];
+                    const cplx<T> Xc = conjg(myc[km]);
+                    const cplx<T> A = X + Xc, Bd = X - Xc;
+                    const cplx<T> dl = conjg(tw_const<T, N3, k>()) * Bd;
+                    v[k] = A + mk(-dl.y, dl.x);
+                    if constexpr (k != 0 && k != km) {
+                        const cplx<T> dl2 = conjg(tw_const<T, N3, km>()) * mk(-Bd.x, Bd.y);  // -conj(Bd)
+                        v[km] = conjg(A) + mk(-dl2.y, dl2.x);
+                    }
+                });
+            } else {
 #pragma unroll
-            for (int r = 0; r < R; ++r) {
-                const int k = p + r * P;
-                const cplx<T> X = myc[k];
-                const cplx<T> Xc = conjg(myc[M - k]);
-                const cplx<T> e = conjg(ldg_c(a.tw.t3 + k));
-                const cplx<T> dl = e * (X - Xc);
-                v[r] = (X + Xc) + mk(-dl.y, dl.x);
+                for (int r = 0; r < R; ++r) {
+                    const int k = p + r * P;
+                    const cplx<T> X = myc[k];
+                    const cplx<T> Xc = conjg(myc[M - k]);
+                    const cplx<T> e = conjg(ldg_c(a.tw.t3 + k));
+                    const cplx<T> dl = e * (X - Xc);
+                    v[r] = (X + Xc) + mk(-dl.y, dl.x);
+                }
             }
             __syncwarp();  // the slot's threads (one warp-aligned group) have read their line
             ColFFT<T, M, R, +1, true, true>::run(v, myc, 1, p, a.tw.tm);
@@ -300,6 +322,22 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? (RW == 32 ? 2 : (RW == 
                 }
 #pragma unroll
                 for (int q = 0; q < 9; ++q) f[q * SB] = (T)Pk[q];
+            }
+        } else if constexpr (OPK == OP_DISP) {
+            // u = Hbar x + u~ at the voxel centre x = (i + 1/2) h; u~ = the real line / N
+            const long long ln = line0 + lv;
+            const long long i1 = ln / d.n2;
+            const double X[3] = {((double)i1 + 0.5) * a.hx[0], ((double)(ln - i1 * d.n2) + 0.5) * a.hx[1],
+                                 ((double)x3 + 0.5) * a.hx[2]};
+            for (int rr = 0; rr < RB; ++rr) {
+                const int bb = g * RB + rr;
+                const T* f = slot_ptr(0, (lv * RB + rr) * NC) + x3;
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    const double v = (double)f[c * SB] * d.invN + (double)s_macro[rr * 9 + 3 * c] * X[0] +
+                                     (double)s_macro[rr * 9 + 3 * c + 1] * X[1] + (double)s_macro[rr * 9 + 3 * c + 2] * X[2];
+                    a.real_out[((long long)bb * 3 + c) * d.V + vox] = v;
+                }
             }
         } else if constexpr (OPK == OP_CP_APPLY) {
             for (int rr = 0; rr < RB; ++rr) {
@@ -421,20 +459,18 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? (RW == 32 ? 2 : (RW == 
             // the whole line is in this thread's registers: X[k] and X[M-k] from
             // Z[k] and Z[M-k] directly, written pairwise
             const T half = T(0.5);
-#pragma unroll
-            for (int k = 0; k <= M / 2; ++k) {
-                const int kc = (M - k) & (M - 1);
+            sfor<0, M / 2 + 1>([&](auto kk) {
+                constexpr int k = decltype(kk)::value;
+                constexpr int kc = (M - k) & (M - 1);
                 const cplx<T> Zk = v[k], Zc = conjg(v[kc]);
-                const cplx<T> e = ldg_c(a.tw.t3 + k);
-                const cplx<T> dl = e * (Zk - Zc);
+                const cplx<T> dl = tw_const<T, N3, k>() * (Zk - Zc);
                 myc[k] = mk(half * (Zk.x + Zc.x) + half * dl.y, half * (Zk.y + Zc.y) - half * dl.x);
-                if (k != 0 && k != M - k) {
+                if constexpr (k != 0 && k != M - k) {
                     const cplx<T> Zk2 = v[kc], Zc2 = conjg(v[k]);
-                    const cplx<T> e2 = ldg_c(a.tw.t3 + (M - k));
-                    const cplx<T> dl2 = e2 * (Zk2 - Zc2);
+                    const cplx<T> dl2 = tw_const<T, N3, M - k>() * (Zk2 - Zc2);
                     myc[M - k] = mk(half * (Zk2.x + Zc2.x) + half * dl2.y, half * (Zk2.y + Zc2.y) - half * dl2.x);
                 }
-            }
+            });
             myc[M] = mk(v[0].x - v[0].y, T(0));
             continue;
         }

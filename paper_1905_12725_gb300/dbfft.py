@@ -23,6 +23,7 @@ STATUS = {0: "DBFFT_OK", 1: "DBFFT_E_ARG", 2: "DBFFT_E_UNSUPPORTED_GRID", 3: "DB
 DBFFT_SMALL, DBFFT_FINITE = 0, 1
 DBFFT_FP64, DBFFT_MIXED = 0, 1
 DBFFT_ISO_ELASTIC, DBFFT_NEO_HOOKE, DBFFT_CP_FCC_POWERLAW, DBFFT_SVK = 0, 1, 2, 3
+DBFFT_PRECOND_PER_INCREMENT, DBFFT_PRECOND_INITIAL, DBFFT_PRECOND_PER_NEWTON = 0, 1, 2
 DBFFT_APPLY_FP32, DBFFT_APPLY_PRECOND, DBFFT_APPLY_RESIDUAL = 1, 2, 4
 
 
@@ -74,7 +75,7 @@ EXPORTS = ["dbfft_create", "dbfft_apply", "dbfft_solve_increment", "dbfft_homoge
            "dbfft_homogenized_tangent", "dbfft_adjoint", "dbfft_get_solution", "dbfft_device_bytes",
            "dbfft_destroy", "dbfft_last_error", "dbfft_status_string", "dbfft_profile",
            "dbfft_profile_read", "dbfft_launch_count", "dbfft_apply_iso_noalloc", "dbfft_autotune",
-           "dbfft_tuning", "dbfft_set_pass3_shape"]
+           "dbfft_tuning", "dbfft_set_pass3_shape", "dbfft_set_precond_refresh", "dbfft_displacement"]
 
 _LIB = None
 
@@ -132,6 +133,10 @@ def load_library(build_if_missing: bool = True):
     lib.dbfft_tuning.restype = C.c_char_p
     lib.dbfft_set_pass3_shape.argtypes = [vp, ip, ip, ip, ip]
     lib.dbfft_set_pass3_shape.restype = ip
+    lib.dbfft_set_precond_refresh.argtypes = [vp, ip]
+    lib.dbfft_set_precond_refresh.restype = ip
+    lib.dbfft_displacement.argtypes = [vp, vp]
+    lib.dbfft_displacement.restype = ip
     _LIB = lib
     return lib
 
@@ -302,6 +307,10 @@ class Solver:
         """Fix pass 3's launch shape for one inner precision (dbfft_set_pass3_shape)."""
         self._check(self.lib.dbfft_set_pass3_shape(self.ctx, int(fp64), int(pipelined), int(radix), int(lines)))
 
+    def set_precond_refresh(self, policy):
+        """Preconditioner refresh policy of the nonlinear models (dbfft_set_precond_refresh)."""
+        self._check(self.lib.dbfft_set_precond_refresh(self.ctx, int(policy)))
+
     def launch_count(self) -> int:
         return int(self.lib.dbfft_launch_count(self.ctx))
 
@@ -365,6 +374,13 @@ class Solver:
         e = np.zeros((self.batch, 9))
         self._check(self.lib.dbfft_get_solution(self.ctx, C.c_void_p(u.data_ptr()), _dptr(e)))
         return u, e
+
+    def displacement(self):
+        """Total displacement at the voxel centres, device float64 [B, 3, n1, n2, n3]."""
+        torch = self.torch
+        out = torch.empty((self.batch, 3) + tuple(self.shape), dtype=torch.float64, device=self.device)
+        self._check(self.lib.dbfft_displacement(self.ctx, C.c_void_p(out.data_ptr())))
+        return out
 
 
 def apply_iso_noalloc(shape, phase_id, lam, mu, u_hat, out, L=None, stream=None):

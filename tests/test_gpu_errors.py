@@ -47,6 +47,10 @@ def test_bad_arguments_are_refused():
     st = s.lib.dbfft_apply(s.ctx, dbfft.DBFFT_APPLY_RESIDUAL | dbfft.DBFFT_APPLY_FP32, u.data_ptr(), None,
                            torch.empty_like(u).data_ptr(), None)  # the residual exists in FP64 only
     assert dbfft.STATUS[st] == "DBFFT_E_ARG"
+    assert dbfft.STATUS[s.lib.dbfft_set_precond_refresh(s.ctx, 7)] == "DBFFT_E_ARG"  # unknown policy
+    with pytest.raises(dbfft.DbfftError) as ei:  # SVK needs finite kinematics
+        dbfft.Solver(shape, np.zeros(shape, np.uint16), dbfft.svk_phases([1.0], [1.5]), np.zeros((1, 3, 3)))
+    assert _status(ei.value) == "DBFFT_E_ARG"
     out, _ = s.apply(u)  # the context still works
     assert torch.isfinite(out).all()
     s.close()

@@ -153,6 +153,36 @@ def test_svk_porous_increments(precision, control):
     s.close()
 
 
+def test_precond_refresh_policies_give_the_same_solution():
+    """The reference stiffness of the preconditioner (initial, per increment, per Newton
+    iterate) changes the CG iteration count, not the converged increments."""
+    c = synth.porous_svk(16, 2, 0.15, seed=5)
+    phase, mu, lam = c["phase"], c["mu"], c["lam"]
+    n_inc, F11 = 3, 1.5
+    targets = []
+    for k in range(n_inc):
+        t = np.eye(3)
+        t[0, 0] = 1.0 + (F11 - 1.0) * (k + 1) / n_inc
+        targets.append(t)
+    prob = o.Problem(phase.shape, "finite")
+    ref, _ = o.newton_increments(prob, o.svk_material(mu[phase], lam[phase]), targets,
+                                 newton_tol=1e-12, load_tol=1e-13, eta=1e-8)
+    dbfft = _dbfft()
+    its = {}
+    for policy in (dbfft.DBFFT_PRECOND_PER_INCREMENT, dbfft.DBFFT_PRECOND_INITIAL, dbfft.DBFFT_PRECOND_PER_NEWTON):
+        s = dbfft.Solver(phase.shape, phase, dbfft.svk_phases(mu, lam), targets[-1][None],
+                         kinematics=dbfft.DBFFT_FINITE, n_increments=n_inc, newton_tol=1e-11, eta_inner=1e-6,
+                         tol=1e-12, max_newton=40)
+        s.set_precond_refresh(policy)
+        its[policy] = []
+        for k in range(n_inc):
+            rep = s.solve_increment(k)
+            its[policy].append(rep["cg_iters"])
+            assert rel_err(s.homogenized_stress()[0], ref[k]["stress_bar"]) < 1e-10, (policy, k)
+        s.close()
+    assert its[dbfft.DBFFT_PRECOND_INITIAL] != its[dbfft.DBFFT_PRECOND_PER_INCREMENT], its
+
+
 # ------------------------------------------------------------------ crystal plasticity
 CP_MASK = np.ones((3, 3), bool)
 CP_MASK[0, 0] = False
