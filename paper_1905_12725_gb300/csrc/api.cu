@@ -475,7 +475,8 @@ Twiddles<float> twid<float>(dbfft_ctx* ctx) {
 }
 
 dbfft_status upload_tables(dbfft_ctx* ctx) {
-    const int lens[4] = {ctx->n1, ctx->n2, ctx->n3, ctx->m};
+    // tm: the half-length transform of an even axis 3 (unused for odd n3)
+    const int lens[4] = {ctx->n1, ctx->n2, ctx->n3, ctx->n3 % 2 == 0 ? ctx->m : 1};
     for (int t = 0; t < 4; ++t) {
         const int n = lens[t];
         std::vector<cplx<double>> td(n);
@@ -1281,6 +1282,10 @@ long long dbfft_launch_count(const dbfft_ctx* ctx) { return ctx ? ctx->launches 
 
 dbfft_status dbfft_autotune(dbfft_ctx* ctx, const char* cache_path) {
     if (!ctx) return DBFFT_E_ARG;
+    if ((ctx->n1 & 1) || (ctx->n2 & 1) || (ctx->n3 & 1)) {  // the odd-length kernels have one shape each
+        ctx->tune_note = "odd grid: fixed launch shapes";
+        return DBFFT_OK;
+    }
     const std::string key = tune_key(ctx);
     // precisions to tune: the inner solve's, and in the MIXED mode also the
     // FP64 passes of the outer residual chain
@@ -1456,9 +1461,12 @@ static dbfft_status create_impl(dbfft_ctx* ctx, const dbfft_grid* grid, const db
     ctx->n3 = grid->n[2];
     for (int a = 0; a < 3; ++a)
         if (!supported_len(grid->n[a]))
-            return fail(ctx, DBFFT_E_UNSUPPORTED_GRID, "grid sizes must be powers of two in [8, 256]");
-    ctx->m = ctx->n3 / 2;
-    ctx->h = ctx->m + 1;
+            return fail(ctx, DBFFT_E_UNSUPPORTED_GRID,
+                        "grid sizes must be powers of two in [8, 256] or odd with prime factors 3, 5, 7 (9 .. 245)");
+    // m: the Nyquist index of an even axis 3 (weight-1 plane of the half spectrum);
+    // 0 for odd n3, whose only weight-1 plane is k3 = 0
+    ctx->m = ctx->n3 % 2 == 0 ? ctx->n3 / 2 : 0;
+    ctx->h = ctx->n3 / 2 + 1;
     ctx->H = (long long)ctx->n1 * ctx->n2 * ctx->h;
     ctx->V = (long long)ctx->n1 * ctx->n2 * ctx->n3;
     ctx->B = grid->batch;
@@ -1478,6 +1486,8 @@ static dbfft_status create_impl(dbfft_ctx* ctx, const dbfft_grid* grid, const db
         if (mat->phases[p].model != ctx->model) return fail(ctx, DBFFT_E_ARG, "all phases must use one model kind");
     if ((ctx->model == DBFFT_NEO_HOOKE || ctx->model == DBFFT_SVK) != (ctx->kin == DBFFT_FINITE))
         return fail(ctx, DBFFT_E_ARG, "NEO_HOOKE and SVK need FINITE kinematics; ISO_ELASTIC and CP need SMALL");
+    if ((ctx->n3 & 1) && ctx->model != DBFFT_ISO_ELASTIC)
+        return fail(ctx, DBFFT_E_UNSUPPORTED_GRID, "odd n3: linear isotropic phases only");
     if (ctx->model != DBFFT_ISO_ELASTIC && ctx->Rm != 1)
         return fail(ctx, DBFFT_E_ARG, "nonlinear models need one material map per right-hand side");
     if (!load || !load->target || load->n_increments < 1) return fail(ctx, DBFFT_E_ARG, "load");
@@ -1814,6 +1824,7 @@ dbfft_status dbfft_get_solution(dbfft_ctx* ctx, void* u_hat, double* e) {
 
 dbfft_status dbfft_displacement(dbfft_ctx* ctx, double* out) {
     if (!ctx || !out) return DBFFT_E_ARG;
+    if (ctx->n3 & 1) return fail(ctx, DBFFT_E_UNSUPPORTED_GRID, "displacement output: even n3 only");
     // Hbar = the whole macro strain (small) or Fbar - I (finite), row-major, from the
     // prescribed part fU (W components) and the solved stress-controlled unknowns
     std::vector<double> fU((size_t)ctx->B * 9), xe((size_t)ctx->B * 9), hb((size_t)ctx->B * 9);
@@ -1952,6 +1963,7 @@ dbfft_status dbfft_adjoint(dbfft_ctx* ctx, const double* dJ_dsigma, double* dJ_d
     if (!ctx || !dJ_dsigma || !dJ_dE) return DBFFT_E_ARG;
     if (ctx->model != DBFFT_ISO_ELASTIC || ctx->dims.ne != 0)
         return fail(ctx, DBFFT_E_STATE, "adjoint needs linear elastic phases under full strain control");
+    if (ctx->n3 & 1) return fail(ctx, DBFFT_E_UNSUPPORTED_GRID, "adjoint: even n3 only");
     const auto t0 = std::chrono::steady_clock::now();
     if (rep) std::memset(rep, 0, sizeof(*rep));
     dbfft_report r1{}, r2{};

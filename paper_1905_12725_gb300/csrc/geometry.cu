@@ -6,7 +6,25 @@ namespace dbfft {
 
 thread_local bool g_pdl_launch = false;
 
-bool supported_len(int n) { return n == 8 || n == 16 || n == 32 || n == 64 || n == 128 || n == 256; }
+bool supported_pow2(int n) { return n == 8 || n == 16 || n == 32 || n == 64 || n == 128 || n == 256; }
+bool supported_odd(int n) {
+#define DBFFT_ODD_CASE(N) case N:
+    switch (n) {
+        DBFFT_ODD_SIZES(DBFFT_ODD_CASE) return true;
+        default: return false;
+    }
+#undef DBFFT_ODD_CASE
+}
+bool supported_len(int n) { return supported_pow2(n) || supported_odd(n); }
+int ax3_odd_lines(int n3, bool dbl) {
+    // 3 component pairs per line, two buffers of n3 complex values each, at most
+    // 96 KB of shared memory and 256 / 8 threads' worth of pairs per CTA
+    const long long per_line = 3LL * 2 * n3 * (dbl ? 16 : 8);
+    long long L = (96LL * 1024) / per_line;
+    if (L > 10) L = 10;
+    if (L < 1) L = 1;
+    return (int)L;
+}
 
 static int radix_for(int n, bool dbl) { return radix_ax2(n, dbl); }
 

@@ -32,14 +32,14 @@ template <typename T>
 cudaError_t launch_fft_ax1(int dir, const Ax2Args<T>& a, cudaStream_t s) {
     switch (a.d.n1) {
         DBFFT_FFT(8, 1) DBFFT_FFT(16, 1) DBFFT_FFT(32, 1) DBFFT_FFT(64, 1) DBFFT_FFT(128, 1) DBFFT_FFT(256, 1)
-        default: return cudaErrorInvalidValue;
+        default: return (a.d.n1 & 1) ? launch_fft_odd<T>(dir, 1, a, s) : cudaErrorInvalidValue;
     }
 }
 template <typename T>
 cudaError_t launch_fft_ax2(int dir, const Ax2Args<T>& a, cudaStream_t s) {
     switch (a.d.n2) {
         DBFFT_FFT(8, 2) DBFFT_FFT(16, 2) DBFFT_FFT(32, 2) DBFFT_FFT(64, 2) DBFFT_FFT(128, 2) DBFFT_FFT(256, 2)
-        default: return cudaErrorInvalidValue;
+        default: return (a.d.n2 & 1) ? launch_fft_odd<T>(dir, 2, a, s) : cudaErrorInvalidValue;
     }
 }
 #undef DBFFT_FFT

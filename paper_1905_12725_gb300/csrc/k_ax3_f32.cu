@@ -3,6 +3,7 @@
 namespace dbfft {
 template <>
 cudaError_t launch_ax3<float>(int opk, const Ax3Args<float>& a, cudaStream_t s) {
+    if (a.d.n3 & 1) return launch_ax3_odd<float>(opk, a, s);
     switch (opk) {
         case OP_ISO: return ax3_sz<float, 6, OP_ISO>(a, s);
         case OP_NH_APPLY: return ax3_sz<float, 9, OP_NH_APPLY>(a, s);

@@ -238,13 +238,13 @@ template cudaError_t launch_mean_tangent<double>(int, int, long long, const doub
                                                  const double*, const double*, double*, int, cudaStream_t);
 
 // Project [B][3][H] half spectra onto Hermitian-consistent vectors: on the
-// planes k3 = 0 and k3 = n3/2 the pair (k1, k2) / (-k1, -k2) is replaced by
+// planes k3 = 0 and (even n3) k3 = n3/2 the pair (k1, k2) / (-k1, -k2) is replaced by
 // its conjugate-symmetric part (one thread per pair).
 template <typename T>
 __global__ void k_herm_planes(Dims d, cplx<T>* v) {
     const long long per = (long long)d.n1 * d.n2;
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= per * 2) return;
+    if (i >= per * (d.n3 % 2 == 0 ? 2 : 1)) return;  // odd n3: the plane k3 = 0 only
     const int plane = (int)(i / per);
     const long long j = i - plane * per;
     const int k1 = (int)(j / d.n2), k2 = (int)(j - (long long)k1 * d.n2);

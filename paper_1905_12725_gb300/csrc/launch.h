@@ -37,7 +37,8 @@ int ax2_tile(int n, bool dbl);                       // columns per CTA of the s
 int ax3_lines(int n3, int nc, int rb, bool dbl, int nfields = 1, int radix = 8);  // default lines per CTA of pass 3
 int ax3_threads_per_line(int n3, int nc, int rb, bool dbl);
 size_t ax3_smem(int n3, int nc, int rb, int lines, bool dbl, bool two_fields);
-bool supported_len(int n);
+bool supported_len(int n);   // powers of two in [8, 256] or the odd lengths below
+bool supported_pow2(int n);  // powers of two in [8, 256]
 
 template <typename T> cudaError_t launch_grad(int mode, const Ax1InvArgs<T>& a, cudaStream_t s);
 template <typename T> cudaError_t launch_div(int mode, const Ax1FwdArgs<T>& a, cudaStream_t s);
@@ -49,6 +50,16 @@ template <typename T> cudaError_t launch_ax3_pipe(int opk, const Ax3Args<T>& a, 
 // pass 3 of the St. Venant-Kirchhoff law (OP_SVK_APPLY in both precisions, OP_SVK_UPDATE in FP64),
 // plain and pipelined; compiled in translation units of their own
 template <typename T> cudaError_t launch_ax3_svk(int opk, const Ax3Args<T>& a, cudaStream_t s);
+// odd transform lengths (prime factors 3, 5, 7; Sec. 2.1's odd grids), compiled in
+// translation units of their own: strided C2C along axis 1 or 2, and pass 3
+// for linear isotropic phases (OP_ISO) with odd n3
+#define DBFFT_ODD_SIZES(X) X(9) X(15) X(21) X(25) X(27) X(35) X(45) X(49) X(63) X(75) X(81) X(105) \
+    X(125) X(135) X(147) X(175) X(189) X(225) X(243) X(245)
+bool supported_odd(int n);
+template <typename T> cudaError_t launch_fft_odd(int dir, int axis, Ax2Args<T> a, cudaStream_t s);
+template <typename T> cudaError_t launch_ax3_odd(int opk, const Ax3Args<T>& a, cudaStream_t s);
+// lines per CTA of the odd pass 3 (one right-hand side per CTA)
+int ax3_odd_lines(int n3, bool dbl);
 // pass 3 of the post-processing transforms (OP_DISP, FP64 only)
 template <typename T> cudaError_t launch_ax3_post(int opk, const Ax3Args<T>& a, cudaStream_t s);
 // shared memory of one pipelined CTA (pipe 1: two stages, 2: one stage), or -1 when (n3, L) is not a valid tile

@@ -65,7 +65,7 @@ extern "C" dbfft_status dbfft_apply_iso_noalloc(const int n[3], const double L[3
                                                 const void* u_hat, void* out, void* stream) {
     if (!n || !phase_id || !lam || !mu || !u_hat || !out || batch < 1) return DBFFT_E_ARG;
     for (int a = 0; a < 3; ++a)
-        if (!supported_len(n[a])) return DBFFT_E_UNSUPPORTED_GRID;
+        if (!supported_pow2(n[a])) return DBFFT_E_UNSUPPORTED_GRID;
     const int n1 = n[0], n2 = n[1], n3 = n[2], m = n3 / 2, h = m + 1;
     const long long H = (long long)n1 * n2 * h;
     const size_t need = (size_t)batch * 6 * (size_t)H * sizeof(cplx<double>);

@@ -86,7 +86,7 @@ def paint_sphere(mask: np.ndarray, centre_vox, radius_vox: float) -> None:
     mask[np.ix_(i1, i2, i3)] = sub | dd
 
 
-def centred_sphere(n: int, radius_vox: int) -> np.ndarray:
+def centred_sphere(n: int, radius_vox: float) -> np.ndarray:
     """Phase map (uint16: 0 matrix, 1 inclusion) of one sphere at the box centre.
 
     With an even n and integer radius, (2d)^2 is a sum of three odd squares,
@@ -271,6 +271,14 @@ def config5(n: int = 64, n_rve: int = 32, radius: float = 6.0, seed: int = SEED_
         vfs.append(vf)
     return dict(phase=np.stack(phases), E=np.array(E), nu=np.array([0.3, 0.3]),
                 vf_target=np.array(vfs))
+
+
+def inclusion(n: int = 63, vf: float = 0.2, contrast: float = 1.0, E: float = 70.0, nu: float = 0.3):
+    """One centred spherical inclusion of volume fraction vf (Sec. 3, first and
+    second benchmarks): matrix E, nu; inclusion contrast * E, same nu. The
+    radius is the one of a ball of volume vf n^3 (voxels)."""
+    r = n * (3.0 * vf / (4.0 * math.pi)) ** (1.0 / 3.0)
+    return dict(phase=centred_sphere(n, r), E=np.array([E, contrast * E]), nu=np.array([nu, nu]), radius=r)
 
 
 def porous_svk(n: int = 64, n_pores: int = 5, porosity: float = 0.2, E: float = 70.0, nu: float = 0.3,
