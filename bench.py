@@ -444,6 +444,35 @@ def case_porous(precision, n=64, n_inc=5, stretch=2.0):
             "other_precond_policies": policies, "phase_sha256": synth.sha256(c["phase"])}
 
 
+def case_inclusion(n=63, tol=1e-8):
+    """The paper's first and second benchmarks on its own odd grid: one centred spherical inclusion
+    (vf 0.2) in a 63^3 box, matrix E 70 / nu 0.3, inclusion k E; uniaxial strain 0.1 % with every
+    component prescribed, and uniaxial stress with every component stress-controlled; PCG to a
+    relative residual of 1e-8 for contrasts k = 1e-5 .. 1e5, FP64 and mixed."""
+    from paper_1905_12725_gb300 import dbfft, synth
+    out = {"case": f"inclusion {n}^3 vf 0.2, contrast sweep", "tol": tol, "rows": []}
+    for k in [1e-5, 1e-4, 1e-3, 1e-2, 1e-1, 1e1, 1e2, 1e3, 1e4, 1e5]:
+        c = synth.inclusion(n, contrast=k)
+        for control in ("strain", "stress"):
+            if control == "strain":
+                mask, target = None, np.diag([1e-3, 0.0, 0.0])
+            else:
+                mask, target = np.ones(9, bool), np.diag([70.0 * 1e-3, 0.0, 0.0])
+            row = {"contrast": k, "control": control}
+            for prec, name in ((dbfft.DBFFT_FP64, "fp64"), (dbfft.DBFFT_MIXED, "mixed")):
+                s = dbfft.Solver((n,) * 3, c["phase"], dbfft.iso_phases(c["E"], c["nu"]), target[None],
+                                 stress_mask=mask, tol=tol, precision=prec, eta_inner=1e-3, max_iter=20000)
+                s.solve_increment(0)  # warm-up (graph capture, first-touch)
+                rep, dt = _timed(lambda: s.solve_increment(0))
+                sig = s.homogenized_stress()[0]
+                row[name] = {"cg": rep["cg_iters"], "ms": dt * 1e3, "true_rel_res": rep["true_rel_res"],
+                             "eps_eq": rep["eps_eq"], "sig_bar_11": sig[0, 0],
+                             "eps_bar_11": float(s.get_solution()[1][0][0]) if control == "stress" else 1e-3}
+                s.close()
+            out["rows"].append(row)
+    return out
+
+
 def case_c4(precision, n=256, n_inc=40, only=None):
     """256^3 Voronoi polycrystal (500 grains), power-law CP, eps_xx to 2% at 1e-3/s in 40 increments."""
     from paper_1905_12725_gb300 import dbfft, synth
@@ -716,11 +745,11 @@ def main():
     ap.add_argument("--skip-256", action="store_true")
     ap.add_argument("--case", default="",
                     choices=["", "op256", "c2", "c1", "c3", "c3fp64", "c4", "c4fp64", "c5", "porous",
-                             "porousfp64"],
+                             "porousfp64", "inclusion"],
                     help="run one sub-measurement only: op256 = 256^3 FP32 CG pass chain, c2 = one mixed "
                          "batched 64^3 solve (profiler captures); c1, c3[fp64], c4[fp64], c5 = the other "
                          "configurations at full size; porous[fp64] = the porous St. Venant-Kirchhoff "
-                         "stretch (64^3)")
+                         "stretch (64^3); inclusion = the 63^3 inclusion contrast sweep")
     args = ap.parse_args()
     if args.case:
         import torch
@@ -730,6 +759,8 @@ def main():
             r = operator_256(torch, dbfft, _peaks()[0], iters=args.steps)
             r["cufft_comparison"] = cufft_operator_256(torch)
             print(json.dumps(r), flush=True)
+        elif args.case == "inclusion":
+            print(json.dumps(case_inclusion(), default=float), flush=True)
         elif args.case in ("c1", "c3", "c3fp64", "c4", "c4fp64", "c5", "porous", "porousfp64"):
             prec = dbfft.DBFFT_FP64 if args.case.endswith("fp64") else dbfft.DBFFT_MIXED
             res = {"c1": lambda: case_c1(), "c3": lambda: case_c3(prec), "c3fp64": lambda: case_c3(prec),

@@ -82,7 +82,10 @@ enum {                                           /* constitutive model of a phas
 
 /* Problem size and solver settings. */
 typedef struct {
-    int n[3];          /* voxels per axis: powers of two in [8, 256]                    */
+    int n[3];          /* voxels per axis: powers of two in [8, 256], or odd lengths
+                          9 .. 245 whose prime factors are 3, 5, 7 (the paper's odd
+                          grids, Sec. 2.1; an odd n3 needs ISO_ELASTIC phases, and
+                          dbfft_adjoint / dbfft_displacement need an even n3)       */
     double L[3];       /* box edge lengths; 0 means 1                                    */
     int batch;         /* B: right-hand sides solved together (>= 1)                     */
     int n_materials;   /* Bm: distinct material maps; B % Bm == 0; solve b uses map
