@@ -436,6 +436,35 @@ def displacement(prob: Problem, u_hat, macro):
     return ut + np.einsum("ij,j...->i...", Hbar, X)
 
 
+def _levi():
+    e = np.zeros((3, 3, 3))
+    for i, j, k in ((0, 1, 2), (1, 2, 0), (2, 0, 1)):
+        e[i, j, k], e[i, k, j] = 1.0, -1.0
+    return e
+
+
+def compatibility(prob: Problem, field_hat, macro_norm):
+    """Compatibility residual (Sec. 3, Eq. chedckcomp; finite strain: curl of F).
+
+    field_hat: the Fourier coefficients (rfftn) of the fluctuating field, [3,3,
+    half spectrum] (strain or displacement gradient). Small strain:
+    eta = curl (curl eps)^T, eta_ij = e_ikl e_jmn d_k d_m eps_ln; finite
+    strain: (curl F)_iJ = e_JKL d_K F_iL, derivatives d = i xi'. Returns
+    (max over the voxels and components of |.|, root mean square over the
+    cell), both divided by macro_norm.
+    """
+    e = _levi()
+    d = np.stack(np.broadcast_arrays(*prob.xi)).astype(np.complex128) * 1j  # [3, half]
+    if prob.kind == "small":
+        eta = np.einsum("ikl,jmn,k...,m...,ln...->ij...", e, e, d, d, field_hat)
+    else:
+        eta = np.einsum("JKL,K...,iL...->iJ...", e, d, field_hat)
+    real = to_real(eta, prob.shape)
+    mx = float(np.abs(real).max())
+    rms = float(np.sqrt(np.sum(real ** 2) / prob.N))  # sqrt of the cell mean of the squared Frobenius norm
+    return mx / macro_norm, rms / macro_norm
+
+
 def linear_rhs(prob: Problem, tangent, target):
     """b = -B^H C epsbar_U + (0, N sigma_f)  (Sec. 2.3 final system, R2)."""
     epsU, sig_f = split_load(prob, target)

@@ -272,6 +272,32 @@ def test_displacement_of_one_fourier_mode_closed_form():
         assert np.abs(u[c] - ref).max() < 1e-15
 
 
+# ---------------------------------------------------------------- compatibility (Eq. chedckcomp)
+def test_compatibility_of_a_gradient_vanishes_and_of_a_shear_wave_is_closed_form():
+    """A symmetric gradient is compatible (0 up to round-off). eps = a sin(2 pi x2) e1 e1
+    (not a gradient) gives eta_33 = -d2 d2 eps_11 = (2 pi)^2 a sin(2 pi x2): max (2 pi)^2 a,
+    RMS (2 pi)^2 a / sqrt 2. For finite strain F = I + b sin(2 pi x2) e1 e1:
+    (curl F)_13 = -d2 F_11, max 2 pi b."""
+    shape = (8, 16, 8)
+    prob = o.Problem(shape, "small")
+    u = synth.random_spectrum(shape, 3, 5)[0]
+    mx, rms = o.compatibility(prob, o.sym_grad_hat(u, prob.xi), 1.0)
+    scale = np.abs(o.to_real(o.sym_grad_hat(u, prob.xi), shape)).max() * (2 * np.pi * 8) ** 2
+    assert mx < 1e-13 * scale and rms < 1e-13 * scale
+    a = 1e-3
+    x2 = (np.arange(16) + 0.5) / 16
+    eps = np.zeros((3, 3) + shape)
+    eps[0, 0] = a * np.sin(2 * np.pi * x2)[None, :, None]
+    mx, rms = o.compatibility(prob, o.to_fourier(eps), 1.0)
+    assert abs(mx - (2 * np.pi) ** 2 * a * np.abs(np.sin(2 * np.pi * x2)).max()) < 1e-12
+    assert abs(rms - (2 * np.pi) ** 2 * a / math.sqrt(2.0)) < 1e-12
+    probf = o.Problem(shape, "finite")
+    G = np.zeros((3, 3) + shape)
+    G[0, 0] = 0.2 * np.sin(2 * np.pi * x2)[None, :, None]
+    mx, _ = o.compatibility(probf, o.to_fourier(G), 1.0)
+    assert abs(mx - 2 * np.pi * 0.2 * np.abs(np.cos(2 * np.pi * x2)).max()) < 1e-12
+
+
 # ---------------------------------------------------------------- laminates (closed forms)
 def _laminate(shape, widths, lam_p, mu_p):
     ph = np.zeros(shape[0], int)
