@@ -245,6 +245,17 @@ dbfft_status dbfft_get_solution(dbfft_ctx* ctx, void* u_hat, double* e);
  */
 dbfft_status dbfft_displacement(dbfft_ctx* ctx, double* out);
 
+/*
+ * Compatibility residual of the current solution (Sec. 3, Eq. chedckcomp and
+ * its finite-strain form): small strain |curl (curl eps)^T| / ||<eps>||,
+ * finite strain |curl F| / ||<F> - I||, with |.| the root mean square over the
+ * cell (Parseval on the half spectrum; the paper takes the maximum over the
+ * voxels) and ||.|| the Frobenius norm. Zero up to round-off, since the
+ * fluctuation is a gradient by construction. out: host double [B]. Errors:
+ * E_ARG, E_STATE (no solution yet), E_CUDA.
+ */
+dbfft_status dbfft_compatibility(dbfft_ctx* ctx, double* out);
+
 /* One row of the per-pass profile. */
 typedef struct {
     char name[40];       /* pass and precision, e.g. "axis3_apply_f32"                  */

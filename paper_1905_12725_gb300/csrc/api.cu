@@ -1822,12 +1822,12 @@ dbfft_status dbfft_get_solution(dbfft_ctx* ctx, void* u_hat, double* e) {
     return DBFFT_OK;
 }
 
-dbfft_status dbfft_displacement(dbfft_ctx* ctx, double* out) {
-    if (!ctx || !out) return DBFFT_E_ARG;
-    if (ctx->n3 & 1) return fail(ctx, DBFFT_E_UNSUPPORTED_GRID, "displacement output: even n3 only");
-    // Hbar = the whole macro strain (small) or Fbar - I (finite), row-major, from the
-    // prescribed part fU (W components) and the solved stress-controlled unknowns
-    std::vector<double> fU((size_t)ctx->B * 9), xe((size_t)ctx->B * 9), hb((size_t)ctx->B * 9);
+// Hbar per right-hand side, row-major [B][9]: the whole macro strain (small) or
+// Fbar - I (finite), from the prescribed part fU (W components) and the solved
+// stress-controlled unknowns.
+dbfft_status macro_hbar(dbfft_ctx* ctx, std::vector<double>& hb) {
+    std::vector<double> fU((size_t)ctx->B * 9), xe((size_t)ctx->B * 9);
+    hb.assign((size_t)ctx->B * 9, 0.0);
     CK(cudaMemcpyAsync(fU.data(), ctx->fU, fU.size() * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaMemcpyAsync(xe.data(), ctx->xe64, xe.size() * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
@@ -1849,6 +1849,39 @@ dbfft_status dbfft_displacement(dbfft_ctx* ctx, double* out) {
             }
         }
     }
+    return DBFFT_OK;
+}
+
+dbfft_status dbfft_compatibility(dbfft_ctx* ctx, double* out) {
+    if (!ctx || !out) return DBFFT_E_ARG;
+    if (!ctx->have_solution) return fail(ctx, DBFFT_E_STATE, "no solution yet");
+    cplx<double>* W = reinterpret_cast<cplx<double>*>(ctx->W);
+    Ax1InvArgs<double> a1{ctx->dims, freq<double>(ctx), twid<double>(ctx), ctx->x64, nullptr, nullptr, W, nullptr,
+                          ctx->pre};
+    TRY(run(ctx, "pass1_grad_f64", (3 + ctx->nc) * cpass(ctx, true, ctx->B),
+            [&] { return launch_grad<double>(AX1_PLAIN, a1, ctx->stream); }));
+    const int nblk = (int)std::min<long long>(256, ctx->nblk_max);
+    TRY(run(ctx, "compatibility", 0.0,
+            [&] { return launch_compat(ctx->dims, freq<double>(ctx), W, ctx->partials, nblk, ctx->stream); }));
+    std::vector<double> ph((size_t)ctx->B * nblk);
+    CK(cudaMemcpyAsync(ph.data(), ctx->partials, ph.size() * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    std::vector<double> hb;
+    TRY(macro_hbar(ctx, hb));
+    for (int b = 0; b < ctx->B; ++b) {
+        double s = 0.0, h2 = 0.0;
+        for (int k = 0; k < nblk; ++k) s += ph[(size_t)b * nblk + k];
+        for (int q = 0; q < 9; ++q) h2 += hb[(size_t)b * 9 + q] * hb[(size_t)b * 9 + q];
+        out[b] = h2 > 0.0 ? std::sqrt(s) / std::sqrt(h2) : std::sqrt(s);
+    }
+    return DBFFT_OK;
+}
+
+dbfft_status dbfft_displacement(dbfft_ctx* ctx, double* out) {
+    if (!ctx || !out) return DBFFT_E_ARG;
+    if (ctx->n3 & 1) return fail(ctx, DBFFT_E_UNSUPPORTED_GRID, "displacement output: even n3 only");
+    std::vector<double> hb;
+    TRY(macro_hbar(ctx, hb));
     CK(cudaMemcpyAsync(ctx->hbar, hb.data(), hb.size() * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
     // the fluctuation: inverse transforms of the three components of u-hat
     cplx<double>* W = reinterpret_cast<cplx<double>*>(ctx->W);

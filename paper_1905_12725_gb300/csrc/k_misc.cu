@@ -276,3 +276,80 @@ template cudaError_t launch_herm_planes<double>(const Dims&, cplx<double>*, cuda
 template cudaError_t launch_herm_planes<float>(const Dims&, cplx<float>*, cudaStream_t);
 
 }  // namespace dbfft
+
+namespace dbfft {
+
+// Levi-Civita symbol e_ijk.
+__device__ __forceinline__ int levi(int i, int j, int k) {
+    return (i == j || j == k || i == k) ? 0 : (((j - i + 3) % 3 == 1) ? 1 : -1);
+}
+
+// Compatibility of the gradient field W ([B][nc][H], Fourier coefficients of the
+// real field; Sec. 3's compatibility check): small strain eta = curl (curl eps)^T,
+// eta_ij = -e_ikl e_jmn xi_k xi_m eps_ln; finite strain (curl F)_iJ =
+// i e_JKL xi_K F_iL. Per right-hand side the whole-spectrum sum of |.|^2 (half
+// spectrum with weights), i.e. the mean of |.|^2 over the cell (Parseval).
+template <int NC>
+__global__ void k_compat(Dims d, Freq<double> f, const cplx<double>* W, double* partials) {
+    __shared__ double red[32];
+    const int b = blockIdx.y;
+    double acc = 0.0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < d.H;
+         i += (long long)gridDim.x * blockDim.x) {
+        const FreqIdx fi = freq_idx(d, i);
+        const double xi[3] = {f.xi1[fi.k1], f.xi2[fi.k2], f.xi3[fi.k3]};
+        const double wgt = hweight(fi.k3, d.m);
+        cplx<double> w[NC];
+        for (int c = 0; c < NC; ++c) w[c] = W[(long long)(b * NC + c) * d.H + i];
+        double s = 0.0;
+        if (NC == 6) {
+            const int ci[6] = {0, 1, 2, 1, 0, 0}, cj[6] = {0, 1, 2, 2, 2, 1};
+            cplx<double> E[3][3];
+            for (int c = 0; c < 6; ++c) E[ci[c]][cj[c]] = E[cj[c]][ci[c]] = w[c];
+            for (int ii = 0; ii < 3; ++ii)
+                for (int jj = 0; jj < 3; ++jj) {
+                    double er = 0.0, ei = 0.0;
+                    for (int k = 0; k < 3; ++k)
+                        for (int l = 0; l < 3; ++l) {
+                            const int e1 = levi(ii, k, l);
+                            if (!e1) continue;
+                            for (int m = 0; m < 3; ++m)
+                                for (int n = 0; n < 3; ++n) {
+                                    const int e2 = levi(jj, m, n);
+                                    if (!e2) continue;
+                                    const double c = -(double)(e1 * e2) * xi[k] * xi[m];
+                                    er += c * E[l][n].x;
+                                    ei += c * E[l][n].y;
+                                }
+                        }
+                    s += er * er + ei * ei;
+                }
+        } else {
+            for (int ii = 0; ii < 3; ++ii)
+                for (int J = 0; J < 3; ++J) {
+                    double er = 0.0, ei = 0.0;
+                    for (int K = 0; K < 3; ++K)
+                        for (int L = 0; L < 3; ++L) {
+                            const int e1 = levi(J, K, L);
+                            if (!e1) continue;
+                            er += e1 * xi[K] * w[3 * ii + L].x;
+                            ei += e1 * xi[K] * w[3 * ii + L].y;
+                        }
+                    s += er * er + ei * ei;  // |i (er + i ei)|^2
+                }
+        }
+        acc += wgt * s;
+    }
+    double v1[1] = {acc};
+    block_sum<1>(v1, red);
+    if (threadIdx.x == 0) partials[(long long)b * gridDim.x + blockIdx.x] = v1[0];
+}
+
+cudaError_t launch_compat(const Dims& d, const Freq<double>& f, const cplx<double>* W, double* partials, int nblk,
+                          cudaStream_t s) {
+    if (d.nc == 6) k_compat<6><<<dim3(nblk, d.B), 256, 0, s>>>(d, f, W, partials);
+    else k_compat<9><<<dim3(nblk, d.B), 256, 0, s>>>(d, f, W, partials);
+    return cudaGetLastError();
+}
+
+}  // namespace dbfft

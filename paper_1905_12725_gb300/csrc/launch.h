@@ -50,6 +50,10 @@ template <typename T> cudaError_t launch_ax3_pipe(int opk, const Ax3Args<T>& a, 
 // pass 3 of the St. Venant-Kirchhoff law (OP_SVK_APPLY in both precisions, OP_SVK_UPDATE in FP64),
 // plain and pipelined; compiled in translation units of their own
 template <typename T> cudaError_t launch_ax3_svk(int opk, const Ax3Args<T>& a, cudaStream_t s);
+// compatibility of the gradient field W (small: curl curl eps; finite: curl F):
+// per-RHS partial sums of |.|^2 over the spectrum into partials [B][nblk]
+cudaError_t launch_compat(const Dims& d, const Freq<double>& f, const cplx<double>* W, double* partials, int nblk,
+                          cudaStream_t s);
 // odd transform lengths (prime factors 3, 5, 7; Sec. 2.1's odd grids), compiled in
 // translation units of their own: strided C2C along axis 1 or 2, and pass 3
 // for linear isotropic phases (OP_ISO) with odd n3

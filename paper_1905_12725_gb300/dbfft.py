@@ -75,7 +75,7 @@ EXPORTS = ["dbfft_create", "dbfft_apply", "dbfft_solve_increment", "dbfft_homoge
            "dbfft_homogenized_tangent", "dbfft_adjoint", "dbfft_get_solution", "dbfft_device_bytes",
            "dbfft_destroy", "dbfft_last_error", "dbfft_status_string", "dbfft_profile",
            "dbfft_profile_read", "dbfft_launch_count", "dbfft_apply_iso_noalloc", "dbfft_autotune",
-           "dbfft_tuning", "dbfft_set_pass3_shape", "dbfft_set_precond_refresh", "dbfft_displacement"]
+           "dbfft_tuning", "dbfft_set_pass3_shape", "dbfft_set_precond_refresh", "dbfft_displacement", "dbfft_compatibility"]
 
 _LIB = None
 
@@ -137,6 +137,8 @@ def load_library(build_if_missing: bool = True):
     lib.dbfft_set_precond_refresh.restype = ip
     lib.dbfft_displacement.argtypes = [vp, vp]
     lib.dbfft_displacement.restype = ip
+    lib.dbfft_compatibility.argtypes = [vp, dp]
+    lib.dbfft_compatibility.restype = ip
     _LIB = lib
     return lib
 
@@ -374,6 +376,12 @@ class Solver:
         e = np.zeros((self.batch, 9))
         self._check(self.lib.dbfft_get_solution(self.ctx, C.c_void_p(u.data_ptr()), _dptr(e)))
         return u, e
+
+    def compatibility(self):
+        """Compatibility residual per right-hand side (dbfft_compatibility), numpy [B]."""
+        out = np.zeros(self.batch)
+        self._check(self.lib.dbfft_compatibility(self.ctx, _dptr(out)))
+        return out
 
     def displacement(self):
         """Total displacement at the voxel centres, device float64 [B, 3, n1, n2, n3]."""

@@ -1,8 +1,12 @@
-"""GPU parity of the total displacement output (Sec. 2.2, Eqs. disp_decomp and
-decomp_displ; Sec. 2.4): dbfft_displacement against the oracle's displacement of
-the same u-hat and macro unknowns, element by element (FP64, 1e-12 of the field's
-largest entry), at small strain with a stress-controlled component on a
-non-cubic box and at finite strain under mixed control.
+"""GPU parity of the post-processing outputs.
+
+* Total displacement (Sec. 2.2, Eqs. disp_decomp and decomp_displ; Sec. 2.4):
+  dbfft_displacement against the oracle's displacement of the same u-hat and
+  macro unknowns, element by element (FP64, 1e-12 of the field's largest
+  entry), at small strain with a stress-controlled component on a non-cubic box
+  and at finite strain under mixed control.
+* Compatibility residual (Sec. 3, Eq. chedckcomp): zero up to round-off on the
+  GPU and in the oracle for the same solutions (bar 1e-12).
 """
 import numpy as np
 import pytest
@@ -76,3 +80,35 @@ def test_displacement_finite_strain_mixed_control_batch():
         fU, _ = o.split_load(prob, t)
         ref = o.displacement(prob, uh.cpu().numpy()[b], o.macro_field(prob, fU, e9_to_oracle(prob, e[b])))
         assert _max_rel(u_gpu[b], ref) < 1e-12, b
+
+
+def test_compatibility_residual_is_round_off():
+    dbfft = _dbfft()
+    shape = (16, 8, 16)
+    phase = (np.random.default_rng(9).random(shape) < 0.3).astype(np.uint16)
+    # small strain, stress-controlled shear
+    mask = np.zeros((3, 3), bool)
+    mask[0, 1] = mask[1, 0] = True
+    tgt = np.diag([1e-3, -2e-4, 0.0])
+    s = dbfft.Solver(shape, phase, dbfft.iso_phases([1.0, 20.0], [0.3, 0.3]), tgt[None],
+                     stress_mask=mask.reshape(-1), tol=1e-12)
+    s.solve_increment(0)
+    c_gpu = s.compatibility()[0]
+    uh, e = s.get_solution()
+    s.close()
+    prob = o.Problem(shape, "small", mask.reshape(-1))
+    fU, _ = o.split_load(prob, tgt)
+    macro = o.macro_field(prob, fU, e9_to_oracle(prob, e[0]))
+    mx, rms = o.compatibility(prob, o.sym_grad_hat(uh.cpu().numpy()[0], prob.xi), np.linalg.norm(macro))
+    assert 0.0 <= c_gpu < 1e-12 and mx < 1e-12 and rms < 1e-12, (c_gpu, mx, rms)
+    # finite strain (Neo-Hooke), full F control
+    F = np.array([[1.1, 0.02, 0.0], [0.0, 0.97, 0.01], [0.0, 0.0, 1.0]])
+    s = dbfft.Solver(shape, phase, dbfft.neo_hooke_phases([1.0, 10.0], [1.5, 15.0]), F[None],
+                     kinematics=dbfft.DBFFT_FINITE, newton_tol=1e-10, eta_inner=1e-6, tol=1e-12)
+    s.solve_increment(0)
+    c_gpu = s.compatibility()[0]
+    uh, _ = s.get_solution()
+    s.close()
+    probf = o.Problem(shape, "finite")
+    mx, rms = o.compatibility(probf, o.grad_hat(uh.cpu().numpy()[0], probf.xi), np.linalg.norm(F - np.eye(3)))
+    assert 0.0 <= c_gpu < 1e-12 and mx < 1e-12 and rms < 1e-12, (c_gpu, mx, rms)
