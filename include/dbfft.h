@@ -84,8 +84,9 @@ enum {                                           /* constitutive model of a phas
 typedef struct {
     int n[3];          /* voxels per axis: powers of two in [8, 256], or odd lengths
                           9 .. 245 whose prime factors are 3, 5, 7 (the paper's odd
-                          grids, Sec. 2.1; an odd n3 needs ISO_ELASTIC phases, and
-                          dbfft_adjoint / dbfft_displacement need an even n3)       */
+                          grids, Sec. 2.1; with nonlinear phases an odd n3 is one
+                          of 9, 15, 21, 27, 45, 63, 81; dbfft_adjoint and
+                          dbfft_displacement need an even n3)                       */
     double L[3];       /* box edge lengths; 0 means 1                                    */
     int batch;         /* B: right-hand sides solved together (>= 1)                     */
     int n_materials;   /* Bm: distinct material maps; B % Bm == 0; solve b uses map

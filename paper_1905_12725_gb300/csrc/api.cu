@@ -1486,8 +1486,8 @@ static dbfft_status create_impl(dbfft_ctx* ctx, const dbfft_grid* grid, const db
         if (mat->phases[p].model != ctx->model) return fail(ctx, DBFFT_E_ARG, "all phases must use one model kind");
     if ((ctx->model == DBFFT_NEO_HOOKE || ctx->model == DBFFT_SVK) != (ctx->kin == DBFFT_FINITE))
         return fail(ctx, DBFFT_E_ARG, "NEO_HOOKE and SVK need FINITE kinematics; ISO_ELASTIC and CP need SMALL");
-    if ((ctx->n3 & 1) && ctx->model != DBFFT_ISO_ELASTIC)
-        return fail(ctx, DBFFT_E_UNSUPPORTED_GRID, "odd n3: linear isotropic phases only");
+    if ((ctx->n3 & 1) && ctx->model != DBFFT_ISO_ELASTIC && !supported_odd_nl(ctx->n3))
+        return fail(ctx, DBFFT_E_UNSUPPORTED_GRID, "odd n3 with nonlinear phases: 9, 15, 21, 27, 45, 63 or 81");
     if (ctx->model != DBFFT_ISO_ELASTIC && ctx->Rm != 1)
         return fail(ctx, DBFFT_E_ARG, "nonlinear models need one material map per right-hand side");
     if (!load || !load->target || load->n_increments < 1) return fail(ctx, DBFFT_E_ARG, "load");

@@ -15,13 +15,22 @@ bool supported_odd(int n) {
     }
 #undef DBFFT_ODD_CASE
 }
+bool supported_odd_nl(int n) {
+#define DBFFT_ODD_CASE(N) case N:
+    switch (n) {
+        DBFFT_ODD_NL_SIZES(DBFFT_ODD_CASE) return true;
+        default: return false;
+    }
+#undef DBFFT_ODD_CASE
+}
 bool supported_len(int n) { return supported_pow2(n) || supported_odd(n); }
-int ax3_odd_lines(int n3, bool dbl) {
-    // 3 component pairs per line, two buffers of n3 complex values each, at most
-    // 96 KB of shared memory and 256 / 8 threads' worth of pairs per CTA
-    const long long per_line = 3LL * 2 * n3 * (dbl ? 16 : 8);
+int ax3_odd_lines(int n3, int nc, bool dbl) {
+    // ceil(nc/2) component pairs per line, two buffers of n3 complex values each,
+    // at most 96 KB of shared memory and 256 / 8 threads' worth of pairs per CTA
+    const int npl = (nc + 1) / 2;
+    const long long per_line = (long long)npl * 2 * n3 * (dbl ? 16 : 8);
     long long L = (96LL * 1024) / per_line;
-    if (L > 10) L = 10;
+    if (L > 32 / npl) L = 32 / npl;
     if (L < 1) L = 1;
     return (int)L;
 }

@@ -59,11 +59,17 @@ cudaError_t launch_compat(const Dims& d, const Freq<double>& f, const cplx<doubl
 // for linear isotropic phases (OP_ISO) with odd n3
 #define DBFFT_ODD_SIZES(X) X(9) X(15) X(21) X(25) X(27) X(35) X(45) X(49) X(63) X(75) X(81) X(105) \
     X(125) X(135) X(147) X(175) X(189) X(225) X(243) X(245)
+// odd n3 with the nonlinear models (their pass-3 instantiations)
+#define DBFFT_ODD_NL_SIZES(X) X(9) X(15) X(21) X(27) X(45) X(63) X(81)
 bool supported_odd(int n);
+bool supported_odd_nl(int n);
 template <typename T> cudaError_t launch_fft_odd(int dir, int axis, Ax2Args<T> a, cudaStream_t s);
 template <typename T> cudaError_t launch_ax3_odd(int opk, const Ax3Args<T>& a, cudaStream_t s);
-// lines per CTA of the odd pass 3 (one right-hand side per CTA)
-int ax3_odd_lines(int n3, bool dbl);
+// the nonlinear operations of the odd pass 3 (translation units of their own)
+template <typename T> cudaError_t launch_ax3_odd_nl(int opk, const Ax3Args<T>& a, cudaStream_t s);
+cudaError_t launch_ax3_odd_cp(int opk, const Ax3Args<double>& a, cudaStream_t s);
+// lines per CTA of the odd pass 3 (one right-hand side per CTA; nc components)
+int ax3_odd_lines(int n3, int nc, bool dbl);
 // pass 3 of the post-processing transforms (OP_DISP, FP64 only)
 template <typename T> cudaError_t launch_ax3_post(int opk, const Ax3Args<T>& a, cudaStream_t s);
 // shared memory of one pipelined CTA (pipe 1: two stages, 2: one stage), or -1 when (n3, L) is not a valid tile

@@ -127,10 +127,92 @@ def test_odd_63_cubed_operator_matches_oracle():
         assert rel_err(out.cpu().numpy()[0], ref) < (2e-5 if fp32 else 1e-12), fp32
 
 
-def test_odd_n3_refuses_nonlinear_models():
+def test_odd_n3_nonlinear_outside_the_compiled_lengths_is_refused():
     dbfft = _dbfft()
-    shape = (8, 8, 9)
+    shape = (8, 8, 25)
     with pytest.raises(dbfft.DbfftError) as ei:
         dbfft.Solver(shape, np.zeros(shape, np.uint16), dbfft.neo_hooke_phases([1.0], [1.5]), np.eye(3)[None],
                      kinematics=dbfft.DBFFT_FINITE)
     assert dbfft.STATUS[ei.value.status] == "DBFFT_E_UNSUPPORTED_GRID"
+
+
+def test_odd_n3_neo_hooke_and_svk_tangent_operators():
+    """Nine gradient components on an odd axis 3 (five component pairs, the last with a
+    zero partner): constitutive update (residual) and tangent application, FP64 and FP32."""
+    shape = (9, 8, 15)
+    phase = (np.random.default_rng(8).random(shape) < 0.3).astype(np.uint16)
+    mu = np.array([1.0, 20.0])
+    lam = 1.5 * mu
+    Fbar = np.array([[1.05, 0.02, 0.0], [0.01, 0.97, 0.03], [0.0, -0.02, 1.01]])
+    dbfft = _dbfft()
+    prob = o.Problem(shape, "finite")
+    for law, phases_fn, oracle_fn in (("nh", dbfft.neo_hooke_phases, o.neo_hooke), ("svk", dbfft.svk_phases, o.svk)):
+        for fp32 in (False, True):
+            s = dbfft.Solver(shape, phase, phases_fn(mu, lam), Fbar[None], kinematics=dbfft.DBFFT_FINITE,
+                             precision=dbfft.DBFFT_MIXED if fp32 else dbfft.DBFFT_FP64)
+            x = synth.random_spectrum(shape, 3, 31) * 2e-4
+            r, _ = s.apply(torch.from_numpy(x).cuda(), residual=True)
+            F = prob.field_from(x[0], np.zeros(0)) + Fbar[:, :, None, None, None]
+            Pf, Kf = oracle_fn(F, mu[phase], lam[phase])
+            qu, _ = prob.adjoint(Pf)
+            assert rel_err(r.cpu().numpy()[0], -qu) < 1e-12, (law, fp32)
+            u = synth.random_spectrum(shape, 3, 32)
+            out, _ = s.apply(torch.from_numpy(u).cuda(), fp32=fp32)
+            ref, _ = prob.apply_K(o.FullTangent(Kf), u[0], np.zeros(0))
+            s.close()
+            assert rel_err(out.cpu().numpy()[0], ref) < (2e-5 if fp32 else 1e-12), (law, fp32)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_odd_n3_porous_svk_increments(precision):
+    """The porous St. Venant-Kirchhoff stretch on an odd 15^3 grid, strain control."""
+    c = synth.porous_svk(15, 2, 0.15, seed=5)
+    phase, mu, lam = c["phase"], c["mu"], c["lam"]
+    n_inc, F11 = 2, 1.2
+    targets = []
+    for k in range(n_inc):
+        t = np.eye(3)
+        t[0, 0] = 1.0 + (F11 - 1.0) * (k + 1) / n_inc
+        targets.append(t)
+    dbfft = _dbfft()
+    s = dbfft.Solver(phase.shape, phase, dbfft.svk_phases(mu, lam), targets[-1][None], kinematics=dbfft.DBFFT_FINITE,
+                     precision=precision, n_increments=n_inc, newton_tol=1e-11 if precision == 0 else 1e-8,
+                     eta_inner=1e-6 if precision == 0 else 1e-3, tol=1e-12, max_newton=40)
+    prob = o.Problem(phase.shape, "finite")
+    ref, _ = o.newton_increments(prob, o.svk_material(mu[phase], lam[phase]), targets, newton_tol=1e-12,
+                                 load_tol=1e-13, eta=1e-8)
+    for k in range(n_inc):
+        rep = s.solve_increment(k)
+        assert rel_err(s.homogenized_stress()[0], ref[k]["stress_bar"]) < (1e-10 if precision == 0 else 1e-6), (k, rep)
+    s.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_odd_n3_crystal_plasticity_increments(precision):
+    """Polycrystal on an 8 x 8 x 9 grid (odd axis 3): CP update and tangent on paired lines."""
+    shape = (8, 8, 9)
+    rng = synth.Xoshiro256ss(777)
+    g8, _ = synth.periodic_voronoi(8, 4, rng)
+    grains = np.concatenate([g8, g8[:, :, :1]], axis=2).astype(np.uint16)
+    quats = synth.uniform_quaternions(4, rng)
+    mask = np.ones((3, 3), bool)
+    mask[0, 0] = False
+    n_inc, dt = 3, 0.5
+    targets = []
+    for k in range(n_inc):
+        t = np.zeros((3, 3))
+        t[0, 0] = 1e-3 * dt * (k + 1)
+        targets.append(t)
+    dbfft = _dbfft()
+    s = dbfft.Solver(shape, grains, dbfft.cp_phases(quats), targets[-1][None], stress_mask=mask.reshape(-1),
+                     precision=precision, n_increments=n_inc, total_time=n_inc * dt,
+                     newton_tol=1e-11 if precision == 0 else 1e-8, load_tol=1e-12 if precision == 0 else 1e-9,
+                     eta_inner=1e-6 if precision == 0 else 1e-3)
+    cp = o.CrystalPlasticity(quats)
+    prob = o.Problem(shape, "small", mask.reshape(-1))
+    ref, _ = o.newton_increments(prob, o.cp_material(cp, grains, dt), targets, newton_tol=1e-12, load_tol=1e-13,
+                                 eta=1e-8)
+    for k in range(n_inc):
+        rep = s.solve_increment(k)
+        assert rel_err(s.homogenized_stress()[0], ref[k]["stress_bar"]) < (1e-10 if precision == 0 else 1e-6), (k, rep)
+    s.close()
