@@ -745,11 +745,11 @@ def main():
     ap.add_argument("--skip-256", action="store_true")
     ap.add_argument("--case", default="",
                     choices=["", "op256", "c2", "c1", "c3", "c3fp64", "c4", "c4fp64", "c5", "porous",
-                             "porousfp64", "inclusion"],
+                             "porousfp64", "porous63", "porous63fp64", "inclusion"],
                     help="run one sub-measurement only: op256 = 256^3 FP32 CG pass chain, c2 = one mixed "
                          "batched 64^3 solve (profiler captures); c1, c3[fp64], c4[fp64], c5 = the other "
                          "configurations at full size; porous[fp64] = the porous St. Venant-Kirchhoff "
-                         "stretch (64^3); inclusion = the 63^3 inclusion contrast sweep")
+                         "stretch (64^3; porous63[fp64] on the paper's 63^3 grid); inclusion = the 63^3 inclusion contrast sweep")
     args = ap.parse_args()
     if args.case:
         import torch
@@ -759,6 +759,9 @@ def main():
             r = operator_256(torch, dbfft, _peaks()[0], iters=args.steps)
             r["cufft_comparison"] = cufft_operator_256(torch)
             print(json.dumps(r), flush=True)
+        elif args.case in ("porous63", "porous63fp64"):
+            prec = dbfft.DBFFT_FP64 if args.case.endswith("fp64") else dbfft.DBFFT_MIXED
+            print(json.dumps(case_porous(prec, n=63), default=float), flush=True)
         elif args.case == "inclusion":
             print(json.dumps(case_inclusion(), default=float), flush=True)
         elif args.case in ("c1", "c3", "c3fp64", "c4", "c4fp64", "c5", "porous", "porousfp64"):
