@@ -14,6 +14,8 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -31,6 +33,7 @@ struct DevBuf {
     void* p = nullptr;
     size_t n = 0;
 };
+
 
 }  // namespace
 
@@ -99,6 +102,8 @@ struct dbfft_ctx {
     cplx<double>* xfwd = nullptr;
     double* fU = nullptr;
     double* hbar = nullptr;  // [B][9] macro displacement gradient (displacement output)
+    char* small_cur = nullptr;  // small-object arena: next free byte and bytes left in the block
+    size_t small_left = 0;
     double* sigf = nullptr;
     double* sig0 = nullptr;
     double* macroW = nullptr;
@@ -248,8 +253,70 @@ double mat_bytes(const dbfft_ctx* ctx, bool dbl, bool update) {
     return (double)ctx->B * V * (2.0 + ctx->ntan * tw + 4 * 6 * 8.0);
 }
 
+// Pinned host buffers (CG state, partial sums) outlive their context in a
+// process-wide cache keyed by size: page-locking memory costs far more than a
+// context's whole set-up, and repeated contexts of one problem reuse the same
+// sizes. At most kPinnedCacheBytes stay cached.
+constexpr size_t kPinnedCacheBytes = 64u << 20;
+std::mutex g_pinned_mu;
+std::multimap<size_t, void*> g_pinned_free;
+size_t g_pinned_cached = 0;
+
+void* pinned_alloc(size_t bytes) {
+    {
+        std::lock_guard<std::mutex> lk(g_pinned_mu);
+        auto it = g_pinned_free.find(bytes);
+        if (it != g_pinned_free.end()) {
+            void* p = it->second;
+            g_pinned_free.erase(it);
+            g_pinned_cached -= bytes;
+            return p;
+        }
+    }
+    void* p = nullptr;
+    if (cudaMallocHost(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return p;
+}
+
+void pinned_free(void* p, size_t bytes) {
+    if (!p) return;
+    {
+        std::lock_guard<std::mutex> lk(g_pinned_mu);
+        if (g_pinned_cached + bytes <= kPinnedCacheBytes) {
+            g_pinned_free.emplace(bytes, p);
+            g_pinned_cached += bytes;
+            return;
+        }
+    }
+    cudaFreeHost(p);
+}
+
+constexpr size_t kSmallMax = 64 * 1024;     // requests up to this size ...
+constexpr size_t kSmallBlock = 1024 * 1024;  // ... are carved from blocks of this size
+
+dbfft_status dalloc_raw(dbfft_ctx* ctx, size_t bytes, void** out);
+
 dbfft_status dalloc(dbfft_ctx* ctx, size_t bytes, void** out) {
     bytes = (bytes + 255) & ~(size_t)255;
+    if (bytes <= kSmallMax) {  // the many small tables of a context share a few allocations
+        if (ctx->small_left < bytes) {
+            void* blk = nullptr;
+            TRY(dalloc_raw(ctx, kSmallBlock, &blk));
+            ctx->small_cur = static_cast<char*>(blk);
+            ctx->small_left = kSmallBlock;
+        }
+        *out = ctx->small_cur;
+        ctx->small_cur += bytes;
+        ctx->small_left -= bytes;
+        return DBFFT_OK;
+    }
+    return dalloc_raw(ctx, bytes, out);
+}
+
+dbfft_status dalloc_raw(dbfft_ctx* ctx, size_t bytes, void** out) {
     void* p = nullptr;
     if (ctx->use_cb) {
         p = ctx->alloc.alloc(bytes, ctx->alloc.user);
@@ -1438,9 +1505,9 @@ void dbfft_destroy(dbfft_ctx* ctx) {
         if (ctx->use_cb) ctx->alloc.free(b.p, ctx->alloc.user);
         else cudaFree(b.p);
     }
-    if (ctx->cg_h) cudaFreeHost(ctx->cg_h);
-    if (ctx->part_h) cudaFreeHost(ctx->part_h);
-    if (ctx->small_h) cudaFreeHost(ctx->small_h);
+    pinned_free(ctx->cg_h, ctx->B * sizeof(CgState));
+    pinned_free(ctx->part_h, ctx->partials_n * sizeof(double));
+    pinned_free(ctx->small_h, (ctx->B * 10 + 8) * sizeof(double));
     delete ctx;
 }
 
@@ -1541,8 +1608,17 @@ static dbfft_status create_impl(dbfft_ctx* ctx, const dbfft_grid* grid, const db
     // materials
     const size_t nvox = (size_t)ctx->Bm * ctx->V;
     TRY(dalloc_t(ctx, nvox, &ctx->phase));
-    for (size_t i = 0; i < nvox; ++i)
-        if (mat->phase_id[i] >= mat->n_phases) return fail(ctx, DBFFT_E_ARG, "phase id out of range");
+    // one pass over the maps: range check and the voxel count of every phase per material group
+    std::vector<long long> pcount((size_t)ctx->Bm * mat->n_phases, 0);
+    for (int g = 0; g < ctx->Bm; ++g) {
+        const uint16_t* ids = mat->phase_id + (size_t)g * ctx->V;
+        long long* cg = pcount.data() + (size_t)g * mat->n_phases;
+        for (long long v = 0; v < ctx->V; ++v) {
+            const unsigned id = ids[v];
+            if (id >= (unsigned)mat->n_phases) return fail(ctx, DBFFT_E_ARG, "phase id out of range");
+            ++cg[id];
+        }
+    }
     CK(cudaMemcpyAsync(ctx->phase, mat->phase_id, nvox * sizeof(uint16_t), cudaMemcpyHostToDevice, ctx->stream));
     if (mat->E_scale) {
         for (size_t i = 0; i < nvox; ++i)
@@ -1645,27 +1721,26 @@ static dbfft_status create_impl(dbfft_ctx* ctx, const dbfft_grid* grid, const db
     ctx->pre_h.assign(ctx->Bm, PrecondData{});
     for (int g = 0; g < ctx->Bm; ++g) {
         double C[3][3][3][3];
-        if (ctx->model == DBFFT_ISO_ELASTIC) {
+        const long long* cnt = pcount.data() + (size_t)g * np;
+        if (ctx->model == DBFFT_ISO_ELASTIC || ctx->model == DBFFT_NEO_HOOKE || ctx->model == DBFFT_SVK) {
+            // ISO: mean stiffness; NH, SVK: initial tangent K(I) = isotropic C of the mean moduli
             double sl = 0.0, sm = 0.0;
-            for (long long v = 0; v < ctx->V; ++v) {
-                const int p = mat->phase_id[(size_t)g * ctx->V + v];
-                const double s = mat->E_scale ? mat->E_scale[(size_t)g * ctx->V + v] : 1.0;
-                sl += ctx->lam_h[p] * s;
-                sm += ctx->mu_h[p] * s;
-            }
-            iso_C(sl / ctx->V, sm / ctx->V, C);
-        } else if (ctx->model == DBFFT_NEO_HOOKE || ctx->model == DBFFT_SVK) {  // initial tangent K(I) = isotropic C
-            double sl = 0.0, sm = 0.0;
-            for (long long v = 0; v < ctx->V; ++v) {
-                const int p = mat->phase_id[(size_t)g * ctx->V + v];
-                sl += ctx->lam_h[p];
-                sm += ctx->mu_h[p];
+            if (ctx->model == DBFFT_ISO_ELASTIC && mat->E_scale) {
+                for (long long v = 0; v < ctx->V; ++v) {
+                    const int p = mat->phase_id[(size_t)g * ctx->V + v];
+                    const double s = mat->E_scale[(size_t)g * ctx->V + v];
+                    sl += ctx->lam_h[p] * s;
+                    sm += ctx->mu_h[p] * s;
+                }
+            } else {
+                for (int p = 0; p < np; ++p) {
+                    sl += (double)cnt[p] * ctx->lam_h[p];
+                    sm += (double)cnt[p] * ctx->mu_h[p];
+                }
             }
             iso_C(sl / ctx->V, sm / ctx->V, C);
         } else {  // elastic stiffness of the grains
             double Cs[3][3][3][3] = {};
-            std::vector<long long> cnt(np, 0);
-            for (long long v = 0; v < ctx->V; ++v) cnt[mat->phase_id[(size_t)g * ctx->V + v]]++;
             for (int p = 0; p < np; ++p) {
                 if (!cnt[p]) continue;
                 CpGrain gg;
@@ -1728,11 +1803,11 @@ static dbfft_status create_impl(dbfft_ctx* ctx, const dbfft_grid* grid, const db
         ctx->nblk_max = (int)nb;
         ctx->partials_n = std::max((size_t)ctx->B * (size_t)nb * 2, (size_t)ctx->B * kMeanTangentBlocks * 81);
         TRY(dalloc_t(ctx, ctx->partials_n, &ctx->partials));
-        if (cudaMallocHost(&ctx->part_h, ctx->partials_n * sizeof(double)) != cudaSuccess)
+        if (!(ctx->part_h = static_cast<double*>(pinned_alloc(ctx->partials_n * sizeof(double)))))
             return fail(ctx, DBFFT_E_NOMEM, "pinned host allocation failed");
     }
-    if (cudaMallocHost(&ctx->cg_h, ctx->B * sizeof(CgState)) != cudaSuccess ||
-        cudaMallocHost(&ctx->small_h, (ctx->B * 10 + 8) * sizeof(double)) != cudaSuccess)
+    if (!(ctx->cg_h = static_cast<CgState*>(pinned_alloc(ctx->B * sizeof(CgState)))) ||
+        !(ctx->small_h = static_cast<double*>(pinned_alloc((ctx->B * 10 + 8) * sizeof(double)))))
         return fail(ctx, DBFFT_E_NOMEM, "pinned host allocation failed");
     // nonlinear tangent and state
     if (ctx->model != DBFFT_ISO_ELASTIC) {
