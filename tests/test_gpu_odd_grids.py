@@ -16,7 +16,8 @@ from tests.helpers import e9_to_oracle, e_oracle_to9, iso_tangent, mask9, rel_er
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-SHAPES = [(15, 9, 21), (21, 16, 9), (16, 15, 32), (9, 9, 9), (27, 25, 45)]
+SHAPES = [(15, 9, 21), (21, 16, 9), (16, 15, 32), (9, 9, 9), (27, 25, 45),
+          (243, 9, 8), (8, 245, 9), (9, 8, 243)]  # the largest compiled odd lengths on each axis
 
 
 def _dbfft():
