@@ -925,8 +925,21 @@ dbfft_status inner_cg(dbfft_ctx* ctx, double tol, long long& it_sum, int& it_max
     const int opk = opk_apply(ctx);
 
     const int pi_ = dbl ? 1 : 0;
-    if (ctx->use_graphs && !ctx->prof && ctx->graph_warm[pi_]) {
-        // the whole inner solve as one graph launch (kernels already configured by a warm run)
+    if (ctx->use_graphs && !ctx->prof && !ctx->graph_warm[pi_] && !ctx->cg_exec[pi_]) {
+        // first inner solve of this context: capture it right away. A launcher whose
+        // one-time set-up cannot run under capture makes this fail; the solve then
+        // runs launch by launch once (which does that set-up) and captures next time.
+        const std::string keep = ctx->err;
+        const bool pdl = ctx->use_pdl;
+        if (build_cg_graph<T>(ctx, a1, a2, a3, a5, opk_apply(ctx), &ctx->cg_exec[pi_]) != DBFFT_OK) {
+            ctx->cg_exec[pi_] = nullptr;
+            ctx->err = keep;
+            ctx->use_pdl = pdl;
+            cudaGetLastError();
+        }
+    }
+    if (ctx->use_graphs && !ctx->prof && (ctx->graph_warm[pi_] || ctx->cg_exec[pi_])) {
+        // the whole inner solve as one graph launch
         if (!ctx->cg_exec[pi_]) TRY(build_cg_graph<T>(ctx, a1, a2, a3, a5, opk_apply(ctx), &ctx->cg_exec[pi_]));
         CK(cudaGraphLaunch(ctx->cg_exec[pi_], ctx->stream));
         CK(cudaMemcpyAsync(ctx->cg_h, ctx->cg, ctx->B * sizeof(CgState), cudaMemcpyDeviceToHost, ctx->stream));

@@ -19,9 +19,10 @@ static cudaError_t ax3_nr(const Ax3Args<T>& a, cudaStream_t s) {
         cudaFuncAttributes fa;
         cudaError_t e = cudaFuncGetAttributes(&fa, k_axis3<T, N3, NC, OPK, RW>);
         if (e != cudaSuccess) return e;
-        max_dyn = 227 * 1024 - (int)fa.sharedSizeBytes;
-        e = cudaFuncSetAttribute(k_axis3<T, N3, NC, OPK, RW>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_dyn);
+        const int md = 227 * 1024 - (int)fa.sharedSizeBytes;
+        e = cudaFuncSetAttribute(k_axis3<T, N3, NC, OPK, RW>, cudaFuncAttributeMaxDynamicSharedMemorySize, md);
         if (e != cudaSuccess) return e;
+        max_dyn = md;  // set once the attribute is in place
     }
     if (smem > (size_t)max_dyn) return cudaErrorInvalidConfiguration;
     return launch_k(k_axis3<T, N3, NC, OPK, RW>, grid, dim3(threads), smem, s, a);

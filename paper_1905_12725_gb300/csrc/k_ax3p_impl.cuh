@@ -22,9 +22,10 @@ static cudaError_t pipe_nrs(const Ax3Args<T>& a, cudaStream_t s) {
         cudaFuncAttributes fa;
         cudaError_t e = cudaFuncGetAttributes(&fa, kern);
         if (e != cudaSuccess) return e;
-        max_dyn = 227 * 1024 - (int)fa.sharedSizeBytes;
-        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, max_dyn);
+        const int md = 227 * 1024 - (int)fa.sharedSizeBytes;
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, md);
         if (e != cudaSuccess) return e;
+        max_dyn = md;  // set once the attribute is in place
     }
     if (smem > max_dyn) return cudaErrorInvalidConfiguration;
     // persistent grid: as many CTAs as fit on the GPU at once, shared among the groups
