@@ -221,6 +221,7 @@ class Solver:
         self.lib = load_library()
         self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
         self.shape = tuple(int(s) for s in shape)
+        self.L = tuple(float(v) for v in L)
         ph = np.ascontiguousarray(phase, dtype=np.uint16)
         if ph.ndim == 3:
             ph = ph[None]
@@ -382,6 +383,23 @@ class Solver:
         out = np.zeros(self.batch)
         self._check(self.lib.dbfft_compatibility(self.ctx, _dptr(out)))
         return out
+
+    def save_deformed_shape(self, path, scale=1.0, rhs=0):
+        """Write the deformed voxel-centre positions x + scale * u(x) of one right-hand side
+        as a raw little-endian float64 array [3, n1, n2, n3] (C order) at `path`, with a
+        JSON sidecar `path + '.json'` giving shape, dtype, box lengths and scale. u comes from
+        dbfft_displacement; the positions are formed on the host for the file."""
+        import json
+        u = self.displacement()[rhs].cpu().numpy()
+        x = [(np.arange(n) + 0.5) * (Lk / n) for n, Lk in zip(self.shape, self.L)]
+        X = np.stack(np.meshgrid(*x, indexing="ij"))
+        pos = np.ascontiguousarray(X + scale * u, dtype="<f8")
+        pos.tofile(path)
+        with open(str(path) + ".json", "w") as f:
+            json.dump({"shape": [3] + list(self.shape), "dtype": "float64", "order": "C",
+                       "box": list(self.L), "scale": float(scale), "rhs": int(rhs),
+                       "content": "x + scale * u at the voxel centres x = (i + 1/2) L / n"}, f)
+        return pos.shape
 
     def displacement(self):
         """Total displacement at the voxel centres, device float64 [B, 3, n1, n2, n3]."""

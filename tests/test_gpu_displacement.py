@@ -112,3 +112,23 @@ def test_compatibility_residual_is_round_off():
     probf = o.Problem(shape, "finite")
     mx, rms = o.compatibility(probf, o.grad_hat(uh.cpu().numpy()[0], probf.xi), np.linalg.norm(F - np.eye(3)))
     assert 0.0 <= c_gpu < 1e-12 and mx < 1e-12 and rms < 1e-12, (c_gpu, mx, rms)
+
+
+def test_deformed_shape_dump(tmp_path):
+    """Raw float64 dump of x + scale * u with its JSON sidecar."""
+    import json
+    dbfft = _dbfft()
+    shape, L = (8, 8, 16), (1.0, 1.0, 2.0)
+    phase = (np.random.default_rng(4).random(shape) < 0.3).astype(np.uint16)
+    tgt = np.diag([1e-3, 0.0, 0.0])
+    s = dbfft.Solver(shape, phase, dbfft.iso_phases([1.0, 10.0], [0.3, 0.3]), tgt[None], tol=1e-12, L=L)
+    s.solve_increment(0)
+    path = tmp_path / "shape.f64"
+    s.save_deformed_shape(str(path), scale=20.0)
+    u = s.displacement().cpu().numpy()[0]
+    s.close()
+    meta = json.load(open(str(path) + ".json"))
+    pos = np.fromfile(str(path), dtype="<f8").reshape(meta["shape"])
+    x = np.stack(np.meshgrid(*[(np.arange(n) + 0.5) * (Lk / n) for n, Lk in zip(shape, L)], indexing="ij"))
+    assert np.allclose(pos, x + 20.0 * u, rtol=0, atol=1e-15)
+    assert meta["scale"] == 20.0 and meta["box"] == list(L)
