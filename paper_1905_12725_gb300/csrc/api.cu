@@ -9,6 +9,7 @@
 // inner system straight to the tolerance; MIXED is iterative refinement;
 // nonlinear problems are Newton steps with an inexact inner solve
 // (Sec. 2.4, Eqs. lineariz and nonlineqf).
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
@@ -102,6 +103,8 @@ struct dbfft_ctx {
     cplx<double>* xfwd = nullptr;
     double* fU = nullptr;
     double* hbar = nullptr;  // [B][9] macro displacement gradient (displacement output)
+    void* stage_h = nullptr;  // page-locked staging of the phase maps
+    size_t stage_n = 0;
     char* small_cur = nullptr;  // small-object arena: next free byte and bytes left in the block
     size_t small_left = 0;
     double* sigf = nullptr;
@@ -542,12 +545,34 @@ Twiddles<float> twid<float>(dbfft_ctx* ctx) {
 }
 
 dbfft_status upload_tables(dbfft_ctx* ctx) {
-    // tm: the half-length transform of an even axis 3 (unused for odd n3)
+    // All tables go to the device in one copy: host staging with 256-byte aligned
+    // offsets, one device block, pointers into it.
+    std::vector<unsigned char> host;
+    auto place = [&](size_t bytes) {
+        const size_t off = (host.size() + 255) & ~(size_t)255;
+        host.resize(off + bytes);
+        return off;
+    };
+    // twiddles exp(-2 pi i k / n) per axis; tm: the half-length transform of an even
+    // axis 3 (unused for odd n3)
     const int lens[4] = {ctx->n1, ctx->n2, ctx->n3, ctx->n3 % 2 == 0 ? ctx->m : 1};
+    size_t off_td[4], off_tf[4], off_xd[3], off_xf[3];
+    for (int t = 0; t < 4; ++t) {
+        off_td[t] = place(lens[t] * sizeof(cplx<double>));
+        off_tf[t] = place(lens[t] * sizeof(cplx<float>));
+    }
+    // frequencies xi_i = 2 pi k_i / L_i in FFT order, Nyquist index set to 0
+    const int nax[3] = {ctx->n1, ctx->n2, ctx->n3};
+    int cnts[3];
+    for (int ax = 0; ax < 3; ++ax) {
+        cnts[ax] = (ax == 2) ? ctx->h : nax[ax];
+        off_xd[ax] = place(cnts[ax] * sizeof(double));
+        off_xf[ax] = place(cnts[ax] * sizeof(float));
+    }
     for (int t = 0; t < 4; ++t) {
         const int n = lens[t];
-        std::vector<cplx<double>> td(n);
-        std::vector<cplx<float>> tf(n);
+        cplx<double>* td = reinterpret_cast<cplx<double>*>(host.data() + off_td[t]);
+        cplx<float>* tf = reinterpret_cast<cplx<float>*>(host.data() + off_tf[t]);
         for (int k = 0; k < n; ++k) {
             const long double ang = -2.0L * 3.14159265358979323846264338327950288L * (long double)k / (long double)n;
             td[k].x = (double)cosl(ang);
@@ -555,33 +580,33 @@ dbfft_status upload_tables(dbfft_ctx* ctx) {
             tf[k].x = (float)td[k].x;
             tf[k].y = (float)td[k].y;
         }
-        TRY(dalloc_t(ctx, n, &ctx->tw_d[t]));
-        TRY(dalloc_t(ctx, n, &ctx->tw_f[t]));
-        CK(cudaMemcpyAsync(ctx->tw_d[t], td.data(), n * sizeof(cplx<double>), cudaMemcpyHostToDevice, ctx->stream));
-        CK(cudaMemcpyAsync(ctx->tw_f[t], tf.data(), n * sizeof(cplx<float>), cudaMemcpyHostToDevice, ctx->stream));
-        CK(cudaStreamSynchronize(ctx->stream));
     }
-    // frequencies xi_i = 2 pi k_i / L_i in FFT order, Nyquist index set to 0
-    const int nax[3] = {ctx->n1, ctx->n2, ctx->n3};
     for (int ax = 0; ax < 3; ++ax) {
         const int n = nax[ax];
-        const int cnt = (ax == 2) ? ctx->h : n;
         const double L = ctx->grid.L[ax] > 0 ? ctx->grid.L[ax] : 1.0;
-        std::vector<double> xd(cnt);
-        std::vector<float> xf(cnt);
-        for (int k = 0; k < cnt; ++k) {
+        double* xd = reinterpret_cast<double*>(host.data() + off_xd[ax]);
+        float* xf = reinterpret_cast<float*>(host.data() + off_xf[ax]);
+        for (int k = 0; k < cnts[ax]; ++k) {
             const int kk = (k < (n + 1) / 2) ? k : k - n;
             double v = 2.0 * kPi * (double)kk / L;
             if (n % 2 == 0 && (k == n / 2)) v = 0.0;
             xd[k] = v;
             xf[k] = (float)v;
         }
-        TRY(dalloc_t(ctx, cnt, &ctx->xi_d[ax]));
-        TRY(dalloc_t(ctx, cnt, &ctx->xi_f[ax]));
-        CK(cudaMemcpyAsync(ctx->xi_d[ax], xd.data(), cnt * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
-        CK(cudaMemcpyAsync(ctx->xi_f[ax], xf.data(), cnt * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
-        CK(cudaStreamSynchronize(ctx->stream));
     }
+    void* blk = nullptr;
+    TRY(dalloc(ctx, host.size(), &blk));
+    unsigned char* dev = static_cast<unsigned char*>(blk);
+    for (int t = 0; t < 4; ++t) {
+        ctx->tw_d[t] = reinterpret_cast<cplx<double>*>(dev + off_td[t]);
+        ctx->tw_f[t] = reinterpret_cast<cplx<float>*>(dev + off_tf[t]);
+    }
+    for (int ax = 0; ax < 3; ++ax) {
+        ctx->xi_d[ax] = reinterpret_cast<double*>(dev + off_xd[ax]);
+        ctx->xi_f[ax] = reinterpret_cast<float*>(dev + off_xf[ax]);
+    }
+    CK(cudaMemcpyAsync(blk, host.data(), host.size(), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
     return DBFFT_OK;
 }
 
@@ -1521,6 +1546,7 @@ void dbfft_destroy(dbfft_ctx* ctx) {
     pinned_free(ctx->cg_h, ctx->B * sizeof(CgState));
     pinned_free(ctx->part_h, ctx->partials_n * sizeof(double));
     pinned_free(ctx->small_h, (ctx->B * 10 + 8) * sizeof(double));
+    pinned_free(ctx->stage_h, ctx->stage_n);
     delete ctx;
 }
 
@@ -1622,17 +1648,44 @@ static dbfft_status create_impl(dbfft_ctx* ctx, const dbfft_grid* grid, const db
     const size_t nvox = (size_t)ctx->Bm * ctx->V;
     TRY(dalloc_t(ctx, nvox, &ctx->phase));
     // one pass over the maps: range check and the voxel count of every phase per material group
+    // (four interleaved count arrays, so that runs of one phase id do not chain their increments)
     std::vector<long long> pcount((size_t)ctx->Bm * mat->n_phases, 0);
-    for (int g = 0; g < ctx->Bm; ++g) {
-        const uint16_t* ids = mat->phase_id + (size_t)g * ctx->V;
-        long long* cg = pcount.data() + (size_t)g * mat->n_phases;
-        for (long long v = 0; v < ctx->V; ++v) {
-            const unsigned id = ids[v];
-            if (id >= (unsigned)mat->n_phases) return fail(ctx, DBFFT_E_ARG, "phase id out of range");
-            ++cg[id];
+    {
+        const size_t np4 = (size_t)mat->n_phases;
+        std::vector<uint32_t> c4(4 * np4);
+        for (int g = 0; g < ctx->Bm; ++g) {
+            const uint16_t* ids = mat->phase_id + (size_t)g * ctx->V;
+            std::fill(c4.begin(), c4.end(), 0u);
+            unsigned mx = 0;
+            long long v = 0;
+            for (; v + 4 <= ctx->V; v += 4) {
+                const unsigned a = ids[v], b = ids[v + 1], c = ids[v + 2], d = ids[v + 3];
+                mx = std::max(mx, std::max(std::max(a, b), std::max(c, d)));
+                if (mx >= (unsigned)mat->n_phases) return fail(ctx, DBFFT_E_ARG, "phase id out of range");
+                ++c4[a];
+                ++c4[np4 + b];
+                ++c4[2 * np4 + c];
+                ++c4[3 * np4 + d];
+            }
+            for (; v < ctx->V; ++v) {
+                const unsigned a = ids[v];
+                if (a >= (unsigned)mat->n_phases) return fail(ctx, DBFFT_E_ARG, "phase id out of range");
+                ++c4[a];
+            }
+            long long* cg = pcount.data() + (size_t)g * np4;
+            for (size_t p = 0; p < np4; ++p) cg[p] = (long long)c4[p] + c4[np4 + p] + c4[2 * np4 + p] + c4[3 * np4 + p];
         }
     }
-    CK(cudaMemcpyAsync(ctx->phase, mat->phase_id, nvox * sizeof(uint16_t), cudaMemcpyHostToDevice, ctx->stream));
+    // through a page-locked staging copy: the transfer then runs while the host
+    // goes on with the set-up (the buffer returns to the cache at destroy)
+    ctx->stage_n = nvox * sizeof(uint16_t);
+    ctx->stage_h = pinned_alloc(ctx->stage_n);
+    if (ctx->stage_h) {
+        std::memcpy(ctx->stage_h, mat->phase_id, ctx->stage_n);
+        CK(cudaMemcpyAsync(ctx->phase, ctx->stage_h, ctx->stage_n, cudaMemcpyHostToDevice, ctx->stream));
+    } else {
+        CK(cudaMemcpyAsync(ctx->phase, mat->phase_id, ctx->stage_n, cudaMemcpyHostToDevice, ctx->stream));
+    }
     if (mat->E_scale) {
         for (size_t i = 0; i < nvox; ++i)
             if (!std::isfinite(mat->E_scale[i])) return fail(ctx, DBFFT_E_NONFINITE, "non-finite E_scale");
