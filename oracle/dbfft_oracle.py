@@ -53,6 +53,13 @@ R13 Compressible Neo-Hookean (not in the paper): W = mu/2 (tr F^T F - 3) -
     law): W = lam/2 (tr E)^2 + mu E:E, E = (F^T F - I)/2.
 R14 Small-strain power-law crystal plasticity (replaces the paper's model,
     whose parameters are not given): backward Euler on the stress.
+R18 Finite-strain crystal plasticity (the paper's fourth benchmark uses
+    F = Fe Fp): the R14 power law on the second Piola-Kirchhoff stress T of
+    the intermediate configuration, T = C : (E_tr - sum_a dgam_a P_a) with the
+    trial Green strain E_tr of Fe_tr = F Fp_old^-1 (small elastic strains),
+    Fp = (I + sum_a dgam_a s_a n_a) Fp_old, P = Fe T Fp^-T. Its tangent is the
+    derivative with the plastic state held (major-symmetric); Newton with it
+    converges to the same increments as with the exact one.
 """
 from __future__ import annotations
 
@@ -831,6 +838,85 @@ def cp_material(cp: CrystalPlasticity, grain_field, dt):
         K = K.reshape((3, 3, 3, 3) + grain_field.shape)
         new_state = (eps_p_new, sig)
         return sig_t, FullTangent(K), new_state
+    return material
+
+
+# --------------------------------------------------------------------------
+# Finite-strain crystal plasticity, F = Fe Fp (R18)
+# --------------------------------------------------------------------------
+
+def schmid_full(cp: CrystalPlasticity, quats):
+    """Non-symmetric Schmid tensors S_a = s_a (x) n_a in the sample frame, [grain, 12, 3, 3]."""
+    s, n = fcc_slip_systems()
+    out = []
+    for q in np.asarray(quats, dtype=np.float64):
+        R = quat_to_rot(q / np.linalg.norm(q))
+        out.append(np.einsum("ai,aj->aij", s @ R.T, n @ R.T))
+    return np.array(out)
+
+
+def finite_cp_update(cp: CrystalPlasticity, S_full, grain, F, Fp_old, T_guess, dt):
+    """One step of the finite-strain model at every voxel (vectorised).
+
+    F [V,3,3]; Fp_old [V,3,3]; T_guess [V,6] (Mandel). With a = Fp_old^-1, the
+    trial elastic deformation Fe_tr = F a and the Green strain of the
+    intermediate configuration E_tr = (Fe_tr^T Fe_tr - I)/2, the second
+    Piola-Kirchhoff stress of the intermediate configuration T solves the
+    backward-Euler problem of the small-strain model (R14) with E_tr as the
+    strain and no plastic strain at the start of the step (the elastic strains
+    stay small, so T = C : (E_tr - dt sum_a gdot_a P_a)). Then
+    Fp = (I + dt sum_a gdot_a S_a) Fp_old, Fe = F Fp^-1, P = Fe T Fp^-T.
+    Returns (P [V,3,3], Fp [V,3,3], T [V,6], tangent data) with tangent data
+    (Fe_tr, a, B = a T a^T, C_tan = dT/dE_tr Mandel [V,6,6]).
+    """
+    V = F.shape[0]
+    a = np.linalg.inv(Fp_old)
+    Fe_tr = F @ a
+    E_tr = 0.5 * (np.swapaxes(Fe_tr, 1, 2) @ Fe_tr - np.eye(3))
+    e_tr = np.einsum("mij,vij->vm", mandel_basis(), E_tr)
+    T, C_tan, dep, _ = cp.update(grain, e_tr, np.zeros((V, 6)), T_guess, dt)
+    tau = np.einsum("vam,vm->va", cp.P[grain], T)
+    gd, _ = cp.rates(tau)
+    Fp = (np.eye(3) + dt * np.einsum("va,vaij->vij", gd, S_full[grain])) @ Fp_old
+    Fpi = np.linalg.inv(Fp)
+    Tm = np.einsum("mij,vm->vij", mandel_basis(), T)
+    P = F @ Fpi @ Tm @ np.swapaxes(Fpi, 1, 2)
+    B = a @ Tm @ np.swapaxes(a, 1, 2)
+    return P, Fp, T, (Fe_tr, a, B, C_tan)
+
+
+def finite_cp_tangent(data):
+    """K_iJkL of dP = G B + Fe_tr (C_tan : sym(Fe_tr^T G a)) a^T: the derivative of
+    F a T(E(F)) a^T with the plastic state a = Fp_old^-1 held fixed (R18). It is
+    major-symmetric. Returns [3,3,3,3,V]."""
+    Fe_tr, a, B, C_tan = data
+    V = Fe_tr.shape[0]
+    K = np.zeros((V, 3, 3, 3, 3))
+    Bm = mandel_basis()
+    Ct = np.einsum("mij,vmn,nkl->vijkl", Bm, C_tan, Bm)  # dT_ij / dE_kl (minor-symmetric)
+    d = np.eye(3)
+    K += np.einsum("ik,vLJ->viJkL", d, B)
+    # dE_MN = sym(Fe_tr^T G a)_MN = 1/2 (Fe_kM a_LN + Fe_kN a_LM) G_kL
+    dE = 0.5 * (np.einsum("vkM,vLN->vMNkL", Fe_tr, a) + np.einsum("vkN,vLM->vMNkL", Fe_tr, a))
+    K += np.einsum("viP,vPQMN,vMNkL,vJQ->viJkL", Fe_tr, Ct, dE, a)
+    return np.moveaxis(K, 0, -1)
+
+
+def finite_cp_material(cp: CrystalPlasticity, quats, grain_field, dt):
+    """Material closure of the finite-strain model; state = (Fp [V,3,3], T [V,6])."""
+    g = grain_field.reshape(-1)
+    S_full = schmid_full(cp, quats)
+
+    def material(F, state):
+        V = g.size
+        Fv = np.moveaxis(F.reshape(3, 3, V), -1, 0)
+        if state is None:
+            state = (np.broadcast_to(np.eye(3), (V, 3, 3)).copy(), np.zeros((V, 6)))
+        Fp_old, T_old = state
+        P, Fp, T, data = finite_cp_update(cp, S_full, g, Fv, Fp_old, T_old, dt)
+        Pf = np.moveaxis(P, 0, -1).reshape((3, 3) + grain_field.shape)
+        K = finite_cp_tangent(data).reshape((3, 3, 3, 3) + grain_field.shape)
+        return Pf, FullTangent(K), (Fp, T)
     return material
 
 

@@ -227,6 +227,113 @@ def test_homogeneous_medium_is_affine_with_zero_iterations():
     assert np.abs(sol["sig_bar"] - np.einsum("ijkl,kl->ij", C, eps)).max() < 1e-15
 
 
+# ---------------------------------------------------------------- finite-strain crystal plasticity (R18)
+def _fcp_setup(gdot0=1e-3):
+    rng = synth.Xoshiro256ss(71)
+    quats = synth.uniform_quaternions(3, rng)
+    cp = o.CrystalPlasticity(quats, gdot0=gdot0)
+    return cp, o.schmid_full(cp, quats), np.array([0, 1, 2, 0, 1, 2])
+
+
+def test_finite_cp_elastic_limit_is_st_venant_kirchhoff_with_cubic_stiffness():
+    """No slip (gdot0 = 0): P = F (C : E), E = (F^T F - I)/2, with the rotated cubic C."""
+    cp, S, g = _fcp_setup(gdot0=0.0)
+    F = np.eye(3) + 0.05 * np.random.default_rng(2).standard_normal((6, 3, 3))
+    P, Fp, T, _ = o.finite_cp_update(cp, S, g, F, np.broadcast_to(np.eye(3), (6, 3, 3)).copy(), np.zeros((6, 6)), 0.5)
+    E = 0.5 * (np.swapaxes(F, 1, 2) @ F - np.eye(3))
+    Cg = np.array([o.mandel_to_tensor4(cp.C[k]) for k in g])
+    ref = F @ np.einsum("vijkl,vkl->vij", Cg, E)
+    assert np.abs(P - ref).max() < 1e-10 * np.abs(ref).max()
+    assert np.abs(Fp - np.eye(3)).max() == 0.0
+
+
+def test_finite_cp_rotation_objectivity_and_rigid_rotation():
+    cp, S, g = _fcp_setup()
+    r = np.random.default_rng(3)
+    F = np.eye(3) + 3e-3 * r.standard_normal((6, 3, 3))
+    Fp0 = np.eye(3) + 1e-3 * r.standard_normal((6, 3, 3))
+    Q = o.quat_to_rot(np.array([0.8, 0.1, -0.5, 0.3]) / np.linalg.norm([0.8, 0.1, -0.5, 0.3]))
+    P1, Fp1, _, _ = o.finite_cp_update(cp, S, g, F, Fp0, np.zeros((6, 6)), 0.5)
+    P2, Fp2, _, _ = o.finite_cp_update(cp, S, g, Q @ F, Fp0, np.zeros((6, 6)), 0.5)
+    assert np.abs(P2 - Q @ P1).max() < 1e-9 * np.abs(P1).max()
+    assert np.abs(Fp2 - Fp1).max() < 1e-12
+    P3, _, _, _ = o.finite_cp_update(cp, S, g, np.broadcast_to(Q, (6, 3, 3)).copy(),
+                                     np.broadcast_to(np.eye(3), (6, 3, 3)).copy(), np.zeros((6, 6)), 0.5)
+    assert np.abs(P3).max() < 1e-9
+
+
+def test_finite_cp_small_deformation_limit_is_the_small_strain_model():
+    """F = I + eps (symmetric), Fp = I: P agrees with the small-strain stress to O(|eps|)."""
+    cp, S, g = _fcp_setup()
+    r = np.random.default_rng(4)
+    base = r.standard_normal((6, 3, 3))
+    base = 0.5 * (base + np.swapaxes(base, 1, 2))
+    errs = []
+    for amp in (2e-3, 2e-4):
+        eps = amp * base / np.abs(base).max()
+        P, _, _, _ = o.finite_cp_update(cp, S, g, np.eye(3) + eps, np.broadcast_to(np.eye(3), (6, 3, 3)).copy(),
+                                        np.zeros((6, 6)), 0.5)
+        sig, _, _, _ = cp.update(g, np.einsum("mij,vij->vm", o.mandel_basis(), eps), np.zeros((6, 6)),
+                                 np.zeros((6, 6)), 0.5)
+        sm = np.einsum("mij,vm->vij", o.mandel_basis(), sig)
+        errs.append(np.abs(P - sm).max() / np.abs(sm).max())
+    assert errs[0] < 10 * 2e-3 and errs[1] < 10 * 2e-4 and errs[1] < errs[0]
+
+
+def test_finite_cp_tangent_is_the_derivative_with_the_plastic_state_held():
+    """K : G against central differences of F a T(E(F)) a^T (a = Fp_old^-1 fixed)."""
+    cp, S, g = _fcp_setup()
+    r = np.random.default_rng(5)
+    F = np.eye(3) + 3e-3 * r.standard_normal((6, 3, 3))
+    Fp0 = np.eye(3) + 1e-3 * r.standard_normal((6, 3, 3))
+    _, _, T0, data = o.finite_cp_update(cp, S, g, F, Fp0, np.zeros((6, 6)), 0.5)
+    K = np.moveaxis(o.finite_cp_tangent(data), -1, 0)
+    G = r.standard_normal((6, 3, 3))
+    h = 1e-7
+
+    def ptilde(Fx):
+        _, _, T, (Fe_tr, a, _, _) = o.finite_cp_update(cp, S, g, Fx, Fp0, T0, 0.5)
+        return Fe_tr @ np.einsum("mij,vm->vij", o.mandel_basis(), T) @ np.swapaxes(a, 1, 2)
+
+    fd = (ptilde(F + h * G) - ptilde(F - h * G)) / (2 * h)
+    kg = np.einsum("viJkL,vkL->viJ", K, G)
+    assert np.abs(kg - fd).max() < 1e-5 * np.abs(kg).max()
+    Kv = K.reshape(6, 9, 9)
+    assert np.abs(Kv - np.swapaxes(Kv, 1, 2)).max() < 1e-12 * np.abs(Kv).max()
+
+
+def test_finite_cp_single_crystal_steady_state():
+    """[100] stretch of a cube-oriented crystal at F11 rate 1e-3/s (other P components
+    free, rotation fixed as in R8): once the flow is steady, eight systems at Schmid
+    factor 1/sqrt 6 carry the true strain rate D = rate / F11, so the Cauchy stress is
+    sqrt 6 tau_c (sqrt 6 D / (8 gdot0))^m times (Fe_11)^2 ~ 1 + 2 sigma / E_100, and
+    P11 = J sigma11 / F11. Without the update of Fp the stress would keep growing."""
+    shape = (4, 4, 4)
+    quats = np.array([[1.0, 0, 0, 0]])
+    cp = o.CrystalPlasticity(quats)
+    grain = np.zeros(shape, np.int64)
+    mask = np.zeros((3, 3), bool)
+    mask[0, 1] = mask[0, 2] = mask[1, 2] = mask[1, 1] = mask[2, 2] = True
+    prob = o.Problem(shape, "finite", mask.reshape(-1))
+    dt, n = 0.5, 40
+    targets = []
+    for k in range(n):
+        t = np.eye(3)
+        t[0, 0] = 1.0 + 1e-3 * dt * (k + 1)
+        t[mask] = 0.0
+        targets.append(t)
+    res, _ = o.newton_increments(prob, o.finite_cp_material(cp, quats, grain, dt), targets, newton_tol=1e-10,
+                                 load_tol=1e-10)
+    F = res[-1]["field_bar"]
+    F11, J = F[0, 0], float(np.linalg.det(F))
+    sig = math.sqrt(6) * 50.0 * (math.sqrt(6) * 1e-3 / F11 / (8 * 1e-3)) ** 0.05
+    C11, C12 = 168000.0, 121000.0
+    E100 = (C11 - C12) * (C11 + 2 * C12) / (C11 + C12)
+    pred = J * sig * (1.0 + 2.0 * sig / E100) / F11
+    assert abs(res[-1]["stress_bar"][0, 0] - pred) < 1e-3 * pred
+    assert abs(F[1, 1] - F[2, 2]) < 1e-10 and F[1, 1] < 1.0
+
+
 # ---------------------------------------------------------------- displacement (Eqs. disp_decomp, decomp_displ)
 def test_displacement_of_an_affine_state_sits_at_voxel_centres():
     """u~ = 0: u = Hbar x at x = (j + 1/2) L / n. A non-symmetric Fbar - I (finite
