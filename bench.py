@@ -512,6 +512,44 @@ def case_c4(precision, n=256, n_inc=40, only=None):
             "phase_sha256": synth.sha256(c["phase"])}
 
 
+def case_fcp(precision, n=64, n_grains=200, n_inc=40, rate=1e-3, dt=0.5):
+    """n^3 Voronoi polycrystal, finite-strain CP (F = Fe Fp): F11 to 1.02 at 1e-3/s in
+    40 increments, the lower off-diagonal F components held at zero and the other P
+    components free (mixed control). With 1e-3 of stretch per increment the plain
+    Newton iteration stalls on this grid; 5e-4, the step of the small-strain
+    polycrystal case, converges."""
+    from paper_1905_12725_gb300 import dbfft, synth
+    t0 = time.perf_counter()
+    rng = synth.Xoshiro256ss(1905)
+    phase, _ = synth.periodic_voronoi(n, n_grains, rng)
+    quats = synth.uniform_quaternions(n_grains, rng)
+    t_gen = time.perf_counter() - t0
+    mask = np.zeros((3, 3), bool)
+    mask[0, 1] = mask[0, 2] = mask[1, 2] = mask[1, 1] = mask[2, 2] = True
+    tgt = np.eye(3)
+    tgt[0, 0] = 1.0 + rate * dt * n_inc
+    tgt[mask] = 0.0
+    s = dbfft.Solver((n,) * 3, phase, dbfft.cp_phases(quats, finite=True), tgt[None], kinematics=dbfft.DBFFT_FINITE,
+                     precision=precision, stress_mask=mask.reshape(-1), n_increments=n_inc, total_time=n_inc * dt,
+                     newton_tol=1e-8, load_tol=1e-10, eta_inner=1e-4, max_newton=40, max_iter=5000)
+    s.autotune(TUNE_CACHE)
+    incs = []
+    t_all = 0.0
+    cg_all = 0
+    for k in range(n_inc):
+        rep, el = _timed(lambda: s.solve_increment(k))
+        t_all += el
+        cg_all += rep["cg_iters"]
+        P = s.homogenized_stress()[0]
+        incs.append({"inc": k, "newton": rep["newton_iters"], "cg": rep["cg_iters"], "eps_eq": rep["eps_eq"],
+                     "P_xx": P[0, 0], "ms": el * 1e3})
+    s.close()
+    return {"case": f"finite-strain CP {n}^3 polycrystal {n_grains} grains", "precision": "mixed" if precision else "fp64",
+            "generate_s": t_gen, "wall_s": t_all, "cg_iters": cg_all,
+            "voxel_cg_iters_per_s": n ** 3 * cg_all / t_all, "increments": incs,
+            "phase_sha256": synth.sha256(phase)}
+
+
 def case_c5(n=64, n_rve=32, n_fd=20):
     """32 RVEs of 64^3: d sigma_xx / dE(x) by the adjoint, checked by central differences on 20 voxels each."""
     from paper_1905_12725_gb300 import dbfft, synth
@@ -745,11 +783,12 @@ def main():
     ap.add_argument("--skip-256", action="store_true")
     ap.add_argument("--case", default="",
                     choices=["", "op256", "c2", "c1", "c3", "c3fp64", "c4", "c4fp64", "c5", "porous",
-                             "porousfp64", "porous63", "porous63fp64", "inclusion"],
+                             "porousfp64", "porous63", "porous63fp64", "inclusion", "fcp", "fcpfp64"],
                     help="run one sub-measurement only: op256 = 256^3 FP32 CG pass chain, c2 = one mixed "
                          "batched 64^3 solve (profiler captures); c1, c3[fp64], c4[fp64], c5 = the other "
                          "configurations at full size; porous[fp64] = the porous St. Venant-Kirchhoff "
-                         "stretch (64^3; porous63[fp64] on the paper's 63^3 grid); inclusion = the 63^3 inclusion contrast sweep")
+                         "stretch (64^3; porous63[fp64] on the paper's 63^3 grid); inclusion = the 63^3 inclusion contrast sweep; "
+                         "fcp[fp64] = the 64^3 finite-strain crystal-plasticity stretch")
     args = ap.parse_args()
     if args.case:
         import torch
@@ -764,6 +803,9 @@ def main():
             print(json.dumps(case_porous(prec, n=63), default=float), flush=True)
         elif args.case == "inclusion":
             print(json.dumps(case_inclusion(), default=float), flush=True)
+        elif args.case in ("fcp", "fcpfp64"):
+            prec = dbfft.DBFFT_FP64 if args.case.endswith("fp64") else dbfft.DBFFT_MIXED
+            print(json.dumps(case_fcp(prec), default=float), flush=True)
         elif args.case in ("c1", "c3", "c3fp64", "c4", "c4fp64", "c5", "porous", "porousfp64"):
             prec = dbfft.DBFFT_FP64 if args.case.endswith("fp64") else dbfft.DBFFT_MIXED
             res = {"c1": lambda: case_c1(), "c3": lambda: case_c3(prec), "c3fp64": lambda: case_c3(prec),

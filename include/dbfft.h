@@ -75,9 +75,16 @@ enum {                                           /* constitutive model of a phas
     DBFFT_ISO_ELASTIC = 0,     /* linear isotropic elasticity (E, nu), small strain     */
     DBFFT_NEO_HOOKE = 1,       /* compressible Neo-Hookean (mu, lambda), finite strain  */
     DBFFT_CP_FCC_POWERLAW = 2, /* small-strain FCC crystal plasticity, power-law flow   */
-    DBFFT_SVK = 3              /* St. Venant-Kirchhoff (mu, lambda), finite strain: the
+    DBFFT_SVK = 3,             /* St. Venant-Kirchhoff (mu, lambda), finite strain: the
                                   porous hyperelastic example of Sec. 3; needs mu > 0 and
                                   3 lambda + 2 mu > 0                                   */
+    DBFFT_CP_FCC_FINITE = 4    /* FCC crystal plasticity at finite strain, F = Fe Fp
+                                  (Sec. 2.4 with the flow rule of Sec. 3): the second
+                                  Piola-Kirchhoff stress of the intermediate
+                                  configuration is the small-strain model's stress at
+                                  the trial Green strain, Fp is advanced by the slip
+                                  rates; same phase fields as DBFFT_CP_FCC_POWERLAW,
+                                  FINITE kinematics required                         */
 };
 
 /* Problem size and solver settings. */
@@ -105,7 +112,7 @@ typedef struct {
 /* One phase. Only the fields of its model are read. */
 typedef struct {
     int model;                /* DBFFT_ISO_ELASTIC, DBFFT_NEO_HOOKE, DBFFT_CP_FCC_POWERLAW,
-                                 DBFFT_SVK                                                 */
+                                 DBFFT_SVK, DBFFT_CP_FCC_FINITE                            */
     double E, nu;             /* ISO_ELASTIC                                               */
     double mu, lambda;        /* NEO_HOOKE and SVK: Lame constants                         */
     double C11, C12, C44;     /* CP: cubic stiffness in the crystal frame                  */

@@ -126,6 +126,8 @@ struct dbfft_ctx {
     double* sig_prev = nullptr;
     double* eps_p_t = nullptr;
     double* sig_t = nullptr;
+    double* fp_c = nullptr;  // finite-strain CP: committed Fp [B][V][9]
+    double* fp_t = nullptr;  // finite-strain CP: trial Fp [B][V][9]
 
     // ---- pinned host staging
     CgState* cg_h = nullptr;
@@ -252,6 +254,8 @@ double mat_bytes(const dbfft_ctx* ctx, bool dbl, bool update) {
     const double t = dbl ? 8.0 : 4.0;
     if (!update) return (double)ctx->B * V * (2.0 + ctx->ntan * t);
     const double tw = ctx->prec == DBFFT_FP64 ? 8.0 : 4.0;
+    if (ctx->model == DBFFT_CP_FCC_FINITE)  // Fp and T: read the committed, write the trial
+        return (double)ctx->B * V * (2.0 + ctx->ntan * tw + 2 * (9 + 6) * 8.0);
     if (ctx->model != DBFFT_CP_FCC_POWERLAW) return (double)ctx->B * V * (2.0 + ctx->ntan * tw);
     return (double)ctx->B * V * (2.0 + ctx->ntan * tw + 4 * 6 * 8.0);
 }
@@ -511,6 +515,10 @@ bool cp_grain(const dbfft_phase& ph, CpGrain& g) {
                     nr[i] += R[i][k] * n[k];
                     sr[i] += R[i][k] * s[k];
                 }
+            for (int i = 0; i < 3; ++i) {
+                g.sv[p * 3 + dd][i] = sr[i];
+                g.nv[p * 3 + dd][i] = nr[i];
+            }
             double Pt[3][3];
             for (int i = 0; i < 3; ++i)
                 for (int j = 0; j < 3; ++j) Pt[i][j] = 0.5 * (sr[i] * nr[j] + nr[i] * sr[j]);
@@ -652,12 +660,14 @@ int opk_apply(const dbfft_ctx* ctx) {
         case DBFFT_ISO_ELASTIC: return OP_ISO;
         case DBFFT_NEO_HOOKE: return OP_NH_APPLY;
         case DBFFT_SVK: return OP_SVK_APPLY;
+        case DBFFT_CP_FCC_FINITE: return OP_FCP_APPLY;
         default: return OP_CP_APPLY;
     }
 }
 int opk_update(const dbfft_ctx* ctx) {
     if (ctx->model == DBFFT_CP_FCC_POWERLAW) return ctx->prec == DBFFT_MIXED ? OP_CP_UPDATE32 : OP_CP_UPDATE;
     if (ctx->model == DBFFT_SVK) return OP_SVK_UPDATE;
+    if (ctx->model == DBFFT_CP_FCC_FINITE) return OP_FCP_UPDATE;
     return ctx->model == DBFFT_ISO_ELASTIC ? OP_ISO : OP_NH_UPDATE;
 }
 
@@ -779,6 +789,8 @@ dbfft_status chain_residual(dbfft_ctx* ctx, const cplx<double>* x, const double*
         a3.eps_p_t = ctx->eps_p_t;
         a3.sig_t = ctx->sig_t;
         a3.guess_trial = ctx->cp_guess_trial;
+        a3.fp_old = ctx->fp_c;
+        a3.fp_new = ctx->fp_t;
     }
     CK(cudaMemsetAsync(ctx->errw, 0, sizeof(unsigned), ctx->stream));
     TRY(run(ctx, "pass3_update_f64", 2 * nc * cp + mat_bytes(ctx, true, true),
@@ -1054,7 +1066,10 @@ constexpr int kMeanTangentBlocks = 456;  // blocks per right-hand side of the me
 // Mean tangent of the current state -> preconditioner (R10), nonlinear only.
 dbfft_status refresh_precond(dbfft_ctx* ctx) {
     const int nblk = kMeanTangentBlocks;
-    const int kind = ctx->model == DBFFT_NEO_HOOKE ? 0 : (ctx->model == DBFFT_SVK ? 2 : 1);
+    const int kind = ctx->model == DBFFT_NEO_HOOKE ? 0
+                   : ctx->model == DBFFT_SVK         ? 2
+                   : ctx->model == DBFFT_CP_FCC_FINITE ? 3
+                                                       : 1;
     TRY(run(ctx, "mean_tangent", 0.0, [&] {
         if (ctx->prec == DBFFT_MIXED)
             return launch_mean_tangent<float>(kind, ctx->B, ctx->V, reinterpret_cast<const float*>(ctx->tan),
@@ -1216,6 +1231,9 @@ dbfft_status solve_current(dbfft_ctx* ctx, dbfft_report* rep) {
 dbfft_status commit_state(dbfft_ctx* ctx) {
     if (ctx->model == DBFFT_CP_FCC_POWERLAW) {
         std::swap(ctx->eps_p, ctx->eps_p_t);
+        std::swap(ctx->sig_prev, ctx->sig_t);
+    } else if (ctx->model == DBFFT_CP_FCC_FINITE) {
+        std::swap(ctx->fp_c, ctx->fp_t);
         std::swap(ctx->sig_prev, ctx->sig_t);
     }
     return DBFFT_OK;
@@ -1590,8 +1608,10 @@ static dbfft_status create_impl(dbfft_ctx* ctx, const dbfft_grid* grid, const db
     ctx->model = mat->phases[0].model;
     for (int p = 0; p < mat->n_phases; ++p)
         if (mat->phases[p].model != ctx->model) return fail(ctx, DBFFT_E_ARG, "all phases must use one model kind");
-    if ((ctx->model == DBFFT_NEO_HOOKE || ctx->model == DBFFT_SVK) != (ctx->kin == DBFFT_FINITE))
-        return fail(ctx, DBFFT_E_ARG, "NEO_HOOKE and SVK need FINITE kinematics; ISO_ELASTIC and CP need SMALL");
+    if ((ctx->model == DBFFT_NEO_HOOKE || ctx->model == DBFFT_SVK || ctx->model == DBFFT_CP_FCC_FINITE) !=
+        (ctx->kin == DBFFT_FINITE))
+        return fail(ctx, DBFFT_E_ARG,
+                    "NEO_HOOKE, SVK and CP_FCC_FINITE need FINITE kinematics; ISO_ELASTIC and CP need SMALL");
     if ((ctx->n3 & 1) && ctx->model != DBFFT_ISO_ELASTIC && !supported_odd_nl(ctx->n3))
         return fail(ctx, DBFFT_E_UNSUPPORTED_GRID, "odd n3 with nonlinear phases: 9, 15, 21, 27, 45, 63 or 81");
     if (ctx->model != DBFFT_ISO_ELASTIC && ctx->Rm != 1)
@@ -1718,7 +1738,7 @@ static dbfft_status create_impl(dbfft_ctx* ctx, const dbfft_grid* grid, const db
                 return fail(ctx, DBFFT_E_ARG, "3 lambda + 2 mu > 0 required");
             ctx->lam_h[p] = ph.lambda;
             ctx->mu_h[p] = ph.mu;
-        } else if (ctx->model == DBFFT_CP_FCC_POWERLAW) {
+        } else if (ctx->model == DBFFT_CP_FCC_POWERLAW || ctx->model == DBFFT_CP_FCC_FINITE) {
             const double vals[9] = {ph.C11, ph.C12, ph.C44, ph.gdot0, ph.m, ph.tau_c, ph.quat[0], ph.quat[1], ph.quat[2]};
             for (double v : vals)
                 if (!std::isfinite(v)) return fail(ctx, DBFFT_E_NONFINITE, "non-finite crystal parameter");
@@ -1743,7 +1763,7 @@ static dbfft_status create_impl(dbfft_ctx* ctx, const dbfft_grid* grid, const db
     CK(cudaMemcpyAsync(ctx->lam1, lam1.data(), np * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
     CK(cudaMemcpyAsync(ctx->mu1, mu1.data(), np * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
-    if (ctx->model == DBFFT_CP_FCC_POWERLAW) {
+    if (ctx->model == DBFFT_CP_FCC_POWERLAW || ctx->model == DBFFT_CP_FCC_FINITE) {
         std::vector<CpGrain> gr(np);
         for (int p = 0; p < np; ++p)
             if (!cp_grain(mat->phases[p], gr[p])) return fail(ctx, DBFFT_E_ARG, "singular crystal stiffness");
@@ -1877,7 +1897,10 @@ static dbfft_status create_impl(dbfft_ctx* ctx, const dbfft_grid* grid, const db
         return fail(ctx, DBFFT_E_NOMEM, "pinned host allocation failed");
     // nonlinear tangent and state
     if (ctx->model != DBFFT_ISO_ELASTIC) {
-        ctx->ntan = ctx->model == DBFFT_NEO_HOOKE ? 10 : (ctx->model == DBFFT_SVK ? 15 : 21);
+        ctx->ntan = ctx->model == DBFFT_NEO_HOOKE       ? 10
+                  : ctx->model == DBFFT_SVK              ? 15
+                  : ctx->model == DBFFT_CP_FCC_FINITE    ? 45
+                                                         : 21;
         const size_t tsz = ctx->prec == DBFFT_FP64 ? 8 : 4;
         TRY(dalloc(ctx, (size_t)ctx->B * ctx->V * ctx->ntan * tsz, &ctx->tan));
         if (ctx->model == DBFFT_CP_FCC_POWERLAW) {
@@ -1888,6 +1911,14 @@ static dbfft_status create_impl(dbfft_ctx* ctx, const dbfft_grid* grid, const db
             TRY(dalloc_t(ctx, ns, &ctx->sig_t));
             CK(cudaMemsetAsync(ctx->eps_p, 0, ns * sizeof(double), ctx->stream));
             CK(cudaMemsetAsync(ctx->sig_prev, 0, ns * sizeof(double), ctx->stream));
+        } else if (ctx->model == DBFFT_CP_FCC_FINITE) {
+            const size_t ns = (size_t)ctx->B * ctx->V * 6, nf = (size_t)ctx->B * ctx->V * 9;
+            TRY(dalloc_t(ctx, ns, &ctx->sig_prev));
+            TRY(dalloc_t(ctx, ns, &ctx->sig_t));
+            TRY(dalloc_t(ctx, nf, &ctx->fp_c));
+            TRY(dalloc_t(ctx, nf, &ctx->fp_t));
+            CK(cudaMemsetAsync(ctx->sig_prev, 0, ns * sizeof(double), ctx->stream));
+            CK(launch_fill_identity(ctx->fp_c, (long long)ctx->B * ctx->V, ctx->stream));
         }
     }
     TRY(set_load(ctx, 0, ctx->target.data()));

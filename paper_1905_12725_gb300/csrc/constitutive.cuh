@@ -9,7 +9,10 @@
 //      R(s) = S s + dt sum_a gdot_a(s) P_a - (eps_{n+1} - eps_p,n) = 0,
 //    solved by Newton (stopped on the full Newton step) with backtracking,
 //    far from the solution, on the convex potential whose gradient R is;
-//    consistent tangent (S + dt sum_a gdot'_a P_a P_a^T)^-1.
+//    consistent tangent (S + dt sum_a gdot'_a P_a P_a^T)^-1;
+//  * finite-strain crystal plasticity, F = Fe Fp: the same local problem on
+//    the second Piola-Kirchhoff stress of the intermediate configuration with
+//    the trial Green strain as the strain, then the update of Fp.
 // The converged stress is FP64; a mixed-precision context runs the first
 // Newton iterations in FP32.
 #pragma once
@@ -22,6 +25,8 @@ namespace dbfft {
 struct CpGrain {
     double S[21];     // Mandel compliance, upper triangle row-major
     double P[12][6];  // Schmid tensors sym(s x n), Mandel, sample frame
+    double sv[12][3]; // slip directions and plane normals, sample frame (finite strain)
+    double nv[12][3];
 };
 
 struct CpGrainF {  // the same in FP32
@@ -175,6 +180,63 @@ __device__ __forceinline__ void svk_apply(const T* tn, T mu, T lam, const T* G, 
         for (int j = 0; j < 3; ++j)
             out[3 * i + j] = G[3 * i] * Sm[j] + G[3 * i + 1] * Sm[3 + j] + G[3 * i + 2] * Sm[6 + j] +
                              F[3 * i] * dS[j] + F[3 * i + 1] * dS[3 + j] + F[3 * i + 2] * dS[6 + j];
+}
+
+// Finite-strain crystal plasticity (F = Fe Fp): tangent data per voxel, 45
+// values: Fe_tr = F a (9), a = Fp_old^-1 (9), B = a T a^T (6, order
+// 11,22,33,23,13,12), C_tan = dT/dE_tr (21, Mandel). dP = G B + Fe_tr dT a^T,
+// dT = C_tan : sym(Fe_tr^T G a): the derivative of F a T(E(F)) a^T with the
+// plastic state held (major-symmetric).
+template <typename T>
+__device__ __forceinline__ void fcp_apply(const T* tn, const T* G, T* out) {
+    const T* Fe = tn;
+    const T* A = tn + 9;
+    const T Bm[9] = {tn[18], tn[23], tn[22], tn[23], tn[19], tn[21], tn[22], tn[21], tn[20]};
+    const T* Ct = tn + 24;
+    T Y[9];  // G a
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) Y[3 * i + j] = G[3 * i] * A[j] + G[3 * i + 1] * A[3 + j] + G[3 * i + 2] * A[6 + j];
+    T H[9];  // Fe^T G a
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) H[3 * i + j] = Fe[i] * Y[j] + Fe[3 + i] * Y[3 + j] + Fe[6 + i] * Y[6 + j];
+    const T r2h = T(0.70710678118654752440);  // sqrt(2) / 2
+    const T e6[6] = {H[0], H[4], H[8], r2h * (H[5] + H[7]), r2h * (H[2] + H[6]), r2h * (H[1] + H[3])};
+    T d6[6];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+        T acc = T(0);
+#pragma unroll
+        for (int j = 0; j < 6; ++j) acc += Ct[sym6(i, j)] * e6[j];
+        d6[i] = acc;
+    }
+    const T dT[9] = {d6[0], r2h * d6[5], r2h * d6[4], r2h * d6[5], d6[1], r2h * d6[3], r2h * d6[4], r2h * d6[3], d6[2]};
+    T Z[9];  // Fe dT
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) Z[3 * i + j] = Fe[3 * i] * dT[j] + Fe[3 * i + 1] * dT[3 + j] + Fe[3 * i + 2] * dT[6 + j];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+            out[3 * i + j] = G[3 * i] * Bm[j] + G[3 * i + 1] * Bm[3 + j] + G[3 * i + 2] * Bm[6 + j] +
+                             Z[3 * i] * A[3 * j] + Z[3 * i + 1] * A[3 * j + 1] + Z[3 * i + 2] * A[3 * j + 2];
+}
+
+// Inverse of a 3x3 matrix (row-major) by cofactors; false when singular.
+__device__ __forceinline__ bool inv3(const double* M, double* R) {
+    const double c00 = M[4] * M[8] - M[5] * M[7], c01 = M[5] * M[6] - M[3] * M[8], c02 = M[3] * M[7] - M[4] * M[6];
+    const double det = M[0] * c00 + M[1] * c01 + M[2] * c02;
+    if (!(det != 0.0) || !isfinite(det)) return false;
+    const double id = 1.0 / det;
+    R[0] = c00 * id; R[1] = (M[2] * M[7] - M[1] * M[8]) * id; R[2] = (M[1] * M[5] - M[2] * M[4]) * id;
+    R[3] = c01 * id; R[4] = (M[0] * M[8] - M[2] * M[6]) * id; R[5] = (M[2] * M[3] - M[0] * M[5]) * id;
+    R[6] = c02 * id; R[7] = (M[1] * M[6] - M[0] * M[7]) * id; R[8] = (M[0] * M[4] - M[1] * M[3]) * id;
+    return true;
 }
 
 // sigma (W components 11,22,33,23,13,12) = C_mandel eps, 21-entry tangent.
@@ -501,6 +563,95 @@ __device__ __forceinline__ bool cp_update(const CpGrain& G, const CpGrainF& Gf, 
 #pragma unroll
         for (int i = 0; i <= j; ++i) tan[sym6(i, j)] = spd ? col[i] : RT(0);
     }
+    return ok;
+}
+
+// Finite-strain crystal-plasticity update at one voxel (FP64): F (9), the
+// committed Fp_old (9), a start guess of T (Mandel 6). With a = Fp_old^-1,
+// Fe_tr = F a and E_tr = (Fe_tr^T Fe_tr - I)/2, T solves the small-strain
+// backward-Euler problem with E_tr as the strain (cp_update, no plastic strain
+// at the start of the step); then Fp = (I + dt sum_a gdot_a s_a n_a) Fp_old,
+// P = F Fp^-1 T Fp^-T. Writes P (9), Fp (9), T (Mandel 6) and the 45 tangent
+// values (fcp_apply). False when the local solve or an inverse fails.
+__device__ __forceinline__ bool fcp_update(const CpGrain& G, const CpGrainF& Gf, const CpParams& cp, const double* F,
+                                           const double* Fp_old, const double* T_guess, double* P, double* Fp,
+                                           double* T, double* tn) {
+    double a[9];
+    bool ok = inv3(Fp_old, a);
+    double Fe[9];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) Fe[3 * i + j] = F[3 * i] * a[j] + F[3 * i + 1] * a[3 + j] + F[3 * i + 2] * a[6 + j];
+    double A[9];  // Fe^T Fe
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) A[3 * i + j] = Fe[i] * Fe[j] + Fe[3 + i] * Fe[3 + j] + Fe[6 + i] * Fe[6 + j];
+    // E_tr in W components (tensor 11, 22, 33, 23, 13, 12)
+    const double Ew[6] = {0.5 * (A[0] - 1.0), 0.5 * (A[4] - 1.0), 0.5 * (A[8] - 1.0), 0.5 * A[5], 0.5 * A[2], 0.5 * A[1]};
+    const double zero6[6] = {0, 0, 0, 0, 0, 0};
+    double dep[6], Ct[21];
+    ok = cp_update<double>(G, Gf, cp, Ew, zero6, T_guess, T, Ct, dep) && ok;
+    // slip increments dt gdot_a(tau_a), tau_a = P_a . T
+    double L[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
+    const CpScalars<double>& c = cp_scalars<double>(cp);
+    for (int al = 0; al < 12; ++al) {
+        double tau = 0.0;
+#pragma unroll
+        for (int m = 0; m < 6; ++m) tau += G.P[al][m] * T[m];
+        const double x = fabs(tau) * c.inv_tc;
+        double xn, xn1;
+        cp_powers<double>(cp, x, xn, xn1);
+        const double dg = tau < 0.0 ? -c.dtg * xn : c.dtg * xn;
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int j = 0; j < 3; ++j) L[3 * i + j] += dg * G.sv[al][i] * G.nv[al][j];
+    }
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+            Fp[3 * i + j] = L[3 * i] * Fp_old[j] + L[3 * i + 1] * Fp_old[3 + j] + L[3 * i + 2] * Fp_old[6 + j];
+    double Fpi[9];
+    ok = inv3(Fp, Fpi) && ok;
+    const double r2h = 0.70710678118654752440084436210485;
+    const double Tm[9] = {T[0], r2h * T[5], r2h * T[4], r2h * T[5], T[1], r2h * T[3], r2h * T[4], r2h * T[3], T[2]};
+    double W1[9], W2[9];  // F Fp^-1, then (F Fp^-1) T
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) W1[3 * i + j] = F[3 * i] * Fpi[j] + F[3 * i + 1] * Fpi[3 + j] + F[3 * i + 2] * Fpi[6 + j];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) W2[3 * i + j] = W1[3 * i] * Tm[j] + W1[3 * i + 1] * Tm[3 + j] + W1[3 * i + 2] * Tm[6 + j];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            const double v = W2[3 * i] * Fpi[3 * j] + W2[3 * i + 1] * Fpi[3 * j + 1] + W2[3 * i + 2] * Fpi[3 * j + 2];
+            ok = ok && isfinite(v);
+            P[3 * i + j] = v;
+        }
+    // tangent data: Fe_tr, a, B = a T a^T, C_tan
+    double aT[9];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) aT[3 * i + j] = a[3 * i] * Tm[j] + a[3 * i + 1] * Tm[3 + j] + a[3 * i + 2] * Tm[6 + j];
+    const int bi[6] = {0, 1, 2, 1, 0, 0}, bj[6] = {0, 1, 2, 2, 2, 1};
+#pragma unroll
+    for (int q = 0; q < 9; ++q) {
+        tn[q] = Fe[q];
+        tn[9 + q] = a[q];
+    }
+#pragma unroll
+    for (int q = 0; q < 6; ++q)
+        tn[18 + q] = aT[3 * bi[q]] * a[3 * bj[q]] + aT[3 * bi[q] + 1] * a[3 * bj[q] + 1] + aT[3 * bi[q] + 2] * a[3 * bj[q] + 2];
+#pragma unroll
+    for (int q = 0; q < 21; ++q) tn[24 + q] = Ct[q];
     return ok;
 }
 

@@ -9,6 +9,7 @@ cudaError_t launch_ax3<float>(int opk, const Ax3Args<float>& a, cudaStream_t s) 
         case OP_NH_APPLY: return ax3_sz<float, 9, OP_NH_APPLY>(a, s);
         case OP_CP_APPLY: return ax3_sz<float, 6, OP_CP_APPLY>(a, s);
         case OP_SVK_APPLY: return launch_ax3_svk<float>(opk, a, s);
+        case OP_FCP_APPLY: return launch_ax3_fcp<float>(opk, a, s);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -1,5 +1,6 @@
 // Pass 3 for odd n3 with the nonlinear models: tangent applications (FP32 and
-// FP64) and the Neo-Hookean / St. Venant-Kirchhoff updates (FP64).
+// FP64) and the Neo-Hookean / St. Venant-Kirchhoff updates (FP64); the
+// crystal-plasticity operations dispatch to their own translation units.
 #include "k_ax3_odd_impl.cuh"
 
 namespace dbfft {
@@ -10,6 +11,8 @@ static cudaError_t odd_nl_n(int opk, const Ax3Args<T>& a, cudaStream_t s) {
         case OP_NH_APPLY: return ax3_odd_n<T, N3, 9, OP_NH_APPLY>(a, s);
         case OP_SVK_APPLY: return ax3_odd_n<T, N3, 9, OP_SVK_APPLY>(a, s);
         case OP_CP_APPLY: return ax3_odd_n<T, N3, 6, OP_CP_APPLY>(a, s);
+        case OP_FCP_APPLY:
+        case OP_FCP_UPDATE: return launch_ax3_odd_fcp<T>(opk, a, s);
         default: break;
     }
     if constexpr (sizeof(T) == 8) {

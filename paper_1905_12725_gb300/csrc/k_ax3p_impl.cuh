@@ -85,6 +85,7 @@ static cudaError_t pipe_dispatch(int opk, const Ax3Args<T>& a, cudaStream_t s) {
         case OP_NH_APPLY: return pipe_sz<T, 9, OP_NH_APPLY>(a, s);
         case OP_CP_APPLY: return pipe_sz<T, 6, OP_CP_APPLY>(a, s);
         case OP_SVK_APPLY: return launch_ax3_svk<T>(opk, a, s);
+        case OP_FCP_APPLY: return launch_ax3_fcp<T>(opk, a, s);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -132,7 +132,8 @@ template cudaError_t launch_precond_field<double>(const Dims&, const Freq<double
 // side (81 components), from the stored tangent data:
 //   kind 0: Neo-Hookean data (F^-T, mu - lam ln J) with per-phase mu, lam;
 //   kind 1: 21-entry Mandel tangent;
-//   kind 2: St. Venant-Kirchhoff data (F, S) with per-phase mu, lam.
+//   kind 2: St. Venant-Kirchhoff data (F, S) with per-phase mu, lam;
+//   kind 3: finite-strain crystal-plasticity data (45 values).
 template <typename TT>
 __global__ void k_mean_tangent(int kind, long long V, const TT* tan, const uint16_t* phase, const double* lam,
                                const double* mu, double* partials /* [B][gridDim.x][81] */) {
@@ -182,6 +183,24 @@ __global__ void k_mean_tangent(int kind, long long V, const TT* tan, const uint1
                                 val += mu[ph] * (F[3 * i] * F[3 * k] + F[3 * i + 1] * F[3 * k + 1] + F[3 * i + 2] * F[3 * k + 2]);
                             loc[((i * 3 + J) * 3 + k) * 3 + L] += val;
                         }
+        }
+        for (int q = 0; q < 81; ++q) atomicAdd(&acc[q], loc[q]);
+        __syncthreads();
+    } else if (kind == 3) {
+        // finite-strain crystal plasticity, 45 values: column (k, L) of K is
+        // the response to the unit gradient e_k (x) e_L
+        double loc[81];
+        for (int q = 0; q < 81; ++q) loc[q] = 0.0;
+        for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < V; v += (long long)gridDim.x * blockDim.x) {
+            const TT* t = tan + ((long long)b * V + v) * 45;
+            double td[45];
+            for (int q = 0; q < 45; ++q) td[q] = (double)t[q];
+            for (int kl = 0; kl < 9; ++kl) {
+                double G[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0}, out[9];
+                G[kl] = 1.0;
+                fcp_apply<double>(td, G, out);
+                for (int iJ = 0; iJ < 9; ++iJ) loc[iJ * 9 + kl] += out[iJ];
+            }
         }
         for (int q = 0; q < 81; ++q) atomicAdd(&acc[q], loc[q]);
         __syncthreads();
@@ -274,6 +293,18 @@ cudaError_t launch_herm_planes(const Dims& d, cplx<T>* v, cudaStream_t s) {
 }
 template cudaError_t launch_herm_planes<double>(const Dims&, cplx<double>*, cudaStream_t);
 template cudaError_t launch_herm_planes<float>(const Dims&, cplx<float>*, cudaStream_t);
+
+__global__ void k_fill_identity(double* m, long long n9) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n9) m[i] = (i % 9 == 0 || i % 9 == 4 || i % 9 == 8) ? 1.0 : 0.0;
+}
+
+cudaError_t launch_fill_identity(double* m, long long n, cudaStream_t s) {
+    const long long n9 = 9 * n;
+    if (n9 == 0) return cudaSuccess;
+    k_fill_identity<<<(unsigned)((n9 + 255) / 256), 256, 0, s>>>(m, n9);
+    return cudaGetLastError();
+}
 
 }  // namespace dbfft
 

@@ -50,6 +50,8 @@ template <typename T> cudaError_t launch_ax3_pipe(int opk, const Ax3Args<T>& a, 
 // pass 3 of the St. Venant-Kirchhoff law (OP_SVK_APPLY in both precisions, OP_SVK_UPDATE in FP64),
 // plain and pipelined; compiled in translation units of their own
 template <typename T> cudaError_t launch_ax3_svk(int opk, const Ax3Args<T>& a, cudaStream_t s);
+// pass 3 of finite-strain crystal plasticity (OP_FCP_APPLY in both precisions, OP_FCP_UPDATE in FP64)
+template <typename T> cudaError_t launch_ax3_fcp(int opk, const Ax3Args<T>& a, cudaStream_t s);
 // compatibility of the gradient field W (small: curl curl eps; finite: curl F):
 // per-RHS partial sums of |.|^2 over the spectrum into partials [B][nblk]
 cudaError_t launch_compat(const Dims& d, const Freq<double>& f, const cplx<double>* W, double* partials, int nblk,
@@ -68,6 +70,7 @@ template <typename T> cudaError_t launch_ax3_odd(int opk, const Ax3Args<T>& a, c
 // the nonlinear operations of the odd pass 3 (translation units of their own)
 template <typename T> cudaError_t launch_ax3_odd_nl(int opk, const Ax3Args<T>& a, cudaStream_t s);
 cudaError_t launch_ax3_odd_cp(int opk, const Ax3Args<double>& a, cudaStream_t s);
+template <typename T> cudaError_t launch_ax3_odd_fcp(int opk, const Ax3Args<T>& a, cudaStream_t s);
 // lines per CTA of the odd pass 3 (one right-hand side per CTA; nc components)
 int ax3_odd_lines(int n3, int nc, bool dbl);
 // pass 3 of the post-processing transforms (OP_DISP, FP64 only)

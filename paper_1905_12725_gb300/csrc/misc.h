@@ -19,4 +19,6 @@ cudaError_t launch_mean_tangent(int kind, int B, long long V, const TT* tan, con
                                 const double* mu, double* partials, int nblk, cudaStream_t s);
 template <typename T>
 cudaError_t launch_herm_planes(const Dims& d, cplx<T>* v, cudaStream_t s);
+// n row-major 3x3 identity matrices at m[9 n]
+cudaError_t launch_fill_identity(double* m, long long n, cudaStream_t s);
 }  // namespace dbfft

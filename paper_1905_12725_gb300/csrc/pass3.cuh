@@ -26,7 +26,9 @@ enum {
     OP_CP_UPDATE32 = 6, // OP_CP_UPDATE for an FP32 inner solve: FP32 Newton start, FP32 tangent
     OP_SVK_APPLY = 7,   // dP = K(F) : (G + macro) from the stored SVK tangent data (F, S)
     OP_SVK_UPDATE = 8,  // St. Venant-Kirchhoff P(F), F = macro (incl. I) + G; stores F and S
-    OP_DISP = 9         // total displacement Hbar x + u~ from the 3 inverse-transformed components (no R2C)
+    OP_DISP = 9,        // total displacement Hbar x + u~ from the 3 inverse-transformed components (no R2C)
+    OP_FCP_APPLY = 10,  // dP = K : (G + macro) from the stored finite-strain crystal-plasticity data (45)
+    OP_FCP_UPDATE = 11  // finite-strain crystal plasticity, F = Fe Fp: P, Fp, T and the tangent data
 };
 
 template <typename T>
@@ -66,12 +68,15 @@ struct Ax3Args {
     unsigned* err;         // error bits (bit 0: local Newton failure)
     double* dJdE;          // OP_ADJ output [B][V]
     double* real_out;      // OP_DISP output [B][3][V]; macroW holds Hbar row-major [B][9]
+    const double* fp_old;  // OP_FCP_UPDATE: committed Fp [B][V][9]
+    double* fp_new;        // OP_FCP_UPDATE: trial Fp [B][V][9]
     double hx[3];          // OP_DISP: voxel edge lengths L_a / n_a
 };
 
 template <int OPK> struct OpInfo {
     static constexpr bool forward = OPK != OP_ADJ && OPK != OP_DISP;
-    static constexpr bool apply = OPK == OP_ISO || OPK == OP_NH_APPLY || OPK == OP_CP_APPLY || OPK == OP_SVK_APPLY;
+    static constexpr bool apply =
+        OPK == OP_ISO || OPK == OP_NH_APPLY || OPK == OP_CP_APPLY || OPK == OP_SVK_APPLY || OPK == OP_FCP_APPLY;
 };
 
 // Complex entries per slot buffer: room for the half-spectrum line (M + 1),
@@ -104,7 +109,7 @@ __host__ __device__ constexpr int ax3_slot_cplx() {
 // loads and stores are done cooperatively: for one (right-hand side,
 // component) the L lines of a CTA are L h contiguous complex values.
 template <typename T, int N3, int NC, int OPK, int RW>
-__global__ void __launch_bounds__(256, (sizeof(T) == 4 ? (RW == 32 ? 2 : (RW == 16 ? 2 : 3)) : ((RW == 32 || OPK == OP_CP_UPDATE || OPK == OP_CP_UPDATE32 || OPK == OP_NH_UPDATE || OPK == OP_SVK_UPDATE) ? 1 : 2))) k_axis3(Ax3Args<T> a) {
+__global__ void __launch_bounds__(256, (sizeof(T) == 4 ? (RW == 32 ? 2 : (RW == 16 ? 2 : 3)) : ((RW == 32 || OPK == OP_CP_UPDATE || OPK == OP_CP_UPDATE32 || OPK == OP_NH_UPDATE || OPK == OP_SVK_UPDATE || OPK == OP_FCP_UPDATE) ? 1 : 2))) k_axis3(Ax3Args<T> a) {
     constexpr bool CPU_ = OPK == OP_CP_UPDATE || OPK == OP_CP_UPDATE32;  // crystal-plasticity update
     pdl_wait();
     pdl_trigger();  // the successor may start launching; it waits for this grid to finish
@@ -319,6 +324,52 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? (RW == 32 ? 2 : (RW == 
                 for (int q = 0; q < NT; ++q) {
                     if (a.tan_out_f) a.tan_out_f[to + q] = (float)tn[q];
                     if (a.tan_out_d) a.tan_out_d[to + q] = tn[q];
+                }
+#pragma unroll
+                for (int q = 0; q < 9; ++q) f[q * SB] = (T)Pk[q];
+            }
+        } else if constexpr (OPK == OP_FCP_APPLY) {
+            for (int rr = 0; rr < RB; ++rr) {
+                const int bb = g * RB + rr;
+                if (rhs_done(rr)) continue;
+                T* f = slot_ptr(0, (lv * RB + rr) * NC) + x3;
+                T G[9], sg[9];
+#pragma unroll
+                for (int q = 0; q < 9; ++q) G[q] = f[q * SB] + s_macro[rr * 9 + q];
+                fcp_apply<T>(a.tan_in + ((long long)bb * d.V + vox) * 45, G, sg);
+                if (a.cg) {
+                    T en = T(0);
+#pragma unroll
+                    for (int q = 0; q < 9; ++q) en += G[q] * sg[q];
+                    eacc[rr] += en;
+                }
+#pragma unroll
+                for (int q = 0; q < 9; ++q) f[q * SB] = sg[q];
+            }
+        } else if constexpr (OPK == OP_FCP_UPDATE) {
+            const long long mv = (long long)mat * d.V + vox;
+            const int gr = a.phase[mv];
+            for (int rr = 0; rr < RB; ++rr) {
+                const int bb = g * RB + rr;
+                T* f = slot_ptr(0, (lv * RB + rr) * NC) + x3;
+                double F[9], Pk[9], Fpn[9], Fpo[9], Tn[6], guess[6], tn[45];
+#pragma unroll
+                for (int q = 0; q < 9; ++q) F[q] = (double)f[q * SB] + s_macro[rr * 9 + q];
+                const long long vo = (long long)bb * d.V + vox;
+#pragma unroll
+                for (int q = 0; q < 9; ++q) Fpo[q] = a.fp_old[vo * 9 + q];
+#pragma unroll
+                for (int q = 0; q < 6; ++q) guess[q] = (a.guess_trial ? a.sig_t : a.sig_prev)[vo * 6 + q];
+                const bool ok = fcp_update(a.grains[gr], a.grains_f[gr], a.cp, F, Fpo, guess, Pk, Fpn, Tn, tn);
+                if (!ok) atomicOr(a.err, 1u);
+#pragma unroll
+                for (int q = 0; q < 9; ++q) a.fp_new[vo * 9 + q] = Fpn[q];
+#pragma unroll
+                for (int q = 0; q < 6; ++q) a.sig_t[vo * 6 + q] = Tn[q];
+#pragma unroll
+                for (int q = 0; q < 45; ++q) {
+                    if (a.tan_out_f) a.tan_out_f[vo * 45 + q] = (float)tn[q];
+                    if (a.tan_out_d) a.tan_out_d[vo * 45 + q] = tn[q];
                 }
 #pragma unroll
                 for (int q = 0; q < 9; ++q) f[q * SB] = (T)Pk[q];

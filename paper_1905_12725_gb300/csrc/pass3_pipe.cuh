@@ -54,6 +54,16 @@ __device__ __forceinline__ T apply_voxel(const Ax3Args<T>& a, int bb, long long 
             en += G[q] * sg[q];
             f[q * CS] = sg[q];
         }
+    } else if constexpr (OPK == OP_FCP_APPLY) {
+        T G[9], sg[9];
+#pragma unroll
+        for (int q = 0; q < 9; ++q) G[q] = f[q * CS] + a.macroW[bb * 9 + q];
+        fcp_apply<T>(a.tan_in + ((long long)bb * a.d.V + vox) * 45, G, sg);
+#pragma unroll
+        for (int q = 0; q < 9; ++q) {
+            en += G[q] * sg[q];
+            f[q * CS] = sg[q];
+        }
     } else if constexpr (OPK == OP_CP_APPLY) {
         T e[6], sg[6];
 #pragma unroll

@@ -22,7 +22,7 @@ STATUS = {0: "DBFFT_OK", 1: "DBFFT_E_ARG", 2: "DBFFT_E_UNSUPPORTED_GRID", 3: "DB
           8: "DBFFT_E_MATERIAL", 9: "DBFFT_E_STATE"}
 DBFFT_SMALL, DBFFT_FINITE = 0, 1
 DBFFT_FP64, DBFFT_MIXED = 0, 1
-DBFFT_ISO_ELASTIC, DBFFT_NEO_HOOKE, DBFFT_CP_FCC_POWERLAW, DBFFT_SVK = 0, 1, 2, 3
+DBFFT_ISO_ELASTIC, DBFFT_NEO_HOOKE, DBFFT_CP_FCC_POWERLAW, DBFFT_SVK, DBFFT_CP_FCC_FINITE = 0, 1, 2, 3, 4
 DBFFT_PRECOND_PER_INCREMENT, DBFFT_PRECOND_INITIAL, DBFFT_PRECOND_PER_NEWTON = 0, 1, 2
 DBFFT_APPLY_FP32, DBFFT_APPLY_PRECOND, DBFFT_APPLY_RESIDUAL = 1, 2, 4
 
@@ -182,10 +182,13 @@ def svk_phases(mu, lam):
     return out
 
 
-def cp_phases(quats, C11=168000.0, C12=121000.0, C44=75000.0, gdot0=1e-3, m=0.05, tau_c=50.0):
+def cp_phases(quats, C11=168000.0, C12=121000.0, C44=75000.0, gdot0=1e-3, m=0.05, tau_c=50.0,
+              finite=False):
+    """One FCC grain per quaternion; finite=True selects the finite-strain
+    form (F = Fe Fp, FINITE kinematics) of the same crystal."""
     out = (dbfft_phase * len(quats))()
     for i, q in enumerate(quats):
-        out[i].model = DBFFT_CP_FCC_POWERLAW
+        out[i].model = DBFFT_CP_FCC_FINITE if finite else DBFFT_CP_FCC_POWERLAW
         out[i].C11, out[i].C12, out[i].C44 = C11, C12, C44
         out[i].gdot0, out[i].m, out[i].tau_c = gdot0, m, tau_c
         for k in range(4):
@@ -207,7 +210,8 @@ class Solver:
     """One dbfft context on the current CUDA device and torch stream.
 
     phase: uint16 array [n_materials, n1, n2, n3] (or [n1, n2, n3]);
-    phases: ctypes array from iso_phases / neo_hooke_phases / svk_phases / cp_phases;
+    phases: ctypes array from iso_phases / neo_hooke_phases / svk_phases / cp_phases
+    (cp_phases(..., finite=True) for the finite-strain crystal);
     target: [batch, 3, 3] end-of-ramp macro targets; stress_mask: 9 booleans.
     """
 
