@@ -783,12 +783,13 @@ def main():
     ap.add_argument("--skip-256", action="store_true")
     ap.add_argument("--case", default="",
                     choices=["", "op256", "c2", "c1", "c3", "c3fp64", "c4", "c4fp64", "c5", "porous",
-                             "porousfp64", "porous63", "porous63fp64", "inclusion", "fcp", "fcpfp64"],
+                             "porousfp64", "porous63", "porous63fp64", "inclusion", "fcp", "fcpfp64", "fcp63",
+                             "fcp63fp64"],
                     help="run one sub-measurement only: op256 = 256^3 FP32 CG pass chain, c2 = one mixed "
                          "batched 64^3 solve (profiler captures); c1, c3[fp64], c4[fp64], c5 = the other "
                          "configurations at full size; porous[fp64] = the porous St. Venant-Kirchhoff "
                          "stretch (64^3; porous63[fp64] on the paper's 63^3 grid); inclusion = the 63^3 inclusion contrast sweep; "
-                         "fcp[fp64] = the 64^3 finite-strain crystal-plasticity stretch")
+                         "fcp[fp64] = the 64^3 finite-strain crystal-plasticity stretch (fcp63[fp64] on 63^3)")
     args = ap.parse_args()
     if args.case:
         import torch
@@ -803,9 +804,9 @@ def main():
             print(json.dumps(case_porous(prec, n=63), default=float), flush=True)
         elif args.case == "inclusion":
             print(json.dumps(case_inclusion(), default=float), flush=True)
-        elif args.case in ("fcp", "fcpfp64"):
+        elif args.case in ("fcp", "fcpfp64", "fcp63", "fcp63fp64"):
             prec = dbfft.DBFFT_FP64 if args.case.endswith("fp64") else dbfft.DBFFT_MIXED
-            print(json.dumps(case_fcp(prec), default=float), flush=True)
+            print(json.dumps(case_fcp(prec, n=63 if "63" in args.case else 64), default=float), flush=True)
         elif args.case in ("c1", "c3", "c3fp64", "c4", "c4fp64", "c5", "porous", "porousfp64"):
             prec = dbfft.DBFFT_FP64 if args.case.endswith("fp64") else dbfft.DBFFT_MIXED
             res = {"c1": lambda: case_c1(), "c3": lambda: case_c3(prec), "c3fp64": lambda: case_c3(prec),
