@@ -667,7 +667,7 @@ int opk_apply(const dbfft_ctx* ctx) {
 int opk_update(const dbfft_ctx* ctx) {
     if (ctx->model == DBFFT_CP_FCC_POWERLAW) return ctx->prec == DBFFT_MIXED ? OP_CP_UPDATE32 : OP_CP_UPDATE;
     if (ctx->model == DBFFT_SVK) return OP_SVK_UPDATE;
-    if (ctx->model == DBFFT_CP_FCC_FINITE) return OP_FCP_UPDATE;
+    if (ctx->model == DBFFT_CP_FCC_FINITE) return ctx->prec == DBFFT_MIXED ? OP_FCP_UPDATE32 : OP_FCP_UPDATE;
     return ctx->model == DBFFT_ISO_ELASTIC ? OP_ISO : OP_NH_UPDATE;
 }
 

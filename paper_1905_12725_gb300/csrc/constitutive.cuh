@@ -493,8 +493,10 @@ __device__ __forceinline__ int cp_refine64(const CpGrain& G, const CpParams& cp,
 // settle; the stored FP32 tangent is built in FP32. With TT = double
 // everything runs in FP64 Newton. Both stop when the FP64 step is below the
 // same tolerance, so both return the same stress to that tolerance.
+// F32START = true with TT = double takes the FP32 start and builds the
+// tangent in FP64.
 // Returns false when the local Newton fails (outputs stay finite).
-template <typename TT>
+template <typename TT, bool F32START = (sizeof(TT) == 4)>
 __device__ __forceinline__ bool cp_update(const CpGrain& G, const CpGrainF& Gf, const CpParams& cp,
                                           const double* eps_w, const double* ep_old, const double* s_guess,
                                           double* s_out, TT* tan, double* ep_new) {
@@ -507,7 +509,7 @@ __device__ __forceinline__ bool cp_update(const CpGrain& G, const CpGrainF& Gf, 
         s[i] = s_guess[i];
     }
     int r = 0;
-    if constexpr (sizeof(TT) == 4) {
+    if constexpr (F32START) {
         float tgf[6], sf[6];
 #pragma unroll
         for (int i = 0; i < 6; ++i) {
@@ -572,7 +574,12 @@ __device__ __forceinline__ bool cp_update(const CpGrain& G, const CpGrainF& Gf, 
 // backward-Euler problem with E_tr as the strain (cp_update, no plastic strain
 // at the start of the step); then Fp = (I + dt sum_a gdot_a s_a n_a) Fp_old,
 // P = F Fp^-1 T Fp^-T. Writes P (9), Fp (9), T (Mandel 6) and the 45 tangent
-// values (fcp_apply). False when the local solve or an inverse fails.
+// values (fcp_apply). False when the local solve or an inverse fails. F32START
+// starts the local solve in FP32, as cp_update does for the mixed-precision
+// inner solve, with the same FP64 stop rule on T; C_tan = J^-1 stays FP64
+// (J has condition numbers of several hundred in plastic flow, so an FP32
+// inverse would lose about 1e-5 of the tangent).
+template <bool F32START>
 __device__ __forceinline__ bool fcp_update(const CpGrain& G, const CpGrainF& Gf, const CpParams& cp, const double* F,
                                            const double* Fp_old, const double* T_guess, double* P, double* Fp,
                                            double* T, double* tn) {
@@ -592,7 +599,7 @@ __device__ __forceinline__ bool fcp_update(const CpGrain& G, const CpGrainF& Gf,
     const double Ew[6] = {0.5 * (A[0] - 1.0), 0.5 * (A[4] - 1.0), 0.5 * (A[8] - 1.0), 0.5 * A[5], 0.5 * A[2], 0.5 * A[1]};
     const double zero6[6] = {0, 0, 0, 0, 0, 0};
     double dep[6], Ct[21];
-    ok = cp_update<double>(G, Gf, cp, Ew, zero6, T_guess, T, Ct, dep) && ok;
+    ok = cp_update<double, F32START>(G, Gf, cp, Ew, zero6, T_guess, T, Ct, dep) && ok;
     // slip increments dt gdot_a(tau_a), tau_a = P_a . T
     double L[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
     const CpScalars<double>& c = cp_scalars<double>(cp);

@@ -15,7 +15,8 @@ cudaError_t launch_ax3<double>(int opk, const Ax3Args<double>& a, cudaStream_t s
         case OP_SVK_APPLY:
         case OP_SVK_UPDATE: return launch_ax3_svk<double>(opk, a, s);
         case OP_FCP_APPLY:
-        case OP_FCP_UPDATE: return launch_ax3_fcp<double>(opk, a, s);
+        case OP_FCP_UPDATE:
+        case OP_FCP_UPDATE32: return launch_ax3_fcp<double>(opk, a, s);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -9,6 +9,7 @@ static cudaError_t odd_fcp_n(int opk, const Ax3Args<T>& a, cudaStream_t s) {
     if (opk == OP_FCP_APPLY) return ax3_odd_n<T, N3, 9, OP_FCP_APPLY>(a, s);
     if constexpr (sizeof(T) == 8) {
         if (opk == OP_FCP_UPDATE) return ax3_odd_n<T, N3, 9, OP_FCP_UPDATE>(a, s);
+        if (opk == OP_FCP_UPDATE32) return ax3_odd_n<T, N3, 9, OP_FCP_UPDATE32>(a, s);
     }
     return cudaErrorInvalidValue;
 }

@@ -12,7 +12,8 @@ static cudaError_t odd_nl_n(int opk, const Ax3Args<T>& a, cudaStream_t s) {
         case OP_SVK_APPLY: return ax3_odd_n<T, N3, 9, OP_SVK_APPLY>(a, s);
         case OP_CP_APPLY: return ax3_odd_n<T, N3, 6, OP_CP_APPLY>(a, s);
         case OP_FCP_APPLY:
-        case OP_FCP_UPDATE: return launch_ax3_odd_fcp<T>(opk, a, s);
+        case OP_FCP_UPDATE:
+        case OP_FCP_UPDATE32: return launch_ax3_odd_fcp<T>(opk, a, s);
         default: break;
     }
     if constexpr (sizeof(T) == 8) {

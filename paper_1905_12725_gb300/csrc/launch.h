@@ -50,7 +50,7 @@ template <typename T> cudaError_t launch_ax3_pipe(int opk, const Ax3Args<T>& a, 
 // pass 3 of the St. Venant-Kirchhoff law (OP_SVK_APPLY in both precisions, OP_SVK_UPDATE in FP64),
 // plain and pipelined; compiled in translation units of their own
 template <typename T> cudaError_t launch_ax3_svk(int opk, const Ax3Args<T>& a, cudaStream_t s);
-// pass 3 of finite-strain crystal plasticity (OP_FCP_APPLY in both precisions, OP_FCP_UPDATE in FP64)
+// pass 3 of finite-strain crystal plasticity (OP_FCP_APPLY in both precisions, OP_FCP_UPDATE[32] in FP64)
 template <typename T> cudaError_t launch_ax3_fcp(int opk, const Ax3Args<T>& a, cudaStream_t s);
 // compatibility of the gradient field W (small: curl curl eps; finite: curl F):
 // per-RHS partial sums of |.|^2 over the spectrum into partials [B][nblk]

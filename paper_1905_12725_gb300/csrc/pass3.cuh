@@ -28,7 +28,8 @@ enum {
     OP_SVK_UPDATE = 8,  // St. Venant-Kirchhoff P(F), F = macro (incl. I) + G; stores F and S
     OP_DISP = 9,        // total displacement Hbar x + u~ from the 3 inverse-transformed components (no R2C)
     OP_FCP_APPLY = 10,  // dP = K : (G + macro) from the stored finite-strain crystal-plasticity data (45)
-    OP_FCP_UPDATE = 11  // finite-strain crystal plasticity, F = Fe Fp: P, Fp, T and the tangent data
+    OP_FCP_UPDATE = 11, // finite-strain crystal plasticity, F = Fe Fp: P, Fp, T and the tangent data
+    OP_FCP_UPDATE32 = 12  // OP_FCP_UPDATE for an FP32 inner solve: FP32 start of the local solve
 };
 
 template <typename T>
@@ -109,7 +110,7 @@ __host__ __device__ constexpr int ax3_slot_cplx() {
 // loads and stores are done cooperatively: for one (right-hand side,
 // component) the L lines of a CTA are L h contiguous complex values.
 template <typename T, int N3, int NC, int OPK, int RW>
-__global__ void __launch_bounds__(256, (sizeof(T) == 4 ? (RW == 32 ? 2 : (RW == 16 ? 2 : 3)) : ((RW == 32 || OPK == OP_CP_UPDATE || OPK == OP_CP_UPDATE32 || OPK == OP_NH_UPDATE || OPK == OP_SVK_UPDATE || OPK == OP_FCP_UPDATE) ? 1 : 2))) k_axis3(Ax3Args<T> a) {
+__global__ void __launch_bounds__(256, (sizeof(T) == 4 ? (RW == 32 ? 2 : (RW == 16 ? 2 : 3)) : ((RW == 32 || OPK == OP_CP_UPDATE || OPK == OP_CP_UPDATE32 || OPK == OP_NH_UPDATE || OPK == OP_SVK_UPDATE || OPK == OP_FCP_UPDATE || OPK == OP_FCP_UPDATE32) ? 1 : 2))) k_axis3(Ax3Args<T> a) {
     constexpr bool CPU_ = OPK == OP_CP_UPDATE || OPK == OP_CP_UPDATE32;  // crystal-plasticity update
     pdl_wait();
     pdl_trigger();  // the successor may start launching; it waits for this grid to finish
@@ -346,7 +347,7 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? (RW == 32 ? 2 : (RW == 
 #pragma unroll
                 for (int q = 0; q < 9; ++q) f[q * SB] = sg[q];
             }
-        } else if constexpr (OPK == OP_FCP_UPDATE) {
+        } else if constexpr (OPK == OP_FCP_UPDATE || OPK == OP_FCP_UPDATE32) {
             const long long mv = (long long)mat * d.V + vox;
             const int gr = a.phase[mv];
             for (int rr = 0; rr < RB; ++rr) {
@@ -360,7 +361,7 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? (RW == 32 ? 2 : (RW == 
                 for (int q = 0; q < 9; ++q) Fpo[q] = a.fp_old[vo * 9 + q];
 #pragma unroll
                 for (int q = 0; q < 6; ++q) guess[q] = (a.guess_trial ? a.sig_t : a.sig_prev)[vo * 6 + q];
-                const bool ok = fcp_update(a.grains[gr], a.grains_f[gr], a.cp, F, Fpo, guess, Pk, Fpn, Tn, tn);
+                const bool ok = fcp_update<OPK == OP_FCP_UPDATE32>(a.grains[gr], a.grains_f[gr], a.cp, F, Fpo, guess, Pk, Fpn, Tn, tn);
                 if (!ok) atomicOr(a.err, 1u);
 #pragma unroll
                 for (int q = 0; q < 9; ++q) a.fp_new[vo * 9 + q] = Fpn[q];

@@ -103,7 +103,7 @@ __device__ __forceinline__ void update_voxel(const Ax3Args<T>& a, int bb, long l
         const double ir2 = 0.70710678118654752440084436210485;
 #pragma unroll
         for (int q = 0; q < 6; ++q) e[q] = (T)(q < 3 ? sg[q] : ir2 * sg[q]);
-    } else if constexpr (OPK == OP_FCP_UPDATE) {
+    } else if constexpr (OPK == OP_FCP_UPDATE || OPK == OP_FCP_UPDATE32) {
         const int gr = a.phase[mv];
         const long long vo = (long long)bb * a.d.V + vox;
         double F[9], Pk[9], Fpn[9], Fpo[9], Tn[6], guess[6], tn[45];
@@ -113,7 +113,7 @@ __device__ __forceinline__ void update_voxel(const Ax3Args<T>& a, int bb, long l
         for (int q = 0; q < 9; ++q) Fpo[q] = a.fp_old[vo * 9 + q];
 #pragma unroll
         for (int q = 0; q < 6; ++q) guess[q] = (a.guess_trial ? a.sig_t : a.sig_prev)[vo * 6 + q];
-        const bool ok = fcp_update(a.grains[gr], a.grains_f[gr], a.cp, F, Fpo, guess, Pk, Fpn, Tn, tn);
+                const bool ok = fcp_update<OPK == OP_FCP_UPDATE32>(a.grains[gr], a.grains_f[gr], a.cp, F, Fpo, guess, Pk, Fpn, Tn, tn);
         if (!ok) atomicOr(a.err, 1u);
 #pragma unroll
         for (int q = 0; q < 9; ++q) a.fp_new[vo * 9 + q] = Fpn[q];
