@@ -524,6 +524,31 @@ def test_config1_invariants():
     assert (lam_m + 2 * mu_m) * 1e-3 < sol["sig_bar"][0, 0] < (lam_i + 2 * mu_i) * 1e-3
 
 
+def test_centred_inclusion_gives_a_cubic_effective_stiffness():
+    """The 16^3 centred sphere is unchanged by the 48 symmetries of the cube, and so is the
+    discrete operator on an equal-sided even grid (a mirror sends k to -k; an integer shift of
+    voxels is exact). C_eff must therefore be cubic. Axis 3 is built apart from axes 1-2 (it is
+    cut to a half spectrum), so a frequency slip on it alone (a 1 % wrong length moves C33 off
+    C11 by 6e-4) fails here, and so does a wrong factor on one Mandel shear component."""
+    c = synth.config1()
+    p = c["phase"]
+    assert all(np.array_equal(p, np.flip(p, a)) for a in range(3))
+    assert np.array_equal(p, p.transpose(1, 0, 2)) and np.array_equal(p, p.transpose(2, 1, 0))
+    lam, mu = o.lame(c["E"][p], c["nu"][p])
+    Ceff, _ = o.homogenized_tangent(p.shape, o.IsoTangent(lam, mu), tol=1e-13)
+    tol = 1e-9 * np.abs(Ceff).max()
+    d = np.diag(Ceff)
+    assert np.ptp(d[:3]) < tol and np.ptp(d[3:]) < tol
+    assert np.ptp([Ceff[0, 1], Ceff[0, 2], Ceff[1, 2]]) < tol
+    assert np.abs(Ceff[:3, 3:]).max() < tol and np.abs(Ceff[3:, :3]).max() < tol
+    assert np.abs(Ceff[3:, 3:] - np.diag(d[3:])).max() < tol
+    # stiffer than the matrix, softer than the inclusion, and not isotropic to round-off
+    lam_m, mu_m = o.lame(1.0, 0.3)
+    assert lam_m + 2 * mu_m < d[0] < 10 * (lam_m + 2 * mu_m)
+    assert 2 * mu_m < d[3] < 20 * mu_m
+    assert abs((d[0] - Ceff[0, 1]) - d[3]) > 1e3 * tol
+
+
 # ---------------------------------------------------------------- Neo-Hooke (R13)
 def test_neo_hooke_stress_and_tangent_by_finite_differences():
     g = np.random.default_rng(5)
