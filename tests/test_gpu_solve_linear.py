@@ -80,6 +80,35 @@ def test_homogenized_tangent_six_rhs_batched(precision):
     assert np.abs(Ceff - Ceff.T).max() < (1e-10 if precision == 0 else 1e-6) * np.abs(Ceff).max()
 
 
+@pytest.mark.parametrize("precision", [0, 1])
+def test_centred_inclusion_64_cubed_gives_a_cubic_stiffness(precision):
+    """A property that holds at any size: one centred sphere on an equal-sided even grid is
+    unchanged by the cube's symmetries, and so is the discrete operator, so C_eff is cubic
+    (C11 = C22 = C33, C12 = C13 = C23, C44 = C55 = C66, no other coupling). Axis 3 runs through
+    other kernels (the real-to-complex pass) than axes 1-2, so an axis-specific slip there
+    breaks it. C_eff also lies between the Reuss and Voigt bounds."""
+    n = 64
+    phase = synth.centred_sphere(n, 16)
+    E, nu = [1.0, 10.0], [0.3, 0.3]
+    dbfft = _dbfft()
+    s = dbfft.Solver((n, n, n), phase, dbfft.iso_phases(E, nu), np.zeros((6, 3, 3)), batch=6,
+                     tol=1e-12 if precision == 0 else 1e-7, precision=precision, eta_inner=1e-3)
+    C, _ = s.homogenized_tangent()
+    C = C[0]
+    bar = (1e-9 if precision == 0 else 1e-6) * np.abs(C).max()
+    d = np.diag(C)
+    assert np.ptp(d[:3]) < bar and np.ptp(d[3:]) < bar
+    assert np.ptp([C[0, 1], C[0, 2], C[1, 2], C[1, 0], C[2, 0], C[2, 1]]) < bar
+    assert np.abs(C[:3, 3:]).max() < bar and np.abs(C[3:, :3]).max() < bar
+    assert np.abs(C[3:, 3:] - np.diag(d[3:])).max() < bar
+    vf = phase.mean()
+    Cm = [o.tensor4_to_mandel(o.iso_stiffness(*o.lame(e, v))) for e, v in zip(E, nu)]
+    Cv = (1 - vf) * Cm[0] + vf * Cm[1]
+    Cr = np.linalg.inv((1 - vf) * np.linalg.inv(Cm[0]) + vf * np.linalg.inv(Cm[1]))
+    assert np.linalg.eigvalsh(Cv - C).min() > -bar
+    assert np.linalg.eigvalsh(C - Cr).min() > -bar
+
+
 def test_zero_load_returns_zero_without_iterations():
     shape = (8, 8, 8)
     dbfft = _dbfft()
