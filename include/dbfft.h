@@ -295,32 +295,42 @@ long long dbfft_launch_count(const dbfft_ctx* ctx);
  * times inside its own iteration). This entry point needs no context: it
  * computes out = K u_hat exactly as dbfft_apply does for FP64, small strain,
  * linear isotropic phases and full strain control (no macro unknowns), and
- * keeps its work buffer and its frequency / twiddle tables in static device
- * arrays inside the library.
+ * keeps its work buffer, its frequency / twiddle tables and a copy of the
+ * Lame constants in static device arrays inside the library.
  *
  * n[3]: grid, powers of two in [8, 256]; L[3]: box lengths (NULL: all 1);
  * batch: right-hand sides, each with its own material map;
- * phase_id: device uint16 [batch][n1][n2][n3]; lam, mu: device double
+ * phase_id: device uint16 [batch][n1][n2][n3], every id < n_phases;
+ * n_phases: entries of lam and mu, in [1, 65536]; lam, mu: device double
  * [n_phases] Lame constants indexed by phase_id; u_hat, out: device
  * complex128 [batch][3][n1][n2][n3/2+1] (out may not alias u_hat); stream: a
- * cudaStream_t (NULL: legacy default stream). Returns after the work is done.
+ * cudaStream_t (NULL: legacy default stream).
+ *
+ * The call is host-synchronous: it returns after the work is done, because
+ * it reports the check of the phase ids. An id at or beyond n_phases is
+ * never used to index the caller's lam / mu (the copies cover every uint16
+ * value); the call then returns DBFFT_E_ARG and out is unspecified. The
+ * frequency and twiddle tables are uploaded only when n or L differs from
+ * the previous call on the device.
  *
  * Limit: the static work buffer holds 16 MiB, i.e.
  * batch * 6 * n1 * n2 * (n3/2 + 1) * 16 bytes <= 16 MiB (one 64^3 field, or
  * seven 32^3 fields) and batch <= 1024; larger requests return DBFFT_E_ARG
- * with a message on stderr and touch no device memory.
+ * and touch no device memory.
  * The buffer is shared by every call in the process and keeps the last
  * call's contents; nothing in it needs to start at zero (each call
- * overwrites what it reads). Calls that overlap on the GPU (from several
- * streams or threads at once) race on it and must be serialised by the
- * caller. The first call on a device looks up the device addresses of the
- * static arrays; every GPU on which the library's device code is loaded
- * holds the 16 MiB (plus the small tables) until the process exits.
- * Errors: E_ARG, E_UNSUPPORTED_GRID, E_CUDA.
+ * overwrites what it reads, and clears the phase-check flag itself). Calls
+ * that overlap on the GPU (from several streams or threads at once) race on
+ * it and must be serialised by the caller. The first call on a device looks
+ * up the device addresses of the static arrays; every GPU on which the
+ * library's device code is loaded holds the 16 MiB (plus 1 MiB of tables)
+ * until the process exits.
+ * Errors: E_ARG, E_UNSUPPORTED_GRID, E_CUDA; the message of the calling
+ * thread's last failure is dbfft_last_error(NULL).
  */
 dbfft_status dbfft_apply_iso_noalloc(const int n[3], const double L[3], int batch, const uint16_t* phase_id,
-                                     const double* lam, const double* mu, const void* u_hat, void* out,
-                                     void* stream);
+                                     int n_phases, const double* lam, const double* mu, const void* u_hat,
+                                     void* out, void* stream);
 
 /*
  * Autotuner (no counterpart in the paper; launch-shape selection for the
@@ -343,7 +353,11 @@ const char* dbfft_tuning(const dbfft_ctx* ctx);
  * pipelined: 0 = one CTA per group of grid lines, loads staged by cp.async;
  * 1 = persistent CTAs looping over tiles of `lines` grid lines with two
  * shared-memory stages filled and drained by bulk copies; 2 = the same with
- * one stage (half the shared memory per CTA). radix: 8 or 16 (FP32), 4
+ * one stage (half the shared memory per CTA); 3 = the line-bulk pass of the
+ * FP32 applications on lines of n3 = 128 or 256 values (linear isotropic,
+ * small-strain crystal-plasticity and Neo-Hookean models): one tile of
+ * `lines` grid lines per CTA moved by bulk copies, each line transformed in
+ * place by two register stages (radix ignored). radix: 8 or 16 (FP32), 4
  * (FP64), or 32 with the plain kernel when n3 <= 256 (FP32) / 64 (FP64):
  * one thread per grid line, or 32 values of a line per thread beyond
  * (FP32) / 4 (FP64); lines: grid lines per CTA (per tile when pipelined;
@@ -375,7 +389,9 @@ size_t dbfft_device_bytes(const dbfft_ctx* ctx);
 /* Release the context and its device memory (NULL is a no-op). */
 void dbfft_destroy(dbfft_ctx* ctx);
 
-/* Message of the last error of ctx ("" if none); valid until the next call. */
+/* Message of the last error of ctx ("" if none); valid until the next call.
+ * ctx = NULL: the calling thread's last failure of a context-free call
+ * (dbfft_apply_iso_noalloc), "" if none. */
 const char* dbfft_last_error(const dbfft_ctx* ctx);
 
 /* Name of a status code. */

@@ -86,6 +86,7 @@ struct dbfft_ctx {
     std::vector<PrecondData> pre_init_h;  // the preconditioner of the initial stiffness
     int pre_refresh = DBFFT_PRECOND_PER_INCREMENT;
     bool pre_is_init = true;  // the device holds pre_init_h
+    long long wait_limit = 0;  // polls of the bulk-copy waits of pass 3 (0: the kernels' default)
 
     // ---- vectors
     cplx<double>* x64 = nullptr;
@@ -163,6 +164,7 @@ struct dbfft_ctx {
     // ---- inner PCG as one CUDA graph (WHILE node), per inner precision
     bool use_graphs = true;
     bool use_pdl = true;     // programmatic dependent launch inside the CG graph
+    bool fuse_ax2 = false;   // FP32 CG: element-wise passes 1 and 5 fused into the axis-2 transforms
     bool graph_warm[2] = {false, false};
     cudaGraphExec_t cg_exec[2] = {nullptr, nullptr};
 };
@@ -710,6 +712,7 @@ Ax3Args<T> ax3_base(dbfft_ctx* ctx, cplx<T>* W) {
     a.grains_f = ctx->grains_f;
     a.cp = ctx->cp;
     a.err = ctx->errw;
+    a.wait_limit = ctx->wait_limit;
     return a;
 }
 
@@ -846,6 +849,13 @@ __global__ void k_cg_continue(cudaGraphConditionalHandle h, const CgState* cg, i
 
 // Capture one PCG iteration (passes 1-5 + the loop condition) as the body of
 // a WHILE conditional node: one graph launch runs the whole inner solve.
+// The FP32 CG iteration runs passes 1 and 5 fused into the axis-2 transforms
+// (5 kernels per iteration instead of 7) where the fused kernels exist.
+template <typename T>
+bool fused_cg(const dbfft_ctx* ctx) {
+    return sizeof(T) == 4 && ctx->fuse_ax2 && fused_ax2_supported(ctx->n2);
+}
+
 template <typename T>
 dbfft_status build_cg_graph(dbfft_ctx* ctx, const Ax1InvArgs<T>& a1, const Ax2Args<T>& a2, const Ax3Args<T>& a3,
                             const Ax1FwdArgs<T>& a5, int opk, cudaGraphExec_t* out) {
@@ -873,13 +883,23 @@ dbfft_status build_cg_graph(dbfft_ctx* ctx, const Ax1InvArgs<T>& a1, const Ax2Ar
         // dependencies: each may launch while its predecessor drains and waits
         // (pdl_wait) before reading the predecessor's output
         g_pdl_launch = ctx->use_pdl;
-        e = launch_grad<T>(AX1_CG, a1, cs);
-        if (e == cudaSuccess) e = launch_fft_ax2<T>(+1, a2, cs);
-        if (e == cudaSuccess) e = launch_fft_ax1<T>(+1, a2, cs);
-        if (e == cudaSuccess) e = launch_ax3<T>(opk, a3, cs);
-        if (e == cudaSuccess) e = launch_fft_ax1<T>(-1, a2, cs);
-        if (e == cudaSuccess) e = launch_fft_ax2<T>(-1, a2, cs);
-        if (e == cudaSuccess) e = launch_div<T>(AX5_CG, a5, cs);
+        if (fused_cg<T>(ctx)) {
+            if constexpr (sizeof(T) == 4) {
+                e = launch_grad_ax2(a1, cs);
+                if (e == cudaSuccess) e = launch_fft_ax1<T>(+1, a2, cs);
+                if (e == cudaSuccess) e = launch_ax3<T>(opk, a3, cs);
+                if (e == cudaSuccess) e = launch_fft_ax1<T>(-1, a2, cs);
+                if (e == cudaSuccess) e = launch_ax2_div(a5, cs);
+            }
+        } else {
+            e = launch_grad<T>(AX1_CG, a1, cs);
+            if (e == cudaSuccess) e = launch_fft_ax2<T>(+1, a2, cs);
+            if (e == cudaSuccess) e = launch_fft_ax1<T>(+1, a2, cs);
+            if (e == cudaSuccess) e = launch_ax3<T>(opk, a3, cs);
+            if (e == cudaSuccess) e = launch_fft_ax1<T>(-1, a2, cs);
+            if (e == cudaSuccess) e = launch_fft_ax2<T>(-1, a2, cs);
+            if (e == cudaSuccess) e = launch_div<T>(AX5_CG, a5, cs);
+        }
         if (e == cudaSuccess) e = launch_k(k_cg_continue, dim3(1), dim3(32), 0, cs, h, (const CgState*)ctx->cg, ctx->B);
         g_pdl_launch = false;
         cudaGraph_t captured = nullptr;
@@ -986,7 +1006,7 @@ dbfft_status inner_cg(dbfft_ctx* ctx, double tol, long long& it_sum, int& it_max
         if (*errh & 2u) return fail(ctx, DBFFT_E_TIMEOUT, "a device wait gave up (pass 3 copy pipeline)");
         int mx = 1;
         for (int b = 0; b < ctx->B; ++b) mx = std::max(mx, ctx->cg_h[b].iter);
-        ctx->launches += 8LL * mx;
+        ctx->launches += (fused_cg<T>(ctx) ? 6LL : 8LL) * mx;
         it_max = 0;
         for (int b = 0; b < ctx->B; ++b) {
             it_sum += ctx->cg_h[b].iter;
@@ -1003,12 +1023,25 @@ dbfft_status inner_cg(dbfft_ctx* ctx, double tol, long long& it_sum, int& it_max
     const char* n_a1 = dbl ? "fft_ax1_f64" : "fft_ax1_f32";
     const char* n_p3 = dbl ? "pass3_tangent_f64" : "pass3_tangent_f32";
     const char* n_p5 = dbl ? "pass5_div_cg_f64" : "pass5_div_cg_f32";
+    const bool fused = fused_cg<T>(ctx);
+    const char* n_p1f = "pass1_grad_ax2_cg_f32";  // fused: pass 1 + inverse axis-2 transform
+    const char* n_p5f = "pass5_ax2_div_cg_f32";   // fused: forward axis-2 transform + pass 5
     std::vector<int> it_before(ctx->B, 0);
     while (true) {
         // launches are timed here; their algorithmic bytes are credited after
         // the chunk, from the iterations each right-hand side really made (a
         // right-hand side that stops inside a chunk skips the later launches)
         for (int k = 0; k < chunk; ++k) {
+            if (fused) {
+                if constexpr (sizeof(T) == 4) {
+                    TRY(run(ctx, n_p1f, 0.0, [&] { return launch_grad_ax2(a1, ctx->stream); }));
+                    TRY(run(ctx, n_a1, 0.0, [&] { return launch_fft_ax1<T>(+1, a2, ctx->stream); }));
+                    TRY(run(ctx, n_p3, 0.0, [&] { return launch_ax3<T>(opk, a3, ctx->stream); }));
+                    TRY(run(ctx, n_a1, 0.0, [&] { return launch_fft_ax1<T>(-1, a2, ctx->stream); }));
+                    TRY(run(ctx, n_p5f, 0.0, [&] { return launch_ax2_div(a5, ctx->stream); }));
+                }
+                continue;
+            }
             TRY(run(ctx, n_p1, 0.0, [&] { return launch_grad<T>(AX1_CG, a1, ctx->stream); }));
             TRY(run(ctx, n_a2, 0.0, [&] { return launch_fft_ax2<T>(+1, a2, ctx->stream); }));
             TRY(run(ctx, n_a1, 0.0, [&] { return launch_fft_ax1<T>(+1, a2, ctx->stream); }));
@@ -1037,11 +1070,11 @@ dbfft_status inner_cg(dbfft_ctx* ctx, double tol, long long& it_sum, int& it_max
                 mat += (ctx->model == DBFFT_ISO_ELASTIC ? (double)mx : 0.0) * mat_bytes(ctx, dbl, false) / ctx->Bm;
             }
             if (ctx->model != DBFFT_ISO_ELASTIC) mat = sum_it * mat_bytes(ctx, dbl, false) / ctx->B;
-            ctx->prof_bytes[prof_slot(ctx, n_p1)] += sum_it * (15 + nc) * cp1;
-            ctx->prof_bytes[prof_slot(ctx, n_a2)] += sum_it * 2 * (2 * nc * cp1);
+            ctx->prof_bytes[prof_slot(ctx, fused ? n_p1f : n_p1)] += sum_it * (15 + nc) * cp1;
+            if (!fused) ctx->prof_bytes[prof_slot(ctx, n_a2)] += sum_it * 2 * (2 * nc * cp1);
             ctx->prof_bytes[prof_slot(ctx, n_a1)] += sum_it * 2 * (2 * nc * cp1);
             ctx->prof_bytes[prof_slot(ctx, n_p3)] += sum_it * 2 * nc * cp1 + mat;
-            ctx->prof_bytes[prof_slot(ctx, n_p5)] += sum_it * (6 + nc) * cp1;
+            ctx->prof_bytes[prof_slot(ctx, fused ? n_p5f : n_p5)] += sum_it * (6 + nc) * cp1;
         }
         bool all = true;
         for (int b = 0; b < ctx->B; ++b) {
@@ -1260,6 +1293,13 @@ float time_launch(dbfft_ctx* ctx, F&& f) {
     return ok ? best : 1e30f;
 }
 
+// The line-bulk pass 3 serves the FP32 applications of the linear, small-strain
+// crystal-plasticity and Neo-Hookean models on lines of 128 or 256 values.
+bool lb_supported(const dbfft_ctx* ctx) {
+    const int opk = opk_apply(ctx);
+    return (ctx->n3 == 128 || ctx->n3 == 256) && (opk == OP_ISO || opk == OP_CP_APPLY || opk == OP_NH_APPLY);
+}
+
 template <typename T>
 void tune_pass3(dbfft_ctx* ctx, int pi_, cplx<T>* W) {
     char buf[256];
@@ -1328,12 +1368,43 @@ void tune_pass3(dbfft_ctx* ctx, int pi_, cplx<T>* W) {
                 }
             }
         }
+        // the line-bulk pass (FP32 applications on lines of 128 or 256 values)
+        float blb = 1e30f;
+        int blbL = 0;
+        if (sizeof(T) == 4 && lb_supported(ctx)) {
+            for (int L : {2, 4, 6, 8, 12, 16}) {
+                const long long sm = ax3_lb_smem(ctx->n3, ctx->nc, ctx->RB, ctx->scale != nullptr, L, nlines);
+                if (sm < 0 || sm > 110 * 1024) continue;
+                Ax3Args<T> a3 = ax3_base<T>(ctx, W);
+                a3.pipe = 3;
+                a3.L = L;
+                if constexpr (sizeof(T) == 4) a3.macroW = ctx->macroWf;
+                else a3.macroW = ctx->macroW;
+                a3.tan_in = reinterpret_cast<const T*>(ctx->tan);
+                const float ms = time_launch(ctx, [&] { return launch_ax3<T>(opk_apply(ctx), a3, ctx->stream); });
+                if (ms < blb * 0.98f) {
+                    blb = ms;
+                    blbL = L;
+                }
+            }
+            if (blbL > 0 && blb < bp) {
+                bp = blb;
+                bpS = 3;
+                bpR = 0;
+                bpL = blbL;
+            }
+        }
         ctx->pipe_on[pi_] = (bpL > 0 && bp < best) ? bpS : 0;
         ctx->pipe_R[pi_] = bpR;
         ctx->pipe_L[pi_] = bpL;
         std::snprintf(buf, sizeof(buf), "pass3 bulk-copy %s radix %d lines %d (%.4f ms)%s; ",
-                      bpS == 2 ? "one-stage" : "two-stage", bpR, bpL, bp, ctx->pipe_on[pi_] ? " used" : "");
+                      bpS == 3 ? "line-bulk" : bpS == 2 ? "one-stage" : "two-stage", bpR, bpL, bp,
+                      ctx->pipe_on[pi_] ? " used" : "");
         ctx->tune_note += buf;
+        if (blbL > 0) {
+            std::snprintf(buf, sizeof(buf), "pass3 line-bulk lines %d (%.4f ms); ", blbL, blb);
+            ctx->tune_note += buf;
+        }
     }
 }
 
@@ -1399,7 +1470,7 @@ const char* dbfft_status_string(dbfft_status s) {
     return "unknown";
 }
 
-const char* dbfft_last_error(const dbfft_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+const char* dbfft_last_error(const dbfft_ctx* ctx) { return ctx ? ctx->err.c_str() : noalloc_last_error(); }
 
 long long dbfft_launch_count(const dbfft_ctx* ctx) { return ctx ? ctx->launches : 0; }
 
@@ -1488,13 +1559,27 @@ const char* dbfft_tuning(const dbfft_ctx* ctx) { return ctx ? ctx->tune_note.c_s
 dbfft_status dbfft_set_pass3_shape(dbfft_ctx* ctx, int fp64, int pipelined, int radix, int lines) {
     if (!ctx || (fp64 != 0 && fp64 != 1) || lines < 1) return DBFFT_E_ARG;
     const bool dbl = fp64 == 1;
+    const long long nlines = (long long)ctx->n1 * ctx->n2;
+    const int pi_ = dbl ? 1 : 0;
+    if (pipelined == 3) {  // line-bulk pass: its transform shape is fixed, radix is ignored
+        const long long sm = ax3_lb_smem(ctx->n3, ctx->nc, ctx->RB, ctx->scale != nullptr, lines, nlines);
+        if (dbl || !lb_supported(ctx) || sm < 0 || sm > 200 * 1024)
+            return fail(ctx, DBFFT_E_ARG,
+                        "line-bulk pass 3: FP32, n3 = 128 or 256, linear / crystal-plasticity / Neo-Hookean model, "
+                        "lines even and dividing n1*n2");
+        ctx->pipe_on[pi_] = 3;
+        ctx->pipe_R[pi_] = 0;
+        ctx->pipe_L[pi_] = lines;
+        for (int k = 0; k < 2; ++k)
+            if (ctx->cg_exec[k]) { cudaGraphExecDestroy(ctx->cg_exec[k]); ctx->cg_exec[k] = nullptr; }
+        return DBFFT_OK;
+    }
+    if (pipelined < 0 || pipelined > 3) return fail(ctx, DBFFT_E_ARG, "pipelined: 0, 1, 2 or 3");
     const bool r32 = radix == 32 && !pipelined && ctx->n3 <= (dbl ? 64 : 256);
     if (dbl ? (radix != 4 && !r32) : (radix != 8 && radix != 16 && !r32))
         return fail(ctx, DBFFT_E_ARG,
                     "radix: 8 or 16 (FP32), 4 (FP64), or 32 with the plain kernel (n3 <= 256 FP32, <= 64 FP64)");
-    const long long nlines = (long long)ctx->n1 * ctx->n2;
     if (lines > nlines) return fail(ctx, DBFFT_E_ARG, "more lines per CTA than grid lines");
-    const int pi_ = dbl ? 1 : 0;
     if (pipelined) {
         const long long sm =
             ax3_pipe_smem(ctx->n3, ctx->nc, ctx->RB, dbl, ctx->scale != nullptr, radix, lines, nlines, pipelined);
@@ -1580,6 +1665,13 @@ static dbfft_status create_impl(dbfft_ctx* ctx, const dbfft_grid* grid, const db
     // -1.8 % at 256^3 x 1
     ctx->use_pdl = (long long)grid->n[0] * grid->n[1] * grid->n[2] * grid->batch <= (4LL << 20);
     if (const char* g = std::getenv("DBFFT_PDL")) ctx->use_pdl = g[0] != '0';
+    // DBFFT_FUSE_AX2=0 keeps passes 1 and 5 as element-wise kernels around separate
+    // axis-2 transforms in the FP32 CG (for comparison; the results agree to rounding)
+    if (const char* g = std::getenv("DBFFT_FUSE_AX2")) ctx->fuse_ax2 = g[0] != '0';
+    // DBFFT_WAIT_POLLS=n bounds the first bulk-copy wait of the line-bulk pass 3
+    // to n polls (a test setting: a limit that runs out makes the solve return
+    // E_TIMEOUT while the copies still land before the CTA exits)
+    if (const char* g = std::getenv("DBFFT_WAIT_POLLS")) ctx->wait_limit = std::atoll(g);
     ctx->n1 = grid->n[0];
     ctx->n2 = grid->n[1];
     ctx->n3 = grid->n[2];
@@ -1885,7 +1977,8 @@ static dbfft_status create_impl(dbfft_ctx* ctx, const dbfft_grid* grid, const db
         const long long nb3 = nlines;  // pass 3 with one line per CTA (any tuned shape fits)
         const long long nb3d = nlines;
         const long long nbi = (ctx->H + 255) / 256;
-        long long nb = std::max(std::max(nb1, nb1d), std::max(std::max(nb3, nb3d), nbi));
+        const long long nbf = fused_ax2_blocks(ctx->n1, ctx->n3 / 2 + 1);  // fused pass 5
+        long long nb = std::max(std::max(std::max(nb1, nb1d), nbf), std::max(std::max(nb3, nb3d), nbi));
         ctx->nblk_max = (int)nb;
         ctx->partials_n = std::max((size_t)ctx->B * (size_t)nb * 2, (size_t)ctx->B * kMeanTangentBlocks * 81);
         TRY(dalloc_t(ctx, ctx->partials_n, &ctx->partials));

@@ -21,4 +21,6 @@ template <typename T>
 cudaError_t launch_herm_planes(const Dims& d, cplx<T>* v, cudaStream_t s);
 // n row-major 3x3 identity matrices at m[9 n]
 cudaError_t launch_fill_identity(double* m, long long n, cudaStream_t s);
+// the calling thread's last failure message of dbfft_apply_iso_noalloc ("" if none)
+const char* noalloc_last_error();
 }  // namespace dbfft

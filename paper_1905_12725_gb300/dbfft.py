@@ -125,7 +125,7 @@ def load_library(build_if_missing: bool = True):
     lib.dbfft_profile_read.restype = ip
     lib.dbfft_launch_count.argtypes = [vp]
     lib.dbfft_launch_count.restype = C.c_longlong
-    lib.dbfft_apply_iso_noalloc.argtypes = [C.POINTER(C.c_int), dp, ip, vp, vp, vp, vp, vp, vp]
+    lib.dbfft_apply_iso_noalloc.argtypes = [C.POINTER(C.c_int), dp, ip, vp, ip, vp, vp, vp, vp, vp]
     lib.dbfft_apply_iso_noalloc.restype = ip
     lib.dbfft_autotune.argtypes = [vp, C.c_char_p]
     lib.dbfft_autotune.restype = ip
@@ -416,23 +416,56 @@ class Solver:
 def apply_iso_noalloc(shape, phase_id, lam, mu, u_hat, out, L=None, stream=None):
     """out = K u_hat through dbfft_apply_iso_noalloc (no device allocation in the call).
 
-    phase_id: torch uint16-compatible device tensor [B, n1, n2, n3] (int16 view is fine);
-    lam, mu: float64 device tensors [n_phases]; u_hat, out: complex128 device tensors
-    [B, 3, n1, n2, n3//2 + 1]. Returns the status code (0 on success).
+    phase_id: contiguous 2-byte CUDA tensor [B, n1, n2, n3] (uint16 values; an
+    int16 view is fine); lam, mu: contiguous float64 CUDA tensors [n_phases];
+    u_hat, out: contiguous complex128 CUDA tensors [B, 3, n1, n2, n3//2 + 1].
+    Every tensor is checked against `shape` before the call (ValueError
+    otherwise), because the C entry point only sees raw device addresses.
+    Returns the status code (0 on success; DBFFT_E_ARG for a phase id at or
+    beyond n_phases, found by the library on the device).
     """
     import torch
 
+    shape = tuple(int(v) for v in shape)
+    if len(shape) != 3:
+        raise ValueError("shape must have three entries")
+    B = int(u_hat.shape[0]) if u_hat.dim() > 0 else 0
+    half = (B, 3, shape[0], shape[1], shape[2] // 2 + 1)
+
+    def need(cond, what):
+        if not cond:
+            raise ValueError(f"apply_iso_noalloc: {what}")
+
+    for name, t in (("u_hat", u_hat), ("out", out)):
+        need(t.is_cuda and t.dtype == torch.complex128 and t.is_contiguous(),
+             f"{name} must be a contiguous complex128 CUDA tensor")
+        need(tuple(t.shape) == half, f"{name} must have shape {half}")
+    need(phase_id.is_cuda and phase_id.element_size() == 2 and phase_id.is_contiguous() and
+         not phase_id.is_floating_point(), "phase_id must be a contiguous 2-byte integer CUDA tensor")
+    need(phase_id.numel() == B * shape[0] * shape[1] * shape[2], "phase_id must hold B * n1 * n2 * n3 ids")
+    for name, t in (("lam", lam), ("mu", mu)):
+        need(t.is_cuda and t.dtype == torch.float64 and t.is_contiguous(),
+             f"{name} must be a contiguous float64 CUDA tensor")
+    need(lam.numel() == mu.numel() and lam.numel() >= 1, "lam and mu must have the same, non-zero length")
+    need(len({t.device for t in (u_hat, out, phase_id, lam, mu)}) == 1, "all tensors must be on one device")
+
     lib = load_library()
-    n = (C.c_int * 3)(*[int(v) for v in shape])
+    n = (C.c_int * 3)(*shape)
     Lh = None
     if L is not None:
         Larr = np.ascontiguousarray(L, dtype=np.float64)
+        need(Larr.shape == (3,), "L must have three entries")
         Lh = _dptr(Larr)
     st = stream if stream is not None else torch.cuda.current_stream()
-    return lib.dbfft_apply_iso_noalloc(n, Lh, int(u_hat.shape[0]), C.c_void_p(phase_id.data_ptr()),
+    return lib.dbfft_apply_iso_noalloc(n, Lh, B, C.c_void_p(phase_id.data_ptr()), int(lam.numel()),
                                        C.c_void_p(lam.data_ptr()), C.c_void_p(mu.data_ptr()),
                                        C.c_void_p(u_hat.data_ptr()), C.c_void_p(out.data_ptr()),
                                        C.c_void_p(st.cuda_stream))
+
+
+def noalloc_last_error() -> str:
+    """Message of the calling thread's last failed dbfft_apply_iso_noalloc call."""
+    return load_library().dbfft_last_error(None).decode()
 
 
 # ---------------------------------------------------------------- autograd
