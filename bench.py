@@ -279,15 +279,28 @@ def operator_256(torch, dbfft, peak, iters=40):
         it_bytes += e["bytes"]
     iters = rep["cg_iters"]
     bytes_it = it_bytes / max(iters, 1)
+    # the method's algorithmic bytes of one FP32 CG iteration: the fused five-pass
+    # operator (54 component passes) plus the CG vector work (21), one component
+    # pass being one complex FP32 component over the half spectrum, plus 1 byte
+    # of phase id per voxel
+    H = n * n * (n // 2 + 1)
+    method_bytes_it = 75 * H * 8 + n ** 3
     return {"grid": "256^3, 1 RHS, FP32 inner CG, iso two-phase (vf 0.3, contrast 100)", "tuning": tuning,
             "graph_ms_per_cg_iter": graph_ms_it,
             "graph_voxel_cg_iters_per_s": n ** 3 / (graph_ms_it * 1e-3),
+            "method_bytes_per_cg_iter": method_bytes_it,
+            "graph_method_GBps": method_bytes_it / (graph_ms_it * 1e-3) / 1e9,
+            "graph_method_frac": method_bytes_it / (graph_ms_it * 1e-3) / 1e9 / peak,
+            "impl_bytes_per_cg_iter": bytes_it,
             "graph_chain_GBps": bytes_it / (graph_ms_it * 1e-3) / 1e9,
             "graph_chain_frac": bytes_it / (graph_ms_it * 1e-3) / 1e9 / peak,
             "cg_iters": iters, "ms_per_cg_iter": it_ms / max(iters, 1),
             "voxel_cg_iters_per_s": n ** 3 * iters / (it_ms * 1e-3) if it_ms else None,
             "chain_GBps": it_bytes / (it_ms * 1e-3) / 1e9 if it_ms else None,
             "chain_frac": (it_bytes / (it_ms * 1e-3) / 1e9) / peak if it_ms else None,
+            "method_frac": (method_bytes_it * iters / (it_ms * 1e-3) / 1e9) / peak if it_ms else None,
+            "fracs_note": "*_method_frac: the method's 75 component passes + 1 B/voxel per CG iteration; "
+                          "*_chain_frac: the bytes this implementation's kernels move",
             "passes": rows, "wall_s": wall}
 
 

@@ -80,6 +80,10 @@ static cudaError_t pipe_sz(const Ax3Args<T>& a, cudaStream_t s) {
 
 template <typename T>
 static cudaError_t pipe_dispatch(int opk, const Ax3Args<T>& a, cudaStream_t s) {
+    if (a.pipe == 3) {  // the line-bulk pass (FP32 only)
+        if constexpr (sizeof(T) == 4) return launch_ax3_lb(opk, a, s);
+        else return cudaErrorInvalidConfiguration;
+    }
     switch (opk) {
         case OP_ISO: return pipe_sz<T, 6, OP_ISO>(a, s);
         case OP_NH_APPLY: return pipe_sz<T, 9, OP_NH_APPLY>(a, s);

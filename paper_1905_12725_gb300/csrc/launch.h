@@ -75,6 +75,18 @@ template <typename T> cudaError_t launch_ax3_odd_fcp(int opk, const Ax3Args<T>& 
 int ax3_odd_lines(int n3, int nc, bool dbl);
 // pass 3 of the post-processing transforms (OP_DISP, FP64 only)
 template <typename T> cudaError_t launch_ax3_post(int opk, const Ax3Args<T>& a, cudaStream_t s);
+// the first and the last pass of the FP32 CG iteration with the element-wise work fused into
+// the axis-2 transforms (n2 = 32 .. 256): k_grad + inverse axis-2 C2C, forward axis-2 C2C + k_div
+cudaError_t launch_grad_ax2(const Ax1InvArgs<float>& a, cudaStream_t s);
+cudaError_t launch_ax2_div(const Ax1FwdArgs<float>& a, cudaStream_t s);
+long long fused_ax2_blocks(int n1, int h);  // CTAs per right-hand side of both
+bool fused_ax2_supported(int n2);
+int fused_tw();  // columns per CTA of the fused passes
+// pass 3 of the FP32 CG applications on long lines (n3 = 128, 256; OP_ISO, OP_CP_APPLY, OP_NH_APPLY):
+// one tile of a.L grid lines per CTA moved by bulk copies, two-stage transforms in registers (pipe = 3)
+cudaError_t launch_ax3_lb(int opk, const Ax3Args<float>& a, cudaStream_t s);
+// shared memory of one such CTA, or -1 when (n3, nc, L) is not a valid tile
+long long ax3_lb_smem(int n3, int nc, int rb, bool scale, int L, long long nlines);
 // shared memory of one pipelined CTA (pipe 1: two stages, 2: one stage), or -1 when (n3, L) is not a valid tile
 long long ax3_pipe_smem(int n3, int nc, int rb, bool dbl, bool scale, int radix, int L, long long nlines, int pipe);
 

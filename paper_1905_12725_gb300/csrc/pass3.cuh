@@ -72,6 +72,7 @@ struct Ax3Args {
     const double* fp_old;  // OP_FCP_UPDATE: committed Fp [B][V][9]
     double* fp_new;        // OP_FCP_UPDATE: trial Fp [B][V][9]
     double hx[3];          // OP_DISP: voxel edge lengths L_a / n_a
+    long long wait_limit;  // polls of a bulk-copy wait before it gives up (0: the default, 2^26)
 };
 
 template <int OPK> struct OpInfo {
