@@ -15,7 +15,8 @@
  *
  * Conventions used by every entry point
  * -------------------------------------
- * Grid: n[0] x n[1] x n[2] voxels, each a power of two in [8, 256]; voxel
+ * Grid: n[0] x n[1] x n[2] voxels, each a power of two in [8, 256] or an
+ *   odd length in [9, 245] whose prime factors are 3, 5 and 7; voxel
  *   (i1, i2, i3) is stored at i3 + n3 * (i2 + n2 * i1) (i3 contiguous).
  * Fourier fields ("half spectrum"): layout [B][3][n1][n2][n3/2 + 1],
  *   interleaved complex (re, im), complex128 (FP64) or complex64 (FP32),
@@ -120,13 +121,16 @@ typedef struct {
     double quat[4];           /* CP: unit quaternion (w, x, y, z), crystal -> sample       */
 } dbfft_phase;
 
-/* Microstructure. All arrays are host memory, copied at creation. */
+/* Microstructure. The maps are copied at creation; the caller keeps ownership. */
 typedef struct {
     const uint16_t* phase_id; /* [n_materials][n1][n2][n3] phase index per voxel          */
     const double* E_scale;    /* optional [n_materials][n1][n2][n3]: factor on the
                                  stiffness of ISO_ELASTIC voxels (NULL means 1)            */
     int n_phases;
-    const dbfft_phase* phases;/* [n_phases]; one context uses one model kind               */
+    const dbfft_phase* phases;/* [n_phases] host array; one context uses one model kind    */
+    int device_arrays;        /* 0: phase_id and E_scale are host memory; 1: device memory
+                                 of the context's GPU (copied device to device on the
+                                 context's stream; ids and scales are checked there)       */
 } dbfft_materials;
 
 /* Macroscopic load program (Sec. 2.3, Sec. 2.4). */
@@ -227,9 +231,12 @@ dbfft_status dbfft_homogenized_tangent(dbfft_ctx* ctx, double* out, dbfft_report
 /*
  * Sensitivity of J_b = sum_ij dJ_dsigma[b][ij] <sigma>_ij to the per-voxel
  * Young's modulus E(x) of ISO_ELASTIC phases under full strain control
- * (C(x) = E(x) C1(nu(x))). Solves the forward problem of increment 0, then
- * the adjoint problem with the same self-adjoint operator (Sec. 2.2: the
- * system is Hermitian) and assembles
+ * (C(x) = E(x) C1(nu(x))). Solves the forward problem of increment 0 (or
+ * reuses it: when the last call that changed the state was a converged
+ * dbfft_solve_increment(ctx, 0) or dbfft_adjoint, no forward solve runs and
+ * the report counts the adjoint solve alone), then the adjoint problem with
+ * the same self-adjoint operator (Sec. 2.2: the system is Hermitian) and
+ * assembles
  *   dJ/dE(x) = (1/N) (g + B lam)(x) : C1(x) : eps(x),  g = sym(dJ_dsigma),
  * where lam solves K lam = -B^H C g. dJ_dsigma: host [B][9];
  * dJ_dE: device [B][n1][n2][n3] double. Not available with stress control.

@@ -748,3 +748,21 @@ def test_adjoint_euler_identity_and_finite_differences():
     gJ2 = np.array([[0.3, 0.1, 0.0], [0.1, -0.7, 0.2], [0.0, 0.2, 0.5]])
     dJ2, J2, _ = o.adjoint_dJ_dE(prob, E, nu, eps, gJ2, tol=1e-14)
     assert abs(np.sum(E * dJ2) - J2) < 1e-10 * abs(J2)
+
+
+def test_equilibrium_residual_of_a_single_mode_stress_closed_form():
+    """Sec. 3, Eq. chedckeq: eps_eq = ||div sigma||_L2 / ||<sigma>||. For
+    sigma(x) = S0 + A cos(2 pi k.x) (L = 1) the divergence is
+    -2 pi sin(2 pi k.x) A k, so ||div sigma||_L2 = 2 pi |A k| / sqrt(2)."""
+    shape = (8, 12, 10)
+    prob = o.Problem(shape)
+    k = np.array([1, -2, 3])
+    x = np.stack(np.meshgrid(*[(np.arange(n) + 0.5) / n for n in shape], indexing="ij"))
+    ph = 2 * np.pi * np.tensordot(k, x, axes=1)
+    A = np.array([[0.3, -0.1, 0.2], [-0.1, 0.5, 0.05], [0.2, 0.05, -0.4]])
+    S0 = np.array([[2.0, 0.1, 0.0], [0.1, -1.0, 0.3], [0.0, 0.3, 0.5]])
+    sig = S0[:, :, None, None, None] + A[:, :, None, None, None] * np.cos(ph)[None, None]
+    r = prob.adjoint(sig)
+    got = o.equilibrium_residual(prob, r, sig.mean(axis=(2, 3, 4)))
+    ref = 2 * np.pi * np.linalg.norm(A @ k) / np.sqrt(2) / np.linalg.norm(S0)
+    assert abs(got - ref) < 1e-12 * ref
