@@ -954,6 +954,28 @@ def adjoint_dJ_dE(prob: Problem, E_field, nu_field, eps_bar, g, tol=1e-12, max_i
     return dJ, J, fwd
 
 
+def effective_stiffness_sensitivity(shape, E_field, nu_field, G, tol=1e-12, max_iter=10000):
+    """dJ/dE(x) for J = sum_IJ G_IJ C_IJ, C the 6x6 Mandel effective stiffness
+    of a linear isotropic C(x) = E(x) C1(nu(x)) (Sec. 2.2, the six unit strains).
+
+    C_IJ = e_I : sigma_bar(e_J), so J = sum_J g_J : sigma_bar(e_J) with the
+    tensor g_J = sum_I G_IJ e_I, and dJ/dE is the sum over J of the adjoint
+    sensitivities of the six strain-controlled problems (adjoint_dJ_dE: a
+    forward and an adjoint solve each). Returns (dJ/dE field, J, C).
+    """
+    prob = Problem(shape, "small")
+    basis = mandel_basis()
+    G = np.asarray(G, dtype=np.float64)
+    dJ = np.zeros(prob.shape)
+    Ceff = np.zeros((6, 6))
+    for j in range(6):
+        gj = np.einsum("i,ikl->kl", G[:, j], basis)
+        dj, _, fwd = adjoint_dJ_dE(prob, E_field, nu_field, basis[j], gj, tol=tol, max_iter=max_iter)
+        dJ += dj
+        Ceff[:, j] = tensor_to_mandel(fwd["sig_bar"])
+    return dJ, float(np.sum(G * Ceff)), Ceff
+
+
 def homogenized_stress_linear(prob, E_field, nu_field, eps_bar, tol=1e-12):
     lam, mu = lame(E_field, nu_field)
     return solve_linear(prob, IsoTangent(lam, mu), eps_bar, tol=tol)["sig_bar"]

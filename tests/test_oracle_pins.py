@@ -766,3 +766,48 @@ def test_equilibrium_residual_of_a_single_mode_stress_closed_form():
     got = o.equilibrium_residual(prob, r, sig.mean(axis=(2, 3, 4)))
     ref = 2 * np.pi * np.linalg.norm(A @ k) / np.sqrt(2) / np.linalg.norm(S0)
     assert abs(got - ref) < 1e-12 * ref
+
+
+def test_effective_stiffness_sensitivity_laminate_closed_forms_and_euler_identity():
+    """dC_IJ/dE(x) of the 6x6 Mandel effective stiffness (six unit strains, Sec. 2.2).
+    Laminate with normal e1 (even layer widths): C_00 = Reuss mean of M = lam + 2 mu,
+    C_33 = 2 x Voigt mean of mu, C_55 = 2 x Reuss mean of mu, so per voxel
+    dC_00/dE = M_R^2 M1 / (N M^2), dC_33/dE = 2 mu1 / N, dC_55/dE = 2 mu_R^2 mu1 / (N mu^2),
+    with M1 = M / E and mu1 = mu / E. The sensitivity of any J = G : C satisfies the
+    Euler identity sum_x E dJ/dE = J (C is homogeneous of degree one in E)."""
+    shape = (16, 4, 4)
+    nu = 0.3
+    E = np.ones(shape)
+    E[6:] = 20.0  # layers of widths 6 and 10 along x1
+    nuf = np.full(shape, nu)
+    lam, mu = o.lame(E, nuf)
+    M = lam + 2 * mu
+    mu1, M1 = mu / E, M / E
+    N = E.size
+    muR, MR = 1.0 / np.mean(1.0 / mu), 1.0 / np.mean(1.0 / M)
+    for (i, j), ref in [((0, 0), MR ** 2 * M1 / (N * M ** 2)), ((3, 3), 2 * mu1 / N),
+                        ((5, 5), 2 * muR ** 2 * mu1 / (N * mu ** 2))]:
+        G = np.zeros((6, 6))
+        G[i, j] = 1.0
+        dJ, J, C = o.effective_stiffness_sensitivity(shape, E, nuf, G, tol=1e-14)
+        assert np.abs(dJ - ref).max() < 1e-10 * np.abs(ref).max(), (i, j)
+        assert abs(np.sum(E * dJ) - J) < 1e-11 * abs(J)
+    # a random microstructure and a general weight: Euler identity and a central difference
+    shape = (8, 8, 8)
+    g = np.random.default_rng(12)
+    E = np.where(g.random(shape) < 0.35, 12.0, 1.0)
+    nuf = np.full(shape, 0.25)
+    G = g.standard_normal((6, 6))
+    dJ, J, C = o.effective_stiffness_sensitivity(shape, E, nuf, G, tol=1e-14)
+    assert abs(np.sum(E * dJ) - J) < 1e-10 * abs(J)
+    idx = (3, 5, 1)
+    d = 1e-3 * E[idx]
+    Js = []
+    for sgn in (1, -1):
+        Ep = E.copy()
+        Ep[idx] += sgn * d
+        lam, mu = o.lame(Ep, nuf)
+        Cp, _ = o.homogenized_tangent(shape, o.IsoTangent(lam, mu), tol=1e-14)
+        Js.append(np.sum(G * Cp))
+    fd = (Js[0] - Js[1]) / (2 * d)
+    assert abs(fd - dJ[idx]) < 1e-5 * np.abs(dJ).max()
