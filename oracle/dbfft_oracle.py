@@ -694,7 +694,14 @@ class CrystalPlasticity:
         dgd = self.gdot0 * e / self.tau_c * x ** (e - 1.0)
         return gd, dgd
 
-    def update(self, grain, eps, eps_p_old, sig_guess, dt, rtol=1e-12, max_it=100):
+    def tangent_at(self, grain, sig, dt, scale=None):
+        """Consistent tangent (S/s + dt sum_a gdot'_a P_a P_a^T)^-1 at the stresses sig [V,6]."""
+        S = self.S[grain] if scale is None else self.S[grain] / np.asarray(scale)[:, None, None]
+        P = self.P[grain]
+        _, dgd = self.rates(np.einsum("vam,vm->va", P, sig))
+        return np.linalg.inv(S + dt * np.einsum("va,vam,van->vmn", dgd, P, P))
+
+    def update(self, grain, eps, eps_p_old, sig_guess, dt, rtol=1e-12, max_it=100, scale=None):
         """Backward Euler at every voxel (vectorised over voxels).
 
         Solves R(sigma) = S sigma + dt sum_a gdot_a(sigma) P_a - (eps - eps_p_old) = 0
@@ -703,9 +710,12 @@ class CrystalPlasticity:
         convex potential
         phi(sigma) = 1/2 sigma.S.sigma + dt sum_a gdot0 tau_c m/(1+m)|tau_a/tau_c|^(1+1/m)
                      - sigma.(eps - eps_p_old).
+        scale (optional, [V]): a factor s(x) on the elastic stiffness, C = s C_grain.
         Returns (sigma, tangent d sigma / d eps [.., 6, 6], eps_p_new, newton iterations).
         """
         S = self.S[grain]              # [V,6,6]
+        if scale is not None:
+            S = S / np.asarray(scale, dtype=np.float64)[:, None, None]
         P = self.P[grain]              # [V,12,6]
         target = eps - eps_p_old       # [V,6]
         sig = sig_guess.copy()
@@ -801,7 +811,7 @@ def newton_increments(prob: Problem, material, targets, newton_tol=1e-8, load_to
             x = (x[0] + d[0], x[1] + d[1])
         state = trial_state  # commit the converged constitutive state
         rec = dict(inc=inc, stress_bar=Pbar, field_bar=tot.reshape(3, 3, -1).mean(axis=-1),
-                   newton=newton, cg_total=cg_total, x=(x[0].copy(), x[1].copy()))
+                   newton=newton, cg_total=cg_total, x=(x[0].copy(), x[1].copy()), state=state)
         out.append(rec)
         if callback is not None:
             callback(rec)
@@ -822,9 +832,11 @@ def svk_material(mu_field, lam_field):
     return material
 
 
-def cp_material(cp: CrystalPlasticity, grain_field, dt):
-    """Material closure for the crystal-plasticity model; state = (eps_p, sigma)."""
+def cp_material(cp: CrystalPlasticity, grain_field, dt, scale=None):
+    """Material closure for the crystal-plasticity model; state = (eps_p, sigma).
+    scale (optional, grain_field's shape): factor s(x) on the elastic stiffness."""
     g = grain_field.reshape(-1)
+    sc = None if scale is None else np.asarray(scale, dtype=np.float64).reshape(-1)
 
     def material(eps, state):
         V = g.size
@@ -832,13 +844,62 @@ def cp_material(cp: CrystalPlasticity, grain_field, dt):
         if state is None:
             state = (np.zeros((V, 6)), np.zeros((V, 6)))
         eps_p, sig_prev = state
-        sig, tan, eps_p_new, _ = cp.update(g, em, eps_p, sig_prev, dt)
+        sig, tan, eps_p_new, _ = cp.update(g, em, eps_p, sig_prev, dt, scale=sc)
         sig_t = mandel_to_tensor(sig.T.reshape((6,) + grain_field.shape))
         K = np.einsum("mij,vmn,nkl->ijklv", mandel_basis(), tan, mandel_basis())
         K = K.reshape((3, 3, 3, 3) + grain_field.shape)
         new_state = (eps_p_new, sig)
         return sig_t, FullTangent(K), new_state
     return material
+
+
+def cp_adjoint_increments(prob: Problem, cp: CrystalPlasticity, grain_field, dt, targets, g,
+                          newton_tol=1e-12, load_tol=1e-12, eta=1e-10, tol=1e-13, max_iter=10000):
+    """dJ/ds(x) for J = g : <sigma> after the last increment of a small-strain
+    crystal-plasticity loading path (Sec. 2.4, Eq. lineariz; R14), s(x) a factor
+    on the elastic stiffness of voxel x, at s = 1 (the derivative per voxel of
+    the logarithm of its stiffness).
+
+    Forward: the Newton increments, keeping the converged stress of every
+    increment as its checkpoint (the consistent tangent T_n and the plastic
+    strain follow from it). Reverse, over the increments n = N .. 1, with the
+    state adjoint q (dJ / d eps_p of the increment's result, 0 after the last)
+    and a = g / N at the last increment (0 before):
+        h = a - S q,  w = q + T_n h,
+        K_n lam = B^H w          (the self-adjoint increment operator, Sec. 2.2),
+        d = h - B lam,
+        dJ/ds += d . T_n S sigma_n + q . S sigma_n,
+        q = -T_n d,
+    all per voxel in Mandel components (S the grain compliance). Returns
+    (dJ/ds field, J, forward records).
+    """
+    V = grain_field.size
+    gidx = grain_field.reshape(-1)
+    recs, _ = newton_increments(prob, cp_material(cp, grain_field, dt), targets, newton_tol=newton_tol,
+                                load_tol=load_tol, eta=eta)
+    gm = tensor_to_mandel(np.asarray(g, dtype=np.float64))
+    J = float(np.sum(np.asarray(g) * recs[-1]["stress_bar"]))
+    S = cp.S[gidx]
+    q = np.zeros((V, 6))
+    dJ = np.zeros(V)
+    basis = mandel_basis()
+    for n in range(len(recs) - 1, -1, -1):
+        sig_n = recs[n]["state"][1]                      # checkpoint: converged stress [V, 6]
+        T = cp.tangent_at(gidx, sig_n, dt)               # [V, 6, 6]
+        a = gm[None, :] / prob.N if n == len(recs) - 1 else np.zeros((V, 6))
+        h = a - np.einsum("vmn,vn->vm", S, q)
+        w = q + np.einsum("vmn,vn->vm", T, h)
+        wt = np.einsum("mij,vm->ijv", basis, w).reshape((3, 3) + prob.shape)
+        rhs = prob.adjoint(wt)
+        Kt = FullTangent(np.einsum("mij,vmn,nkl->ijklv", basis, T, basis).reshape((3, 3, 3, 3) + prob.shape))
+        M = prob.make_preconditioner(Kt.mean())
+        lam, _, _ = pcg(prob, lambda v: prob.apply_K(Kt, v[0], v[1]), M, rhs, tol, max_iter)
+        Blam = tensor_to_mandel(prob.field_from(lam[0], lam[1])).reshape(6, V).T
+        d = h - Blam
+        Ssig = np.einsum("vmn,vn->vm", S, sig_n)
+        dJ += np.einsum("vm,vm->v", d, np.einsum("vmn,vn->vm", T, Ssig)) + np.einsum("vm,vm->v", q, Ssig)
+        q = -np.einsum("vmn,vn->vm", T, d)
+    return dJ.reshape(prob.shape), J, recs
 
 
 # --------------------------------------------------------------------------

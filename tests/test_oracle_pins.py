@@ -811,3 +811,56 @@ def test_effective_stiffness_sensitivity_laminate_closed_forms_and_euler_identit
         Js.append(np.sum(G * Cp))
     fd = (Js[0] - Js[1]) / (2 * d)
     assert abs(fd - dJ[idx]) < 1e-5 * np.abs(dJ).max()
+
+
+def _cp_adjoint_case(strain_per_inc, n_inc=4):
+    shape = (8, 4, 4)
+    rng = synth.Xoshiro256ss(4242)
+    grains, _ = synth.periodic_voronoi(8, 5, rng)
+    grains = grains[:, :4, :4].copy()
+    cp = o.CrystalPlasticity(synth.uniform_quaternions(5, rng))
+    mask = np.ones((3, 3), bool)
+    mask[0, 0] = False  # uniaxial: eps_11 prescribed, the other macro stresses zero
+    prob = o.Problem(shape, "small", mask.reshape(-1))
+    targets = []
+    for k in range(n_inc):
+        t = np.zeros((3, 3))
+        t[0, 0] = strain_per_inc * (k + 1)
+        targets.append(t)
+    return shape, grains, cp, prob, targets
+
+
+def test_cp_adjoint_over_increments_matches_finite_differences():
+    """Path-dependent adjoint (R14 crystal plasticity, Sec. 2.4 increments under mixed
+    control): dJ/ds(x) for J = <sigma_11> after the last of four plastic increments,
+    s(x) a factor on the stiffness of voxel x, against central differences of whole
+    Newton runs (each voxel's stiffness perturbed by 1e-4)."""
+    shape, grains, cp, prob, targets = _cp_adjoint_case(1e-3)
+    dt = 0.5
+    g = np.zeros((3, 3))
+    g[0, 0] = 1.0
+    dJ, J, recs = o.cp_adjoint_increments(prob, cp, grains, dt, targets, g)
+    assert J > 120.0  # beyond the elastic limit: the history matters
+    assert np.abs(recs[-1]["state"][0]).max() > 1e-4  # plastic strain
+
+    def J_of(scale):
+        r, _ = o.newton_increments(prob, o.cp_material(cp, grains, dt, scale=scale), targets, newton_tol=1e-12,
+                                   load_tol=1e-12, eta=1e-10)
+        return float(np.sum(g * r[-1]["stress_bar"]))
+
+    for idx in [(0, 0, 0), (3, 2, 1), (7, 3, 3)]:
+        d = 1e-4
+        sp, sm = np.ones(shape), np.ones(shape)
+        sp[idx] += d
+        sm[idx] -= d
+        fd = (J_of(sp) - J_of(sm)) / (2 * d)
+        assert abs(fd - dJ[idx]) < 1e-6 * np.abs(dJ).max(), idx
+
+
+def test_cp_adjoint_in_the_elastic_limit_satisfies_the_euler_identity():
+    """With strains far below the elastic limit the response is linear in the stiffness
+    factor: sum_x dJ/ds(x) = J."""
+    shape, grains, cp, prob, targets = _cp_adjoint_case(1e-6, n_inc=2)
+    g = np.array([[1.0, 0.2, 0.0], [0.2, -0.4, 0.1], [0.0, 0.1, 0.3]])
+    dJ, J, _ = o.cp_adjoint_increments(prob, cp, grains, 0.5, targets, g)
+    assert abs(dJ.sum() - J) < 1e-9 * abs(J)
