@@ -244,6 +244,25 @@ dbfft_status dbfft_homogenized_tangent(dbfft_ctx* ctx, double* out, dbfft_report
 dbfft_status dbfft_adjoint(dbfft_ctx* ctx, const double* dJ_dsigma, double* dJ_dE,
                            dbfft_report* rep);
 
+/*
+ * Sensitivity of J_g = sum_IJ G[g][I][J] C_g,IJ, C_g the 6x6 Mandel effective
+ * stiffness of material map g (dbfft_homogenized_tangent, Sec. 2.2: the six
+ * unit Mandel strains), to the per-voxel Young's modulus E(x) of
+ * ISO_ELASTIC phases (C(x) = E(x) C1(nu(x))). C_IJ = (1/N) sum_x
+ * eps^I : C : eps^J with eps^I the strain field of unit strain I, and the
+ * system is self-adjoint (Sec. 2.2), so the adjoint fields are the forward
+ * ones and no further solve is needed:
+ *   dJ/dE(x) = (1/N) sum_IJ G_IJ eps^I(x) : C1(x) : eps^J(x).
+ * Runs the six unit-strain solves unless the last call that changed the state
+ * was a converged dbfft_homogenized_tangent (or this function), then
+ * assembles in FP64. Requirements as dbfft_homogenized_tangent, even n3.
+ * G: host [n_materials][6][6]; dJ_dE: device [n_materials][n1][n2][n3]
+ * double; C_eff: host [n_materials][6][6] or NULL (the stiffness used).
+ * Errors: E_ARG, E_STATE, E_UNSUPPORTED_GRID, and those of the solve.
+ */
+dbfft_status dbfft_tangent_sensitivity(dbfft_ctx* ctx, const double* G, double* dJ_dE, double* C_eff,
+                                       dbfft_report* rep);
+
 /* Copy the current FP64 solution: u_hat device complex128 [B][3][n1][n2][n3/2+1]
  * (may be NULL), e host [B][9] (may be NULL). */
 dbfft_status dbfft_get_solution(dbfft_ctx* ctx, void* u_hat, double* e);

@@ -87,6 +87,11 @@ struct dbfft_ctx {
     int pre_refresh = DBFFT_PRECOND_PER_INCREMENT;
     bool pre_is_init = true;  // the device holds pre_init_h
     long long wait_limit = 0;  // polls of the bulk-copy waits of pass 3 (0: the kernels' default)
+    bool fwd_inc0 = false;     // x64 holds the converged solve of increment 0 (the adjoint reuses it)
+    bool tangent_ready = false;  // x64 holds the six unit-strain solves of dbfft_homogenized_tangent
+    std::vector<double> tangent_C;  // their C_eff [Bm][6][6]
+    double* sens_tmp = nullptr;  // [B][V] per right-hand side sensitivity terms
+    double* sens_G = nullptr;    // [Bm][6][6] weights on the device
 
     // ---- vectors
     cplx<double>* x64 = nullptr;
@@ -1476,6 +1481,8 @@ long long dbfft_launch_count(const dbfft_ctx* ctx) { return ctx ? ctx->launches 
 
 dbfft_status dbfft_autotune(dbfft_ctx* ctx, const char* cache_path) {
     if (!ctx) return DBFFT_E_ARG;
+    ctx->fwd_inc0 = false;  // timing runs the passes on the context's buffers
+    ctx->tangent_ready = false;
     if ((ctx->n1 & 1) || (ctx->n2 & 1) || (ctx->n3 & 1)) {  // the odd-length kernels have one shape each
         ctx->tune_note = "odd grid: fixed launch shapes";
         return DBFFT_OK;
@@ -1759,54 +1766,77 @@ static dbfft_status create_impl(dbfft_ctx* ctx, const dbfft_grid* grid, const db
     // materials
     const size_t nvox = (size_t)ctx->Bm * ctx->V;
     TRY(dalloc_t(ctx, nvox, &ctx->phase));
-    // one pass over the maps: range check and the voxel count of every phase per material group
-    // (four interleaved count arrays, so that runs of one phase id do not chain their increments)
+    const bool dev_maps = mat->device_arrays != 0;
     std::vector<long long> pcount((size_t)ctx->Bm * mat->n_phases, 0);
-    {
-        const size_t np4 = (size_t)mat->n_phases;
-        std::vector<uint32_t> c4(4 * np4);
-        for (int g = 0; g < ctx->Bm; ++g) {
-            const uint16_t* ids = mat->phase_id + (size_t)g * ctx->V;
-            std::fill(c4.begin(), c4.end(), 0u);
-            unsigned mx = 0;
-            long long v = 0;
-            for (; v + 4 <= ctx->V; v += 4) {
-                const unsigned a = ids[v], b = ids[v + 1], c = ids[v + 2], d = ids[v + 3];
-                mx = std::max(mx, std::max(std::max(a, b), std::max(c, d)));
-                if (mx >= (unsigned)mat->n_phases) return fail(ctx, DBFFT_E_ARG, "phase id out of range");
-                ++c4[a];
-                ++c4[np4 + b];
-                ++c4[2 * np4 + c];
-                ++c4[3 * np4 + d];
-            }
-            for (; v < ctx->V; ++v) {
-                const unsigned a = ids[v];
-                if (a >= (unsigned)mat->n_phases) return fail(ctx, DBFFT_E_ARG, "phase id out of range");
-                ++c4[a];
-            }
-            long long* cg = pcount.data() + (size_t)g * np4;
-            for (size_t p = 0; p < np4; ++p) cg[p] = (long long)c4[p] + c4[np4 + p] + c4[2 * np4 + p] + c4[3 * np4 + p];
-        }
-    }
-    // through a page-locked staging copy: the transfer then runs while the host
-    // goes on with the set-up (the buffer returns to the cache at destroy)
-    ctx->stage_n = nvox * sizeof(uint16_t);
-    ctx->stage_h = pinned_alloc(ctx->stage_n);
-    if (ctx->stage_h) {
-        std::memcpy(ctx->stage_h, mat->phase_id, ctx->stage_n);
-        CK(cudaMemcpyAsync(ctx->phase, ctx->stage_h, ctx->stage_n, cudaMemcpyHostToDevice, ctx->stream));
-    } else {
-        CK(cudaMemcpyAsync(ctx->phase, mat->phase_id, ctx->stage_n, cudaMemcpyHostToDevice, ctx->stream));
-    }
-    if (mat->E_scale) {
-        for (size_t i = 0; i < nvox; ++i)
-            if (!std::isfinite(mat->E_scale[i])) return fail(ctx, DBFFT_E_NONFINITE, "non-finite E_scale");
-        TRY(dalloc_t(ctx, nvox, &ctx->scale));
-        CK(cudaMemcpyAsync(ctx->scale, mat->E_scale, nvox * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
-        std::vector<float> sf(mat->E_scale, mat->E_scale + nvox);
-        TRY(dalloc_t(ctx, nvox, &ctx->scale_f));
-        CK(cudaMemcpyAsync(ctx->scale_f, sf.data(), nvox * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
+    if (dev_maps) {
+        // the maps live on the device: copy them there, count the phases and check
+        // the ids with a kernel (the stiffness scale is checked once lam and mu are
+        // uploaded, below)
+        CK(cudaMemcpyAsync(ctx->phase, mat->phase_id, nvox * sizeof(uint16_t), cudaMemcpyDeviceToDevice, ctx->stream));
+        unsigned long long* cnt_d = nullptr;
+        const size_t ncnt = (size_t)ctx->Bm * mat->n_phases + 1;  // counts, then the bad-id count
+        TRY(dalloc_t(ctx, ncnt, &cnt_d));
+        CK(cudaMemsetAsync(cnt_d, 0, ncnt * sizeof(unsigned long long), ctx->stream));
+        CK(launch_phase_counts(ctx->phase, ctx->Bm, ctx->V, mat->n_phases, cnt_d, cnt_d + ncnt - 1, ctx->stream));
+        std::vector<unsigned long long> cnt_h(ncnt);
+        CK(cudaMemcpyAsync(cnt_h.data(), cnt_d, ncnt * sizeof(unsigned long long), cudaMemcpyDeviceToHost, ctx->stream));
         CK(cudaStreamSynchronize(ctx->stream));
+        if (cnt_h[ncnt - 1]) return fail(ctx, DBFFT_E_ARG, "phase id out of range");
+        for (size_t k = 0; k + 1 < ncnt; ++k) pcount[k] = (long long)cnt_h[k];
+        if (mat->E_scale) {
+            TRY(dalloc_t(ctx, nvox, &ctx->scale));
+            TRY(dalloc_t(ctx, nvox, &ctx->scale_f));
+            CK(cudaMemcpyAsync(ctx->scale, mat->E_scale, nvox * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
+        }
+    } else {
+        // one pass over the maps: range check and the voxel count of every phase per material group
+        // (four interleaved count arrays, so that runs of one phase id do not chain their increments)
+        {
+            const size_t np4 = (size_t)mat->n_phases;
+            std::vector<uint32_t> c4(4 * np4);
+            for (int g = 0; g < ctx->Bm; ++g) {
+                const uint16_t* ids = mat->phase_id + (size_t)g * ctx->V;
+                std::fill(c4.begin(), c4.end(), 0u);
+                unsigned mx = 0;
+                long long v = 0;
+                for (; v + 4 <= ctx->V; v += 4) {
+                    const unsigned a = ids[v], b = ids[v + 1], c = ids[v + 2], d = ids[v + 3];
+                    mx = std::max(mx, std::max(std::max(a, b), std::max(c, d)));
+                    if (mx >= (unsigned)mat->n_phases) return fail(ctx, DBFFT_E_ARG, "phase id out of range");
+                    ++c4[a];
+                    ++c4[np4 + b];
+                    ++c4[2 * np4 + c];
+                    ++c4[3 * np4 + d];
+                }
+                for (; v < ctx->V; ++v) {
+                    const unsigned a = ids[v];
+                    if (a >= (unsigned)mat->n_phases) return fail(ctx, DBFFT_E_ARG, "phase id out of range");
+                    ++c4[a];
+                }
+                long long* cg = pcount.data() + (size_t)g * np4;
+                for (size_t p = 0; p < np4; ++p) cg[p] = (long long)c4[p] + c4[np4 + p] + c4[2 * np4 + p] + c4[3 * np4 + p];
+            }
+        }
+        // through a page-locked staging copy: the transfer then runs while the host
+        // goes on with the set-up (the buffer returns to the cache at destroy)
+        ctx->stage_n = nvox * sizeof(uint16_t);
+        ctx->stage_h = pinned_alloc(ctx->stage_n);
+        if (ctx->stage_h) {
+            std::memcpy(ctx->stage_h, mat->phase_id, ctx->stage_n);
+            CK(cudaMemcpyAsync(ctx->phase, ctx->stage_h, ctx->stage_n, cudaMemcpyHostToDevice, ctx->stream));
+        } else {
+            CK(cudaMemcpyAsync(ctx->phase, mat->phase_id, ctx->stage_n, cudaMemcpyHostToDevice, ctx->stream));
+        }
+        if (mat->E_scale) {
+            for (size_t i = 0; i < nvox; ++i)
+                if (!std::isfinite(mat->E_scale[i])) return fail(ctx, DBFFT_E_NONFINITE, "non-finite E_scale");
+            TRY(dalloc_t(ctx, nvox, &ctx->scale));
+            CK(cudaMemcpyAsync(ctx->scale, mat->E_scale, nvox * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+            std::vector<float> sf(mat->E_scale, mat->E_scale + nvox);
+            TRY(dalloc_t(ctx, nvox, &ctx->scale_f));
+            CK(cudaMemcpyAsync(ctx->scale_f, sf.data(), nvox * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
+            CK(cudaStreamSynchronize(ctx->stream));
+        }
     }
     const int np = mat->n_phases;
     ctx->lam_h.assign(np, 0.0);
@@ -1895,6 +1925,32 @@ static dbfft_status create_impl(dbfft_ctx* ctx, const dbfft_grid* grid, const db
         ctx->cp.max_it = 100;
     }
 
+    // device-resident stiffness scale: FP32 copy, finite check and the per-map
+    // sums of lam s and mu s for the mean stiffness, on the device
+    std::vector<double> scaled_sums;  // [Bm][2]
+    if (dev_maps && mat->E_scale) {
+        const int nblk = (int)std::min<long long>((ctx->V + 255) / 256, 1024);
+        double* part_d = nullptr;
+        unsigned long long* bad_d = nullptr;
+        TRY(dalloc_t(ctx, (size_t)ctx->Bm * nblk * 2, &part_d));
+        TRY(dalloc_t(ctx, 1, &bad_d));
+        CK(cudaMemsetAsync(bad_d, 0, sizeof(unsigned long long), ctx->stream));
+        CK(launch_scale_stats(ctx->phase, ctx->scale, ctx->scale_f, ctx->Bm, ctx->V, np, ctx->lam, ctx->mu, part_d, nblk,
+                              bad_d, ctx->stream));
+        std::vector<double> part_h((size_t)ctx->Bm * nblk * 2);
+        unsigned long long bad_h = 0;
+        CK(cudaMemcpyAsync(part_h.data(), part_d, part_h.size() * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+        CK(cudaMemcpyAsync(&bad_h, bad_d, sizeof(bad_h), cudaMemcpyDeviceToHost, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+        if (bad_h) return fail(ctx, DBFFT_E_NONFINITE, "non-finite E_scale");
+        scaled_sums.assign((size_t)ctx->Bm * 2, 0.0);
+        for (int g = 0; g < ctx->Bm; ++g)
+            for (int k = 0; k < nblk; ++k) {  // fixed order: the same sums on every run
+                scaled_sums[g * 2 + 0] += part_h[((size_t)g * nblk + k) * 2 + 0];
+                scaled_sums[g * 2 + 1] += part_h[((size_t)g * nblk + k) * 2 + 1];
+            }
+    }
+
     // preconditioner of the linear problem: mean stiffness (Sec. 2.5, R10)
     ctx->pre_h.assign(ctx->Bm, PrecondData{});
     for (int g = 0; g < ctx->Bm; ++g) {
@@ -1903,7 +1959,10 @@ static dbfft_status create_impl(dbfft_ctx* ctx, const dbfft_grid* grid, const db
         if (ctx->model == DBFFT_ISO_ELASTIC || ctx->model == DBFFT_NEO_HOOKE || ctx->model == DBFFT_SVK) {
             // ISO: mean stiffness; NH, SVK: initial tangent K(I) = isotropic C of the mean moduli
             double sl = 0.0, sm = 0.0;
-            if (ctx->model == DBFFT_ISO_ELASTIC && mat->E_scale) {
+            if (ctx->model == DBFFT_ISO_ELASTIC && mat->E_scale && dev_maps) {
+                sl = scaled_sums[g * 2 + 0];
+                sm = scaled_sums[g * 2 + 1];
+            } else if (ctx->model == DBFFT_ISO_ELASTIC && mat->E_scale) {
                 for (long long v = 0; v < ctx->V; ++v) {
                     const int p = mat->phase_id[(size_t)g * ctx->V + v];
                     const double s = mat->E_scale[(size_t)g * ctx->V + v];
@@ -2047,12 +2106,15 @@ dbfft_status dbfft_solve_increment(dbfft_ctx* ctx, int inc, dbfft_report* rep) {
         return fail(ctx, DBFFT_E_STATE, "path-dependent solves must run increments in order");
     const auto t0 = std::chrono::steady_clock::now();
     if (rep) std::memset(rep, 0, sizeof(*rep));
+    ctx->fwd_inc0 = false;
+    ctx->tangent_ready = false;
     TRY(set_load(ctx, inc, ctx->target.data()));
     dbfft_status s = solve_current(ctx, rep);
     if (s == DBFFT_OK || s == DBFFT_E_NOT_CONVERGED) {
         commit_state(ctx);
         ctx->cur_inc = inc;
     }
+    ctx->fwd_inc0 = s == DBFFT_OK && inc == 0;
     if (rep) rep->wall_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     return s;
 }
@@ -2226,6 +2288,7 @@ dbfft_status dbfft_apply(dbfft_ctx* ctx, int flags, const void* u_hat, const voi
 }
 
 dbfft_status dbfft_homogenized_tangent(dbfft_ctx* ctx, double* out, dbfft_report* rep) {
+    if (ctx) ctx->fwd_inc0 = false;  // the unit-strain solves replace the state
     if (!ctx || !out) return DBFFT_E_ARG;
     if (ctx->model != DBFFT_ISO_ELASTIC || ctx->nc != 6 || ctx->dims.ne != 0 || ctx->B != 6 * ctx->Bm)
         return fail(ctx, DBFFT_E_STATE, "homogenized tangent needs linear small strain, strain control, B = 6 n_materials");
@@ -2252,6 +2315,8 @@ dbfft_status dbfft_homogenized_tangent(dbfft_ctx* ctx, double* out, dbfft_report
         for (int j = 0; j < 6; ++j)
             for (int i = 0; i < 6; ++i)
                 out[(g * 6 + i) * 6 + j] = sg[(g * 6 + j) * 9 + i] * (i >= 3 ? std::sqrt(2.0) : 1.0);
+    ctx->tangent_ready = s == DBFFT_OK;
+    ctx->tangent_C.assign(out, out + (size_t)ctx->Bm * 36);
     TRY(set_load(ctx, 0, ctx->target.data()));
     if (rep) rep->wall_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     return s;
@@ -2265,10 +2330,16 @@ dbfft_status dbfft_adjoint(dbfft_ctx* ctx, const double* dJ_dsigma, double* dJ_d
     const auto t0 = std::chrono::steady_clock::now();
     if (rep) std::memset(rep, 0, sizeof(*rep));
     dbfft_report r1{}, r2{};
-    // forward solve of increment 0
-    TRY(set_load(ctx, 0, ctx->target.data()));
-    dbfft_status s = solve_current(ctx, &r1);
-    if (s != DBFFT_OK && s != DBFFT_E_NOT_CONVERGED) return s;
+    // forward solve of increment 0, unless the context holds it already (a
+    // dbfft_solve_increment(ctx, 0) that converged, or an earlier adjoint)
+    ctx->tangent_ready = false;  // the solves below replace the state
+    dbfft_status s = DBFFT_OK;
+    if (!ctx->fwd_inc0) {
+        TRY(set_load(ctx, 0, ctx->target.data()));
+        s = solve_current(ctx, &r1);
+        if (s != DBFFT_OK && s != DBFFT_E_NOT_CONVERGED) return s;
+    }
+    const bool fwd_ok = s == DBFFT_OK;
     const size_t nU = (size_t)ctx->B * 3 * ctx->H;
     if (!ctx->xfwd) TRY(dalloc_t(ctx, nU, &ctx->xfwd));
     if (!ctx->W2) TRY(dalloc(ctx, (size_t)ctx->B * ctx->nc * ctx->H * sizeof(cplx<double>), &ctx->W2));
@@ -2317,6 +2388,7 @@ dbfft_status dbfft_adjoint(dbfft_ctx* ctx, const double* dJ_dsigma, double* dJ_d
     TRY(set_load(ctx, 0, ctx->target.data()));
     std::vector<double> ru2, re2;
     TRY(chain_residual(ctx, ctx->x64, ctx->xe64, ru2, re2));  // restores sig0 of the forward solution
+    ctx->fwd_inc0 = fwd_ok;
     if (rep) {
         rep->cg_iters = r1.cg_iters + r2.cg_iters;
         rep->cg_iters_max = std::max(r1.cg_iters_max, r2.cg_iters_max);
@@ -2327,6 +2399,73 @@ dbfft_status dbfft_adjoint(dbfft_ctx* ctx, const double* dJ_dsigma, double* dJ_d
         rep->wall_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     }
     return s;
+}
+
+dbfft_status dbfft_tangent_sensitivity(dbfft_ctx* ctx, const double* G, double* dJ_dE, double* C_eff,
+                                       dbfft_report* rep) {
+    if (!ctx || !G || !dJ_dE) return DBFFT_E_ARG;
+    if (ctx->model != DBFFT_ISO_ELASTIC || ctx->nc != 6 || ctx->dims.ne != 0 || ctx->B != 6 * ctx->Bm)
+        return fail(ctx, DBFFT_E_STATE,
+                    "stiffness sensitivity needs linear small strain, strain control, B = 6 n_materials");
+    if (ctx->n3 & 1) return fail(ctx, DBFFT_E_UNSUPPORTED_GRID, "stiffness sensitivity: even n3 only");
+    const auto t0 = std::chrono::steady_clock::now();
+    if (rep) std::memset(rep, 0, sizeof(*rep));
+    // the six unit-strain solves of every map, unless the context holds them
+    // (a converged dbfft_homogenized_tangent, or an earlier call of this one)
+    std::vector<double> C((size_t)ctx->Bm * 36);
+    if (!ctx->tangent_ready) {
+        const dbfft_status s = dbfft_homogenized_tangent(ctx, C.data(), rep);
+        if (s != DBFFT_OK) return s;
+    } else {
+        C = ctx->tangent_C;
+    }
+    const size_t nU = (size_t)ctx->B * 3 * ctx->H;
+    if (!ctx->xfwd) TRY(dalloc_t(ctx, nU, &ctx->xfwd));
+    if (!ctx->W2) TRY(dalloc(ctx, (size_t)ctx->B * ctx->nc * ctx->H * sizeof(cplx<double>), &ctx->W2));
+    if (!ctx->sens_tmp) TRY(dalloc_t(ctx, (size_t)ctx->B * ctx->V, &ctx->sens_tmp));
+    if (!ctx->sens_G) TRY(dalloc_t(ctx, (size_t)ctx->Bm * 36, &ctx->sens_G));
+    CK(cudaMemcpyAsync(ctx->sens_G, G, (size_t)ctx->Bm * 36 * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+    // dJ/dE(x) = (1/N) sum_I eps^I(x) : C1(x) : eta^I(x), eta^I = sum_J G_IJ eps^J: the
+    // strain fields of the unit strains and their combinations, both through pass 3
+    // (C_IJ = (1/N) sum_x eps^I : C : eps^J is stationary in the fluctuations, so no
+    // adjoint solve is needed: the adjoint fields are the forward ones)
+    TRY(run(ctx, "combine6", 0.0, [&] { return launch_combine6(ctx->x64, ctx->sens_G, ctx->xfwd, 3 * ctx->H, ctx->Bm,
+                                                             ctx->stream); }));
+    std::vector<double> mw((size_t)ctx->B * 9, 0.0), mw2((size_t)ctx->B * 9, 0.0);
+    for (int b = 0; b < ctx->B; ++b) mw[b * 9 + b % 6] = b % 6 < 3 ? 1.0 : 0.70710678118654752440084436210485;
+    for (int g = 0; g < ctx->Bm; ++g)
+        for (int I = 0; I < 6; ++I)
+            for (int J = 0; J < 6; ++J) mw2[(g * 6 + I) * 9 + J] = G[(g * 6 + I) * 6 + J] * mw[(g * 6 + J) * 9 + J];
+    CK(cudaMemcpyAsync(ctx->macroW, mw.data(), mw.size() * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->macroW2, mw2.data(), mw2.size() * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+    cplx<double>* W = reinterpret_cast<cplx<double>*>(ctx->W);
+    cplx<double>* W2 = reinterpret_cast<cplx<double>*>(ctx->W2);
+    Ax1InvArgs<double> a1{ctx->dims, freq<double>(ctx), twid<double>(ctx), ctx->x64, nullptr, nullptr, W, nullptr, ctx->pre};
+    Ax2Args<double> a2 = fft_args<double>(ctx, W, nullptr);
+    TRY(run(ctx, "pass1_grad_f64", 0.0, [&] { return launch_grad<double>(AX1_PLAIN, a1, ctx->stream); }));
+    TRY(run(ctx, "fft_ax2_f64", 0.0, [&] { return launch_fft_ax2<double>(+1, a2, ctx->stream); }));
+    TRY(run(ctx, "fft_ax1_f64", 0.0, [&] { return launch_fft_ax1<double>(+1, a2, ctx->stream); }));
+    Ax1InvArgs<double> b1{ctx->dims, freq<double>(ctx), twid<double>(ctx), ctx->xfwd, nullptr, nullptr, W2, nullptr, ctx->pre};
+    Ax2Args<double> b2 = fft_args<double>(ctx, W2, nullptr);
+    TRY(run(ctx, "pass1_grad_f64", 0.0, [&] { return launch_grad<double>(AX1_PLAIN, b1, ctx->stream); }));
+    TRY(run(ctx, "fft_ax2_f64", 0.0, [&] { return launch_fft_ax2<double>(+1, b2, ctx->stream); }));
+    TRY(run(ctx, "fft_ax1_f64", 0.0, [&] { return launch_fft_ax1<double>(+1, b2, ctx->stream); }));
+    Ax3Args<double> a3 = ax3_base<double>(ctx, W);
+    a3.L = ax3_lines(ctx->n3, ctx->nc, ctx->RB, true, 2, a3.radix);
+    a3.W2 = W2;
+    a3.macroW = ctx->macroW;
+    a3.macroW2 = ctx->macroW2;
+    a3.lam = ctx->lam1;
+    a3.mu = ctx->mu1;
+    a3.scale = nullptr;
+    a3.dJdE = ctx->sens_tmp;
+    TRY(run(ctx, "pass3_adjoint_f64", 0.0, [&] { return launch_ax3<double>(OP_ADJ, a3, ctx->stream); }));
+    TRY(run(ctx, "sum6", 0.0, [&] { return launch_sum6(ctx->sens_tmp, dJ_dE, ctx->V, ctx->Bm, ctx->stream); }));
+    TRY(set_load(ctx, 0, ctx->target.data()));  // the context's own macro fields again
+    CK(cudaStreamSynchronize(ctx->stream));
+    if (C_eff) std::memcpy(C_eff, C.data(), C.size() * sizeof(double));
+    if (rep) rep->wall_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    return DBFFT_OK;
 }
 
 }  // extern "C"

@@ -1,6 +1,8 @@
 // k_misc.cu -- small kernels around the passes: macro fields, precision
 // conversion between the FP64 outer loop and the inner CG, the
 // preconditioner as a stand-alone operator, and the mean tangent.
+#include <algorithm>
+
 #include "launch.h"
 #include "misc.h"
 
@@ -380,6 +382,127 @@ cudaError_t launch_compat(const Dims& d, const Freq<double>& f, const cplx<doubl
                           cudaStream_t s) {
     if (d.nc == 6) k_compat<6><<<dim3(nblk, d.B), 256, 0, s>>>(d, f, W, partials);
     else k_compat<9><<<dim3(nblk, d.B), 256, 0, s>>>(d, f, W, partials);
+    return cudaGetLastError();
+}
+
+}  // namespace dbfft
+
+namespace dbfft {
+
+// Device-resident material maps (dbfft_materials.device_arrays): what the host
+// path computes from host arrays at creation, computed where the maps are.
+// k_phase_counts: voxels of each phase id per material map (a block histogram
+// in shared memory, added to counts [Bm][np]); ids at or beyond np counted in *bad.
+constexpr int kHistShared = 8192;  // phase ids counted in shared memory (more: global atomics)
+
+__global__ void k_phase_counts(const uint16_t* __restrict__ phase, long long V, int np,
+                               unsigned long long* counts, unsigned long long* bad) {
+    __shared__ unsigned hist[kHistShared];
+    const int g = blockIdx.y;
+    const bool sh = np <= kHistShared;
+    if (sh)
+        for (int k = threadIdx.x; k < np; k += blockDim.x) hist[k] = 0u;
+    __syncthreads();
+    unsigned nbad = 0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < V; i += (long long)gridDim.x * blockDim.x) {
+        const int id = phase[(long long)g * V + i];
+        if (id >= np) ++nbad;
+        else if (sh) atomicAdd(&hist[id], 1u);
+        else atomicAdd(&counts[(long long)g * np + id], 1ull);
+    }
+    if (nbad) atomicAdd(bad, (unsigned long long)nbad);
+    __syncthreads();
+    if (sh)
+        for (int k = threadIdx.x; k < np; k += blockDim.x)
+            if (hist[k]) atomicAdd(&counts[(long long)g * np + k], (unsigned long long)hist[k]);
+}
+
+// k_scale_stats: FP32 copy of the per-voxel stiffness scale, a count of
+// non-finite values, and per-block partial sums of lam(id) s and mu(id) s
+// (partials [Bm][nblk][2], summed in a fixed order on the host).
+__global__ void k_scale_stats(const uint16_t* __restrict__ phase, const double* __restrict__ scale, float* scale_f,
+                              long long V, int np, const double* lam, const double* mu, double* partials,
+                              unsigned long long* bad) {
+    __shared__ double red[32 * 2];
+    const int g = blockIdx.y;
+    double v[2] = {0.0, 0.0};
+    unsigned nbad = 0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < V; i += (long long)gridDim.x * blockDim.x) {
+        const long long j = (long long)g * V + i;
+        const double s = scale[j];
+        scale_f[j] = (float)s;
+        if (!isfinite(s)) ++nbad;
+        const int id = phase[j];
+        if (id < np) {
+            v[0] += lam[id] * s;
+            v[1] += mu[id] * s;
+        }
+    }
+    if (nbad) atomicAdd(bad, (unsigned long long)nbad);
+    block_sum<2>(v, red);
+    if (threadIdx.x == 0) {
+        partials[((long long)g * gridDim.x + blockIdx.x) * 2 + 0] = v[0];
+        partials[((long long)g * gridDim.x + blockIdx.x) * 2 + 1] = v[1];
+    }
+}
+
+cudaError_t launch_phase_counts(const uint16_t* phase, int Bm, long long V, int np, unsigned long long* counts,
+                                unsigned long long* bad, cudaStream_t s) {
+    const long long nb = std::min<long long>((V + 255) / 256, 1024);
+    k_phase_counts<<<dim3((unsigned)nb, (unsigned)Bm), 256, 0, s>>>(phase, V, np, counts, bad);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scale_stats(const uint16_t* phase, const double* scale, float* scale_f, int Bm, long long V, int np,
+                               const double* lam, const double* mu, double* partials, int nblk,
+                               unsigned long long* bad, cudaStream_t s) {
+    k_scale_stats<<<dim3((unsigned)nblk, (unsigned)Bm), 256, 0, s>>>(phase, scale, scale_f, V, np, lam, mu, partials,
+                                                                    bad);
+    return cudaGetLastError();
+}
+
+}  // namespace dbfft
+
+namespace dbfft {
+
+// Effective-stiffness sensitivity: out[g 6 + I] = sum_J G[g][I][J] x[g 6 + J]
+// over the n = 3 H complex values of each right-hand side (six per material map).
+__global__ void k_combine6(const cplx<double>* __restrict__ x, const double* __restrict__ G, cplx<double>* out,
+                           long long n) {
+    const int g = blockIdx.y / 6, I = blockIdx.y % 6;
+    double c[6];
+#pragma unroll
+    for (int J = 0; J < 6; ++J) c[J] = G[(g * 6 + I) * 6 + J];
+    const cplx<double>* xg = x + (long long)g * 6 * n;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        cplx<double> s = zero_c<double>();
+#pragma unroll
+        for (int J = 0; J < 6; ++J) s = s + c[J] * ldc(xg + J * n + i);
+        stc(out + (long long)blockIdx.y * n + i, s);
+    }
+}
+
+// out[g][v] = sum over the six right-hand sides of map g of tmp[g 6 + I][v]
+__global__ void k_sum6(const double* __restrict__ tmp, double* out, long long V) {
+    const int g = blockIdx.y;
+    for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < V; v += (long long)gridDim.x * blockDim.x) {
+        double s = 0.0;
+#pragma unroll
+        for (int I = 0; I < 6; ++I) s += tmp[((long long)g * 6 + I) * V + v];
+        out[(long long)g * V + v] = s;
+    }
+}
+
+cudaError_t launch_combine6(const cplx<double>* x, const double* G, cplx<double>* out, long long n, int Bm,
+                            cudaStream_t s) {
+    const long long nb = std::min<long long>((n + 255) / 256, 512);
+    k_combine6<<<dim3((unsigned)nb, (unsigned)(6 * Bm)), 256, 0, s>>>(x, G, out, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sum6(const double* tmp, double* out, long long V, int Bm, cudaStream_t s) {
+    const long long nb = std::min<long long>((V + 255) / 256, 1024);
+    k_sum6<<<dim3((unsigned)nb, (unsigned)Bm), 256, 0, s>>>(tmp, out, V);
     return cudaGetLastError();
 }
 

@@ -21,6 +21,19 @@ template <typename T>
 cudaError_t launch_herm_planes(const Dims& d, cplx<T>* v, cudaStream_t s);
 // n row-major 3x3 identity matrices at m[9 n]
 cudaError_t launch_fill_identity(double* m, long long n, cudaStream_t s);
+// device-resident material maps: per-map phase counts [Bm][np] (ids >= np counted in *bad), and the FP32
+// copy of the stiffness scale with its non-finite count and per-block sums of lam(id) s, mu(id) s
+cudaError_t launch_phase_counts(const uint16_t* phase, int Bm, long long V, int np, unsigned long long* counts,
+                                unsigned long long* bad, cudaStream_t s);
+cudaError_t launch_scale_stats(const uint16_t* phase, const double* scale, float* scale_f, int Bm, long long V, int np,
+                               const double* lam, const double* mu, double* partials, int nblk,
+                               unsigned long long* bad, cudaStream_t s);
+// effective-stiffness sensitivity: six-term combinations of the six solutions of each
+// material map (out[g 6 + I] = sum_J G[g][I][J] x[g 6 + J], n complex values each), and
+// the sum of the six per-right-hand-side fields of each map
+cudaError_t launch_combine6(const cplx<double>* x, const double* G, cplx<double>* out, long long n, int Bm,
+                            cudaStream_t s);
+cudaError_t launch_sum6(const double* tmp, double* out, long long V, int Bm, cudaStream_t s);
 // the calling thread's last failure message of dbfft_apply_iso_noalloc ("" if none)
 const char* noalloc_last_error();
 }  // namespace dbfft

@@ -42,7 +42,7 @@ class dbfft_phase(C.Structure):
 
 class dbfft_materials(C.Structure):
     _fields_ = [("phase_id", C.POINTER(C.c_uint16)), ("E_scale", C.POINTER(C.c_double)),
-                ("n_phases", C.c_int), ("phases", C.POINTER(dbfft_phase))]
+                ("n_phases", C.c_int), ("phases", C.POINTER(dbfft_phase)), ("device_arrays", C.c_int)]
 
 
 class dbfft_load(C.Structure):
@@ -75,7 +75,8 @@ EXPORTS = ["dbfft_create", "dbfft_apply", "dbfft_solve_increment", "dbfft_homoge
            "dbfft_homogenized_tangent", "dbfft_adjoint", "dbfft_get_solution", "dbfft_device_bytes",
            "dbfft_destroy", "dbfft_last_error", "dbfft_status_string", "dbfft_profile",
            "dbfft_profile_read", "dbfft_launch_count", "dbfft_apply_iso_noalloc", "dbfft_autotune",
-           "dbfft_tuning", "dbfft_set_pass3_shape", "dbfft_set_precond_refresh", "dbfft_displacement", "dbfft_compatibility"]
+           "dbfft_tuning", "dbfft_set_pass3_shape", "dbfft_set_precond_refresh", "dbfft_displacement", "dbfft_compatibility",
+           "dbfft_tangent_sensitivity"]
 
 _LIB = None
 
@@ -139,6 +140,8 @@ def load_library(build_if_missing: bool = True):
     lib.dbfft_displacement.restype = ip
     lib.dbfft_compatibility.argtypes = [vp, dp]
     lib.dbfft_compatibility.restype = ip
+    lib.dbfft_tangent_sensitivity.argtypes = [vp, dp, vp, dp, C.POINTER(dbfft_report)]
+    lib.dbfft_tangent_sensitivity.restype = ip
     _LIB = lib
     return lib
 
@@ -226,9 +229,19 @@ class Solver:
         self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
         self.shape = tuple(int(s) for s in shape)
         self.L = tuple(float(v) for v in L)
-        ph = np.ascontiguousarray(phase, dtype=np.uint16)
-        if ph.ndim == 3:
-            ph = ph[None]
+        # maps on the device (torch CUDA tensors) are handed over as device
+        # pointers: the library copies them on the GPU, nothing crosses to the host
+        dev_maps = isinstance(phase, torch.Tensor) and phase.is_cuda
+        if dev_maps:
+            ph = phase.contiguous()
+            if ph.element_size() != 2 or ph.is_floating_point():
+                raise ValueError("a device phase map must hold 2-byte integers")
+            if ph.dim() == 3:
+                ph = ph.unsqueeze(0)
+        else:
+            ph = np.ascontiguousarray(phase, dtype=np.uint16)
+            if ph.ndim == 3:
+                ph = ph[None]
         self.n_materials = ph.shape[0]
         tgt = np.ascontiguousarray(np.asarray(target, dtype=np.float64).reshape(-1, 9))
         self.batch = int(batch if batch is not None else tgt.shape[0])
@@ -245,11 +258,22 @@ class Solver:
         self.kinematics, self.precision = kinematics, precision
         self._keep = [ph, tgt, phases]
         mat = dbfft_materials()
-        mat.phase_id = ph.ctypes.data_as(C.POINTER(C.c_uint16))
-        if E_scale is not None:
-            es = np.ascontiguousarray(E_scale, dtype=np.float64).reshape(ph.shape)
-            self._keep.append(es)
-            mat.E_scale = _dptr(es)
+        if dev_maps:
+            mat.device_arrays = 1
+            mat.phase_id = C.cast(C.c_void_p(ph.data_ptr()), C.POINTER(C.c_uint16))
+            if E_scale is not None:
+                es = torch.as_tensor(E_scale, dtype=torch.float64, device=ph.device).reshape(tuple(ph.shape))
+                es = es.contiguous()
+                self._keep.append(es)
+                mat.E_scale = C.cast(C.c_void_p(es.data_ptr()), C.POINTER(C.c_double))
+        else:
+            mat.phase_id = ph.ctypes.data_as(C.POINTER(C.c_uint16))
+            if E_scale is not None:
+                if isinstance(E_scale, torch.Tensor):
+                    E_scale = E_scale.detach().cpu().numpy()
+                es = np.ascontiguousarray(E_scale, dtype=np.float64).reshape(ph.shape)
+                self._keep.append(es)
+                mat.E_scale = _dptr(es)
         mat.n_phases = len(phases)
         mat.phases = C.cast(phases, C.POINTER(dbfft_phase))
         ld = dbfft_load()
@@ -375,6 +399,20 @@ class Solver:
         self._check(self.lib.dbfft_adjoint(self.ctx, _dptr(g), C.c_void_p(out.data_ptr()), C.byref(rep)))
         return out, rep.as_dict()
 
+    def tangent_sensitivity(self, G):
+        """dJ/dE(x) for J = sum_IJ G_IJ C_IJ per material map (dbfft_tangent_sensitivity).
+
+        G: [n_materials, 6, 6] Mandel weights. Returns (dJ/dE device tensor
+        [n_materials, n1, n2, n3], C_eff [n_materials, 6, 6], report)."""
+        torch = self.torch
+        g = np.ascontiguousarray(np.asarray(G, dtype=np.float64).reshape(self.n_materials, 6, 6))
+        out = torch.empty((self.n_materials,) + self.shape, dtype=torch.float64, device=self.device)
+        C_eff = np.zeros((self.n_materials, 6, 6))
+        rep = dbfft_report()
+        self._check(self.lib.dbfft_tangent_sensitivity(self.ctx, _dptr(g), C.c_void_p(out.data_ptr()), _dptr(C_eff),
+                                                       C.byref(rep)))
+        return out, C_eff, rep.as_dict()
+
     def get_solution(self):
         torch = self.torch
         u = torch.empty((self.batch, 3) + self.half, dtype=torch.complex128, device=self.device)
@@ -478,13 +516,16 @@ def homogenized_stress_fn():
     import torch
 
     class HomogenizedStress(torch.autograd.Function):
+        last_adjoint_report = None  # report of the latest backward's dbfft_adjoint call
+
         @staticmethod
         def forward(ctx, E_field, nu, eps_bar, precision=DBFFT_FP64, tol=1e-10):
             B = E_field.shape[0]
             shape = tuple(E_field.shape[1:])
-            phase = np.zeros((B,) + shape, dtype=np.uint16)
+            # the field stays on the device: one phase (E = 1) scaled voxel by voxel by E(x)
+            phase = torch.zeros((B,) + shape, dtype=torch.int16, device=E_field.device)
             s = Solver(shape, phase, iso_phases([1.0], [float(nu)]), eps_bar.detach().cpu().numpy().reshape(B, 9),
-                       precision=precision, tol=tol, E_scale=E_field.detach().double().cpu().numpy())
+                       precision=precision, tol=tol, E_scale=E_field.detach().double().contiguous())
             s.solve_increment(0)
             sig = torch.as_tensor(s.homogenized_stress(), device=E_field.device)
             ctx.solver = s
@@ -493,8 +534,44 @@ def homogenized_stress_fn():
         @staticmethod
         def backward(ctx, grad_out):
             s = ctx.solver
-            dJ, _ = s.adjoint(grad_out.detach().cpu().numpy().reshape(s.batch, 9))
+            # the adjoint reuses the forward solution of this context (no second forward solve)
+            dJ, rep = s.adjoint(grad_out.detach().cpu().numpy().reshape(s.batch, 9))
+            HomogenizedStress.last_adjoint_report = rep
             s.close()
             return dJ.to(grad_out.device), None, None, None, None
 
     return HomogenizedStress
+
+
+def effective_stiffness_fn():
+    """torch.autograd.Function: C_eff(E(x)) for linear isotropic RVEs, backward by the
+    stiffness sensitivity (the six unit-strain solves of the forward pass are reused).
+
+    forward(E_field [Bm, n1, n2, n3] float64, nu) -> C_eff [Bm, 6, 6] (Mandel);
+    backward returns dJ/dE(x) from dbfft_tangent_sensitivity with G = grad_output.
+    """
+    import torch
+
+    class EffectiveStiffness(torch.autograd.Function):
+        last_report = None  # report of the latest backward's sensitivity call
+
+        @staticmethod
+        def forward(ctx, E_field, nu, precision=DBFFT_FP64, tol=1e-10):
+            Bm = E_field.shape[0]
+            shape = tuple(E_field.shape[1:])
+            phase = torch.zeros((Bm,) + shape, dtype=torch.int16, device=E_field.device)
+            s = Solver(shape, phase, iso_phases([1.0], [float(nu)]), np.zeros((6 * Bm, 3, 3)), batch=6 * Bm,
+                       precision=precision, tol=tol, E_scale=E_field.detach().double().contiguous())
+            C_eff, _ = s.homogenized_tangent()
+            ctx.solver = s
+            return torch.as_tensor(C_eff, device=E_field.device)
+
+        @staticmethod
+        def backward(ctx, grad_out):
+            s = ctx.solver
+            dJ, _, rep = s.tangent_sensitivity(grad_out.detach().cpu().numpy())
+            EffectiveStiffness.last_report = rep
+            s.close()
+            return dJ.to(grad_out.device), None, None, None
+
+    return EffectiveStiffness
