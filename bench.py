@@ -215,6 +215,43 @@ def unit_mandel(m):
     return t
 
 
+def fp64_roofline(dbfft, prof, hbm_peak, n, nc):
+    """The FP64 residual chain against the measured FP64 FMA rate of this GPU.
+
+    Flop model (stated, not counted): a complex transform of length n costs
+    5 n log2 n flops, so 5 log2 n per complex element it reads and writes once
+    (16 + 16 bytes in FP64); pass 3 runs two real transforms of length n per
+    component and voxel (2.5 log2 n flops each) and about 36 flops of
+    contraction per voxel. The element-wise passes are reported against HBM.
+    """
+    try:
+        peak64 = dbfft.fp64_fma_rate()
+    except Exception as exc:  # measurement aid only
+        return {"error": str(exc)[:200]}
+    lg = math.log2(n)
+    tot = sum(v["ms"] for v in prof.values())
+    rows, ms64 = {}, 0.0
+    for k, v in prof.items():
+        if not k.endswith("_f64") or not v["launches"] or v["ms"] <= 0:
+            continue
+        ms64 += v["ms"]
+        row = {"launches": v["launches"], "ms_per_launch": v["ms"] / v["launches"],
+               "GBps": v["bytes"] / (v["ms"] * 1e-3) / 1e9, "frac_of_hbm": v["bytes"] / (v["ms"] * 1e-3) / 1e9 / hbm_peak}
+        if k.startswith("fft_"):
+            flops = v["bytes"] / 32.0 * 5.0 * lg
+        elif k.startswith("pass3"):
+            voxels = (v["bytes"] / (2 * nc)) / 8.0  # bytes ~ 2 nc component passes of H * 16 B = V * 8 B each
+            flops = voxels * (2 * nc * 2.5 * lg + 36.0)
+        else:
+            flops = None
+        if flops is not None:
+            row["tflops"] = flops / (v["ms"] * 1e-3) / 1e12
+            row["frac_of_fp64_peak"] = row["tflops"] / peak64
+        rows[k] = row
+    return {"fma_peak_tflops": peak64, "share_of_step": ms64 / tot if tot else None, "kernels": rows,
+            "flop_model": "5 log2 n flops per complex element per transform; pass 3: 2 nc x 2.5 log2 n + 36 per voxel"}
+
+
 def operator_256(torch, dbfft, peak, iters=40):
     """FP32 inner-CG pass chain on a 256^3 linear two-phase RVE (one right-hand side)."""
     from paper_1905_12725_gb300 import synth
@@ -264,7 +301,8 @@ def operator_256(torch, dbfft, peak, iters=40):
     prof = s.profile_read()
     s.profile(False)
     s.close()
-    names = ["pass1_grad_cg_f32", "fft_ax2_f32", "fft_ax1_f32", "pass3_tangent_f32", "pass5_div_cg_f32"]
+    names = ["pass1_grad_cg_f32", "pass1_grad_ax2_cg_f32", "fft_ax2_f32", "fft_ax1_f32", "pass3_tangent_f32",
+             "pass5_div_cg_f32", "pass5_ax2_div_cg_f32"]
     rows = {}
     it_ms = 0.0
     it_bytes = 0.0
@@ -694,6 +732,7 @@ def our_arm(args, rank, world, local_rank):
     kernels = {k: {"launches": v["launches"], "ms": v["ms"],
                    "GBps": (v["bytes"] / (v["ms"] * 1e-3) / 1e9) if v["ms"] > 0 and v["bytes"] > 0 else None}
                for k, v in sorted(prof.items(), key=lambda kv: -kv[1]["ms"])}
+    fp64 = fp64_roofline(dbfft, prof, peak, N_GRID, 6)
 
     # --- FP64 plain: six right-hand sides one after another, FP64 PCG to 1e-6
     plain = [make_solver(c, dbfft.DBFFT_FP64, 1, targets=unit_mandel(m)[None]) for m in range(6)]
@@ -772,6 +811,7 @@ def our_arm(args, rank, world, local_rank):
                      "frac": achieved / peak, "traffic": traffic, "peak_source": peak_kind,
                      "algorithmic_bytes_per_launch": per_launch_bytes, "ms_per_launch": per_launch_ms},
         "kernels": kernels,
+        "fp64": fp64,
         "tuning": s.tuning,
         "gpu_launches": int(gpu_launches),
         "e2e": {"value": e2e_work / e2e_t, "unit": UNIT, "h2d_bytes_per_step": int(c["phase"].nbytes + 6 * 9 * 8),

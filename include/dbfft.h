@@ -263,6 +263,34 @@ dbfft_status dbfft_adjoint(dbfft_ctx* ctx, const double* dJ_dsigma, double* dJ_d
 dbfft_status dbfft_tangent_sensitivity(dbfft_ctx* ctx, const double* G, double* dJ_dE, double* C_eff,
                                        dbfft_report* rep);
 
+/*
+ * Checkpoints of the crystal-plasticity increments (DBFFT_CP_FCC_POWERLAW):
+ * with enable = 1, set before the first increment, every converged increment
+ * keeps its stress field (device, B * V * 6 doubles per increment, allocated
+ * at the first increment for all n_increments) as the record that
+ * dbfft_cp_adjoint sweeps back over. Errors: E_STATE (another model, or
+ * increments already solved).
+ */
+dbfft_status dbfft_set_checkpointing(dbfft_ctx* ctx, int enable);
+
+/*
+ * Adjoint of the path-dependent crystal-plasticity increments (Sec. 2.4,
+ * Eq. lineariz: each increment is a converged Newton solve with the
+ * self-adjoint tangent operator of Sec. 2.2; R14 flow rule). J_b =
+ * sum_ij dJ_dsigma[b][ij] <sigma>_ij after the current (last solved)
+ * increment; s(x) a factor on the elastic stiffness of voxel x. Returns
+ * dJ/ds(x) at s = 1 (the derivative with respect to the logarithm of each
+ * voxel's stiffness) in dJ_ds: device [B][n1][n2][n3] double. The reverse
+ * sweep runs one FP64 PCG solve per increment, to grid.tol, with the
+ * tangent rebuilt from each increment's checkpoint; the state adjoint
+ * carries dJ / d(plastic strain) from one increment to the one before.
+ * Needs dbfft_set_checkpointing(ctx, 1) before increment 0, the FP64
+ * precision and an even n3. The forward state is restored afterwards.
+ * Errors: E_ARG, E_STATE, E_UNSUPPORTED_GRID, E_MATERIAL (a checkpoint whose
+ * tangent is not positive definite), E_NOT_CONVERGED.
+ */
+dbfft_status dbfft_cp_adjoint(dbfft_ctx* ctx, const double* dJ_dsigma, double* dJ_ds, dbfft_report* rep);
+
 /* Copy the current FP64 solution: u_hat device complex128 [B][3][n1][n2][n3/2+1]
  * (may be NULL), e host [B][9] (may be NULL). */
 dbfft_status dbfft_get_solution(dbfft_ctx* ctx, void* u_hat, double* e);
@@ -408,6 +436,15 @@ dbfft_status dbfft_set_pass3_shape(dbfft_ctx* ctx, int fp64, int pipelined, int 
  */
 enum { DBFFT_PRECOND_PER_INCREMENT = 0, DBFFT_PRECOND_INITIAL = 1, DBFFT_PRECOND_PER_NEWTON = 2 };
 dbfft_status dbfft_set_precond_refresh(dbfft_ctx* ctx, int policy);
+
+/*
+ * FP64 fused multiply-add rate of the current device in TFLOP/s (no
+ * counterpart in the paper; a measurement aid for the FP64 roofline of the
+ * residual chain): eight independent FMA chains per thread, eight 256-thread
+ * CTAs per SM, best of four timed launches on `stream`. Allocates a small
+ * output buffer with cudaMallocAsync. Errors: E_ARG, E_NOMEM, E_CUDA.
+ */
+dbfft_status dbfft_fp64_fma_rate(double* tflops, void* stream);
 
 /* Device bytes held by the context. */
 size_t dbfft_device_bytes(const dbfft_ctx* ctx);

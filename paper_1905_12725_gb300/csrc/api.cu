@@ -92,6 +92,13 @@ struct dbfft_ctx {
     std::vector<double> tangent_C;  // their C_eff [Bm][6][6]
     double* sens_tmp = nullptr;  // [B][V] per right-hand side sensitivity terms
     double* sens_G = nullptr;    // [Bm][6][6] weights on the device
+    // checkpoints of the crystal-plasticity increments (the adjoint's forward record)
+    bool ckpt_on = false;
+    double* ckpt = nullptr;      // [n_inc][B][V][6] converged stress of each increment (Mandel)
+    int ckpt_n = 0;              // increments 0 .. ckpt_n - 1 recorded
+    double* adj_q = nullptr;     // [B][V][6] state adjoint
+    double* adj_w = nullptr;     // [B][V][6] w, then B lam
+    double* adj_a = nullptr;     // [B][6]
 
     // ---- vectors
     cplx<double>* x64 = nullptr;
@@ -2115,6 +2122,18 @@ dbfft_status dbfft_solve_increment(dbfft_ctx* ctx, int inc, dbfft_report* rep) {
         ctx->cur_inc = inc;
     }
     ctx->fwd_inc0 = s == DBFFT_OK && inc == 0;
+    if (ctx->ckpt_on && ctx->model == DBFFT_CP_FCC_POWERLAW) {
+        // the converged stress of this increment: the adjoint's checkpoint
+        if (s == DBFFT_OK && inc == ctx->ckpt_n) {
+            const size_t per = (size_t)ctx->B * ctx->V * 6;
+            if (!ctx->ckpt) TRY(dalloc_t(ctx, per * ctx->n_inc, &ctx->ckpt));
+            CK(cudaMemcpyAsync(ctx->ckpt + per * inc, ctx->sig_prev, per * sizeof(double), cudaMemcpyDeviceToDevice,
+                               ctx->stream));
+            ctx->ckpt_n = inc + 1;
+        } else {
+            ctx->ckpt_n = 0;  // a gap in the record: no adjoint for this path
+        }
+    }
     if (rep) rep->wall_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     return s;
 }
@@ -2465,6 +2484,146 @@ dbfft_status dbfft_tangent_sensitivity(dbfft_ctx* ctx, const double* G, double* 
     CK(cudaStreamSynchronize(ctx->stream));
     if (C_eff) std::memcpy(C_eff, C.data(), C.size() * sizeof(double));
     if (rep) rep->wall_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    return DBFFT_OK;
+}
+
+dbfft_status dbfft_set_checkpointing(dbfft_ctx* ctx, int enable) {
+    if (!ctx) return DBFFT_E_ARG;
+    if (ctx->model != DBFFT_CP_FCC_POWERLAW)
+        return fail(ctx, DBFFT_E_STATE, "checkpoints are kept for the small-strain crystal-plasticity model");
+    if (enable && ctx->cur_inc >= 0)
+        return fail(ctx, DBFFT_E_STATE, "enable checkpoints before the first increment");
+    ctx->ckpt_on = enable != 0;
+    ctx->ckpt_n = 0;
+    return DBFFT_OK;
+}
+
+dbfft_status dbfft_cp_adjoint(dbfft_ctx* ctx, const double* dJ_dsigma, double* dJ_ds, dbfft_report* rep) {
+    if (!ctx || !dJ_dsigma || !dJ_ds) return DBFFT_E_ARG;
+    if (ctx->model != DBFFT_CP_FCC_POWERLAW || ctx->prec != DBFFT_FP64)
+        return fail(ctx, DBFFT_E_STATE, "the increment adjoint needs the small-strain crystal-plasticity model in FP64");
+    if (ctx->n3 & 1) return fail(ctx, DBFFT_E_UNSUPPORTED_GRID, "increment adjoint: even n3 only");
+    if (!ctx->ckpt_on || ctx->cur_inc < 0 || ctx->ckpt_n != ctx->cur_inc + 1)
+        return fail(ctx, DBFFT_E_STATE, "no checkpoint of every increment up to the current one");
+    const auto t0 = std::chrono::steady_clock::now();
+    if (rep) std::memset(rep, 0, sizeof(*rep));
+    ctx->fwd_inc0 = false;
+    ctx->tangent_ready = false;
+    const size_t per = (size_t)ctx->B * ctx->V * 6;
+    const size_t nU = (size_t)ctx->B * 3 * ctx->H;
+    if (!ctx->adj_q) TRY(dalloc_t(ctx, per, &ctx->adj_q));
+    if (!ctx->adj_w) TRY(dalloc_t(ctx, per, &ctx->adj_w));
+    if (!ctx->adj_a) TRY(dalloc_t(ctx, (size_t)ctx->B * 6, &ctx->adj_a));
+    if (!ctx->xfwd) TRY(dalloc_t(ctx, nU, &ctx->xfwd));
+    CK(cudaMemsetAsync(ctx->adj_q, 0, per * sizeof(double), ctx->stream));
+    CK(cudaMemsetAsync(dJ_ds, 0, (size_t)ctx->B * ctx->V * sizeof(double), ctx->stream));
+    CK(cudaMemsetAsync(ctx->errw, 0, sizeof(unsigned), ctx->stream));
+    // the forward state, restored at the end
+    CK(cudaMemcpyAsync(ctx->xfwd, ctx->x64, nU * sizeof(cplx<double>), cudaMemcpyDeviceToDevice, ctx->stream));
+    std::vector<double> xe_save((size_t)ctx->B * 9), sig0_save((size_t)ctx->B * 9);
+    CK(cudaMemcpyAsync(xe_save.data(), ctx->xe64, xe_save.size() * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemcpyAsync(sig0_save.data(), ctx->sig0, sig0_save.size() * sizeof(double), cudaMemcpyDeviceToHost,
+                       ctx->stream));
+    // a = sym(dJ/dsigma) / N in Mandel components at the last increment
+    static const int pi[6] = {0, 1, 2, 1, 0, 0}, pj[6] = {0, 1, 2, 2, 2, 1};
+    std::vector<double> a_last((size_t)ctx->B * 6), a_zero((size_t)ctx->B * 6, 0.0);
+    for (int b = 0; b < ctx->B; ++b)
+        for (int m = 0; m < 6; ++m) {
+            const double gs = 0.5 * (dJ_dsigma[b * 9 + 3 * pi[m] + pj[m]] + dJ_dsigma[b * 9 + 3 * pj[m] + pi[m]]);
+            a_last[b * 6 + m] = (m < 3 ? gs : std::sqrt(2.0) * gs) * ctx->dims.invN;
+        }
+    cplx<double>* W = reinterpret_cast<cplx<double>*>(ctx->W);
+    double* tan = reinterpret_cast<double*>(ctx->tan);
+    long long it_sum = 0;
+    int it_max = 0;
+    for (int n = ctx->cur_inc; n >= 0; --n) {
+        const double* sig_n = ctx->ckpt + per * n;
+        CK(cudaMemcpyAsync(ctx->adj_a, (n == ctx->cur_inc ? a_last : a_zero).data(), a_last.size() * sizeof(double),
+                           cudaMemcpyHostToDevice, ctx->stream));
+        // w = q + T_n (a - S q), and T_n as the context's tangent
+        TRY(run(ctx, "cp_adjoint_pre", 0.0, [&] {
+            return launch_cp_adj(0, ctx->B, ctx->Rm, ctx->V, ctx->phase, ctx->grains, ctx->cp, sig_n, ctx->adj_q,
+                                 ctx->adj_a, ctx->adj_w, tan, nullptr, ctx->errw, 1, ctx->stream);
+        }));
+        TRY(refresh_precond(ctx));
+        // right-hand side B^H w: the real field through R2C, the forward transforms and the divergence
+        Ax3Args<double> a3 = ax3_base<double>(ctx, W);
+        a3.zero_in = 1;
+        a3.real_in = ctx->adj_w;
+        a3.macroW = ctx->macroW;
+        TRY(run(ctx, "pass3_loadw_f64", 0.0, [&] { return launch_ax3_post<double>(OP_LOADW, a3, ctx->stream); }));
+        Ax2Args<double> a2 = fft_args<double>(ctx, W, nullptr);
+        TRY(run(ctx, "fft_ax1_f64", 0.0, [&] { return launch_fft_ax1<double>(-1, a2, ctx->stream); }));
+        TRY(run(ctx, "fft_ax2_f64", 0.0, [&] { return launch_fft_ax2<double>(-1, a2, ctx->stream); }));
+        Ax1FwdArgs<double> a5;
+        std::memset(&a5, 0, sizeof(a5));
+        a5.d = ctx->dims;
+        a5.f = freq<double>(ctx);
+        a5.tw = twid<double>(ctx);
+        a5.W = W;
+        a5.out = ctx->r64;
+        a5.e_out = ctx->re64;
+        TRY(run(ctx, "pass5_div_f64", 0.0, [&] { return launch_div<double>(AX5_PLAIN, a5, ctx->stream); }));
+        TRY(run(ctx, "hermitian_planes", 0.0, [&] { return launch_herm_planes<double>(ctx->dims, ctx->r64, ctx->stream); }));
+        // K_n lam = B^H w by PCG in FP64 (x = 0 start, tolerance grid.tol)
+        CK(cudaMemsetAsync(ctx->x64, 0, nU * sizeof(cplx<double>), ctx->stream));
+        CK(cudaMemsetAsync(ctx->xe64, 0, (size_t)ctx->B * 9 * sizeof(double), ctx->stream));
+        TRY(set_scales(ctx, std::vector<double>(ctx->B, 1.0)));
+        TRY(run(ctx, "to_inner", 0.0, [&] {
+            return launch_to_inner<double>(ctx->dims, ctx->r64, ctx->re64, ctx->scal,
+                                           reinterpret_cast<cplx<double>*>(ctx->ri), ctx->re_i,
+                                           reinterpret_cast<cplx<double>*>(ctx->xi), ctx->xe_i, ctx->stream);
+        }));
+        int itm = 0;
+        TRY(inner_cg<double>(ctx, ctx->grid.tol, it_sum, itm));
+        it_max = std::max(it_max, itm);
+        TRY(run(ctx, "from_inner", 0.0, [&] {
+            return launch_from_inner<double>(ctx->dims, reinterpret_cast<const cplx<double>*>(ctx->xi),
+                                             reinterpret_cast<const cplx<double>*>(ctx->pi), ctx->cg, ctx->xe_i,
+                                             ctx->scal, ctx->x64, ctx->xe64, ctx->stream);
+        }));
+        // e_lam = B lam as a real field (fluctuation and macro part)
+        TRY(run(ctx, "macro", 0.0, [&] {
+            return launch_macro(ctx->B, ctx->nc, ctx->activeflag, nullptr, ctx->xe64, ctx->macroW, ctx->macroWf,
+                                ctx->stream);
+        }));
+        Ax1InvArgs<double> a1{ctx->dims, freq<double>(ctx), twid<double>(ctx), ctx->x64, nullptr, nullptr, W, nullptr,
+                              ctx->pre};
+        TRY(run(ctx, "pass1_grad_f64", 0.0, [&] { return launch_grad<double>(AX1_PLAIN, a1, ctx->stream); }));
+        TRY(run(ctx, "fft_ax2_f64", 0.0, [&] { return launch_fft_ax2<double>(+1, a2, ctx->stream); }));
+        TRY(run(ctx, "fft_ax1_f64", 0.0, [&] { return launch_fft_ax1<double>(+1, a2, ctx->stream); }));
+        Ax3Args<double> b3 = ax3_base<double>(ctx, W);
+        b3.real_out = ctx->adj_w;
+        b3.macroW = ctx->macroW;
+        TRY(run(ctx, "pass3_storew_f64", 0.0, [&] { return launch_ax3_post<double>(OP_STOREW, b3, ctx->stream); }));
+        // dJ/ds += d . T_n S sigma_n + q . S sigma_n, q = -T_n d
+        TRY(run(ctx, "cp_adjoint_post", 0.0, [&] {
+            return launch_cp_adj(1, ctx->B, ctx->Rm, ctx->V, ctx->phase, ctx->grains, ctx->cp, sig_n, ctx->adj_q,
+                                 ctx->adj_a, ctx->adj_w, nullptr, dJ_ds, ctx->errw, 0, ctx->stream);
+        }));
+    }
+    unsigned errh = 0;
+    CK(cudaMemcpyAsync(&errh, ctx->errw, sizeof(unsigned), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    // the forward state again: solution, macro fields, mean stress and the tangent of the
+    // last increment (from its checkpoint; a constitutive update here would start a new step)
+    CK(cudaMemcpyAsync(ctx->x64, ctx->xfwd, nU * sizeof(cplx<double>), cudaMemcpyDeviceToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->xe64, xe_save.data(), xe_save.size() * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->sig0, sig0_save.data(), sig0_save.size() * sizeof(double), cudaMemcpyHostToDevice,
+                       ctx->stream));
+    TRY(set_load(ctx, ctx->cur_inc, ctx->target.data()));
+    TRY(run(ctx, "cp_adjoint_pre", 0.0, [&] {
+        return launch_cp_adj(0, ctx->B, ctx->Rm, ctx->V, ctx->phase, ctx->grains, ctx->cp, ctx->ckpt + per * ctx->cur_inc,
+                             ctx->adj_q, ctx->adj_a, ctx->adj_w, tan, nullptr, ctx->errw, 0, ctx->stream);
+    }));
+    CK(cudaStreamSynchronize(ctx->stream));
+    if (errh & 1u) return fail(ctx, DBFFT_E_MATERIAL, "a checkpoint gave a tangent that is not positive definite");
+    if (rep) {
+        rep->cg_iters = it_sum;
+        rep->cg_iters_max = it_max;
+        rep->outer_iters = ctx->cur_inc + 1;
+        rep->wall_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    }
     return DBFFT_OK;
 }
 

@@ -3,6 +3,7 @@
 // preconditioner as a stand-alone operator, and the mean tangent.
 #include <algorithm>
 
+#include "../../include/dbfft.h"
 #include "launch.h"
 #include "misc.h"
 
@@ -507,3 +508,56 @@ cudaError_t launch_sum6(const double* tmp, double* out, long long V, int Bm, cud
 }
 
 }  // namespace dbfft
+
+namespace dbfft {
+
+// FP64 fused multiply-add rate: eight independent dependency chains per
+// thread, so that the FP64 pipe, not the latency of one chain, sets the pace.
+__global__ void k_fp64_fma(double* out, int iters, double a, double b) {
+    double x[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) x[k] = (double)(threadIdx.x + k) * 1e-3;
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) x[k] = fma(x[k], a, b);
+    }
+    double s = 0.0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) s += x[k];
+    out[(long long)blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
+}  // namespace dbfft
+
+extern "C" dbfft_status dbfft_fp64_fma_rate(double* tflops, void* stream) {
+    using namespace dbfft;
+    if (!tflops) return DBFFT_E_ARG;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    int dev = 0, nsm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return DBFFT_E_CUDA;
+    const int blocks = nsm * 8, threads = 256, iters = 4096;
+    double* out = nullptr;
+    if (cudaMallocAsync(reinterpret_cast<void**>(&out), (size_t)blocks * threads * sizeof(double), s) != cudaSuccess)
+        return DBFFT_E_NOMEM;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best = 1e30f;
+    for (int rep = 0; rep < 5; ++rep) {
+        cudaEventRecord(e0, s);
+        k_fp64_fma<<<blocks, threads, 0, s>>>(out, iters, 0.999999, 1e-7);
+        cudaEventRecord(e1, s);
+        cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (rep > 0) best = ms < best ? ms : best;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFreeAsync(out, s);
+    const bool ok = cudaStreamSynchronize(s) == cudaSuccess && cudaGetLastError() == cudaSuccess;
+    *tflops = 2.0 * 8.0 * (double)iters * blocks * threads / (best * 1e-3) / 1e12;
+    return ok ? DBFFT_OK : DBFFT_E_CUDA;
+}

@@ -34,6 +34,12 @@ cudaError_t launch_scale_stats(const uint16_t* phase, const double* scale, float
 cudaError_t launch_combine6(const cplx<double>* x, const double* G, cplx<double>* out, long long n, int Bm,
                             cudaStream_t s);
 cudaError_t launch_sum6(const double* tmp, double* out, long long V, int Bm, cudaStream_t s);
+// per-voxel steps of the crystal-plasticity adjoint (k_cpadj.cu): post = 0 writes the
+// tangent T_n (tan, may be null) and, with write_w, w = q + T_n (a - S q); post = 1
+// reads e_lam from w, accumulates dJds and updates q
+cudaError_t launch_cp_adj(int post, int B, int Rm, long long V, const uint16_t* phase, const CpGrain* grains,
+                          const CpParams& cp, const double* sig, double* q, const double* aw, double* w, double* tan,
+                          double* dJds, unsigned* err, int write_w, cudaStream_t s);
 // the calling thread's last failure message of dbfft_apply_iso_noalloc ("" if none)
 const char* noalloc_last_error();
 }  // namespace dbfft

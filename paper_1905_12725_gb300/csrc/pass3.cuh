@@ -29,7 +29,9 @@ enum {
     OP_DISP = 9,        // total displacement Hbar x + u~ from the 3 inverse-transformed components (no R2C)
     OP_FCP_APPLY = 10,  // dP = K : (G + macro) from the stored finite-strain crystal-plasticity data (45)
     OP_FCP_UPDATE = 11, // finite-strain crystal plasticity, F = Fe Fp: P, Fp, T and the tangent data
-    OP_FCP_UPDATE32 = 12  // OP_FCP_UPDATE for an FP32 inner solve: FP32 start of the local solve
+    OP_FCP_UPDATE32 = 12, // OP_FCP_UPDATE for an FP32 inner solve: FP32 start of the local solve
+    OP_LOADW = 13,        // real field from real_in ([B][V][6], Mandel) into the lines, then R2C (zero_in)
+    OP_STOREW = 14        // C2R, then the real field plus the macro part to real_out ([B][V][6], Mandel)
 };
 
 template <typename T>
@@ -73,10 +75,11 @@ struct Ax3Args {
     double* fp_new;        // OP_FCP_UPDATE: trial Fp [B][V][9]
     double hx[3];          // OP_DISP: voxel edge lengths L_a / n_a
     long long wait_limit;  // polls of a bulk-copy wait before it gives up (0: the default, 2^26)
+    const double* real_in; // OP_LOADW input [B][V][6] (Mandel components)
 };
 
 template <int OPK> struct OpInfo {
-    static constexpr bool forward = OPK != OP_ADJ && OPK != OP_DISP;
+    static constexpr bool forward = OPK != OP_ADJ && OPK != OP_DISP && OPK != OP_STOREW;
     static constexpr bool apply =
         OPK == OP_ISO || OPK == OP_NH_APPLY || OPK == OP_CP_APPLY || OPK == OP_SVK_APPLY || OPK == OP_FCP_APPLY;
 };
@@ -375,6 +378,24 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? (RW == 32 ? 2 : (RW == 
                 }
 #pragma unroll
                 for (int q = 0; q < 9; ++q) f[q * SB] = (T)Pk[q];
+            }
+        } else if constexpr (OPK == OP_LOADW || OPK == OP_STOREW) {
+            // real 6-component fields in Mandel components (shear sqrt(2) x the tensor
+            // component); the lines hold W components (the tensor components)
+            const double r2 = 1.41421356237309504880168872420970;
+            for (int rr = 0; rr < RB; ++rr) {
+                const int bb = g * RB + rr;
+                T* f = slot_ptr(0, (lv * RB + rr) * NC) + x3;
+                const long long o = ((long long)bb * d.V + vox) * 6;
+#pragma unroll
+                for (int q = 0; q < 6; ++q) {
+                    if constexpr (OPK == OP_LOADW) {
+                        f[q * SB] = (T)(q < 3 ? a.real_in[o + q] : a.real_in[o + q] / r2);
+                    } else {
+                        const double v = (double)f[q * SB] + (double)s_macro[rr * 9 + q];
+                        a.real_out[o + q] = q < 3 ? v : r2 * v;
+                    }
+                }
             }
         } else if constexpr (OPK == OP_DISP) {
             // u = Hbar x + u~ at the voxel centre x = (i + 1/2) h; u~ = the real line / N

@@ -76,7 +76,8 @@ EXPORTS = ["dbfft_create", "dbfft_apply", "dbfft_solve_increment", "dbfft_homoge
            "dbfft_destroy", "dbfft_last_error", "dbfft_status_string", "dbfft_profile",
            "dbfft_profile_read", "dbfft_launch_count", "dbfft_apply_iso_noalloc", "dbfft_autotune",
            "dbfft_tuning", "dbfft_set_pass3_shape", "dbfft_set_precond_refresh", "dbfft_displacement", "dbfft_compatibility",
-           "dbfft_tangent_sensitivity"]
+           "dbfft_tangent_sensitivity", "dbfft_set_checkpointing", "dbfft_cp_adjoint",
+           "dbfft_fp64_fma_rate"]
 
 _LIB = None
 
@@ -142,6 +143,12 @@ def load_library(build_if_missing: bool = True):
     lib.dbfft_compatibility.restype = ip
     lib.dbfft_tangent_sensitivity.argtypes = [vp, dp, vp, dp, C.POINTER(dbfft_report)]
     lib.dbfft_tangent_sensitivity.restype = ip
+    lib.dbfft_set_checkpointing.argtypes = [vp, ip]
+    lib.dbfft_set_checkpointing.restype = ip
+    lib.dbfft_cp_adjoint.argtypes = [vp, dp, vp, C.POINTER(dbfft_report)]
+    lib.dbfft_cp_adjoint.restype = ip
+    lib.dbfft_fp64_fma_rate.argtypes = [dp, vp]
+    lib.dbfft_fp64_fma_rate.restype = ip
     _LIB = lib
     return lib
 
@@ -413,6 +420,19 @@ class Solver:
                                                        C.byref(rep)))
         return out, C_eff, rep.as_dict()
 
+    def set_checkpointing(self, enable=True):
+        """Keep every converged crystal-plasticity increment (dbfft_set_checkpointing)."""
+        self._check(self.lib.dbfft_set_checkpointing(self.ctx, 1 if enable else 0))
+
+    def cp_adjoint(self, dJ_dsigma):
+        """dJ/ds(x) over the solved increments (dbfft_cp_adjoint); dJ_dsigma [batch, 3, 3]."""
+        torch = self.torch
+        g = np.ascontiguousarray(np.asarray(dJ_dsigma, dtype=np.float64).reshape(self.batch, 9))
+        out = torch.empty((self.batch,) + self.shape, dtype=torch.float64, device=self.device)
+        rep = dbfft_report()
+        self._check(self.lib.dbfft_cp_adjoint(self.ctx, _dptr(g), C.c_void_p(out.data_ptr()), C.byref(rep)))
+        return out, rep.as_dict()
+
     def get_solution(self):
         torch = self.torch
         u = torch.empty((self.batch, 3) + self.half, dtype=torch.complex128, device=self.device)
@@ -499,6 +519,18 @@ def apply_iso_noalloc(shape, phase_id, lam, mu, u_hat, out, L=None, stream=None)
                                        C.c_void_p(lam.data_ptr()), C.c_void_p(mu.data_ptr()),
                                        C.c_void_p(u_hat.data_ptr()), C.c_void_p(out.data_ptr()),
                                        C.c_void_p(st.cuda_stream))
+
+
+def fp64_fma_rate(stream=None) -> float:
+    """Measured FP64 FMA rate of the current GPU in TFLOP/s (dbfft_fp64_fma_rate)."""
+    import torch
+
+    v = C.c_double(0.0)
+    st = stream if stream is not None else torch.cuda.current_stream()
+    rc = load_library().dbfft_fp64_fma_rate(C.byref(v), C.c_void_p(st.cuda_stream))
+    if rc != DBFFT_OK:
+        raise DbfftError(rc, "dbfft_fp64_fma_rate failed")
+    return v.value
 
 
 def noalloc_last_error() -> str:
