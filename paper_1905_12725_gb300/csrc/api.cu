@@ -1383,12 +1383,17 @@ void tune_pass3(dbfft_ctx* ctx, int pi_, cplx<T>* W) {
         // the line-bulk pass (FP32 applications on lines of 128 or 256 values)
         float blb = 1e30f;
         int blbL = 0;
+        int blbT = 0;
         if (sizeof(T) == 4 && lb_supported(ctx)) {
+            for (int cap : {384, 192, -1})  // threads per CTA (more, smaller CTAs overlap each other's
+                                              // phases); -1: warp lines (16-line tiles)
             for (int L : {2, 4, 6, 8, 12, 16}) {
+                if (cap < 0 && L != 16) continue;
                 const long long sm = ax3_lb_smem(ctx->n3, ctx->nc, ctx->RB, ctx->scale != nullptr, L, nlines);
                 if (sm < 0 || sm > 110 * 1024) continue;
                 Ax3Args<T> a3 = ax3_base<T>(ctx, W);
                 a3.pipe = 3;
+                a3.radix = cap;
                 a3.L = L;
                 if constexpr (sizeof(T) == 4) a3.macroW = ctx->macroWf;
                 else a3.macroW = ctx->macroW;
@@ -1397,12 +1402,13 @@ void tune_pass3(dbfft_ctx* ctx, int pi_, cplx<T>* W) {
                 if (ms < blb * 0.98f) {
                     blb = ms;
                     blbL = L;
+                    blbT = cap;
                 }
             }
             if (blbL > 0 && blb < bp) {
                 bp = blb;
                 bpS = 3;
-                bpR = 0;
+                bpR = blbT;
                 bpL = blbL;
             }
         }
@@ -1414,7 +1420,7 @@ void tune_pass3(dbfft_ctx* ctx, int pi_, cplx<T>* W) {
                       ctx->pipe_on[pi_] ? " used" : "");
         ctx->tune_note += buf;
         if (blbL > 0) {
-            std::snprintf(buf, sizeof(buf), "pass3 line-bulk lines %d (%.4f ms); ", blbL, blb);
+            std::snprintf(buf, sizeof(buf), "pass3 line-bulk lines %d threads<=%d (%.4f ms); ", blbL, blbT, blb);
             ctx->tune_note += buf;
         }
     }
@@ -1582,7 +1588,8 @@ dbfft_status dbfft_set_pass3_shape(dbfft_ctx* ctx, int fp64, int pipelined, int 
                         "line-bulk pass 3: FP32, n3 = 128 or 256, linear / crystal-plasticity / Neo-Hookean model, "
                         "lines even and dividing n1*n2");
         ctx->pipe_on[pi_] = 3;
-        ctx->pipe_R[pi_] = 0;
+        if (radix < 0 && lines != 16) return fail(ctx, DBFFT_E_ARG, "line-bulk warp lines need 16-line tiles");
+        ctx->pipe_R[pi_] = radix < 0 ? -1 : (radix > 0 && radix < 384 ? radix : 0);  // thread cap / warp lines
         ctx->pipe_L[pi_] = lines;
         for (int k = 0; k < 2; ++k)
             if (ctx->cg_exec[k]) { cudaGraphExecDestroy(ctx->cg_exec[k]); ctx->cg_exec[k] = nullptr; }

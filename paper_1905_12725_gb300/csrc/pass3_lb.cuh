@@ -64,17 +64,18 @@ struct LbPlan {
 };
 
 // Threads per CTA: every (padded) line slot gets P threads, in as few rounds
-// as keep the CTA at or below 384 threads.
+// as keep the CTA at or below max_thr (at most 384) threads.
 template <int N3>
-__host__ __device__ constexpr int lb_threads(int nslot) {
+__host__ __device__ constexpr int lb_threads(int nslot, int max_thr = 384) {
     constexpr int P = LbShape<N3 / 2>::P;
+    const int cap = max_thr > 0 && max_thr < 384 ? max_thr : 384;
     const int ns16 = (nslot + 15) / 16 * 16;
     for (int rounds = 1; rounds <= ns16; ++rounds) {
         const int groups = (ns16 + rounds - 1) / rounds;
         const int thr = (groups * P + 31) / 32 * 32;
-        if (thr <= 384) return thr;
+        if (thr <= cap) return thr;
     }
-    return 384;
+    return 32;
 }
 
 // line slot of group gi: inside each block of 16 slots, the GH = 16 / P groups
@@ -89,8 +90,13 @@ __device__ __forceinline__ int lb_slot(int gi) {
 __device__ __forceinline__ float4 ld4(const float* p) { return *reinterpret_cast<const float4*>(p); }
 __device__ __forceinline__ void st4(float* p, float4 v) { *reinterpret_cast<float4*>(p) = v; }
 
-template <int N3, int NC, int OPK>
-__global__ void __launch_bounds__(384, 2) k_axis3_lb(Ax3Args<float> a) {
+// WL (warp lines): a tile of 16 lines, P warps; warp w owns the 16 / P lines
+// w + P j and takes them alone through C2R, contraction and R2C (component
+// slots two per round, one per half-warp), so only warp barriers separate the
+// phases. The lines of a half-warp are P line buffers apart, which keeps its
+// 64-bit accesses free of bank conflicts as lb_slot does.
+template <int N3, int NC, int OPK, bool WL = false>
+__global__ void __launch_bounds__(WL ? 256 : 384, 2) k_axis3_lb(Ax3Args<float> a) {
     using T = float;
     static_assert(OpInfo<OPK>::apply, "the line-bulk pass serves the CG applications");
     constexpr int M = N3 / 2;
@@ -180,12 +186,24 @@ __global__ void __launch_bounds__(384, 2) k_axis3_lb(Ax3Args<float> a) {
 
     const int nslot = RB * NC * L;
     const int ngr = nthr / P;  // line slots per round
-    const int nrounds = ((nslot + 15) / 16 * 16 + ngr - 1) / ngr;
+    const int warp = t >> 5;
+    const int nrounds = WL ? (RB * NC + 1) / 2 : ((nslot + 15) / 16 * 16 + ngr - 1) / ngr;
     // slot -> (ok, line buffer); the aligned region of an odd slot starts 8 bytes in
     auto slot_of = [&](int rd, bool& ok, int& sig) {
-        sig = lb_slot<P>(rd * ngr + t / P);
-        ok = sig < nslot && !((done_mask >> (sig / (NC * L))) & 1u);
+        if constexpr (WL) {
+            const int cs = 2 * rd + (lane >> 4);            // (rhs, component) slot of this half-warp
+            const int ll = warp + P * ((lane & 15) / P);    // one of the warp's lines
+            sig = cs * L + ll;
+            ok = cs < RB * NC && !((done_mask >> (cs / NC)) & 1u);
+        } else {
+            sig = lb_slot<P>(rd * ngr + t / P);
+            ok = sig < nslot && !((done_mask >> (sig / (NC * L))) & 1u);
+        }
         if (!ok) sig = 0;
+    };
+    auto phase_sync = [&]() {
+        if constexpr (WL) __syncwarp();
+        else __syncthreads();
     };
 
     // ---------------------------------------------------------------- C2R
@@ -254,7 +272,7 @@ __global__ void __launch_bounds__(384, 2) k_axis3_lb(Ax3Args<float> a) {
             }
         }
     }
-    __syncthreads();
+    phase_sync();
 
     // ---------------------------------------------------------------- per-voxel operation
     // one right-hand side at a time (its curvature share is reduced before the next)
@@ -263,8 +281,10 @@ __global__ void __launch_bounds__(384, 2) k_axis3_lb(Ax3Args<float> a) {
         constexpr int Q4 = N3 / 4;
         const int CS = 2 * L * H;  // floats between the components of one line
         T en = T(0);
-        for (int it = t; it < L * Q4; it += nthr) {
-            const int ll = it / Q4, x4 = (it - ll * Q4) * 4;
+        // all lines of the tile (block-strided), or the warp's own 16 / P lines (lane-strided)
+        const int it0 = WL ? lane : t, itn = WL ? (16 / P) * Q4 : L * Q4, its = WL ? 32 : nthr;
+        for (int it = it0; it < itn; it += its) {
+            const int ll = WL ? warp + P * (it / Q4) : it / Q4, x4 = (it % Q4) * 4;
             const uint2 pp = *reinterpret_cast<const uint2*>(phs + ll * N3 + x4);
             const float4 s4 = has_scale ? ld4(scs + ll * N3 + x4) : make_float4(1.f, 1.f, 1.f, 1.f);
             const int sig0 = (rr * NC) * L + ll;  // component 0; all components share its parity
@@ -307,7 +327,7 @@ __global__ void __launch_bounds__(384, 2) k_axis3_lb(Ax3Args<float> a) {
             if (lane == 0) atomicAdd(&s_eacc[rr], (double)en);
         }
     }
-    __syncthreads();
+    phase_sync();
 
     // ---------------------------------------------------------------- R2C
     load_twB();

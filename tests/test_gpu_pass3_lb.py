@@ -189,3 +189,30 @@ def test_line_bulk_bounded_wait_returns_timeout():
     assert r.returncode == 0, r.stderr[-2000:]
     lines = r.stdout.split()
     assert "DBFFT_E_TIMEOUT" in lines and "SYNC_OK" in lines, r.stdout
+
+
+@pytest.mark.parametrize("shape,B,nmat,threads", [((8, 16, 256), 1, 1, -1), ((16, 8, 128), 3, 1, -1),
+                                                   ((8, 8, 256), 2, 2, -1), ((16, 16, 256), 1, 1, 192),
+                                                   ((8, 16, 128), 2, 1, 192)])
+def test_line_bulk_warp_lines_and_thread_caps_match_oracle(shape, B, nmat, threads):
+    """The warp-lines form (every warp takes its own lines of a 16-line tile through all
+    phases, radix = -1) and a 192-thread cap (more, smaller CTAs), both against the oracle."""
+    dbfft = _dbfft()
+    g = np.random.default_rng(sum(shape) + B + threads)
+    phase = (g.random((nmat,) + shape) < 0.4).astype(np.uint16)
+    E, nu = [1.0, 25.0], [0.3, 0.2]
+    scale = 0.5 + g.random((nmat,) + shape)
+    s = dbfft.Solver(shape, phase, dbfft.iso_phases(E, nu), np.zeros((B, 3, 3)), batch=B, E_scale=scale,
+                     precision=dbfft.DBFFT_MIXED)
+    s.set_pass3_shape(0, 3, threads, 16)
+    u = synth.random_spectrum(shape, 3, 700 + B, batch=B)
+    out, _ = s.apply(torch.from_numpy(u).cuda(), fp32=True)
+    out = out.cpu().numpy()
+    prob = o.Problem(shape)
+    Rm = B // nmat
+    for b in range(B):
+        ref, _ = prob.apply_K(iso_tangent(phase[b // Rm], E, nu, scale[b // Rm]), u[b], np.zeros(0))
+        assert rel_err(out[b], ref) < FP32_OP, b
+    with pytest.raises(dbfft.DbfftError):  # warp lines need 16-line tiles
+        s.set_pass3_shape(0, 3, -1, 8)
+    s.close()
