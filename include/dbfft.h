@@ -413,7 +413,8 @@ const char* dbfft_tuning(const dbfft_ctx* ctx);
  * `lines` grid lines per CTA moved by bulk copies, each line transformed in
  * place by two register stages (radix: the most threads per CTA, e.g. 192;
  * 0 or 384 for up to 384; -1 for warp lines: every warp takes its own lines
- * of a 16-line tile through all phases). radix: 8 or 16 (FP32), 4
+ * of a 16-line tile through all phases; -2 the same with tiles of 8 lines
+ * (n3 = 256) or 4 lines (n3 = 128), two lines per warp). radix: 8 or 16 (FP32), 4
  * (FP64), or 32 with the plain kernel when n3 <= 256 (FP32) / 64 (FP64):
  * one thread per grid line, or 32 values of a line per thread beyond
  * (FP32) / 4 (FP64); lines: grid lines per CTA (per tile when pipelined;

@@ -1385,10 +1385,11 @@ void tune_pass3(dbfft_ctx* ctx, int pi_, cplx<T>* W) {
         int blbL = 0;
         int blbT = 0;
         if (sizeof(T) == 4 && lb_supported(ctx)) {
-            for (int cap : {384, 192, -1})  // threads per CTA (more, smaller CTAs overlap each other's
-                                              // phases); -1: warp lines (16-line tiles)
+            for (int cap : {384, 192, -1, -2})  // threads per CTA (more, smaller CTAs overlap each
+                                                  // other's phases); -1, -2: warp lines
             for (int L : {2, 4, 6, 8, 12, 16}) {
-                if (cap < 0 && L != 16) continue;
+                if (cap == -1 && L != 16) continue;
+                if (cap == -2 && L != (ctx->n3 == 256 ? 8 : 4)) continue;
                 const long long sm = ax3_lb_smem(ctx->n3, ctx->nc, ctx->RB, ctx->scale != nullptr, L, nlines);
                 if (sm < 0 || sm > 110 * 1024) continue;
                 Ax3Args<T> a3 = ax3_base<T>(ctx, W);
@@ -1588,8 +1589,11 @@ dbfft_status dbfft_set_pass3_shape(dbfft_ctx* ctx, int fp64, int pipelined, int 
                         "line-bulk pass 3: FP32, n3 = 128 or 256, linear / crystal-plasticity / Neo-Hookean model, "
                         "lines even and dividing n1*n2");
         ctx->pipe_on[pi_] = 3;
-        if (radix < 0 && lines != 16) return fail(ctx, DBFFT_E_ARG, "line-bulk warp lines need 16-line tiles");
-        ctx->pipe_R[pi_] = radix < 0 ? -1 : (radix > 0 && radix < 384 ? radix : 0);  // thread cap / warp lines
+        if (radix == -1 && lines != 16) return fail(ctx, DBFFT_E_ARG, "line-bulk warp lines (-1) need 16-line tiles");
+        if (radix == -2 && lines != (ctx->n3 == 256 ? 8 : 4))
+            return fail(ctx, DBFFT_E_ARG, "line-bulk warp lines (-2) need tiles of 8 (n3 = 256) or 4 (n3 = 128) lines");
+        if (radix < -2) return fail(ctx, DBFFT_E_ARG, "line-bulk: radix is a thread cap, -1 or -2");
+        ctx->pipe_R[pi_] = radix < 0 ? radix : (radix > 0 && radix < 384 ? radix : 0);  // thread cap / warp lines
         ctx->pipe_L[pi_] = lines;
         for (int k = 0; k < 2; ++k)
             if (ctx->cg_exec[k]) { cudaGraphExecDestroy(ctx->cg_exec[k]); ctx->cg_exec[k] = nullptr; }

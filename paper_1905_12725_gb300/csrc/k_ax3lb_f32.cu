@@ -6,13 +6,13 @@ namespace dbfft {
 
 namespace {
 
-template <int N3, int NC, int OPK, bool WL>
+template <int N3, int NC, int OPK, int WL>
 cudaError_t lb_launch(const Ax3Args<float>& a, cudaStream_t s) {
     using Plan = LbPlan<N3>;
     const long long nlines = (long long)a.d.n1 * a.d.n2;
     if (a.L < 2 || (a.L & 1) || nlines % a.L != 0 || a.RB < 1 || a.RB > 8 || a.d.B % a.RB != 0)
         return cudaErrorInvalidConfiguration;
-    if (WL && a.L != 16) return cudaErrorInvalidConfiguration;
+    if ((WL == 1 && a.L != 16) || (WL == 2 && a.L != LbShape<N3 / 2>::P)) return cudaErrorInvalidConfiguration;
     const long long smem = Plan::total_bytes(a.L, a.RB, NC, a.scale != nullptr);
     auto kern = k_axis3_lb<N3, NC, OPK, WL>;
     static int max_dyn = -1;
@@ -26,16 +26,23 @@ cudaError_t lb_launch(const Ax3Args<float>& a, cudaStream_t s) {
         max_dyn = md;  // set once the attribute is in place
     }
     if (smem > max_dyn) return cudaErrorInvalidConfiguration;
-    // a.radix: the thread cap (0: 384); -1: warp lines (one warp per P lines, P warps)
-    const int threads = WL ? 32 * LbShape<N3 / 2>::P : lb_threads<N3>(a.RB * NC * a.L, a.radix);
+    // a.radix: the thread cap (0: 384); -1, -2: warp lines (WL = 1: P warps; WL = 2: P / 2 warps)
+    constexpr int P = LbShape<N3 / 2>::P;
+    const int threads = WL == 1 ? 32 * P : (WL == 2 ? 16 * P : lb_threads<N3>(a.RB * NC * a.L, a.radix));
     return launch_k(kern, dim3((unsigned)(nlines / a.L), (unsigned)(a.d.B / a.RB)), dim3(threads), (size_t)smem, s, a);
 }
 
 template <int NC, int OPK>
 cudaError_t lb_n(const Ax3Args<float>& a, cudaStream_t s) {
     switch (a.d.n3) {
-        case 128: return a.radix < 0 ? lb_launch<128, NC, OPK, true>(a, s) : lb_launch<128, NC, OPK, false>(a, s);
-        case 256: return a.radix < 0 ? lb_launch<256, NC, OPK, true>(a, s) : lb_launch<256, NC, OPK, false>(a, s);
+        case 128:
+            return a.radix == -2 ? lb_launch<128, NC, OPK, 2>(a, s)
+                 : a.radix < 0   ? lb_launch<128, NC, OPK, 1>(a, s)
+                                 : lb_launch<128, NC, OPK, 0>(a, s);
+        case 256:
+            return a.radix == -2 ? lb_launch<256, NC, OPK, 2>(a, s)
+                 : a.radix < 0   ? lb_launch<256, NC, OPK, 1>(a, s)
+                                 : lb_launch<256, NC, OPK, 0>(a, s);
         default: return cudaErrorInvalidConfiguration;
     }
 }

@@ -90,13 +90,18 @@ __device__ __forceinline__ int lb_slot(int gi) {
 __device__ __forceinline__ float4 ld4(const float* p) { return *reinterpret_cast<const float4*>(p); }
 __device__ __forceinline__ void st4(float* p, float4 v) { *reinterpret_cast<float4*>(p) = v; }
 
-// WL (warp lines): a tile of 16 lines, P warps; warp w owns the 16 / P lines
-// w + P j and takes them alone through C2R, contraction and R2C (component
-// slots two per round, one per half-warp), so only warp barriers separate the
-// phases. The lines of a half-warp are P line buffers apart, which keeps its
-// 64-bit accesses free of bank conflicts as lb_slot does.
-template <int N3, int NC, int OPK, bool WL = false>
-__global__ void __launch_bounds__(WL ? 256 : 384, 2) k_axis3_lb(Ax3Args<float> a) {
+// WL (warp lines): every warp takes its own lines alone through C2R,
+// contraction and R2C, so only warp barriers separate the phases.
+//  WL = 1: a tile of 16 lines, P warps; warp w owns the 16 / P lines w + P j,
+//          a half-warp does one (rhs, component) slot of each of them per round;
+//          they are P line buffers apart (64 or 32 bytes modulo 128).
+//  WL = 2: a tile of L = P lines, L / 2 warps; warp w owns lines 2w and 2w + 1
+//          (one per half-warp), a half-warp does 16 / P components of its line
+//          per round; those are L line buffers apart (again 64 or 32 bytes
+//          modulo 128). Smaller CTAs, more of them per SM.
+// Either way the 64-bit accesses of a half-warp are free of bank conflicts.
+template <int N3, int NC, int OPK, int WL = 0>
+__global__ void __launch_bounds__(WL == 0 ? 384 : (WL == 1 ? 256 : 128), WL == 2 ? 4 : 2) k_axis3_lb(Ax3Args<float> a) {
     using T = float;
     static_assert(OpInfo<OPK>::apply, "the line-bulk pass serves the CG applications");
     constexpr int M = N3 / 2;
@@ -187,12 +192,20 @@ __global__ void __launch_bounds__(WL ? 256 : 384, 2) k_axis3_lb(Ax3Args<float> a
     const int nslot = RB * NC * L;
     const int ngr = nthr / P;  // line slots per round
     const int warp = t >> 5;
-    const int nrounds = WL ? (RB * NC + 1) / 2 : ((nslot + 15) / 16 * 16 + ngr - 1) / ngr;
+    constexpr int GH = 16 / P;  // line slots (groups) per half-warp
+    const int nrounds = WL == 1   ? (RB * NC + 1) / 2
+                        : WL == 2 ? (RB * NC + GH - 1) / GH
+                                  : ((nslot + 15) / 16 * 16 + ngr - 1) / ngr;
     // slot -> (ok, line buffer); the aligned region of an odd slot starts 8 bytes in
     auto slot_of = [&](int rd, bool& ok, int& sig) {
-        if constexpr (WL) {
+        if constexpr (WL == 1) {
             const int cs = 2 * rd + (lane >> 4);            // (rhs, component) slot of this half-warp
             const int ll = warp + P * ((lane & 15) / P);    // one of the warp's lines
+            sig = cs * L + ll;
+            ok = cs < RB * NC && !((done_mask >> (cs / NC)) & 1u);
+        } else if constexpr (WL == 2) {
+            const int cs = GH * rd + (lane & 15) / P;       // one of this half-warp's components
+            const int ll = 2 * warp + (lane >> 4);          // the half-warp's line
             sig = cs * L + ll;
             ok = cs < RB * NC && !((done_mask >> (cs / NC)) & 1u);
         } else {
@@ -202,7 +215,7 @@ __global__ void __launch_bounds__(WL ? 256 : 384, 2) k_axis3_lb(Ax3Args<float> a
         if (!ok) sig = 0;
     };
     auto phase_sync = [&]() {
-        if constexpr (WL) __syncwarp();
+        if constexpr (WL != 0) __syncwarp();
         else __syncthreads();
     };
 
@@ -282,9 +295,11 @@ __global__ void __launch_bounds__(WL ? 256 : 384, 2) k_axis3_lb(Ax3Args<float> a
         const int CS = 2 * L * H;  // floats between the components of one line
         T en = T(0);
         // all lines of the tile (block-strided), or the warp's own 16 / P lines (lane-strided)
-        const int it0 = WL ? lane : t, itn = WL ? (16 / P) * Q4 : L * Q4, its = WL ? 32 : nthr;
+        const int it0 = WL ? lane : t, itn = WL == 1 ? (16 / P) * Q4 : (WL == 2 ? 2 * Q4 : L * Q4);
+        const int its = WL ? 32 : nthr;
         for (int it = it0; it < itn; it += its) {
-            const int ll = WL ? warp + P * (it / Q4) : it / Q4, x4 = (it % Q4) * 4;
+            const int ll = WL == 1 ? warp + P * (it / Q4) : (WL == 2 ? 2 * warp + it / Q4 : it / Q4);
+            const int x4 = (it % Q4) * 4;
             const uint2 pp = *reinterpret_cast<const uint2*>(phs + ll * N3 + x4);
             const float4 s4 = has_scale ? ld4(scs + ll * N3 + x4) : make_float4(1.f, 1.f, 1.f, 1.f);
             const int sig0 = (rr * NC) * L + ll;  // component 0; all components share its parity

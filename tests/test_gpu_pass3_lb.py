@@ -193,10 +193,11 @@ def test_line_bulk_bounded_wait_returns_timeout():
 
 @pytest.mark.parametrize("shape,B,nmat,threads", [((8, 16, 256), 1, 1, -1), ((16, 8, 128), 3, 1, -1),
                                                    ((8, 8, 256), 2, 2, -1), ((16, 16, 256), 1, 1, 192),
-                                                   ((8, 16, 128), 2, 1, 192)])
+                                                   ((8, 16, 128), 2, 1, 192), ((8, 16, 256), 1, 1, -2),
+                                                   ((16, 8, 128), 3, 1, -2), ((8, 8, 256), 2, 2, -2)])
 def test_line_bulk_warp_lines_and_thread_caps_match_oracle(shape, B, nmat, threads):
-    """The warp-lines form (every warp takes its own lines of a 16-line tile through all
-    phases, radix = -1) and a 192-thread cap (more, smaller CTAs), both against the oracle."""
+    """The warp-lines forms (every warp takes its own lines through all phases: radix -1 with
+    16-line tiles, -2 with two lines per warp) and a 192-thread cap, against the oracle."""
     dbfft = _dbfft()
     g = np.random.default_rng(sum(shape) + B + threads)
     phase = (g.random((nmat,) + shape) < 0.4).astype(np.uint16)
@@ -204,7 +205,8 @@ def test_line_bulk_warp_lines_and_thread_caps_match_oracle(shape, B, nmat, threa
     scale = 0.5 + g.random((nmat,) + shape)
     s = dbfft.Solver(shape, phase, dbfft.iso_phases(E, nu), np.zeros((B, 3, 3)), batch=B, E_scale=scale,
                      precision=dbfft.DBFFT_MIXED)
-    s.set_pass3_shape(0, 3, threads, 16)
+    lines = (8 if shape[2] == 256 else 4) if threads == -2 else 16
+    s.set_pass3_shape(0, 3, threads, lines)
     u = synth.random_spectrum(shape, 3, 700 + B, batch=B)
     out, _ = s.apply(torch.from_numpy(u).cuda(), fp32=True)
     out = out.cpu().numpy()
