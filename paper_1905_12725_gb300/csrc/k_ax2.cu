@@ -21,6 +21,9 @@ static cudaError_t fft_n(Ax2Args<T> a, int axis, cudaStream_t s) {
         a.ncols = (long long)a.d.B * a.d.nc * a.d.n1 * a.d.h;
         a.cols_per_b = (long long)a.d.nc * a.d.n1 * a.d.h;
     }
+    if (a.ncols >= (1LL << 32) - 512) return cudaErrorInvalidValue;  // 32-bit column indices
+    a.div_inner = make_fastdiv((unsigned)a.inner);
+    a.div_cpb = make_fastdiv((unsigned)a.cols_per_b);
     const dim3 block(TW, P);
     const dim3 grid((unsigned)((a.ncols + TW - 1) / TW));
     const size_t smem = (ColFFT<T, N, R, DIR>::NST > 1) ? (size_t)N * TW * sizeof(cplx<T>) : 0;

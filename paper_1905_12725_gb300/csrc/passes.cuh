@@ -285,6 +285,7 @@ struct Ax2Args {
     long long inner;    // stride of the transformed axis (in entries)
     long long ncols;    // columns in total
     long long cols_per_b;
+    FastDiv div_inner, div_cpb;  // by inner and cols_per_b (set with them; ncols < 2^32)
     int tw_ax1, tw_ax2; // columns per CTA along axis 1 / axis 2 (0: default)
 };
 
@@ -298,20 +299,20 @@ __global__ void __launch_bounds__(512) k_fft_strided(Ax2Args<T> a) {
     cplx<T>* sm = reinterpret_cast<cplx<T>*>(smraw);
     const int TW = blockDim.x;
     const int w = threadIdx.x, p = threadIdx.y;
-    const long long c0 = (long long)blockIdx.x * TW;
+    const unsigned c0 = blockIdx.x * (unsigned)TW;  // columns < 2^32 (checked by the launcher)
     if (a.cg) {  // skip tiles whose right-hand sides are all finished
-        const int bfirst = (int)(c0 / a.cols_per_b);
-        const long long clast = min(c0 + TW, a.ncols) - 1;
-        const int blast = (int)(clast / a.cols_per_b);
+        const int bfirst = (int)fastdiv(c0, a.div_cpb);
+        const unsigned clast = (unsigned)min((long long)c0 + TW, a.ncols) - 1u;
+        const int blast = (int)fastdiv(clast, a.div_cpb);
         bool all_done = true;
         for (int bb = bfirst; bb <= blast; ++bb) all_done &= (a.cg[bb].done != 0);
         if (all_done) return;
     }
-    const long long col = c0 + w;
+    const unsigned col = c0 + w;
     const bool valid = col < a.ncols;
-    const long long outer = valid ? col / a.inner : 0;
-    const long long in = valid ? col - outer * a.inner : 0;
-    const long long base = outer * (long long)N * a.inner + in;
+    const unsigned outer = valid ? fastdiv(col, a.div_inner) : 0u;
+    const unsigned in = valid ? col - outer * a.div_inner.d : 0u;
+    const long long base = (long long)outer * N * a.inner + in;
     cplx<T> v[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) v[r] = valid ? ldc(a.W + base + (long long)(p + r * P) * a.inner) : zero_c<T>();

@@ -76,7 +76,7 @@ def test_cuda_sources_include_nothing_from_the_oracle():
 def test_oracle_is_imported_only_by_the_smoke_check_and_the_cpu_baseline():
     expected = {
         os.path.join(ROOT, "__graft_entry__.py"): {"smoke"},
-        os.path.join(ROOT, "bench.py"): {"oracle_sample"},
+        os.path.join(ROOT, "bench.py"): {"oracle_sample", "_oracle_rhs_job"},  # the CPU baseline (1 core, all cores)
     }
     for path, funcs in expected.items():
         users = {f for mod, f in _imports(path) if mod.split(".")[0] == "oracle"}
