@@ -112,7 +112,7 @@ __global__ void __launch_bounds__(WL == 0 ? 384 : (WL == 1 ? 256 : 128), WL == 2
     static_assert(R * P == M && G * P == R && (G == 2 || G == 4), "supported line shapes");
     using Plan = LbPlan<N3>;
     extern __shared__ __align__(16) unsigned char smlb[];
-    __shared__ double red[32 * 8];
+    __shared__ double red[32];  // block_sum<1> scratch (kept small: four CTAs per SM at 8-line tiles)
     __shared__ double s_eacc[8];
     __shared__ float s_macro[8 * 9];
     __shared__ bool is_last;

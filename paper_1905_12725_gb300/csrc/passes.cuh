@@ -326,6 +326,7 @@ __global__ void __launch_bounds__(512) k_fft_strided(Ax2Args<T> a) {
 // ------------------------------------------------------------------ pass 5
 enum { AX5_PLAIN = 0, AX5_CG = 1, AX5_RESID = 2 };
 
+
 template <typename T>
 struct Ax1FwdArgs {
     Dims d;
