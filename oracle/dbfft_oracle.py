@@ -937,20 +937,23 @@ def finite_cp_update(cp: CrystalPlasticity, S_full, grain, F, Fp_old, T_guess, d
     e_tr = np.einsum("mij,vij->vm", mandel_basis(), E_tr)
     T, C_tan, dep, _ = cp.update(grain, e_tr, np.zeros((V, 6)), T_guess, dt)
     tau = np.einsum("vam,vm->va", cp.P[grain], T)
-    gd, _ = cp.rates(tau)
-    Fp = (np.eye(3) + dt * np.einsum("va,vaij->vij", gd, S_full[grain])) @ Fp_old
+    gd, dgd = cp.rates(tau)
+    Mm = np.eye(3) + dt * np.einsum("va,vaij->vij", gd, S_full[grain])
+    Fp = Mm @ Fp_old
     Fpi = np.linalg.inv(Fp)
     Tm = np.einsum("mij,vm->vij", mandel_basis(), T)
     P = F @ Fpi @ Tm @ np.swapaxes(Fpi, 1, 2)
     B = a @ Tm @ np.swapaxes(a, 1, 2)
-    return P, Fp, T, (Fe_tr, a, B, C_tan)
+    # for the consistent tangent: N = M^-1 and D = dM / dT = sum_a dt gdot'_a S_a (x) P_a
+    D = dt * np.einsum("va,vaij,vam->vijm", dgd, S_full[grain], cp.P[grain])
+    return P, Fp, T, (Fe_tr, a, B, C_tan, np.linalg.inv(Mm), D, Tm)
 
 
 def finite_cp_tangent(data):
     """K_iJkL of dP = G B + Fe_tr (C_tan : sym(Fe_tr^T G a)) a^T: the derivative of
     F a T(E(F)) a^T with the plastic state a = Fp_old^-1 held fixed (R18). It is
     major-symmetric. Returns [3,3,3,3,V]."""
-    Fe_tr, a, B, C_tan = data
+    Fe_tr, a, B, C_tan = data[:4]
     V = Fe_tr.shape[0]
     K = np.zeros((V, 3, 3, 3, 3))
     Bm = mandel_basis()
@@ -963,8 +966,38 @@ def finite_cp_tangent(data):
     return np.moveaxis(K, 0, -1)
 
 
-def finite_cp_material(cp: CrystalPlasticity, quats, grain_field, dt):
-    """Material closure of the finite-strain model; state = (Fp [V,3,3], T [V,6])."""
+def finite_cp_tangent_consistent(data, symmetric=True):
+    """The consistent tangent K_iJkL = dP_iJ / dF_kL of the finite-strain update (R18b),
+    with the plastic flow of the step active: P = F a N T N^T a^T, N = M^-1,
+    M = I + sum_a dt gdot_a(T) S_a, T(E_tr(F)) with dT = C_tan : sym(Fe_tr^T dF a),
+    dM = D : dT. So
+        dP = dF a N T N^T a^T + sum_m dT_m X_m,
+        X_m = Fe B_m (aN)^T - Fe D_m N T (aN)^T - Fe T N^T D_m^T (aN)^T,  Fe = F a N,
+    with B_m the Mandel basis and D_m = D[..., m]; dT_m = sum_n C_tan,mn Fe_tr B_n a^T : dF.
+    It is not major-symmetric; symmetric=True returns (K + K^T)/2 over (iJ) <-> (kL),
+    the form PCG needs (R11). Returns [3,3,3,3,V]."""
+    Fe_tr, a, B, C_tan, N, D, Tm = data
+    V = Fe_tr.shape[0]
+    Bm = mandel_basis()
+    aN = a @ N
+    Fe = Fe_tr @ N  # F a N
+    Bc = aN @ Tm @ np.swapaxes(aN, 1, 2)
+    NT = N @ Tm
+    K = np.einsum("ik,vLJ->viJkL", np.eye(3), Bc)
+    X = (np.einsum("viP,mPQ,vJQ->vmiJ", Fe, Bm, aN)
+         - np.einsum("viP,vPQm,vQR,vJR->vmiJ", Fe, D, NT, aN)
+         - np.einsum("viP,vPQ,vRQ,vSRm,vJS->vmiJ", Fe, Tm, N, D, aN))
+    Y = np.einsum("vmn,vkP,nPQ,vLQ->vmkL", C_tan, Fe_tr, Bm, a)
+    K += np.einsum("vmiJ,vmkL->viJkL", X, Y)
+    if symmetric:
+        K = 0.5 * (K + np.einsum("viJkL->vkLiJ", K))
+    return np.moveaxis(K, 0, -1)
+
+
+def finite_cp_material(cp: CrystalPlasticity, quats, grain_field, dt, tangent="held"):
+    """Material closure of the finite-strain model; state = (Fp [V,3,3], T [V,6]).
+    tangent: "held" (R18, the plastic state held; the library's tangent) or
+    "consistent" (the symmetrised consistent tangent, finite_cp_tangent_consistent)."""
     g = grain_field.reshape(-1)
     S_full = schmid_full(cp, quats)
 
@@ -976,7 +1009,8 @@ def finite_cp_material(cp: CrystalPlasticity, quats, grain_field, dt):
         Fp_old, T_old = state
         P, Fp, T, data = finite_cp_update(cp, S_full, g, Fv, Fp_old, T_old, dt)
         Pf = np.moveaxis(P, 0, -1).reshape((3, 3) + grain_field.shape)
-        K = finite_cp_tangent(data).reshape((3, 3, 3, 3) + grain_field.shape)
+        Kv = finite_cp_tangent_consistent(data) if tangent == "consistent" else finite_cp_tangent(data)
+        K = Kv.reshape((3, 3, 3, 3) + grain_field.shape)
         return Pf, FullTangent(K), (Fp, T)
     return material
 

@@ -292,7 +292,8 @@ def test_finite_cp_tangent_is_the_derivative_with_the_plastic_state_held():
     h = 1e-7
 
     def ptilde(Fx):
-        _, _, T, (Fe_tr, a, _, _) = o.finite_cp_update(cp, S, g, Fx, Fp0, T0, 0.5)
+        _, _, T, data_x = o.finite_cp_update(cp, S, g, Fx, Fp0, T0, 0.5)
+        Fe_tr, a = data_x[0], data_x[1]
         return Fe_tr @ np.einsum("mij,vm->vij", o.mandel_basis(), T) @ np.swapaxes(a, 1, 2)
 
     fd = (ptilde(F + h * G) - ptilde(F - h * G)) / (2 * h)
@@ -864,3 +865,41 @@ def test_cp_adjoint_in_the_elastic_limit_satisfies_the_euler_identity():
     g = np.array([[1.0, 0.2, 0.0], [0.2, -0.4, 0.1], [0.0, 0.1, 0.3]])
     dJ, J, _ = o.cp_adjoint_increments(prob, cp, grains, 0.5, targets, g)
     assert abs(dJ.sum() - J) < 1e-9 * abs(J)
+
+
+def test_finite_cp_consistent_tangent_by_finite_differences():
+    """The consistent tangent of the finite-strain crystal update with the plastic flow
+    of the step active (dM = D : dT, M = I + sum_a dt gdot_a S_a): central differences of
+    P(F) at a plastic state agree to 1e-7, where the tangent with the plastic state held
+    (R18) is off by about 1e-2; the major asymmetry of the consistent tangent is small."""
+    rng = synth.Xoshiro256ss(5)
+    quats = synth.uniform_quaternions(3, rng)
+    cp = o.CrystalPlasticity(quats)
+    S_full = o.schmid_full(cp, quats)
+    g = np.array([0, 1, 2])
+    base = np.array([[4e-3, 1e-3, 0.0], [0.5e-3, -1e-3, 0.2e-3], [0.0, 0.3e-3, -1.5e-3]])
+    F = np.eye(3)[None] + base[None] * np.array([1.0, 1.3, 0.7])[:, None, None]
+    Fp_old = np.eye(3)[None].repeat(3, 0) + 1e-3 * np.array([[0.5, 0.2, 0.0], [0.1, -0.3, 0.0], [0.0, 0.1, -0.2]])
+    dt = 0.5
+    P, Fp, T, data = o.finite_cp_update(cp, S_full, g, F, Fp_old, np.zeros((3, 6)), dt)
+    assert np.abs(Fp - Fp_old).max() > 1e-3  # the step flows plastically
+    K = o.finite_cp_tangent_consistent(data, symmetric=False)
+    Kh = o.finite_cp_tangent(data)
+    h = 1e-7
+    err = err_h = mx = 0.0
+    for k in range(3):
+        for L in range(3):
+            Fa, Fb = F.copy(), F.copy()
+            Fa[:, k, L] += h
+            Fb[:, k, L] -= h
+            fd = (o.finite_cp_update(cp, S_full, g, Fa, Fp_old, T, dt)[0]
+                  - o.finite_cp_update(cp, S_full, g, Fb, Fp_old, T, dt)[0]) / (2 * h)
+            err = max(err, np.abs(fd - np.moveaxis(K[:, :, k, L, :], -1, 0)).max())
+            err_h = max(err_h, np.abs(fd - np.moveaxis(Kh[:, :, k, L, :], -1, 0)).max())
+            mx = max(mx, np.abs(fd).max())
+    assert err < 1e-7 * mx
+    assert err_h > 1e-3 * mx
+    asym = np.abs(K - np.einsum("iJkLv->kLiJv", K)).max() / np.abs(K).max()
+    assert asym < 0.02
+    Ks = o.finite_cp_tangent_consistent(data)
+    assert np.allclose(Ks, np.einsum("iJkLv->kLiJv", Ks))
