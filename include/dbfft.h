@@ -408,13 +408,13 @@ const char* dbfft_tuning(const dbfft_ctx* ctx);
  * 1 = persistent CTAs looping over tiles of `lines` grid lines with two
  * shared-memory stages filled and drained by bulk copies; 2 = the same with
  * one stage (half the shared memory per CTA); 3 = the line-bulk pass of the
- * FP32 applications on lines of n3 = 128 or 256 values (linear isotropic,
+ * FP32 applications on lines of n3 = 64, 128 or 256 values (linear isotropic,
  * small-strain crystal-plasticity and Neo-Hookean models): one tile of
  * `lines` grid lines per CTA moved by bulk copies, each line transformed in
  * place by two register stages (radix: the most threads per CTA, e.g. 192;
  * 0 or 384 for up to 384; -1 for warp lines: every warp takes its own lines
  * of a 16-line tile through all phases; -2 the same with tiles of 8 lines
- * (n3 = 256) or 4 lines (n3 = 128), two lines per warp). radix: 8 or 16 (FP32), 4
+ * (n3 = 256) or 4 lines (n3 = 64, 128), two lines per warp). radix: 8 or 16 (FP32), 4
  * (FP64), or 32 with the plain kernel when n3 <= 256 (FP32) / 64 (FP64):
  * one thread per grid line, or 32 values of a line per thread beyond
  * (FP32) / 4 (FP64); lines: grid lines per CTA (per tile when pipelined;
@@ -423,6 +423,18 @@ const char* dbfft_tuning(const dbfft_ctx* ctx);
  * not depend on the shape beyond floating-point reassociation.
  */
 dbfft_status dbfft_set_pass3_shape(dbfft_ctx* ctx, int fp64, int pipelined, int radix, int lines);
+
+/* Right-hand sides per CTA of the line-bulk pass 3 (pipelined = 3 above; an
+ * execution choice, no counterpart in the paper). rhs: 0 for the context's
+ * default group (the largest divisor of the right-hand sides per material map,
+ * at most 8, that the plain pass fits in 256 threads), else 1 to 8 dividing the
+ * right-hand sides per material map: fewer per CTA give more, smaller CTAs.
+ * dbfft_autotune sets it with the line-bulk shape. Returns DBFFT_E_ARG for a
+ * value that does not divide, or (when the line-bulk pass is in use) a tile
+ * that no longer fits in shared memory; results do not depend on it beyond
+ * floating-point reassociation of the curvature sums.
+ */
+dbfft_status dbfft_set_pass3_rhs_group(dbfft_ctx* ctx, int rhs);
 
 /*
  * Refresh policy of the preconditioner's reference stiffness for the

@@ -171,6 +171,7 @@ struct dbfft_ctx {
     int fft_tw[2][2] = {{0, 0}, {0, 0}};  // [precision][axis 1, axis 2]
     // pipelined pass 3 for the CG applications: [precision] on/off, radix, lines per tile
     int pipe_on[2] = {0, 0}, pipe_R[2] = {8, 4}, pipe_L[2] = {0, 0};
+    int lb_RB = 0;  // right-hand sides per CTA of the line-bulk pass (0: RB)
     std::string tune_note;
 
     // ---- inner PCG as one CUDA graph (WHILE node), per inner precision
@@ -736,6 +737,7 @@ void apply_shape(const dbfft_ctx* ctx, Ax3Args<T>& a) {
         a.pipe = ctx->pipe_on[pi_];
         a.radix = ctx->pipe_R[pi_];
         a.L = ctx->pipe_L[pi_];
+        if (a.pipe == 3 && ctx->lb_RB > 0) a.RB = ctx->lb_RB;
     }
 }
 
@@ -1306,10 +1308,10 @@ float time_launch(dbfft_ctx* ctx, F&& f) {
 }
 
 // The line-bulk pass 3 serves the FP32 applications of the linear, small-strain
-// crystal-plasticity and Neo-Hookean models on lines of 128 or 256 values.
+// crystal-plasticity and Neo-Hookean models on lines of 64, 128 or 256 values.
 bool lb_supported(const dbfft_ctx* ctx) {
     const int opk = opk_apply(ctx);
-    return (ctx->n3 == 128 || ctx->n3 == 256) && (opk == OP_ISO || opk == OP_CP_APPLY || opk == OP_NH_APPLY);
+    return (ctx->n3 == 64 || ctx->n3 == 128 || ctx->n3 == 256) && (opk == OP_ISO || opk == OP_CP_APPLY || opk == OP_NH_APPLY);
 }
 
 template <typename T>
@@ -1380,22 +1382,26 @@ void tune_pass3(dbfft_ctx* ctx, int pi_, cplx<T>* W) {
                 }
             }
         }
-        // the line-bulk pass (FP32 applications on lines of 128 or 256 values)
+        // the line-bulk pass (FP32 applications on lines of 64, 128 or 256 values)
         float blb = 1e30f;
         int blbL = 0;
         int blbT = 0;
+        int blbB = 0;
         if (sizeof(T) == 4 && lb_supported(ctx)) {
+            for (int rb = std::min(ctx->Rm, 8); rb >= 1; --rb)  // right-hand sides per CTA
             for (int cap : {384, 192, -1, -2})  // threads per CTA (more, smaller CTAs overlap each
                                                   // other's phases); -1, -2: warp lines
             for (int L : {2, 4, 6, 8, 12, 16}) {
+                if (ctx->Rm % rb != 0) continue;
                 if (cap == -1 && L != 16) continue;
                 if (cap == -2 && L != (ctx->n3 == 256 ? 8 : 4)) continue;
-                const long long sm = ax3_lb_smem(ctx->n3, ctx->nc, ctx->RB, ctx->scale != nullptr, L, nlines);
+                const long long sm = ax3_lb_smem(ctx->n3, ctx->nc, rb, ctx->scale != nullptr, L, nlines);
                 if (sm < 0 || sm > 110 * 1024) continue;
                 Ax3Args<T> a3 = ax3_base<T>(ctx, W);
                 a3.pipe = 3;
                 a3.radix = cap;
                 a3.L = L;
+                a3.RB = rb;
                 if constexpr (sizeof(T) == 4) a3.macroW = ctx->macroWf;
                 else a3.macroW = ctx->macroW;
                 a3.tan_in = reinterpret_cast<const T*>(ctx->tan);
@@ -1404,6 +1410,7 @@ void tune_pass3(dbfft_ctx* ctx, int pi_, cplx<T>* W) {
                     blb = ms;
                     blbL = L;
                     blbT = cap;
+                    blbB = rb;
                 }
             }
             if (blbL > 0 && blb < bp) {
@@ -1416,12 +1423,14 @@ void tune_pass3(dbfft_ctx* ctx, int pi_, cplx<T>* W) {
         ctx->pipe_on[pi_] = (bpL > 0 && bp < best) ? bpS : 0;
         ctx->pipe_R[pi_] = bpR;
         ctx->pipe_L[pi_] = bpL;
+        if (sizeof(T) == 4) ctx->lb_RB = ctx->pipe_on[pi_] == 3 ? blbB : 0;
         std::snprintf(buf, sizeof(buf), "pass3 bulk-copy %s radix %d lines %d (%.4f ms)%s; ",
                       bpS == 3 ? "line-bulk" : bpS == 2 ? "one-stage" : "two-stage", bpR, bpL, bp,
                       ctx->pipe_on[pi_] ? " used" : "");
         ctx->tune_note += buf;
         if (blbL > 0) {
-            std::snprintf(buf, sizeof(buf), "pass3 line-bulk lines %d threads<=%d (%.4f ms); ", blbL, blbT, blb);
+            std::snprintf(buf, sizeof(buf), "pass3 line-bulk lines %d threads<=%d rhs/CTA %d (%.4f ms); ", blbL, blbT,
+                          blbB, blb);
             ctx->tune_note += buf;
         }
     }
@@ -1463,7 +1472,7 @@ std::string tune_key(const dbfft_ctx* ctx) {
     for (char& c : name)
         if (c == ' ') c = '_';
     char buf[256];
-    std::snprintf(buf, sizeof(buf), "%s n=%dx%dx%d B=%d RB=%d nc=%d prec=%d model=%d scale=%d", name.c_str(), ctx->n1,
+    std::snprintf(buf, sizeof(buf), "v2 %s n=%dx%dx%d B=%d RB=%d nc=%d prec=%d model=%d scale=%d", name.c_str(), ctx->n1,
                   ctx->n2, ctx->n3, ctx->B, ctx->RB, ctx->nc, ctx->prec, ctx->model, ctx->scale != nullptr ? 1 : 0);
     return buf;
 }
@@ -1518,12 +1527,12 @@ dbfft_status dbfft_autotune(dbfft_ctx* ctx, const char* cache_path) {
                 std::string ln(line);
                 if (ln.compare(0, key.size(), key) != 0 || ln.size() <= key.size() || ln[key.size()] != '|') continue;
                 const char* p = ln.c_str() + key.size() + 1;
-                int v[2][7];
+                int v[2][8];
                 int n = 0;
                 for (size_t k = 0; k < pis.size(); ++k) {
                     int used = 0;
-                    if (std::sscanf(p, "%d %d %d %d %d %d %d%n", &v[k][0], &v[k][1], &v[k][2], &v[k][3], &v[k][4],
-                                    &v[k][5], &v[k][6], &used) != 7)
+                    if (std::sscanf(p, "%d %d %d %d %d %d %d %d%n", &v[k][0], &v[k][1], &v[k][2], &v[k][3], &v[k][4],
+                                    &v[k][5], &v[k][6], &v[k][7], &used) != 8)
                         break;
                     p += used;
                     ++n;
@@ -1538,8 +1547,23 @@ dbfft_status dbfft_autotune(dbfft_ctx* ctx, const char* cache_path) {
                     ctx->pipe_on[pi_] = v[k][4];
                     ctx->pipe_R[pi_] = v[k][5];
                     ctx->pipe_L[pi_] = v[k][6];
+                    if (pi_ == 0) ctx->lb_RB = v[k][7];
                 }
-                ctx->tune_note = "from cache";
+                ctx->tune_note = "from cache:";
+                for (int pi_ : pis) {  // the shapes in force, as the tuner reports them
+                    char b[160];
+                    std::snprintf(b, sizeof(b), " [%s] pass3 %s radix %d lines %d rhs/CTA %d, fft tiles %d/%d;",
+                                  pi_ ? "FP64" : "FP32",
+                                  ctx->pipe_on[pi_] == 3   ? "line-bulk"
+                                  : ctx->pipe_on[pi_] == 2 ? "bulk-copy one-stage"
+                                  : ctx->pipe_on[pi_] == 1 ? "bulk-copy two-stage"
+                                                           : "plain",
+                                  ctx->pipe_on[pi_] ? ctx->pipe_R[pi_] : ctx->ax3_radix[pi_],
+                                  ctx->pipe_on[pi_] ? ctx->pipe_L[pi_] : ctx->ax3_L[pi_],
+                                  ctx->pipe_on[pi_] == 3 && ctx->lb_RB > 0 ? ctx->lb_RB : ctx->RB,
+                                  ctx->fft_tw[pi_][0], ctx->fft_tw[pi_][1]);
+                    ctx->tune_note += b;
+                }
                 std::fclose(f);
                 drop_graphs();
                 return DBFFT_OK;
@@ -1566,8 +1590,9 @@ dbfft_status dbfft_autotune(dbfft_ctx* ctx, const char* cache_path) {
         if (FILE* f = std::fopen(cache_path, "a")) {
             std::fprintf(f, "%s|", key.c_str());
             for (int pi_ : pis)
-                std::fprintf(f, " %d %d %d %d %d %d %d", ctx->ax3_radix[pi_], ctx->ax3_L[pi_], ctx->fft_tw[pi_][0],
-                             ctx->fft_tw[pi_][1], ctx->pipe_on[pi_], ctx->pipe_R[pi_], ctx->pipe_L[pi_]);
+                std::fprintf(f, " %d %d %d %d %d %d %d %d", ctx->ax3_radix[pi_], ctx->ax3_L[pi_], ctx->fft_tw[pi_][0],
+                             ctx->fft_tw[pi_][1], ctx->pipe_on[pi_], ctx->pipe_R[pi_], ctx->pipe_L[pi_],
+                             pi_ == 0 ? ctx->lb_RB : 0);
             std::fprintf(f, "\n");
             std::fclose(f);
         }
@@ -1583,16 +1608,18 @@ dbfft_status dbfft_set_pass3_shape(dbfft_ctx* ctx, int fp64, int pipelined, int 
     const long long nlines = (long long)ctx->n1 * ctx->n2;
     const int pi_ = dbl ? 1 : 0;
     if (pipelined == 3) {  // line-bulk pass: its transform shape is fixed, radix is ignored
-        const long long sm = ax3_lb_smem(ctx->n3, ctx->nc, ctx->RB, ctx->scale != nullptr, lines, nlines);
+        const int rb = ctx->lb_RB > 0 ? ctx->lb_RB : ctx->RB;
+        const long long sm = ax3_lb_smem(ctx->n3, ctx->nc, rb, ctx->scale != nullptr, lines, nlines);
         if (dbl || !lb_supported(ctx) || sm < 0 || sm > 200 * 1024)
             return fail(ctx, DBFFT_E_ARG,
-                        "line-bulk pass 3: FP32, n3 = 128 or 256, linear / crystal-plasticity / Neo-Hookean model, "
-                        "lines even and dividing n1*n2");
-        ctx->pipe_on[pi_] = 3;
+                        "line-bulk pass 3: FP32, n3 = 64, 128 or 256, linear / crystal-plasticity / Neo-Hookean "
+                        "model, lines even and dividing n1*n2");
         if (radix == -1 && lines != 16) return fail(ctx, DBFFT_E_ARG, "line-bulk warp lines (-1) need 16-line tiles");
         if (radix == -2 && lines != (ctx->n3 == 256 ? 8 : 4))
-            return fail(ctx, DBFFT_E_ARG, "line-bulk warp lines (-2) need tiles of 8 (n3 = 256) or 4 (n3 = 128) lines");
+            return fail(ctx, DBFFT_E_ARG,
+                        "line-bulk warp lines (-2) need tiles of 8 (n3 = 256) or 4 (n3 = 64, 128) lines");
         if (radix < -2) return fail(ctx, DBFFT_E_ARG, "line-bulk: radix is a thread cap, -1 or -2");
+        ctx->pipe_on[pi_] = 3;
         ctx->pipe_R[pi_] = radix < 0 ? radix : (radix > 0 && radix < 384 ? radix : 0);  // thread cap / warp lines
         ctx->pipe_L[pi_] = lines;
         for (int k = 0; k < 2; ++k)
@@ -1619,6 +1646,20 @@ dbfft_status dbfft_set_pass3_shape(dbfft_ctx* ctx, int fp64, int pipelined, int 
         ctx->ax3_L[pi_] = lines;
     }
     for (int k = 0; k < 2; ++k)  // graphs captured with the old shape
+        if (ctx->cg_exec[k]) { cudaGraphExecDestroy(ctx->cg_exec[k]); ctx->cg_exec[k] = nullptr; }
+    return DBFFT_OK;
+}
+
+dbfft_status dbfft_set_pass3_rhs_group(dbfft_ctx* ctx, int rhs) {
+    if (!ctx) return DBFFT_E_ARG;
+    if (rhs < 0 || rhs > 8 || (rhs > 0 && ctx->Rm % rhs != 0))
+        return fail(ctx, DBFFT_E_ARG, "line-bulk right-hand sides per CTA: 0, or 1 to 8 dividing those of a material map");
+    if (rhs > 0 && ctx->pipe_on[0] == 3 &&
+        ax3_lb_smem(ctx->n3, ctx->nc, rhs, ctx->scale != nullptr, ctx->pipe_L[0], (long long)ctx->n1 * ctx->n2) >
+            200 * 1024)
+        return fail(ctx, DBFFT_E_ARG, "line-bulk tile does not fit in shared memory with that many right-hand sides");
+    ctx->lb_RB = rhs;
+    for (int k = 0; k < 2; ++k)
         if (ctx->cg_exec[k]) { cudaGraphExecDestroy(ctx->cg_exec[k]); ctx->cg_exec[k] = nullptr; }
     return DBFFT_OK;
 }

@@ -1,4 +1,4 @@
-// Line-bulk pass 3 (FP32 CG applications, n3 = 128 and 256): launchers.
+// Line-bulk pass 3 (FP32 CG applications, n3 = 64, 128 and 256): launchers.
 #include "launch.h"
 #include "pass3_lb.cuh"
 
@@ -35,6 +35,10 @@ cudaError_t lb_launch(const Ax3Args<float>& a, cudaStream_t s) {
 template <int NC, int OPK>
 cudaError_t lb_n(const Ax3Args<float>& a, cudaStream_t s) {
     switch (a.d.n3) {
+        case 64:
+            return a.radix == -2 ? lb_launch<64, NC, OPK, 2>(a, s)
+                 : a.radix < 0   ? lb_launch<64, NC, OPK, 1>(a, s)
+                                 : lb_launch<64, NC, OPK, 0>(a, s);
         case 128:
             return a.radix == -2 ? lb_launch<128, NC, OPK, 2>(a, s)
                  : a.radix < 0   ? lb_launch<128, NC, OPK, 1>(a, s)
@@ -62,6 +66,7 @@ long long ax3_lb_smem(int n3, int nc, int rb, bool scale, int L, long long nline
     if (L < 2 || (L & 1) || nlines % L != 0 || rb < 1 || rb > 8 || (nc != 6 && nc != 9)) return -1;
     if (lb_threads<256>(rb * nc * L) > 384) return -1;
     switch (n3) {
+        case 64: return LbPlan<64>::total_bytes(L, rb, nc, scale);
         case 128: return LbPlan<128>::total_bytes(L, rb, nc, scale);
         case 256: return LbPlan<256>::total_bytes(L, rb, nc, scale);
         default: return -1;

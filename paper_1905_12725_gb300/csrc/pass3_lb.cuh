@@ -1,5 +1,5 @@
 // pass3_lb.cuh -- axis-3 pass of the FP32 CG operator applications for the
-// long lines (n3 = 128, 256), built to cut the instructions per voxel:
+// long lines (n3 = 64, 128, 256), built to cut the instructions per voxel:
 //
 //  * data movement by the copy engine only: for one (right-hand side,
 //    component) the half-spectrum lines of a tile of L grid lines are
@@ -15,13 +15,14 @@
 //    per thread (k1 = G p + g); the forward transform runs the same stages in
 //    the transposed order. The exchange moves G complex values (16 or 32
 //    bytes) per access through an XOR-swizzled chunk layout that keeps the
-//    8 threads of a line on distinct banks;
+//    P threads of a line on distinct banks;
 //  * twiddles are registers: the stage-B factors W_M^(n2 k1) of a thread are
 //    read once per CTA, the pre/post factors e^(-2 pi i k / n3) of
 //    k = p + P r are one per-thread value times compile-time constants;
 //  * the per-voxel operation reads and writes four voxels per access;
-//  * the 2 (or 4) line slots that share a half-warp sit 8 (or 4) line
-//    buffers apart, i.e. 64 (or 32) bytes apart modulo 128, so the 64-bit
+//  * the 2 (n3 = 256) or 4 (n3 = 64, 128) line slots that share a half-warp
+//    sit 8 (or 4) line buffers apart; a line buffer is 8 bytes long modulo
+//    128, so they are 64 (or 32) bytes apart modulo 128 and the 64-bit
 //    accesses of the C2R/R2C pre- and post-processing are free of bank
 //    conflicts.
 //
@@ -45,6 +46,7 @@ namespace dbfft {
 template <int M> struct LbShape;
 template <> struct LbShape<128> { static constexpr int R = 16, P = 8; };
 template <> struct LbShape<64> { static constexpr int R = 16, P = 4; };
+template <> struct LbShape<32> { static constexpr int R = 8, P = 4; };
 
 // Shared-memory plan of one CTA (bytes), shared by host and device:
 // [RB][NC][L] line buffers of M + 1 complex values, phase ids [L][N3],

@@ -75,7 +75,8 @@ EXPORTS = ["dbfft_create", "dbfft_apply", "dbfft_solve_increment", "dbfft_homoge
            "dbfft_homogenized_tangent", "dbfft_adjoint", "dbfft_get_solution", "dbfft_device_bytes",
            "dbfft_destroy", "dbfft_last_error", "dbfft_status_string", "dbfft_profile",
            "dbfft_profile_read", "dbfft_launch_count", "dbfft_apply_iso_noalloc", "dbfft_autotune",
-           "dbfft_tuning", "dbfft_set_pass3_shape", "dbfft_set_precond_refresh", "dbfft_displacement", "dbfft_compatibility",
+           "dbfft_tuning", "dbfft_set_pass3_shape", "dbfft_set_pass3_rhs_group", "dbfft_set_precond_refresh",
+           "dbfft_displacement", "dbfft_compatibility",
            "dbfft_tangent_sensitivity", "dbfft_set_checkpointing", "dbfft_cp_adjoint",
            "dbfft_fp64_fma_rate"]
 
@@ -135,6 +136,8 @@ def load_library(build_if_missing: bool = True):
     lib.dbfft_tuning.restype = C.c_char_p
     lib.dbfft_set_pass3_shape.argtypes = [vp, ip, ip, ip, ip]
     lib.dbfft_set_pass3_shape.restype = ip
+    lib.dbfft_set_pass3_rhs_group.argtypes = [vp, ip]
+    lib.dbfft_set_pass3_rhs_group.restype = ip
     lib.dbfft_set_precond_refresh.argtypes = [vp, ip]
     lib.dbfft_set_precond_refresh.restype = ip
     lib.dbfft_displacement.argtypes = [vp, vp]
@@ -344,6 +347,10 @@ class Solver:
     def set_pass3_shape(self, fp64, pipelined, radix, lines):
         """Fix pass 3's launch shape for one inner precision (dbfft_set_pass3_shape)."""
         self._check(self.lib.dbfft_set_pass3_shape(self.ctx, int(fp64), int(pipelined), int(radix), int(lines)))
+
+    def set_pass3_rhs_group(self, rhs):
+        """Right-hand sides per CTA of the line-bulk pass 3 (dbfft_set_pass3_rhs_group); 0 = default."""
+        self._check(self.lib.dbfft_set_pass3_rhs_group(self.ctx, int(rhs)))
 
     def set_precond_refresh(self, policy):
         """Preconditioner refresh policy of the nonlinear models (dbfft_set_precond_refresh)."""

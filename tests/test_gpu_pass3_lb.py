@@ -1,4 +1,4 @@
-"""The line-bulk pass 3 (FP32 CG applications on lines of n3 = 128 or 256 values).
+"""The line-bulk pass 3 (FP32 CG applications on lines of n3 = 64, 128 or 256 values).
 
 The kernel moves whole tiles by bulk copies and runs each line's half-length
 transform as two register stages with one swizzled exchange (Sec. 2.2,
@@ -40,6 +40,9 @@ CASES = [
     ((8, 16, 128), 1, 1, 16),
     ((8, 8, 128), 2, 2, 4),
     ((16, 8, 128), 3, 1, 8),
+    ((8, 8, 64), 1, 1, 16),
+    ((16, 8, 64), 6, 1, 4),
+    ((8, 8, 64), 6, 6, 2),
 ]
 
 
@@ -68,9 +71,9 @@ def test_line_bulk_pass3_matches_oracle(shape, B, nmat, lines, scaled):
 
 def test_line_bulk_refuses_unsupported_shapes():
     dbfft = _dbfft()
-    s = dbfft.Solver((8, 8, 64), np.zeros((8, 8, 64), np.uint16), dbfft.iso_phases([1.0], [0.3]), np.zeros((1, 3, 3)),
+    s = dbfft.Solver((8, 8, 32), np.zeros((8, 8, 32), np.uint16), dbfft.iso_phases([1.0], [0.3]), np.zeros((1, 3, 3)),
                      precision=dbfft.DBFFT_MIXED)
-    with pytest.raises(dbfft.DbfftError):  # n3 = 64 has no line-bulk kernel
+    with pytest.raises(dbfft.DbfftError):  # n3 = 32 has no line-bulk kernel
         s.set_pass3_shape(0, 3, 0, 8)
     s.close()
     s = dbfft.Solver((8, 8, 128), np.zeros((8, 8, 128), np.uint16), dbfft.iso_phases([1.0], [0.3]),
@@ -81,10 +84,11 @@ def test_line_bulk_refuses_unsupported_shapes():
     s.close()
 
 
-def test_line_bulk_neo_hooke_tangent_matches_oracle():
+@pytest.mark.parametrize("n3", [128, 64])
+def test_line_bulk_neo_hooke_tangent_matches_oracle(n3):
     """Finite strain (nine components): K(F) in FP32 after a constitutive update at a random F."""
     dbfft = _dbfft()
-    shape = (8, 8, 128)
+    shape = (8, 8, n3)
     g = np.random.default_rng(5)
     phase = (g.random(shape) < 0.3).astype(np.uint16)
     mu = np.array([1.0, 20.0])
@@ -105,14 +109,15 @@ def test_line_bulk_neo_hooke_tangent_matches_oracle():
     s.close()
 
 
-def test_line_bulk_crystal_plasticity_tangent_equals_plain_kernel():
+@pytest.mark.parametrize("n3", [256, 64])
+def test_line_bulk_crystal_plasticity_tangent_equals_plain_kernel(n3):
     """Small-strain crystal plasticity: the stored 21-value tangent applied by the
     line-bulk and the plain kernel, after the same constitutive update."""
     dbfft = _dbfft()
-    shape = (8, 8, 256)
+    shape = (8, 8, n3)
     rng = synth.Xoshiro256ss(77)
     grains, _ = synth.periodic_voronoi(8, 6, rng)
-    grains = np.tile(grains, (1, 1, 32))
+    grains = np.tile(grains, (1, 1, n3 // 8))
     quats = synth.uniform_quaternions(6, rng)
     tgt = np.zeros((1, 3, 3))
     tgt[0, 0, 0] = 4e-3  # beyond the elastic limit: the tangent differs from grain to grain and in slip
@@ -128,7 +133,7 @@ def test_line_bulk_crystal_plasticity_tangent_equals_plain_kernel():
     s.close()
 
 
-@pytest.mark.parametrize("shape", [(8, 16, 128), (8, 8, 256)])
+@pytest.mark.parametrize("shape", [(8, 16, 128), (8, 8, 256), (16, 8, 64)])
 def test_pcg_with_line_bulk_pass3_matches_oracle(shape):
     """Mixed-control solves of two right-hand sides (graph-captured inner PCG,
     right-hand sides that stop at different iterations) with the line-bulk pass."""
@@ -194,7 +199,9 @@ def test_line_bulk_bounded_wait_returns_timeout():
 @pytest.mark.parametrize("shape,B,nmat,threads", [((8, 16, 256), 1, 1, -1), ((16, 8, 128), 3, 1, -1),
                                                    ((8, 8, 256), 2, 2, -1), ((16, 16, 256), 1, 1, 192),
                                                    ((8, 16, 128), 2, 1, 192), ((8, 16, 256), 1, 1, -2),
-                                                   ((16, 8, 128), 3, 1, -2), ((8, 8, 256), 2, 2, -2)])
+                                                   ((16, 8, 128), 3, 1, -2), ((8, 8, 256), 2, 2, -2),
+                                                   ((16, 8, 64), 6, 1, -2), ((8, 16, 64), 2, 1, -1),
+                                                   ((8, 8, 64), 3, 3, 192)])
 def test_line_bulk_warp_lines_and_thread_caps_match_oracle(shape, B, nmat, threads):
     """The warp-lines forms (every warp takes its own lines through all phases: radix -1 with
     16-line tiles, -2 with two lines per warp) and a 192-thread cap, against the oracle."""
@@ -217,4 +224,29 @@ def test_line_bulk_warp_lines_and_thread_caps_match_oracle(shape, B, nmat, threa
         assert rel_err(out[b], ref) < FP32_OP, b
     with pytest.raises(dbfft.DbfftError):  # warp lines need 16-line tiles
         s.set_pass3_shape(0, 3, -1, 8)
+    s.close()
+
+
+@pytest.mark.parametrize("rhs,threads,lines", [(1, 0, 4), (2, -2, 4), (3, 192, 2), (6, -1, 16)])
+def test_line_bulk_rhs_groups_match_oracle(rhs, threads, lines):
+    """Six right-hand sides on one material map, the line-bulk CTAs taking 1, 2, 3 or 6 of them."""
+    dbfft = _dbfft()
+    shape = (16, 8, 64)
+    g = np.random.default_rng(90 + rhs)
+    phase = (g.random(shape) < 0.4).astype(np.uint16)
+    E, nu = [1.0, 25.0], [0.3, 0.2]
+    s = dbfft.Solver(shape, phase, dbfft.iso_phases(E, nu), np.zeros((6, 3, 3)), batch=6, precision=dbfft.DBFFT_MIXED)
+    s.set_pass3_rhs_group(rhs)
+    s.set_pass3_shape(0, 3, threads, lines)
+    u = synth.random_spectrum(shape, 3, 800 + rhs, batch=6)
+    out, _ = s.apply(torch.from_numpy(u).cuda(), fp32=True)
+    out = out.cpu().numpy()
+    prob = o.Problem(shape)
+    T = iso_tangent(phase, E, nu)
+    for b in range(6):
+        ref, _ = prob.apply_K(T, u[b], np.zeros(0))
+        assert rel_err(out[b], ref) < FP32_OP, b
+    for bad in (4, 9, -1):  # 4 does not divide 6; at most 8
+        with pytest.raises(dbfft.DbfftError):
+            s.set_pass3_rhs_group(bad)
     s.close()
