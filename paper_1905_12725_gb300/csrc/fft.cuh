@@ -33,6 +33,18 @@ template <typename T> __device__ __forceinline__ cplx<T> operator*(cplx<T> a, cp
 }
 template <typename T> __device__ __forceinline__ cplx<T> operator*(T s, cplx<T> a) { return mk(s * a.x, s * a.y); }
 template <typename T> __device__ __forceinline__ cplx<T> conjg(cplx<T> a) { return mk(a.x, -a.y); }
+
+// FP32 complex sums and differences as one packed two-lane instruction each
+// (Blackwell's float2 add): the butterflies' additions take half the issue
+// slots. Round-to-nearest on each lane, the same results as two scalar adds.
+__device__ __forceinline__ cplx<float> operator+(cplx<float> a, cplx<float> b) {
+    const float2 r = __fadd2_rn(make_float2(a.x, a.y), make_float2(b.x, b.y));
+    return mk(r.x, r.y);
+}
+__device__ __forceinline__ cplx<float> operator-(cplx<float> a, cplx<float> b) {
+    const float2 r = __fadd2_rn(make_float2(a.x, a.y), make_float2(-b.x, -b.y));
+    return mk(r.x, r.y);
+}
 // multiply by i * s (s real)
 template <typename T> __device__ __forceinline__ cplx<T> mul_i(T s, cplx<T> a) { return mk(-s * a.y, s * a.x); }
 // a * conj(w) when INV, else a * w  (w from the forward table)
