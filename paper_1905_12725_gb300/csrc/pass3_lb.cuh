@@ -299,6 +299,13 @@ __global__ void __launch_bounds__(WL == 0 ? 384 : (WL == 1 ? 256 : 128), WL == 2
         // all lines of the tile (block-strided), or the warp's own 16 / P lines (lane-strided)
         const int it0 = WL ? lane : t, itn = WL == 1 ? (16 / P) * Q4 : (WL == 2 ? 2 * Q4 : L * Q4);
         const int its = WL ? 32 : nthr;
+        float2 mac[NC];  // the macro strain of this right-hand side, in both lanes (warp-lines forms;
+                         // the 384-thread form rereads it, having no registers to spare)
+#pragma unroll
+        for (int q = 0; q < NC; ++q) mac[q] = make_float2(s_macro[rr * 9 + q], s_macro[rr * 9 + q]);
+        auto macro_of = [&](int q) {
+            return WL == 0 ? make_float2(s_macro[rr * 9 + q], s_macro[rr * 9 + q]) : mac[q];
+        };
         for (int it = it0; it < itn; it += its) {
             const int ll = WL == 1 ? warp + P * (it / Q4) : (WL == 2 ? 2 * warp + it / Q4 : it / Q4);
             const int x4 = (it % Q4) * 4;
@@ -307,24 +314,39 @@ __global__ void __launch_bounds__(WL == 0 ? 384 : (WL == 1 ? 256 : 128), WL == 2
             const int sig0 = (rr * NC) * L + ll;  // component 0; all components share its parity
             T* f = reinterpret_cast<T*>(lines + (long long)sig0 * H + (sig0 & 1)) + x4;
             if constexpr (OPK == OP_ISO) {
+                // two voxels per packed instruction: lanes (x, y) and (z, w) of the
+                // float4 of each component are neighbouring voxels
+                static_assert(NC == 6, "small-strain isotropic contraction");
                 float4 e4[NC];
 #pragma unroll
                 for (int q = 0; q < NC; ++q) e4[q] = ld4(f + q * CS);
-                float* ev = reinterpret_cast<float*>(e4);
+                float2* ev = reinterpret_cast<float2*>(e4);
+                const float2 two = make_float2(2.f, 2.f);
 #pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    const int ph = (int)(((j < 2 ? pp.x : pp.y) >> (16 * (j & 1))) & 0xffffu);
-                    const T sc = j == 0 ? s4.x : j == 1 ? s4.y : j == 2 ? s4.z : s4.w;
-                    const T lam = __ldg(a.lam + ph) * sc, mu = __ldg(a.mu + ph) * sc;
-                    T e[NC], sg[NC];
+                for (int h = 0; h < 2; ++h) {
+                    const unsigned pw = h == 0 ? pp.x : pp.y;
+                    const float2 sc = h == 0 ? make_float2(s4.x, s4.y) : make_float2(s4.z, s4.w);
+                    const float2 lam = __fmul2_rn(make_float2(__ldg(a.lam + (pw & 0xffffu)), __ldg(a.lam + (pw >> 16))), sc);
+                    const float2 mu2 = __fmul2_rn(
+                        __fmul2_rn(make_float2(__ldg(a.mu + (pw & 0xffffu)), __ldg(a.mu + (pw >> 16))), sc), two);
+                    float2 e[NC];
 #pragma unroll
-                    for (int q = 0; q < NC; ++q) e[q] = ev[4 * q + j] + s_macro[rr * 9 + q];
-                    iso_stress<T, NC>(e, lam, mu, sg);
+                    for (int q = 0; q < NC; ++q) e[q] = __fadd2_rn(ev[2 * q + h], macro_of(q));
+                    const float2 ltr = __fmul2_rn(lam, __fadd2_rn(__fadd2_rn(e[0], e[1]), e[2]));
+                    float2 en_n = make_float2(0.f, 0.f), en_s = make_float2(0.f, 0.f);
 #pragma unroll
-                    for (int q = 0; q < NC; ++q) {
-                        en += (q >= 3 && NC == 6 ? T(2) : T(1)) * e[q] * sg[q];
-                        ev[4 * q + j] = sg[q];
+                    for (int q = 0; q < 3; ++q) {
+                        const float2 sg = __ffma2_rn(mu2, e[q], ltr);  // lambda tr + 2 mu e
+                        en_n = __ffma2_rn(e[q], sg, en_n);
+                        ev[2 * q + h] = sg;
                     }
+#pragma unroll
+                    for (int q = 3; q < 6; ++q) {
+                        const float2 sg = __fmul2_rn(mu2, e[q]);  // 2 mu e (shear, Mandel weight 2 in the energy)
+                        en_s = __ffma2_rn(e[q], sg, en_s);
+                        ev[2 * q + h] = sg;
+                    }
+                    en += (en_n.x + en_n.y) + T(2) * (en_s.x + en_s.y);
                 }
 #pragma unroll
                 for (int q = 0; q < NC; ++q) st4(f + q * CS, e4[q]);
