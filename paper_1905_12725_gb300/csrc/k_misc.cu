@@ -501,6 +501,51 @@ cudaError_t launch_combine6(const cplx<double>* x, const double* G, cplx<double>
     return cudaGetLastError();
 }
 
+// The stress spectra of all right-hand sides at zero fluctuation, for linear
+// isotropic phases: sigma(x) = lambda(x) tr(E) I + 2 mu(x) E is linear in the two
+// fields lambda(x), mu(x), so with s the stress of the unit strain e11 of the
+// same material map (s11 = lambda + 2 mu, s22 = lambda), every right-hand side
+// is sigma = tr(E) s22 I + (s11 - s22) E, component by component and, the
+// transform being linear, frequency by frequency. W holds the transformed s of
+// map m in the slots of right-hand side m (components 0 and 1); all of them are
+// read before any right-hand side is written (Bm <= 8).
+__global__ void k_affine_combine(Dims d, int Bm, cplx<double>* W, const double* __restrict__ macroW) {
+    const long long H = d.H;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < H; i += (long long)gridDim.x * blockDim.x) {
+        cplx<double> s11[8], s22[8];
+#pragma unroll
+        for (int m = 0; m < 8; ++m) {
+            if (m >= Bm) break;
+            s11[m] = ldc(W + (long long)(m * 6 + 0) * H + i);
+            s22[m] = ldc(W + (long long)(m * 6 + 1) * H + i);
+        }
+        for (int b = 0; b < d.B; ++b) {
+            const int m = b / d.Rm;
+            const double* E = macroW + b * 9;
+            const double tr = E[0] + E[1] + E[2];
+            cplx<double> dif = zero_c<double>(), iso = zero_c<double>();
+#pragma unroll
+            for (int mm = 0; mm < 8; ++mm)
+                if (mm == m) {
+                    dif = s11[mm] - s22[mm];
+                    iso = tr * s22[mm];
+                }
+#pragma unroll
+            for (int c = 0; c < 6; ++c) {
+                const cplx<double> v = c < 3 ? iso + E[c] * dif : E[c] * dif;
+                stc(W + (long long)(b * 6 + c) * H + i, v);
+            }
+        }
+    }
+}
+
+cudaError_t launch_affine_combine(const Dims& d, int Bm, cplx<double>* W, const double* macroW, cudaStream_t s) {
+    if (Bm < 1 || Bm > 8 || d.nc != 6) return cudaErrorInvalidValue;
+    const long long nb = std::min<long long>((d.H + 255) / 256, 1216);
+    k_affine_combine<<<(unsigned)nb, 256, 0, s>>>(d, Bm, W, macroW);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_sum6(const double* tmp, double* out, long long V, int Bm, cudaStream_t s) {
     const long long nb = std::min<long long>((V + 255) / 256, 1024);
     k_sum6<<<dim3((unsigned)nb, (unsigned)Bm), 256, 0, s>>>(tmp, out, V);

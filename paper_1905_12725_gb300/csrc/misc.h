@@ -34,6 +34,9 @@ cudaError_t launch_scale_stats(const uint16_t* phase, const double* scale, float
 cudaError_t launch_combine6(const cplx<double>* x, const double* G, cplx<double>* out, long long n, int Bm,
                             cudaStream_t s);
 cudaError_t launch_sum6(const double* tmp, double* out, long long V, int Bm, cudaStream_t s);
+// sigma-hat of every right-hand side from the unit-strain stress spectra of each
+// material map (linear isotropic phases, zero fluctuation; Bm <= 8, nc = 6)
+cudaError_t launch_affine_combine(const Dims& d, int Bm, cplx<double>* W, const double* macroW, cudaStream_t s);
 // per-voxel steps of the crystal-plasticity adjoint (k_cpadj.cu): post = 0 writes the
 // tangent T_n (tan, may be null) and, with write_w, w = q + T_n (a - S q); post = 1
 // reads e_lam from w, accumulates dJds and updates q
