@@ -44,10 +44,11 @@ WORKLOAD = "64^3 random-sphere composite (r=6 vox, vf 0.25, contrast 100, nu 0.3
 # DRAM traffic per launch of the dominant kernel from an ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum), keyed by kernel; valid only
 # for the kernel sources it was taken on (hash of KERNEL_SOURCES below).
-# pass3_tangent_f32: k_axis3<float, 64, 6, OP_ISO, 32> of the 64^3 x 6 RHS step,
-# `ncu --set full` with caches flushed before the launch (39.52 MB read +
-# 0.14 MB written; inside the timed step the fields are L2-resident).
-NCU_TRAFFIC = {"pass3_tangent_f32": {"bytes": 39516672 + 138496, "src": "b00847a54d3ee0f8"}}
+# pass3_tangent_f32: the line-bulk k_axis3_lb<64, 6, OP_ISO, 2> of the 64^3 x 6 RHS
+# step (two right-hand sides per CTA), `ncu --set full` with caches flushed before
+# the launch (39.50 MB read + 0.003 MB written; inside the timed step the fields
+# are L2-resident).
+NCU_TRAFFIC = {"pass3_tangent_f32": {"bytes": 39502592 + 3072, "src": "bb9ee7ca49b287f3"}}
 
 
 def _peaks():
@@ -62,7 +63,8 @@ def _peaks():
 # sources that make up each profiled pass's kernels (a change invalidates its ncu counters)
 KERNEL_SOURCES = {
     "pass3_tangent_f32": ["dbfft_dev.cuh", "fft.cuh", "passes.cuh", "constitutive.cuh", "pass3.cuh", "pass3_pipe.cuh",
-                          "tma.cuh", "launch.h", "k_ax3_impl.cuh", "k_ax3_f32.cu", "k_ax3p_impl.cuh", "k_ax3p_f32.cu"],
+                          "pass3_lb.cuh", "tma.cuh", "launch.h", "k_ax3_impl.cuh", "k_ax3_f32.cu", "k_ax3p_impl.cuh",
+                          "k_ax3p_f32.cu", "k_ax3lb_f32.cu"],
 }
 
 
