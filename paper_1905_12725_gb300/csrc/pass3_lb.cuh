@@ -230,16 +230,33 @@ __global__ void __launch_bounds__(WL == 0 ? 384 : (WL == 1 ? 256 : 128), WL == 2
         cplx<T>* line = lines + (long long)sig * H;
         T* xr = reinterpret_cast<T*>(line + (sig & 1));  // aligned exchange / real line
         cplx<T> v[R];
-        // Z[k], k = p + P r: e^{+2 pi i k / n3} = conj(ep) conj(e^{-2 pi i P r / n3})
-        sfor<0, R>([&](auto rc) {
+        // Z[k], k = p + P r, and Z[M - k] from the same pair: with S = X[k] + conj X[M-k],
+        // Q = e^{+2 pi i k / n3} (X[k] - conj X[M-k]) (e = conj(ep) conj(e^{-2 pi i P r / n3})),
+        // Z[k] = S + i Q and Z[M - k] = conj(S) + i conj(Q). Each thread takes the pairs of
+        // its registers r < R/2; Z[M - k] is register R - 1 - r of the partner thread P - p,
+        // which receives it by shuffle. Thread 0 is its own partner: its Z[M - P r] is its
+        // register R - r (moved into place below), Z[M/2] = 2 conj X[M/2] is computed apart,
+        // and the r = 0 pair (k = 0 with the Nyquist value X[M]) has no partner register.
+        const int partner = (lane & ~(P - 1)) | ((P - p) & (P - 1));
+        sfor<0, R / 2>([&](auto rc) {
             constexpr int r = decltype(rc)::value;
             const int k = p + P * r;
             const cplx<T> X = line[k];
             const cplx<T> Xc = conjg(line[M - k]);
             const cplx<T> e = conjg(ep * tw_const<T, N3, P * r>());
-            const cplx<T> dl = e * (X - Xc);
-            v[r] = (X + Xc) + mk(-dl.y, dl.x);
+            const cplx<T> S = X + Xc, Q = e * (X - Xc);
+            v[r] = S + mk(-Q.y, Q.x);
+            const cplx<T> zp = mk(S.x + Q.y, Q.x - S.y);
+            v[R - 1 - r].x = __shfl_sync(0xffffffffu, zp.x, partner);
+            v[R - 1 - r].y = __shfl_sync(0xffffffffu, zp.y, partner);
         });
+        {
+            const bool p0 = p == 0;
+#pragma unroll
+            for (int j = R - 1; j > R / 2; --j) v[j] = p0 ? v[j - 1] : v[j];
+            const cplx<T> xm = line[M / 2];
+            if (p0) v[R / 2] = mk(T(2) * xm.x, T(-2) * xm.y);
+        }
         __syncwarp();
         RegDFT<R, +1, 1, 0, T>::run(v);  // stage A over n1; v[k1] = Y[n2 = p][k1]
         // exchange: block n2 = p, chunk c (k1 = cG .. cG + G - 1) at slot n2 P + (c ^ n2)
@@ -427,8 +444,12 @@ __global__ void __launch_bounds__(WL == 0 ? 384 : (WL == 1 ? 256 : 128), WL == 2
         // line has read the exchange
         const int src_lane = (lane & ~(P - 1)) | ((P - p) & (P - 1));
         const T half = T(0.5);
+        // Both X[k] and X[M - k] come from the pair (Z[k], Z[M - k]): with S = Z[k] + conj Z[M-k]
+        // and Q = e^{-2 pi i k / n3} (Z[k] - conj Z[M-k]), X[k] = (S - i Q) / 2 and
+        // X[M - k] = (conj S - i conj Q) / 2; each thread takes its registers r < R/2 (for
+        // thread 0, r = 0 gives X[0] and the Nyquist value X[M]) and thread 0 adds X[M/2].
         __syncwarp();
-        sfor<0, R>([&](auto rc) {
+        sfor<0, R / 2>([&](auto rc) {
             constexpr int r = decltype(rc)::value;
             cplx<T> zc;
             zc.x = __shfl_sync(0xffffffffu, v[R - 1 - r].x, src_lane);
@@ -436,10 +457,13 @@ __global__ void __launch_bounds__(WL == 0 ? 384 : (WL == 1 ? 256 : 128), WL == 2
             if (p == 0) zc = v[(R - r) % R];
             const cplx<T> Zk = v[r], Zc = conjg(zc);
             const cplx<T> e = ep * tw_const<T, N3, P * r>();  // e^{-2 pi i k / n3}
-            const cplx<T> dl = e * (Zk - Zc);
-            if (ok) line[p + P * r] = mk(half * (Zk.x + Zc.x) + half * dl.y, half * (Zk.y + Zc.y) - half * dl.x);
+            const cplx<T> S = Zk + Zc, Q = e * (Zk - Zc);
+            if (ok) {
+                line[p + P * r] = mk(half * (S.x + Q.y), half * (S.y - Q.x));
+                line[M - p - P * r] = mk(half * (S.x - Q.y), -half * (S.y + Q.x));
+            }
         });
-        if (ok && p == 0) line[M] = mk(v[0].x - v[0].y, T(0));
+        if (ok && p == 0) line[M / 2] = conjg(v[R / 2]);
     }
     fence_proxy_async_smem();  // this thread's generic writes before the bulk stores read them
     __syncthreads();
