@@ -461,6 +461,16 @@ dbfft_status dbfft_set_precond_refresh(dbfft_ctx* ctx, int policy);
  */
 dbfft_status dbfft_fp64_fma_rate(double* tflops, void* stream);
 
+/*
+ * L2 copy bandwidth of the current device in GB/s (no counterpart in the
+ * paper; a measurement aid for workloads whose fields stay in L2 between
+ * passes, such as 64^3 x 6 right-hand sides): 16 MB copied to 16 MB, 32 times
+ * over by eight 256-thread CTAs per SM, read and write bytes counted, best of
+ * four timed launches on `stream`. Allocates the 32 MB with cudaMallocAsync.
+ * Errors: E_ARG, E_NOMEM, E_CUDA.
+ */
+dbfft_status dbfft_l2_copy_rate(double* gbs, void* stream);
+
 /* Device bytes held by the context. */
 size_t dbfft_device_bytes(const dbfft_ctx* ctx);
 

@@ -572,7 +572,54 @@ __global__ void k_fp64_fma(double* out, int iters, double a, double b) {
     out[(long long)blockIdx.x * blockDim.x + threadIdx.x] = s;
 }
 
+// L2 copy rate: every thread copies float4 elements of a buffer that fits in
+// L2, reps times over, so that after the first sweep reads and writes hit L2.
+__global__ void k_l2_copy(const float4* __restrict__ src, float4* __restrict__ dst, long long n, int reps) {
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (int r = 0; r < reps; ++r)
+        for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+            float4 v = __ldcg(src + i);
+            v.x += 1.0f;
+            __stcg(dst + i, v);
+        }
+}
+
 }  // namespace dbfft
+
+extern "C" dbfft_status dbfft_l2_copy_rate(double* gbs, void* stream) {
+    using namespace dbfft;
+    if (!gbs) return DBFFT_E_ARG;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    int dev = 0, nsm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return DBFFT_E_CUDA;
+    const long long bytes = 16LL << 20;  // each of source and destination: 32 MB in all
+    const long long n = bytes / (long long)sizeof(float4);
+    const int reps = 32;
+    float4* buf = nullptr;
+    if (cudaMallocAsync(reinterpret_cast<void**>(&buf), 2 * (size_t)bytes, s) != cudaSuccess) return DBFFT_E_NOMEM;
+    cudaMemsetAsync(buf, 0, 2 * (size_t)bytes, s);
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best = 1e30f;
+    for (int rep = 0; rep < 5; ++rep) {
+        cudaEventRecord(e0, s);
+        k_l2_copy<<<nsm * 8, 256, 0, s>>>(buf, buf + n, n, reps);
+        cudaEventRecord(e1, s);
+        cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (rep > 0) best = ms < best ? ms : best;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFreeAsync(buf, s);
+    const bool ok = cudaStreamSynchronize(s) == cudaSuccess && cudaGetLastError() == cudaSuccess;
+    *gbs = 2.0 * (double)bytes * reps / (best * 1e-3) / 1e9;
+    return ok ? DBFFT_OK : DBFFT_E_CUDA;
+}
 
 extern "C" dbfft_status dbfft_fp64_fma_rate(double* tflops, void* stream) {
     using namespace dbfft;

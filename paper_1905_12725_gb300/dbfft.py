@@ -78,7 +78,7 @@ EXPORTS = ["dbfft_create", "dbfft_apply", "dbfft_solve_increment", "dbfft_homoge
            "dbfft_tuning", "dbfft_set_pass3_shape", "dbfft_set_pass3_rhs_group", "dbfft_set_precond_refresh",
            "dbfft_displacement", "dbfft_compatibility",
            "dbfft_tangent_sensitivity", "dbfft_set_checkpointing", "dbfft_cp_adjoint",
-           "dbfft_fp64_fma_rate"]
+           "dbfft_fp64_fma_rate", "dbfft_l2_copy_rate"]
 
 _LIB = None
 
@@ -152,6 +152,8 @@ def load_library(build_if_missing: bool = True):
     lib.dbfft_cp_adjoint.restype = ip
     lib.dbfft_fp64_fma_rate.argtypes = [dp, vp]
     lib.dbfft_fp64_fma_rate.restype = ip
+    lib.dbfft_l2_copy_rate.argtypes = [dp, vp]
+    lib.dbfft_l2_copy_rate.restype = ip
     _LIB = lib
     return lib
 
@@ -537,6 +539,18 @@ def fp64_fma_rate(stream=None) -> float:
     rc = load_library().dbfft_fp64_fma_rate(C.byref(v), C.c_void_p(st.cuda_stream))
     if rc != DBFFT_OK:
         raise DbfftError(rc, "dbfft_fp64_fma_rate failed")
+    return v.value
+
+
+def l2_copy_rate(stream=None) -> float:
+    """Measured L2 copy bandwidth of the current GPU in GB/s (dbfft_l2_copy_rate)."""
+    import torch
+
+    v = C.c_double(0.0)
+    st = stream if stream is not None else torch.cuda.current_stream()
+    rc = load_library().dbfft_l2_copy_rate(C.byref(v), C.c_void_p(st.cuda_stream))
+    if rc != DBFFT_OK:
+        raise DbfftError(rc, "dbfft_l2_copy_rate failed")
     return v.value
 
 
