@@ -48,7 +48,11 @@ WORKLOAD = "64^3 random-sphere composite (r=6 vox, vf 0.25, contrast 100, nu 0.3
 # step (two right-hand sides per CTA), `ncu --set full` with caches flushed before
 # the launch (39.50 MB read + 0.003 MB written; inside the timed step the fields
 # are L2-resident).
-NCU_TRAFFIC = {"pass3_tangent_f32": {"bytes": 39502592 + 3072, "src": "bb9ee7ca49b287f3"}}
+# fft_ax1_f32 / fft_ax2_f32: k_fft_strided<float, 64, +-1> of the same step, `ncu --set full`
+# with caches flushed (38.94 MB read + 0.02 MB written per launch, either direction).
+NCU_TRAFFIC = {"pass3_tangent_f32": {"bytes": 39502592 + 3072, "src": "bb9ee7ca49b287f3"},
+               "fft_ax1_f32": {"bytes": 38943488 + 19968, "src": "5c4f9345cff55668"},
+               "fft_ax2_f32": {"bytes": 38943488 + 19968, "src": "5c4f9345cff55668"}}
 
 
 def _peaks():
@@ -65,6 +69,8 @@ KERNEL_SOURCES = {
     "pass3_tangent_f32": ["dbfft_dev.cuh", "fft.cuh", "passes.cuh", "constitutive.cuh", "pass3.cuh", "pass3_pipe.cuh",
                           "pass3_lb.cuh", "tma.cuh", "launch.h", "k_ax3_impl.cuh", "k_ax3_f32.cu", "k_ax3p_impl.cuh",
                           "k_ax3p_f32.cu", "k_ax3lb_f32.cu"],
+    "fft_ax1_f32": ["dbfft_dev.cuh", "fft.cuh", "passes.cuh", "launch.h", "k_ax2.cu"],
+    "fft_ax2_f32": ["dbfft_dev.cuh", "fft.cuh", "passes.cuh", "launch.h", "k_ax2.cu"],
 }
 
 
@@ -623,6 +629,44 @@ def case_c4(precision, n=256, n_inc=40, only=None):
             "phase_sha256": synth.sha256(c["phase"])}
 
 
+def case_sens():
+    """dC_eff,1111 / dE(x) of the headline composite for the per-voxel Young's modulus E(x)
+    (dbfft_tangent_sensitivity): the six unit-strain solves (dbfft_homogenized_tangent) and
+    the contraction of their strain fields, timed apart, with the Euler identity
+    sum_x E(x) dC/dE(x) = C_eff,1111 (C_eff is homogeneous of degree one in the moduli)."""
+    import torch
+    from paper_1905_12725_gb300 import dbfft
+    c = workload_inputs()
+    shape = (N_GRID,) * 3
+    G = np.zeros((1, 6, 6))
+    G[0, 0, 0] = 1.0
+    E_vox = np.asarray(c["E"], dtype=np.float64)[c["phase"]]
+    out = {"case": "stiffness sensitivity, 64^3 composite, J = C_1111"}
+    for prec, name in [(dbfft.DBFFT_MIXED, "mixed"), (dbfft.DBFFT_FP64, "fp64")]:
+        s = dbfft.Solver(shape, c["phase"], dbfft.iso_phases(c["E"], c["nu"]), np.zeros((6, 3, 3)), batch=6,
+                         E_scale=np.ones(shape), precision=prec, tol=TOL, eta_inner=ETA_INNER, max_iter=20000,
+                         max_newton=100)
+        s.autotune(TUNE_CACHE)
+        s.homogenized_tangent()
+        s.tangent_sensitivity(G)
+        t_solve, t_sens = [], []
+        for _ in range(3):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            s.homogenized_tangent()
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            dJ, C_eff, rep = s.tangent_sensitivity(G)  # reuses the six solves just made
+            torch.cuda.synchronize()
+            t_solve.append(t1 - t0)
+            t_sens.append(time.perf_counter() - t1)
+        tot = float(np.sum(dJ.cpu().numpy()[0] * E_vox))
+        out[name] = {"solves_ms": 1e3 * float(np.median(t_solve)), "assembly_ms": 1e3 * float(np.median(t_sens)),
+                     "C1111": float(C_eff[0, 0, 0]), "euler_rel": abs(tot - C_eff[0, 0, 0]) / abs(C_eff[0, 0, 0])}
+        s.close()
+    return out
+
+
 def case_cpadj(n=64, n_inc=10):
     """Sensitivity of sigma_xx after a plastic loading path to every voxel's stiffness:
     the 500-grain Voronoi polycrystal of the 256^3 case generated on n^3, power-law CP,
@@ -939,7 +983,7 @@ def main():
     ap.add_argument("--case", default="",
                     choices=["", "op256", "c2", "c1", "c3", "c3fp64", "c4", "c4fp64", "c5", "porous",
                              "porousfp64", "porous63", "porous63fp64", "inclusion", "fcp", "fcpfp64", "fcp63",
-                             "fcp63fp64", "cpadj"],
+                             "fcp63fp64", "cpadj", "sens"],
                     help="run one sub-measurement only: op256 = 256^3 FP32 CG pass chain, c2 = one mixed "
                          "batched 64^3 solve (profiler captures); c1, c3[fp64], c4[fp64], c5 = the other "
                          "configurations at full size; porous[fp64] = the porous St. Venant-Kirchhoff "
@@ -957,6 +1001,8 @@ def main():
         elif args.case in ("porous63", "porous63fp64"):
             prec = dbfft.DBFFT_FP64 if args.case.endswith("fp64") else dbfft.DBFFT_MIXED
             print(json.dumps(case_porous(prec, n=63), default=float), flush=True)
+        elif args.case == "sens":
+            print(json.dumps(case_sens(), default=float), flush=True)
         elif args.case == "cpadj":
             print(json.dumps(case_cpadj(), default=float), flush=True)
         elif args.case == "inclusion":

@@ -177,7 +177,7 @@ struct dbfft_ctx {
 
     // ---- inner PCG as one CUDA graph (WHILE node), per inner precision
     bool use_graphs = true;
-    bool use_pdl = true;     // programmatic dependent launch inside the CG graph
+    bool use_pdl = false;    // programmatic dependent launch inside the CG graph
     bool fuse_ax2 = false;   // FP32 CG: element-wise passes 1 and 5 fused into the axis-2 transforms
     bool graph_warm[2] = {false, false};
     cudaGraphExec_t cg_exec[2] = {nullptr, nullptr};
@@ -1787,11 +1787,12 @@ static dbfft_status create_impl(dbfft_ctx* ctx, const dbfft_grid* grid, const db
     // DBFFT_CUDA_GRAPHS=0 runs every inner PCG launch by launch (same kernels,
     // same order), e.g. for profilers that cannot look inside conditional graphs
     if (const char* g = std::getenv("DBFFT_CUDA_GRAPHS")) ctx->use_graphs = g[0] != '0';
-    // programmatic dependent launch pays where the passes are short (launch
-    // latency is a visible part of them); on large grids the early-launched
-    // successor only holds SM resources: measured +1.3 % at 64^3 x 6 RHS,
-    // -1.8 % at 256^3 x 1
-    ctx->use_pdl = (long long)grid->n[0] * grid->n[1] * grid->n[2] * grid->batch <= (4LL << 20);
+    // programmatic dependent launch inside the CG graph (DBFFT_PDL=1): the
+    // early-launched successor holds SM resources while it waits. Measured in
+    // graph order on the current kernels: 64^3 x 6 RHS mixed step 10.75 ms with
+    // it against 10.65 ms without, the FP64 CG of 64^3 x 1 RHS 23.8 against
+    // 18.5 ms per solve, 256^3 x 1 FP32 iteration 1.080 ms either way; off.
+    ctx->use_pdl = false;
     if (const char* g = std::getenv("DBFFT_PDL")) ctx->use_pdl = g[0] != '0';
     // DBFFT_FUSE_AX2=0 keeps passes 1 and 5 as element-wise kernels around separate
     // axis-2 transforms in the FP32 CG (for comparison; the results agree to rounding)

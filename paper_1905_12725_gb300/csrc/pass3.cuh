@@ -214,15 +214,30 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? (RW == 32 ? 2 : (RW == 
                     }
                 });
             } else {
+                // pairs (k, M - k): with S = X[k] + conj X[M-k] and Q = e^{+2 pi i k/n} (X[k] - conj X[M-k]),
+                // Z[k] = S + i Q and Z[M - k] = conj(S) + i conj(Q). Each thread takes its registers
+                // r < R/2; Z[M - k] is register R - 1 - r of the partner thread P - p (the P threads
+                // of a slot are consecutive lanes), which receives it by shuffle. Thread 0 is its own
+                // partner: its Z[M - P r] belongs in register R - r (moved below), Z[M/2] = 2 conj X[M/2].
+                const int lane = t & 31;
+                const int partner = (lane & ~(P - 1)) | ((P - p) & (P - 1));
 #pragma unroll
-                for (int r = 0; r < R; ++r) {
+                for (int r = 0; r < R / 2; ++r) {
                     const int k = p + r * P;
                     const cplx<T> X = myc[k];
                     const cplx<T> Xc = conjg(myc[M - k]);
                     const cplx<T> e = conjg(ldg_c(a.tw.t3 + k));
-                    const cplx<T> dl = e * (X - Xc);
-                    v[r] = (X + Xc) + mk(-dl.y, dl.x);
+                    const cplx<T> S = X + Xc, Q = e * (X - Xc);
+                    v[r] = S + mk(-Q.y, Q.x);
+                    const cplx<T> zp = mk(S.x + Q.y, Q.x - S.y);
+                    v[R - 1 - r].x = __shfl_sync(0xffffffffu, zp.x, partner);
+                    v[R - 1 - r].y = __shfl_sync(0xffffffffu, zp.y, partner);
                 }
+                const bool p0 = p == 0;
+#pragma unroll
+                for (int j = R - 1; j > R / 2; --j) v[j] = p0 ? v[j - 1] : v[j];
+                const cplx<T> xm = myc[M / 2];
+                if (p0) v[R / 2] = mk(T(2) * xm.x, T(-2) * xm.y);
             }
             __syncwarp();  // the slot's threads (one warp-aligned group) have read their line
             ColFFT<T, M, R, +1, true, true>::run(v, myc, 1, p, a.tw.tm);
@@ -551,26 +566,29 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? (RW == 32 ? 2 : (RW == 
 #pragma unroll
         for (int r = 0; r < R; ++r) myc[p + r * P] = v[r];
         __syncwarp();
-        cplx<T> X[R];
-        cplx<T> XM = zero_c<T>();
+        // pairs (k, M - k): with S = Z[k] + conj Z[M-k] and Q = e^{-2 pi i k/n} (Z[k] - conj Z[M-k]),
+        // X[k] = (S - i Q) / 2 and X[M - k] = (conj S - i conj Q) / 2; each thread takes r < R/2
+        // (thread 0: r = 0 gives X[0] and the Nyquist X[M]) and thread 0 adds X[M/2] = conj Z[M/2]
+        cplx<T> Xa[R / 2], Xb[R / 2];
         const T half = T(0.5);
 #pragma unroll
-        for (int r = 0; r < R; ++r) {
+        for (int r = 0; r < R / 2; ++r) {
             const int k = p + r * P;
             const cplx<T> Zk = myc[k];
             const cplx<T> Zc = conjg(myc[(M - k) & (M - 1)]);
             const cplx<T> e = ldg_c(a.tw.t3 + k);  // e^{-2 pi i k / n}
-            const cplx<T> dl = e * (Zk - Zc);
-            X[r] = mk(half * (Zk.x + Zc.x) + half * dl.y, half * (Zk.y + Zc.y) - half * dl.x);
+            const cplx<T> S = Zk + Zc, Q = e * (Zk - Zc);
+            Xa[r] = mk(half * (S.x + Q.y), half * (S.y - Q.x));
+            Xb[r] = mk(half * (S.x - Q.y), -half * (S.y + Q.x));
         }
-        if (p == 0) {
-            const cplx<T> Z0 = myc[0];
-            XM = mk(Z0.x - Z0.y, T(0));
-        }
+        const cplx<T> Xmid = conjg(myc[M / 2]);
         __syncwarp();
 #pragma unroll
-        for (int r = 0; r < R; ++r) myc[p + r * P] = X[r];
-        if (p == 0) myc[M] = XM;
+        for (int r = 0; r < R / 2; ++r) {
+            myc[p + r * P] = Xa[r];
+            myc[M - p - r * P] = Xb[r];
+        }
+        if (p == 0) myc[M / 2] = Xmid;
     }
     __syncthreads();
 

@@ -140,3 +140,38 @@ def test_graph_and_launch_by_launch_inner_solves_agree():
     assert r0["cg_iters"] == r1["cg_iters"]
     assert np.abs(sig_graph - sig_plain).max() <= 1e-14 * np.abs(sig_plain).max()
     assert s.launch_count() > n0
+
+
+_PDL_CHILD = r"""
+import sys
+import numpy as np
+sys.path.insert(0, sys.argv[1])
+from paper_1905_12725_gb300 import dbfft
+shape = (16, 16, 32)
+g = np.random.default_rng(23)
+phase = (g.random(shape) < 0.3).astype(np.uint16)
+tgt = np.zeros((2, 3, 3)); tgt[0, 0, 0] = 1e-3; tgt[1, 0, 1] = tgt[1, 1, 0] = 5e-4
+s = dbfft.Solver(shape, phase, dbfft.iso_phases([1.0, 30.0], [0.3, 0.3]), tgt, batch=2, tol=1e-10, precision=1,
+                 eta_inner=1e-3)
+s.solve_increment(0)
+r = s.solve_increment(0)  # graph-captured inner solves
+np.save(sys.argv[2], np.concatenate([s.homogenized_stress().ravel(), [r["cg_iters"]]]))
+"""
+
+
+def test_programmatic_dependent_launch_gives_the_same_solve(tmp_path):
+    """The CG graph with programmatic dependencies between its kernels (DBFFT_PDL=1, off by
+    default) and without them reach the same iterates."""
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    out = {}
+    for flag in ("0", "1"):
+        f = str(tmp_path / f"pdl{flag}.npy")
+        r = subprocess.run([sys.executable, "-c", _PDL_CHILD, root, f], env=dict(os.environ, DBFFT_PDL=flag),
+                           capture_output=True, text=True, timeout=300)
+        assert r.returncode == 0, r.stderr[-2000:]
+        out[flag] = np.load(f)
+    assert out["0"][-1] == out["1"][-1]  # CG iterations
+    assert np.abs(out["0"][:-1] - out["1"][:-1]).max() <= 1e-14 * np.abs(out["0"][:-1]).max()
