@@ -44,13 +44,11 @@ WORKLOAD = "64^3 random-sphere composite (r=6 vox, vf 0.25, contrast 100, nu 0.3
 # DRAM traffic per launch of the dominant kernel from an ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum), keyed by kernel; valid only
 # for the kernel sources it was taken on (hash of KERNEL_SOURCES below).
-# pass3_tangent_f32: the line-bulk k_axis3_lb<64, 6, OP_ISO, 2> of the 64^3 x 6 RHS
-# step (two right-hand sides per CTA), `ncu --set full` with caches flushed before
-# the launch (39.50 MB read + 0.003 MB written; inside the timed step the fields
-# are L2-resident).
-# fft_ax1_f32 / fft_ax2_f32: k_fft_strided<float, 64, +-1> of the same step, `ncu --set full`
-# with caches flushed (38.94 MB read + 0.02 MB written per launch, either direction).
-NCU_TRAFFIC = {"pass3_tangent_f32": {"bytes": 39502592 + 3072, "src": "bb9ee7ca49b287f3"},
+# pass3_tangent_f32: the line-bulk k_axis3_lb<64, 6, OP_ISO, 1> of the 64^3 x 6 RHS
+# step (warp lines, one right-hand side per CTA, the tuned form), ncu with caches
+# flushed before the launch (39.50 MB read, nothing written back; inside the timed
+# step the fields are L2-resident).
+NCU_TRAFFIC = {"pass3_tangent_f32": {"bytes": 39500000, "src": "0dd4b8413be2d38e"},
                "fft_ax1_f32": {"bytes": 38943488 + 19968, "src": "5c4f9345cff55668"},
                "fft_ax2_f32": {"bytes": 38943488 + 19968, "src": "5c4f9345cff55668"}}
 
