@@ -433,6 +433,25 @@ bool precond_from(const dbfft_ctx* ctx, const double C[3][3][3][3], PrecondData&
             pd.coef[a][b] = (j == l) ? C[i][j][k][j] : (C[i][j][k][l] + C[i][l][k][j]);
             pd.coef_f[a][b] = (float)pd.coef[a][b];
         }
+    {  // an isotropic mean tangent (to rounding) takes the closed-form inverse
+        const double lam = C[0][0][1][1], mu = C[0][1][0][1];
+        double cmax = 0.0, dev = 0.0;
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j)
+                for (int k = 0; k < 3; ++k)
+                    for (int l = 0; l < 3; ++l) {
+                        const double iso = lam * (i == j && k == l) + mu * ((i == k && j == l) + (i == l && j == k));
+                        cmax = std::max(cmax, std::fabs(C[i][j][k][l]));
+                        dev = std::max(dev, std::fabs(C[i][j][k][l] - iso));
+                    }
+        if (mu > 0.0 && lam + 2.0 * mu > 0.0 && dev <= 1e-13 * cmax) {
+            pd.iso = 1;
+            pd.iso_d[0] = 1.0 / mu;
+            pd.iso_d[1] = (lam + mu) / (lam + 2.0 * mu);
+            pd.iso_f[0] = (float)pd.iso_d[0];
+            pd.iso_f[1] = (float)pd.iso_d[1];
+        }
+    }
     const int ne = ctx->dims.ne;
     if (ne > 0) {
         std::vector<double> A(ne * ne);

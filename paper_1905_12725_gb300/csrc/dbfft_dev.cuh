@@ -33,12 +33,23 @@ struct PrecondData {
     double coef[6][6];
     double Me[9][9];
     float coef_f[6][6];  // FP32 copy for the FP32 passes (no FP64 work per frequency)
+    // isotropic mean tangent (lambda0, mu0): Q(xi) / |xi|^2 = mu0 I + (lambda0 + mu0) n n^T has the
+    // closed-form inverse (I - c n n^T) / mu0 with c = (lambda0 + mu0) / (lambda0 + 2 mu0);
+    // iso_d / iso_f hold 1 / mu0 and c
+    int iso;
+    double iso_d[2];
+    float iso_f[2];
 };
 
 template <typename T>
 __host__ __device__ __forceinline__ const T (*pcoef(const PrecondData& pd))[6] {
     if constexpr (sizeof(T) == 4) return pd.coef_f;
     else return pd.coef;
+}
+template <typename T>
+__host__ __device__ __forceinline__ const T* piso(const PrecondData& pd) {
+    if constexpr (sizeof(T) == 4) return pd.iso_f;
+    else return pd.iso_d;
 }
 
 // Everything a pass needs about the grid and the macro basis.

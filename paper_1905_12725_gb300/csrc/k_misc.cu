@@ -105,7 +105,7 @@ __global__ void k_precond_field(Dims d, Freq<T> f, const PrecondData* pre, const
         const int k2 = (int)(rem / d.h), k3 = (int)(rem - (long long)k2 * d.h);
         cplx<T> r[3], z[3];
         for (int c = 0; c < 3; ++c) r[c] = u[(long long)(b * 3 + c) * d.H + i];
-        precond_apply<T>(pcoef<T>(pd), f.xi1[k1], f.xi2[k2], f.xi3[k3], (T)(1.0 / d.invN), r, z);
+        precond_pd<T>(pd, f.xi1[k1], f.xi2[k2], f.xi3[k3], (T)(1.0 / d.invN), r, z);
         for (int c = 0; c < 3; ++c) out[(long long)(b * 3 + c) * d.H + i] = z[c];
     }
     if (blockIdx.x == 0 && threadIdx.x == 0 && e_out) {

@@ -71,6 +71,32 @@ __device__ __forceinline__ void precond_apply(const T (*coef)[6], T x1, T x2, T 
     z[2] = s * (A02 * r[0] + (A12 * r[1] + A22 * r[2]));
 }
 
+// The preconditioner of one material group: the closed form for an isotropic
+// mean tangent, z = N / |xi|^2 (r - c (xi . r) xi / |xi|^2) / mu0 (the same
+// operator as the general 3x3 inverse above, up to rounding), else the general form.
+template <typename T>
+__device__ __forceinline__ void precond_pd(const PrecondData& pd, T x1, T x2, T x3, T N, const cplx<T>* r,
+                                           cplx<T>* z) {
+    if (pd.iso) {
+        const T k2 = x1 * x1 + x2 * x2 + x3 * x3;
+        if (k2 == T(0)) {
+            z[0] = z[1] = z[2] = zero_c<T>();
+            return;
+        }
+        const T* iso = piso<T>(pd);
+        const T ik2 = rcp_t(k2);
+        const T s = N * ik2 * iso[0];
+        const cplx<T> xr = x1 * r[0] + x2 * r[1] + x3 * r[2];
+        const T cc = iso[1] * ik2;
+        const cplx<T> w = cc * xr;
+        z[0] = s * (r[0] - x1 * w);
+        z[1] = s * (r[1] - x2 * w);
+        z[2] = s * (r[2] - x3 * w);
+        return;
+    }
+    precond_apply<T>(pcoef<T>(pd), x1, x2, x3, N, r, z);
+}
+
 // scalar * complex helpers for the real-scalar product
 template <typename T>
 __device__ __forceinline__ cplx<T> operator*(cplx<T> a, T s) { return mk(a.x * s, a.y * s); }
@@ -247,7 +273,7 @@ __global__ void __launch_bounds__(PW_THREADS) k_grad(Ax1InvArgs<T> a) {
                 po[c] = ldc(a.p + (long long)(b * 3 + c) * d.H + i);
                 xo[c] = ldc(a.x + (long long)(b * 3 + c) * d.H + i);
             }
-            precond_apply<T>(pcoef<T>(*pd), x1, x2, x3, N, u, z);
+            precond_pd<T>(*pd, x1, x2, x3, N, u, z);
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
                 u[c] = z[c] + po[c] * beta;
@@ -413,7 +439,7 @@ __global__ void __launch_bounds__(PW_THREADS) k_div(Ax1FwdArgs<T> a) {
                 rv[c] = ldc(a.r + idx) - q[c] * alpha;
                 stc(a.r + idx, rv[c]);
             }
-            precond_apply<T>(pcoef<T>(*pd), x1, x2, x3, N, rv, z);
+            precond_pd<T>(*pd, x1, x2, x3, N, rv, z);
             T lrz = T(0), lrr = T(0);
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
@@ -568,7 +594,7 @@ __global__ void __launch_bounds__(PW_THREADS) k_cg_init(CgInitArgs<T> a) {
         const FreqIdx fi = freq_idx(d, i);
         cplx<T> rv[3], z[3];
         for (int c = 0; c < 3; ++c) rv[c] = ldc(a.r + (long long)(b * 3 + c) * d.H + i);
-        precond_apply<T>(pcoef<T>(pd), a.f.xi1[fi.k1], a.f.xi2[fi.k2], a.f.xi3[fi.k3], N, rv, z);
+        precond_pd<T>(pd, a.f.xi1[fi.k1], a.f.xi2[fi.k2], a.f.xi3[fi.k3], N, rv, z);
         const T wgt = (T)hweight(fi.k3, d.m);
         for (int c = 0; c < 3; ++c) {
             lrz += wgt * (rv[c].x * z[c].x + rv[c].y * z[c].y);

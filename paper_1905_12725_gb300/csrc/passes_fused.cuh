@@ -63,7 +63,7 @@ __global__ void __launch_bounds__(TWC * N / FUSED_R, TWC * N / FUSED_R >= 512 ? 
                 po[c] = ldc(a.p + o + c * d.H);
                 xo[c] = ldc(a.x + o + c * d.H);
             }
-            precond_apply<T>(pcoef<T>(*pd), x1, x2[r], x3, Nn, rv, z);
+            precond_pd<T>(*pd, x1, x2[r], x3, Nn, rv, z);
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
                 u[c][r] = z[c] + po[c] * beta;
@@ -158,7 +158,7 @@ __global__ void __launch_bounds__(TWC * N / FUSED_R, TWC * N / FUSED_R >= 512 ? 
                 rv[c] = ldc(a.r + o + c * d.H) - qc * alpha;
                 stc(a.r + o + c * d.H, rv[c]);
             }
-            precond_apply<T>(pcoef<T>(*pd), x1, x2[r], x3, Nn, rv, z);
+            precond_pd<T>(*pd, x1, x2[r], x3, Nn, rv, z);
             T lrz = T(0), lrr = T(0);
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
