@@ -512,27 +512,27 @@ cudaError_t launch_combine6(const cplx<double>* x, const double* G, cplx<double>
 __global__ void k_affine_combine(Dims d, int Bm, cplx<double>* W, const double* __restrict__ macroW) {
     const long long H = d.H;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < H; i += (long long)gridDim.x * blockDim.x) {
-        cplx<double> s11[8], s22[8];
+        cplx<double> s22[8], dif[8];
 #pragma unroll
         for (int m = 0; m < 8; ++m) {
             if (m >= Bm) break;
-            s11[m] = ldc(W + (long long)(m * 6 + 0) * H + i);
             s22[m] = ldc(W + (long long)(m * 6 + 1) * H + i);
+            dif[m] = ldc(W + (long long)(m * 6 + 0) * H + i) - s22[m];
         }
         for (int b = 0; b < d.B; ++b) {
             const int m = b / d.Rm;
-            const double* E = macroW + b * 9;
-            const double tr = E[0] + E[1] + E[2];
-            cplx<double> dif = zero_c<double>(), iso = zero_c<double>();
+            cplx<double> sm = s22[0], dm = dif[0];  // the map's values by selection (no arithmetic)
 #pragma unroll
-            for (int mm = 0; mm < 8; ++mm)
+            for (int mm = 1; mm < 8; ++mm)
                 if (mm == m) {
-                    dif = s11[mm] - s22[mm];
-                    iso = tr * s22[mm];
+                    sm = s22[mm];
+                    dm = dif[mm];
                 }
+            const double* E = macroW + b * 9;
+            const cplx<double> iso = (E[0] + E[1] + E[2]) * sm;
 #pragma unroll
             for (int c = 0; c < 6; ++c) {
-                const cplx<double> v = c < 3 ? iso + E[c] * dif : E[c] * dif;
+                const cplx<double> v = c < 3 ? iso + E[c] * dm : E[c] * dm;
                 stc(W + (long long)(b * 6 + c) * H + i, v);
             }
         }
