@@ -37,8 +37,8 @@ int ax3_odd_lines(int n3, int nc, bool dbl) {
 
 static int radix_for(int n, bool dbl) { return radix_ax2(n, dbl); }
 
-long long pw_blocks(long long H, int B) {
-    // about two waves of blocks over the whole GPU, shared among the right-hand
+long long pw_blocks(long long H, int B, int waves) {
+    // about `waves` waves of blocks over the whole GPU, shared among the right-hand
     // sides: the element-wise kernels end with a block reduction, whose cost
     // is amortised over several frequencies per thread (grid-stride loops)
     static int nsm = 0;
@@ -48,7 +48,7 @@ long long pw_blocks(long long H, int B) {
             nsm < 1)
             nsm = 152;
     }
-    const long long target = 2LL * 5 * nsm;  // ~5 resident 256-thread blocks per SM
+    const long long target = (long long)waves * 5 * nsm;  // ~5 resident 256-thread blocks per SM
     long long per = (target + (B > 0 ? B : 1) - 1) / (B > 0 ? B : 1);
     const long long need = (H + PW_THREADS - 1) / PW_THREADS;
     if (per > need) per = need;

@@ -32,7 +32,7 @@ cudaError_t launch_k(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem,
 namespace dbfft {
 
 // Launch geometry shared by the launchers and the buffer sizing.
-long long pw_blocks(long long H, int B);                    // grid (per right-hand side) of the element-wise kernels
+long long pw_blocks(long long H, int B, int waves = 2);     // grid (per right-hand side) of the element-wise kernels
 int ax2_tile(int n, bool dbl);                       // columns per CTA of the strided transforms
 int ax3_lines(int n3, int nc, int rb, bool dbl, int nfields = 1, int radix = 8);  // default lines per CTA of pass 3
 int ax3_threads_per_line(int n3, int nc, int rb, bool dbl);
