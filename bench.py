@@ -48,9 +48,9 @@ WORKLOAD = "64^3 random-sphere composite (r=6 vox, vf 0.25, contrast 100, nu 0.3
 # step (warp lines, one right-hand side per CTA, the tuned form), ncu with caches
 # flushed before the launch (39.50 MB read, nothing written back; inside the timed
 # step the fields are L2-resident).
-NCU_TRAFFIC = {"pass3_tangent_f32": {"bytes": 39500000, "src": "0dd4b8413be2d38e"},
-               "fft_ax1_f32": {"bytes": 38943488 + 19968, "src": "5c4f9345cff55668"},
-               "fft_ax2_f32": {"bytes": 38943488 + 19968, "src": "5c4f9345cff55668"}}
+NCU_TRAFFIC = {"pass3_tangent_f32": {"bytes": 39500000, "src": "68eb58e000c68c8f"},
+               "fft_ax1_f32": {"bytes": 38940000 + 1020, "src": "e961a92289cf89dd"},
+               "fft_ax2_f32": {"bytes": 38940000 + 1020, "src": "e961a92289cf89dd"}}
 
 
 def _peaks():
