@@ -56,6 +56,25 @@ long long pw_blocks(long long H, int B, int waves) {
     return per;
 }
 
+long long pw_blocks_resident(long long H, int B, int waves, int per_sm) {
+    // whole waves: `waves` times the blocks that fit on the GPU at once (per_sm
+    // resident blocks of the kernel on each SM), split evenly among the right-hand
+    // sides and rounded down, so that no block starts a wave of its own
+    static int nsm = 0;
+    if (nsm == 0) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+            nsm < 1)
+            nsm = 152;
+    }
+    const int b = B > 0 ? B : 1;
+    long long per = (long long)waves * (per_sm > 0 ? per_sm : 1) * nsm / b;
+    const long long need = (H + PW_THREADS - 1) / PW_THREADS;
+    if (per > need) per = need;
+    if (per < 1) per = 1;
+    return per;
+}
+
 int ax2_tile(int n2, bool dbl) {
     const int P = n2 / radix_ax2(n2, dbl);
     int tw = 256 / P;

@@ -33,6 +33,7 @@ namespace dbfft {
 
 // Launch geometry shared by the launchers and the buffer sizing.
 long long pw_blocks(long long H, int B, int waves = 2);     // grid (per right-hand side) of the element-wise kernels
+long long pw_blocks_resident(long long H, int B, int waves, int per_sm);  // the same in whole waves of per_sm blocks per SM
 int ax2_tile(int n, bool dbl);                       // columns per CTA of the strided transforms
 int ax3_lines(int n3, int nc, int rb, bool dbl, int nfields = 1, int radix = 8);  // default lines per CTA of pass 3
 int ax3_threads_per_line(int n3, int nc, int rb, bool dbl);
