@@ -48,7 +48,7 @@ WORKLOAD = "64^3 random-sphere composite (r=6 vox, vf 0.25, contrast 100, nu 0.3
 # step (warp lines, one right-hand side per CTA, the tuned form), ncu with caches
 # flushed before the launch (39.50 MB read, nothing written back; inside the timed
 # step the fields are L2-resident).
-NCU_TRAFFIC = {"pass3_tangent_f32": {"bytes": 39500000, "src": "632d608f075e1f58"},
+NCU_TRAFFIC = {"pass3_tangent_f32": {"bytes": 39500000, "src": "67fa03f4f67dfddf"},
                "fft_ax1_f32": {"bytes": 38940000 + 256, "src": "d1758b792b1f9b63"},
                "fft_ax2_f32": {"bytes": 38940000 + 256, "src": "d1758b792b1f9b63"}}
 

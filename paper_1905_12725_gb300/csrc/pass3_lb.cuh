@@ -19,7 +19,12 @@
 //  * twiddles are registers: the stage-B factors W_M^(n2 k1) of a thread are
 //    read once per CTA, the pre/post factors e^(-2 pi i k / n3) of
 //    k = p + P r are one per-thread value times compile-time constants;
-//  * the per-voxel operation reads and writes four voxels per access;
+//  * the pre- and post-processing take each (k, M - k) pair once: a thread
+//    forms both values of its pairs and hands the partner thread (P - p)
+//    its half by shuffle;
+//  * the per-voxel operation reads and writes four voxels per access, and the
+//    isotropic contraction runs two voxels per packed FP32x2 instruction
+//    (complex sums and differences everywhere are packed too, fft.cuh);
 //  * the 2 (n3 = 256) or 4 (n3 = 64, 128) line slots that share a half-warp
 //    sit 8 (or 4) line buffers apart; a line buffer is 8 bytes long modulo
 //    128, so they are 64 (or 32) bytes apart modulo 128 and the 64-bit
